@@ -1,0 +1,262 @@
+"""FP64 CPU oracle for the method-of-lines substep of arXiv:1806.04182.
+
+TEST INFRASTRUCTURE.  This package is the plain, slow reference that the CUDA
+path is checked against.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import it; the product package never
+does, and it shares no code with the CUDA library.
+
+The arithmetic lives in ``sf_oracle.cpp`` (plain C++17, FP64, one cell at a
+time, OpenMP only over the outer z loop of the right-hand-side sweep).  This
+module compiles it with g++ on first use and wraps it with ctypes.
+
+Functions and what pins them (tests/test_oracle_*.py):
+  rhs(WAVE)        Sec. IV.A (first-order form) + Sec. II.B.1 stencils.
+                   Pinned: exact per-Fourier-mode symbols, closed-form RK4
+                   evolution of a single mode, 4th-order convergence to the
+                   continuum plane wave, energy decay.
+  rhs(WAVE_ADJ)    transpose of the wave operator.  Pinned: <L u, v> = <u, L^T v>.
+  rhs(MHD)         Sec. IV.B + Sec. II.B.2 + App. B.  Pinned: uniform state
+                   gives zero, telescoping conservation, 1D data, axis
+                   permutation equivariance, WENO5 exactness on quartic data
+                   (JS weights reduce to the linear ones), convergence on the
+                   circularly polarised Alfven wave (Sec. IV.B.1).
+  rhs(Z4)          Sec. V.  Pinned: Minkowski gives zero, gauge-wave exact
+                   solution (4th-order truncation), flat metric in curvilinear
+                   coordinates (Ricci and Christoffels), lapse Laplacian.
+                   The Z^i / Theta coupling terms vanish on every exact
+                   solution available: parity unpinned for those terms.
+  rk4_step         Sec. II.C Table RK44.  Pinned: amplification polynomial
+                   of a single Fourier mode.
+  ssprk3_step      App. C/D (garbles read as stated in the design doc).  Pinned:
+                   third-order amplification polynomial; equal to the
+                   Shu-Osher form.
+  misfit_gradient  discrete adjoint of the RK4 wave evolution.  Pinned:
+                   central finite differences (exact for the quadratic misfit).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+WAVE, MHD, Z4, WAVE_ADJ = 0, 1, 2, 3
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sf_oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``or_params`` in sf_oracle.cpp."""
+
+    _fields_ = [
+        ("sigma", ctypes.c_double),
+        ("gamma_eos", ctypes.c_double),
+        ("weno_eps", ctypes.c_double),
+        ("weno_q", ctypes.c_double),
+        ("kappa_z", ctypes.c_double),
+        ("kappa_c", ctypes.c_double),
+        ("eta", ctypes.c_double),
+        ("g_shift", ctypes.c_double),
+        ("ch", ctypes.c_double),
+        ("kappa_psi", ctypes.c_double),
+        ("weno_variant", ctypes.c_int32),
+        ("slicing", ctypes.c_int32),
+        ("shift_frozen", ctypes.c_int32),
+        ("mhd_glm", ctypes.c_int32),
+    ]
+
+
+def params(**kw) -> Params:
+    """Defaults: sigma = 0.1, Gamma = 5/3, eps = dx^4, JS weights, q = 2,
+    kappa_z = kappa_c = 1, eta = 2, g = 3/4, 1+log slicing (Sec. V with M = 1)."""
+    d = dict(sigma=0.1, gamma_eos=5.0 / 3.0, weno_eps=0.0, weno_q=2.0, kappa_z=1.0,
+             kappa_c=1.0, eta=2.0, g_shift=0.75, ch=0.0, kappa_psi=0.0, weno_variant=0,
+             slicing=0, shift_frozen=0, mhd_glm=0)
+    d.update(kw)
+    return Params(**d)
+
+
+def build(force: bool = False) -> str:
+    """Compile sf_oracle.cpp into oracle/_build/liboracle.so (g++, -O2, OpenMP)."""
+    with _lock:
+        if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+            return _SO
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = _SO + f".tmp{os.getpid()}"
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+        return _SO
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        pp = ctypes.POINTER(Params)
+        L.or_nfields.argtypes = [ctypes.c_int, pp]
+        L.or_fill_ghosts_periodic.argtypes = [ctypes.c_int, ip, ctypes.c_int, dp]
+        L.or_rhs.argtypes = [ctypes.c_int, pp, ip, ctypes.c_int, dp, dp, dp]
+        L.or_rk4_step.argtypes = [ctypes.c_int, pp, ip, ctypes.c_int, dp, ctypes.c_double, dp, dp]
+        L.or_ssprk3_step.argtypes = [ctypes.c_int, pp, ip, ctypes.c_int, dp, ctypes.c_double, dp, dp]
+        L.or_mhd_max_rate.argtypes = [pp, ip, ctypes.c_int, dp, dp]
+        L.or_mhd_max_rate.restype = ctypes.c_double
+        L.or_wave_energy.argtypes = [ip, ctypes.c_int, dp, dp]
+        L.or_wave_energy.restype = ctypes.c_double
+        L.or_z4_monitors.argtypes = [ip, ctypes.c_int, dp, dp, dp]
+        L.or_wave_misfit_gradient.argtypes = [pp, ip, dp, ctypes.c_double, ctypes.c_int, dp, dp,
+                                              ctypes.c_int, ctypes.POINTER(ctypes.c_int64), dp,
+                                              dp, dp]
+        L.or_wave_misfit_gradient.restype = ctypes.c_double
+        L.or_count_ops.argtypes = [ctypes.c_int, pp, ip, ctypes.c_int, dp, dp,
+                                   ctypes.POINTER(ctypes.c_long)]
+        L.or_stencil.argtypes = [ctypes.c_int, ip, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_double]
+        L.or_stencil.restype = ctypes.c_double
+        _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ivec(n):
+    return (ctypes.c_int * 3)(*[int(x) for x in n])
+
+
+def _dvec(d):
+    return (ctypes.c_double * 3)(*[float(x) for x in d])
+
+
+def shape_info(U: np.ndarray, g: int):
+    """(nf, n=(nx,ny,nz)) of a ghosted array of shape (nf, nz+2g, ny+2g, nx+2g)."""
+    nf, Nz, Ny, Nx = U.shape
+    return nf, (Nx - 2 * g, Ny - 2 * g, Nz - 2 * g)
+
+
+def nfields(system: int, p: Params | None = None) -> int:
+    return lib().or_nfields(system, ctypes.byref(p or params()))
+
+
+def fill_ghosts(U: np.ndarray, g: int) -> np.ndarray:
+    nf, n = shape_info(U, g)
+    lib().or_fill_ghosts_periodic(nf, _ivec(n), g, _dp(U))
+    return U
+
+
+def rhs(system: int, U: np.ndarray, dx, p: Params | None = None, g: int = 3) -> np.ndarray:
+    """(L + Q_d)(U) on the interior; U ghosted and ghost-filled."""
+    p = p or params()
+    nf, n = shape_info(U, g)
+    out = np.zeros((nf, n[2], n[1], n[0]))
+    rc = lib().or_rhs(system, ctypes.byref(p), _ivec(n), g, _dvec(dx), _dp(U), _dp(out))
+    if rc:
+        raise ValueError("oracle rhs: bad arguments")
+    return out
+
+
+def rk4_step(system: int, U: np.ndarray, dx, dt: float, p: Params | None = None, g: int = 3,
+             stages: bool = False):
+    """One RK(4,4) step in place; returns the interior U(2), U(3), U(4), U^{n+1} if asked."""
+    p = p or params()
+    nf, n = shape_info(U, g)
+    st = np.zeros((4, nf, n[2], n[1], n[0])) if stages else None
+    rc = lib().or_rk4_step(system, ctypes.byref(p), _ivec(n), g, _dvec(dx), dt, _dp(U),
+                           _dp(st) if stages else None)
+    if rc:
+        raise ValueError("oracle rk4: bad arguments")
+    return st
+
+
+def ssprk3_step(system: int, U: np.ndarray, dx, dt: float, p: Params | None = None, g: int = 3,
+                stages: bool = False):
+    """One SSP-RK(3,3) step in place; returns the interior U(2), U(3), U^{n+1} if asked."""
+    p = p or params()
+    nf, n = shape_info(U, g)
+    st = np.zeros((3, nf, n[2], n[1], n[0])) if stages else None
+    rc = lib().or_ssprk3_step(system, ctypes.byref(p), _ivec(n), g, _dvec(dx), dt, _dp(U),
+                              _dp(st) if stages else None)
+    if rc:
+        raise ValueError("oracle ssprk3: bad arguments")
+    return st
+
+
+def mhd_max_rate(U: np.ndarray, dx, p: Params | None = None, g: int = 3) -> float:
+    p = p or params()
+    nf, n = shape_info(U, g)
+    return lib().or_mhd_max_rate(ctypes.byref(p), _ivec(n), g, _dvec(dx), _dp(U))
+
+
+def wave_energy(U: np.ndarray, dx, g: int = 3) -> float:
+    nf, n = shape_info(U, g)
+    return lib().or_wave_energy(_ivec(n), g, _dvec(dx), _dp(U))
+
+
+def z4_monitors(U: np.ndarray, dx, g: int = 3) -> np.ndarray:
+    nf, n = shape_info(U, g)
+    out = np.zeros(4)
+    lib().or_z4_monitors(_ivec(n), g, _dvec(dx), _dp(U), _dp(out))
+    return out
+
+
+def misfit_gradient(phi0: np.ndarray, Pi0: np.ndarray, dx, dt: float, nsteps: int,
+                    obs: np.ndarray, ref: np.ndarray, p: Params | None = None):
+    """(J, dJ/dphi0, dJ/dPi0) of the RK4 wave evolution; phi0/Pi0 shape (nz, ny, nx)."""
+    p = p or params()
+    nz, ny, nx = phi0.shape
+    phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+    Pi0 = np.ascontiguousarray(Pi0, dtype=np.float64)
+    obs = np.ascontiguousarray(obs, dtype=np.int64)
+    ref = np.ascontiguousarray(ref, dtype=np.float64)
+    assert ref.shape == (nsteps, obs.size)
+    gphi = np.zeros_like(phi0)
+    gPi = np.zeros_like(Pi0)
+    J = lib().or_wave_misfit_gradient(ctypes.byref(p), _ivec((nx, ny, nz)), _dvec(dx), dt,
+                                      nsteps, _dp(phi0), _dp(Pi0), obs.size,
+                                      obs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                      _dp(ref), _dp(gphi), _dp(gPi))
+    return J, gphi, gPi
+
+
+D1, D2, DMIX, KO = 0, 1, 2, 3
+
+
+def stencil(op: int, U: np.ndarray, dx, f: int, i: int, j: int, k: int, d1: int = 0,
+            d2: int = 1, sigma: float = 0.1, g: int = 3) -> float:
+    """One Sec. II.B.1 operator at interior point (i, j, k) of field f."""
+    nf, n = shape_info(U, g)
+    return lib().or_stencil(op, _ivec(n), g, _dvec(dx), _dp(U), f, i, j, k, d1, d2, sigma)
+
+
+def count_ops(system: int, U: np.ndarray, dx, p: Params | None = None, g: int = 3) -> dict:
+    """Per-cell operation counts of the right-hand side (counting scalar)."""
+    p = p or params()
+    nf, n = shape_info(U, g)
+    out = (ctypes.c_long * 6)()
+    lib().or_count_ops(system, ctypes.byref(p), _ivec(n), g, _dvec(dx), _dp(U), out)
+    keys = ("add", "mul", "div", "sqrt", "log", "cmp")
+    return dict(zip(keys, list(out)))
+
+
+def ghosted(interior: np.ndarray, g: int = 3) -> np.ndarray:
+    """Embed an interior array (nf, nz, ny, nx) into a ghost-filled periodic array."""
+    nf, nz, ny, nx = interior.shape
+    U = np.zeros((nf, nz + 2 * g, ny + 2 * g, nx + 2 * g))
+    U[:, g:g + nz, g:g + ny, g:g + nx] = interior
+    return fill_ghosts(U, g)
+
+
+def interior(U: np.ndarray, g: int = 3) -> np.ndarray:
+    return U[:, g:U.shape[1] - g, g:U.shape[2] - g, g:U.shape[3] - g]
