@@ -1,0 +1,384 @@
+"""Benchmark: CCZ4 RK4 substeps on a 96^3 periodic patch (cell-updates/s).
+
+One "step" is one full RK4 step (four fused RHS + stage-update launches)
+of the conformal Z4 system (25 fields, 1+log slicing, Gamma-driver shift,
+KO sigma = 0.1, dt = 0.25 dx) on Minkowski data plus seeded uniform noise
+of amplitude 1e-10.  The headline value is the FP32-bulk path; the plain
+FP64 path is timed on the same data and reported beside it.
+
+Metric: cell-updates per second per RK substep = 96^3 * 4 * steps / time.
+Every array of the working set (5 ghosted arrays of 25 x 102^3 values) is
+larger than the 129 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank advances its own independent 96^3 patch (weak
+scaling, no collective on the data path); rank 0 prints one JSON line with
+the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import threading
+import time
+
+import numpy as np
+
+N = 96
+GHOST = 3
+NF = 25
+WORKLOAD = "ccz4_96cubed_rk4_periodic"
+METRIC = "cell-updates/s per RK substep (Z4 96^3, FP32-bulk; FP64 beside it)"
+UNIT = "cell-updates/s"
+ROOT = os.path.dirname(os.path.abspath(__file__))
+
+
+def bytes_per_cell_update(precision: str) -> float:
+    """Algorithmic HBM bytes per interior cell and RK substep (every array
+    pass of one RK4 step, divided by its four substeps).
+    FP64: stage 0 reads U^n and writes acc, U(2) (3 passes); stages 1-2 read
+    U(i), U^n, acc and write acc, U(i+1) (5 each); stage 3 reads U(4), acc and
+    writes U^{n+1} (3): 16 passes.  FP32-bulk adds the Kahan array and U^n in
+    stage 3 (read U(4), acc, U^n, c; write U^{n+1}, c: 6): 19 passes."""
+    if precision == "fp64":
+        return 16 / 4 * NF * 8
+    return 19 / 4 * NF * 4
+
+
+STAGE_PASSES = {"fp64": [3, 5, 5, 3], "fp32": [3, 5, 5, 6]}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+def make_state(precision: str, seed: int, device):
+    import torch
+    from paper_1806_04182_gb300 import capi, inputs
+    from paper_1806_04182_gb300.state import PatchState
+    U0, dx = inputs.z4_minkowski_noise((N, N, N), seed=seed, amp=1e-10)
+    prec = capi.SF_FP64 if precision == "fp64" else capi.SF_FP32_BULK
+    st = PatchState(capi.SF_Z4, (N, N, N), dx, 0.25 * dx[0], precision=prec,
+                    prm=capi.params(), device=device)
+    st.upload(U0)
+    torch.cuda.synchronize()
+    return st
+
+
+def time_device(st, steps: int, warmup: int):
+    """Per-launch CUDA-event durations (ms) of `steps` RK4 steps after warm-up."""
+    import torch
+    from paper_1806_04182_gb300 import capi
+    stream = torch.cuda.current_stream()
+    h = stream.cuda_stream
+    patches = [st.stage_patch(s) for s in range(4)]
+    for _ in range(warmup):
+        for s in range(4):
+            capi.sf_substep(st.prm, patches[s], s, h)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4 * steps + 1)]
+    c0 = capi.sf_launch_count()
+    ev[0].record(stream)
+    for k in range(steps):
+        for s in range(4):
+            capi.sf_substep(st.prm, patches[s], s, h)
+            ev[4 * k + s + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = capi.sf_launch_count() - c0
+    per = np.array([ev[q].elapsed_time(ev[q + 1]) for q in range(4 * steps)]).reshape(steps, 4)
+    total = ev[0].elapsed_time(ev[-1])
+    return total, per, launches
+
+
+def time_e2e(st, steps: int, warmup: int):
+    """Same steps through host buffers: pinned H2D of U^n, four stages, D2H of U^{n+1}."""
+    import torch
+    from paper_1806_04182_gb300 import capi
+    stream = torch.cuda.current_stream()
+    h = stream.cuda_stream
+    host_in = torch.empty(st.shape, dtype=st.dtype, pin_memory=True)
+    host_in.copy_(st.A.cpu())
+    host_out = torch.empty_like(host_in, pin_memory=True)
+    patches = [st.stage_patch(s) for s in range(4)]
+
+    def one():
+        st.A.copy_(host_in, non_blocking=True)
+        if st.E is not None:
+            st.E.zero_()
+        for s in range(4):
+            capi.sf_substep(st.prm, patches[s], s, h)
+        host_out.copy_(st.A, non_blocking=True)
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        one()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    nbytes = host_in.numel() * host_in.element_size()
+    return e0.elapsed_time(e1), nbytes, nbytes
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_1806_04182_gb300 import build as sfbuild
+    sfbuild.build()
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    cells = N ** 3
+    res = {}
+    clocks = None
+    precisions = ("fp32", "fp64") if args.only is None else (args.only,)
+    for precision in precisions:
+        st = make_state(precision, seed=rank, device=device)
+        barrier()
+        sampler = ClockSampler(local) if precision == "fp32" else None
+        if sampler:
+            sampler.start()
+        total_ms, per, launches = time_device(st, args.steps, args.warmup)
+        if sampler:
+            clocks = sampler.stop()
+        barrier()
+        total_ms = max_over_ranks(total_ms)
+        substeps = 4 * args.steps
+        value = world * cells * substeps / (total_ms * 1e-3)
+        # dominant kernel: the stage kernel; average launch duration
+        avg_launch_ms = float(per.mean())
+        bpc = bytes_per_cell_update(precision)
+        achieved = cells * bpc / (avg_launch_ms * 1e-3) / 1e9
+        per_stage_ms = per.mean(axis=0).tolist()
+        stage_gbs = [cells * p * NF * (8 if precision == "fp64" else 4) / (ms * 1e-3) / 1e9
+                     for p, ms in zip(STAGE_PASSES[precision], per_stage_ms)]
+        res[precision] = dict(value=value, ms_per_step=total_ms / args.steps, launches=launches,
+                              avg_launch_ms=avg_launch_ms, achieved_gbs=achieved,
+                              per_stage_ms=per_stage_ms, per_stage_gbs=stage_gbs,
+                              bytes_per_cell_update=bpc, state=st)
+    if args.only is not None:
+        if world > 1:
+            dist.destroy_process_group()
+        r = res[args.only]
+        return None if rank else {"profiling_run": args.only, "value": r["value"],
+                                  "ms_per_step": r["ms_per_step"], "achieved_gbs": r["achieved_gbs"]}
+    # end to end through host buffers (FP32-bulk)
+    st = res["fp32"]["state"]
+    barrier()
+    e2e_ms, bi, bo = time_e2e(st, args.steps, args.warmup)
+    barrier()
+    e2e_ms = max_over_ranks(e2e_ms)
+    e2e_value = world * cells * 4 * args.steps / (e2e_ms * 1e-3)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    r32, r64 = res["fp32"], res["fp64"]
+    line = {
+        "metric": METRIC,
+        "value": r32["value"],
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": r32["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic: Minkowski + seeded uniform noise 1e-10 on all 25 fields",
+        "config": {"workload": WORKLOAD, "n": N, "ghost": GHOST, "fields": NF, "rk": "RK4",
+                   "substeps_per_step": 4, "precision": "fp32_bulk (fp64 det/inverse/ln det/"
+                   "trace removals, Kahan RK accumulation)", "slicing": "1+log",
+                   "shift": "Gamma-driver", "sigma_ko": 0.1, "dt_over_dx": 0.25,
+                   "l2": "inputs larger than L2 (5 arrays x 106 MB fp32)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": r32["achieved_gbs"], "peak": hbm_peak,
+                     "unit": "GB/s", "frac": r32["achieved_gbs"] / hbm_peak, "traffic": None,
+                     "peak_source": peak_src,
+                     "kernel": "z4_stage_kernel<float,double>",
+                     "bytes_per_cell_update": r32["bytes_per_cell_update"],
+                     "per_stage_ms": r32["per_stage_ms"], "per_stage_gbs": r32["per_stage_gbs"]},
+        "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"],
+                 "achieved_gbs": r64["achieved_gbs"], "hbm_frac": r64["achieved_gbs"] / hbm_peak,
+                 "bytes_per_cell_update": r64["bytes_per_cell_update"],
+                 "per_stage_ms": r64["per_stage_ms"]},
+        "speedup_fp32_bulk_over_fp64": r32["value"] / r64["value"],
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
+                "d2h_bytes_per_step": bo},
+        "gpu_launches": int(r32["launches"]),
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
+    return line
+
+
+# ---------------------------------------------------------------- oracle arm
+def cpu_baseline(seconds: float = 15.0, nz: int = 4) -> dict:
+    """The FP64 oracle as it stands (OpenMP over z) on a bounded sample of the
+    same workload: a 96 x 96 x nz periodic slab with the same spacing, data
+    distribution and parameters, RK4 steps until `seconds` have passed."""
+    import oracle
+    from paper_1806_04182_gb300 import inputs
+    oracle.build()
+    U0, _ = inputs.z4_minkowski_noise((N, N, nz), seed=0, amp=1e-10)
+    dx = (1.0 / N,) * 3
+    G = oracle.ghosted(U0)
+    p = oracle.params()
+    dt = 0.25 * dx[0]
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        oracle.rk4_step(oracle.Z4, G, dx, dt, p)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > seconds or steps >= 1000:
+            break
+    cells = N * N * nz
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": cells * 4 * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} RK4 steps of a 96x96x{nz} periodic slab (same dx, data, params), "
+                      f"{el:.1f} s"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import oracle
+    from paper_1806_04182_gb300 import inputs
+    oracle.build()
+    nz = 2
+    U0, _ = inputs.z4_minkowski_noise((N, N, nz), seed=0, amp=1e-10)
+    dx = (1.0 / N,) * 3
+    G = oracle.ghosted(U0)
+    p = oracle.params()
+    dt = 0.25 * dx[0]
+    for _ in range(args.warmup):
+        oracle.rk4_step(oracle.Z4, G, dx, dt, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.rk4_step(oracle.Z4, G, dx, dt, p)
+    el = time.perf_counter() - t0
+    cells = N * N * nz
+    value = cells * 4 * args.steps / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = f"each step: one RK4 step of a 96x96x{nz} periodic slab of the 96^3 workload"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic: Minkowski + seeded uniform noise 1e-10",
+            "config": {"workload": WORKLOAD, "n": N, "sample_nz": nz},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["fp32", "fp64"], default=None,
+                    help="time one precision only (profiling runs)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    line = reference_arm(args) if args.impl == "reference" else gpu_arm(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * sf.h - C ABI of the GB300 method-of-lines substep library (libsf.so).
+ *
+ * The library advances ghosted grid patches by one Runge-Kutta substep of the
+ * semi-discrete system dU/dt = L(U) + Q_d(U) (arXiv:1806.04182, Sec. II.A,
+ * Eq. (2)), with
+ *   - SF_WAVE: scalar wave equation in first-order form (phi, Pi, d_x, d_y, d_z)
+ *     (Sec. IV.A), 4th-order centred derivatives (Sec. II.B.1),
+ *   - SF_Z4:   CCZ4 with Bona-Masso slicing and Gamma-driver shift, vacuum,
+ *     25 fields (Sec. V), 4th-order centred first, second and mixed
+ *     derivatives (Sec. II.B.1),
+ *   - SF_MHD:  ideal Newtonian MHD, 8 conserved fields (Sec. IV.B), WENO5
+ *     reconstruction of the evolved fields (App. B) and local Lax-Friedrichs
+ *     flux (Sec. II.B.2, Eq. LLF) in conservative form (Eq. 5),
+ * and 6th-order Kreiss-Oliger dissipation Q_d on the wave and Z4 systems
+ * (Sec. II.B.1).  Time integration: RK(4,4) (Sec. II.C, Table RK44) or
+ * SSP-RK(3,3) (App. C/D), one call per stage.
+ *
+ * Memory: the caller owns every buffer (device memory for all pointers
+ * unless stated).  The library keeps no pointer after a call returns, except
+ * inside an sf_batch object, which records the patch table it was created
+ * with.  Calls are asynchronous on the given CUDA stream (NULL = legacy
+ * default stream) and return after enqueueing work.
+ *
+ * Errors: argument errors are reported synchronously as SF_EINVAL with a
+ * message from sf_last_error() (thread-local) and nothing is enqueued.  CUDA
+ * launch errors return SF_ECUDA.  Conditions found on the device (non-finite
+ * values, work-queue time-outs) set a device status word that
+ * sf_get_device_status() reads.  Nothing aborts, traps or throws across the
+ * ABI.
+ */
+#ifndef SF_H
+#define SF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SF_OK = 0,
+  SF_EINVAL = 1,      /* bad argument; see sf_last_error() */
+  SF_ENOTSUP = 2,     /* valid but unsupported combination */
+  SF_ECUDA = 3,       /* a CUDA runtime call failed */
+  SF_ENONFINITE = 4,  /* device found NaN/Inf in an output */
+  SF_ETIMEOUT = 5     /* a bounded device wait gave up */
+} sf_status;
+
+typedef enum { SF_WAVE = 0, SF_MHD = 1, SF_Z4 = 2 } sf_system;
+
+/* SF_FP64: storage and arithmetic in double.
+ * SF_FP32_BULK: storage and stencil arithmetic in float; the Z4 conformal
+ * metric determinant, inverse, ln det and the trace removals are evaluated
+ * in double; the last RK4 stage adds the step increment to U^n with a
+ * compensated (Kahan) sum carried across steps in the `kahan` array. */
+typedef enum { SF_FP64 = 0, SF_FP32_BULK = 1 } sf_precision;
+
+typedef enum { SF_RK4 = 0, SF_SSPRK3 = 1 } sf_rk;
+
+/* Ghost handling of the stage output. */
+typedef enum {
+  SF_GHOSTS_NONE = 0,     /* caller fills ghosts of u_next (e.g. from neighbours) */
+  SF_GHOSTS_PERIODIC = 1  /* the substep also writes u_next's periodic ghost shell
+                             (the patch is periodic onto itself; needs n >= ghost) */
+} sf_ghosts;
+
+/*
+ * One ghosted box (Sec. III: a patch with a ghost zone of `ghost` points).
+ * Every array of a patch has the same layout: nf fields, field f, interior
+ * point (i,j,k) (0 <= i < n[0], ...) at element
+ *     f*sf + (k+ghost)*sz + (j+ghost)*sy + (i+ghost)
+ * with x fastest.  Elements are double (SF_FP64) or float (SF_FP32_BULK).
+ * Strides may be 0, meaning contiguous: sy = n[0]+2g, sz = sy*(n[1]+2g),
+ * sf = sz*(n[2]+2g).
+ *
+ * Stage semantics, RK4 (k_j = dt (L+Q_d)(U(j)), r = (L+Q_d)(u_stage)):
+ *   stage 0: u_stage = U^n (may alias u_n); acc = U^n + dt/6 r; u_next = U^n + dt/2 r
+ *   stage 1: acc += dt/3 r;  u_next = U^n + dt/2 r
+ *   stage 2: acc += dt/3 r;  u_next = U^n + dt r
+ *   stage 3: u_next = acc + dt/6 r  (= U^{n+1})
+ * In SF_FP32_BULK acc holds only the increment (acc = dt/6 r at stage 0) and
+ * stage 3 forms U^{n+1} = U^n + (acc + dt/6 r) with Kahan compensation:
+ * kahan is read and written in stage 3 and must start at zero.
+ * SSP-RK3 (Shu-Osher form; acc unused):
+ *   stage 0: u_next = U^n + dt r
+ *   stage 1: u_next = 3/4 U^n + 1/4 (u_stage + dt r)
+ *   stage 2: u_next = 1/3 U^n + 2/3 (u_stage + dt r)
+ * u_next must not alias u_stage or acc; it may alias u_n in the last stage
+ * only (each point reads its own U^n before overwriting it, and no stencil
+ * reads U^n), which updates the state in place.  Only interior points of
+ * u_next/acc/kahan are written (plus u_next's ghost shell under
+ * SF_GHOSTS_PERIODIC).  u_stage must have valid ghosts.
+ */
+typedef struct {
+  int32_t n[3];      /* interior points x, y, z (>= 1) */
+  int32_t ghost;     /* ghost width, >= 3 */
+  double dx[3];      /* grid spacing per direction (> 0) */
+  double dt;         /* time step of this patch */
+  int32_t system;    /* sf_system */
+  int32_t precision; /* sf_precision */
+  int64_t sy, sz, sf;/* element strides (0 = contiguous) */
+  void* u_stage;     /* in:  stage input U(i) */
+  void* u_n;         /* in:  U^n */
+  void* acc;         /* in/out: RK4 accumulator (unused by SSP-RK3) */
+  void* u_next;      /* out: next stage input, or U^{n+1} after the last stage */
+  void* kahan;       /* in/out: FP32_BULK compensation (NULL otherwise) */
+} sf_patch;
+
+typedef struct {
+  int32_t rk;           /* sf_rk */
+  int32_t ghosts;       /* sf_ghosts */
+  double sigma_ko;      /* KO strength sigma (Sec. II.B.1), >= 0 */
+  double gamma_eos;     /* MHD adiabatic index (Sec. IV.B) */
+  double weno_eps;      /* WENO epsilon; <= 0 means dx_d^4 (App. B) */
+  double weno_q;        /* WENO-Z exponent (App. B) */
+  int32_t weno_variant; /* 0: WENO5-JS, 1: WENO5-Z */
+  int32_t slicing;      /* 0: 1+log (f = 2/alpha), 1: harmonic (f = 1) (Sec. V) */
+  int32_t shift_frozen; /* 1: d/dt beta = d/dt B = 0 */
+  int32_t check_finite; /* 1: flag NaN/Inf written to u_next in the status word */
+  double kappa_z;       /* Z4 damping kappa_z (Sec. V) */
+  double kappa_c;       /* conformal-constraint damping kappa_c (Sec. V) */
+  double eta;           /* Gamma-driver damping eta (Sec. V) */
+  double g_shift;       /* Gamma-driver coefficient g (Sec. V) */
+} sf_params;
+
+/* Number of evolved fields of a system (5, 8 or 25); -1 if unknown. */
+int32_t sf_nfields(int32_t system);
+
+/*
+ * One RK stage on each of `npatch` patches (Sec. II.C; one launch per patch).
+ * stage in [0,4) for RK4, [0,3) for SSP-RK3.  All patches must use the
+ * same system and precision in this entry point (see sf_batch for mixed).
+ */
+sf_status sf_substep(const sf_params* prm, const sf_patch* patches, int32_t npatch,
+                     int32_t stage, void* stream);
+
+/*
+ * Right-hand side only: rhs_out[f][k][j][i] = (L + Q_d)(u_stage) on the
+ * interior, an unghosted contiguous array of nf * n[0]*n[1]*n[2] elements of
+ * the patch's precision.  For tests and diagnostics.
+ */
+sf_status sf_rhs(const sf_params* prm, const sf_patch* patch, void* rhs_out, void* stream);
+
+/*
+ * Periodic ghost fill of `array` (layout of `patch`, `nf` fields): every ghost
+ * point takes the value of the interior point congruent to it modulo n
+ * (the periodic boundary of Sec. IV tests).  Works for any n >= 1.
+ */
+sf_status sf_fill_ghosts_periodic(const sf_patch* patch, void* array, int32_t nf, void* stream);
+
+/*
+ * MHD CFL rate (Sec. II.A footnote): *d_rate = max over interior points and
+ * directions d of (|v_d| + c_fast,d) / dx_d of `array` (layout of `patch`,
+ * FP64 or FP32 per patch).  d_rate is one device double; dt = cfl / rate.
+ */
+sf_status sf_mhd_max_rate(const sf_params* prm, const sf_patch* patch, const void* array,
+                          double* d_rate, void* stream);
+
+/*
+ * Adjoint RK stage of the wave system: same stage semantics as sf_substep
+ * with L replaced by its transpose L^T on the periodic grid (D_i^T = -D_i,
+ * Q_d^T = Q_d), acting on adjoint fields (l_phi, l_Pi, l_d).  Because the
+ * wave operator is linear and autonomous, four such stages apply
+ * P(dt L)^T = P(dt L^T), the exact transpose of one forward RK4 step.
+ */
+sf_status sf_adjoint_substep(const sf_params* prm, const sf_patch* adj, int32_t npatch,
+                             int32_t stage, void* stream);
+
+/*
+ * out[o] = array[field][obs[o]] for nobs interior linear indices
+ * obs[o] = (k*n[1] + j)*n[0] + i (device int64 array); out is a device
+ * array of the patch's precision.  sf_scatter_add does array[field][obs[o]] += vals[o]
+ * (observer indices must be distinct).
+ */
+sf_status sf_gather(const sf_patch* patch, const void* array, int32_t field, const int64_t* obs,
+                    int32_t nobs, void* out, void* stream);
+sf_status sf_scatter_add(const sf_patch* patch, void* array, int32_t field, const int64_t* obs,
+                         int32_t nobs, const void* vals, void* stream);
+
+/*
+ * FP64 diagnostics of `array` (interior), written to device doubles d_out:
+ *   SF_WAVE: d_out[0] = 1/2 sum (Pi^2 + |d|^2) dx dy dz (wave energy)
+ *   SF_Z4:   d_out[0..3] = sums over points of Theta^2, |Z|^2, (ln det gt)^2,
+ *            (tr A~)^2, with Z^i = chi/2 (Gammahat^i - Gamma~^i) (Sec. V)
+ *   all:     d_out[4] = number of non-finite values (as a double)
+ * d_out must hold 5 doubles.
+ */
+sf_status sf_diagnostics(const sf_params* prm, const sf_patch* patch, const void* array,
+                         double* d_out, void* stream);
+
+/*
+ * Batched AMR-patch dispatch: one persistent launch per stage over a table of
+ * patches of mixed systems (SF_WAVE and SF_Z4) and sizes, each with its own
+ * dx and dt.  CTAs take (patch, tile) work items from a device queue.
+ * sf_batch_create copies the patch table to the device (allocates; not in
+ * the hot path).  sf_batch_tune times the tile shapes of each (system, size
+ * class) on `stream` and keeps the fastest.  sf_batch_capture records the
+ * RK stages of one full step into a CUDA graph; sf_batch_launch replays it.
+ */
+typedef struct sf_batch sf_batch;
+sf_status sf_batch_create(const sf_params* prm, const sf_patch* patches, int32_t npatch,
+                          sf_batch** out);
+sf_status sf_batch_substep(sf_batch* b, int32_t stage, void* stream);
+sf_status sf_batch_tune(sf_batch* b, void* stream);
+sf_status sf_batch_capture(sf_batch* b, void* stream);
+sf_status sf_batch_launch(sf_batch* b, void* stream);
+/* Number of persistent-kernel launches made by one sf_batch_launch. */
+int32_t sf_batch_launches_per_step(const sf_batch* b);
+sf_status sf_batch_destroy(sf_batch* b);
+
+/*
+ * Synchronises `stream`, returns and clears the device status word:
+ * SF_OK, SF_ENONFINITE or SF_ETIMEOUT.
+ */
+sf_status sf_get_device_status(void* stream);
+
+/* Message for the last failing call on this host thread ("" if none). */
+const char* sf_last_error(void);
+
+/* Count of kernel launches enqueued by this library since load (all threads). */
+int64_t sf_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SF_H */

@@ -119,6 +119,8 @@ def lib() -> ctypes.CDLL:
         L.or_wave_misfit_gradient.restype = ctypes.c_double
         L.or_count_ops.argtypes = [ctypes.c_int, pp, ip, ctypes.c_int, dp, dp,
                                    ctypes.POINTER(ctypes.c_long)]
+        L.or_rhs_points.argtypes = [ctypes.c_int, pp, ip, ctypes.c_int, dp, dp, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int64), dp]
         L.or_stencil.argtypes = [ctypes.c_int, ip, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_double]
@@ -164,6 +166,20 @@ def rhs(system: int, U: np.ndarray, dx, p: Params | None = None, g: int = 3) -> 
     rc = lib().or_rhs(system, ctypes.byref(p), _ivec(n), g, _dvec(dx), _dp(U), _dp(out))
     if rc:
         raise ValueError("oracle rhs: bad arguments")
+    return out
+
+
+def rhs_points(system: int, U: np.ndarray, dx, pts: np.ndarray, p: Params | None = None,
+               g: int = 3) -> np.ndarray:
+    """(L + Q_d)(U) at interior linear indices pts; returns shape (nf, npts)."""
+    p = p or params()
+    nf, n = shape_info(U, g)
+    pts = np.ascontiguousarray(pts, dtype=np.int64)
+    out = np.zeros((nf, pts.size))
+    rc = lib().or_rhs_points(system, ctypes.byref(p), _ivec(n), g, _dvec(dx), _dp(U), pts.size,
+                             pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(out))
+    if rc:
+        raise ValueError("oracle rhs_points: bad arguments")
     return out
 
 

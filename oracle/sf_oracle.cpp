@@ -951,6 +951,26 @@ double or_wave_misfit_gradient(const or_params* p, const int* n, const double* d
   return J;
 }
 
+// (L + Q_d)(U) at `npts` interior points given as linear indices
+// (k*ny + j)*nx + i; out[f*npts + q].  For sampled checks of large grids.
+int or_rhs_points(int system, const or_params* p, const int* n, int g, const double* dx,
+                  const double* u, int npts, const int64_t* pts, double* out) {
+  int nf = nfields(system, *p);
+  if (nf < 0 || g < 3) return 1;
+  Grid G(n, g);
+#pragma omp parallel for schedule(static)
+  for (int q = 0; q < npts; ++q) {
+    int64_t lin = pts[q];
+    int i = (int)(lin % G.n[0]);
+    int j = (int)((lin / G.n[0]) % G.n[1]);
+    int k = (int)(lin / ((int64_t)G.n[0] * G.n[1]));
+    double r[32];
+    cell_rhs<double>(system, *p, u, G, dx, i, j, k, r);
+    for (int f = 0; f < nf; ++f) out[(size_t)f * npts + q] = r[f];
+  }
+  return 0;
+}
+
 // One stencil of Sec. II.B.1 at interior point (i,j,k) of field f of a
 // ghost-filled array: op 0 = D_d1, 1 = D_d1d1, 2 = D_d2(D_d1) (d1 != d2),
 // 3 = Q_d with strength sigma (all three directions).

@@ -1,0 +1,340 @@
+// C ABI entry points of libsf.so: argument validation, dispatch to the
+// per-system stage kernels, periodic ghost fill, observer gather/scatter,
+// device status word and error reporting.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "sf_internal.cuh"
+
+namespace sf {
+
+__device__ unsigned int g_status_word;
+
+static thread_local char t_err[512] = "";
+static std::atomic<long long> g_launches{0};
+
+sf_status set_error(sf_status code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(t_err, sizeof(t_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+sf_status after_launch(const char* what) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(SF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  return SF_OK;
+}
+
+// Device address of the status word, cached per device.
+unsigned int* status_ptr() {
+  static unsigned int* cache[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!cache[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
+    cache[dev] = static_cast<unsigned int*>(p);
+  }
+  return cache[dev];
+}
+
+void normalise_strides(sf_patch& p, int nf) {
+  (void)nf;
+  const long long g2 = 2LL * p.ghost;
+  if (p.sy == 0) p.sy = p.n[0] + g2;
+  if (p.sz == 0) p.sz = p.sy * (p.n[1] + g2);
+  if (p.sf == 0) p.sf = p.sz * (p.n[2] + g2);
+}
+
+static bool aligned(const void* ptr, size_t a) { return (reinterpret_cast<uintptr_t>(ptr) % a) == 0; }
+
+sf_status check_patch(const sf_params* prm, const sf_patch& p, int need_stage_arrays, int stage) {
+  if (!prm) return set_error(SF_EINVAL, "params is NULL");
+  if (p.system < 0 || p.system > 2) return set_error(SF_EINVAL, "unknown system %d", p.system);
+  if (p.precision != SF_FP64 && p.precision != SF_FP32_BULK)
+    return set_error(SF_EINVAL, "unknown precision %d", p.precision);
+  for (int d = 0; d < 3; ++d) {
+    if (p.n[d] < 1) return set_error(SF_EINVAL, "n[%d] = %d < 1", d, p.n[d]);
+    if (p.n[d] > 65535) return set_error(SF_EINVAL, "n[%d] = %d > 65535", d, p.n[d]);
+    if (!(p.dx[d] > 0.0) || !(p.dx[d] < 1e300)) return set_error(SF_EINVAL, "dx[%d] must be > 0", d);
+  }
+  if (p.ghost < 3) return set_error(SF_EINVAL, "ghost = %d < 3 (4th-order FD + 6th-order KO need 3)", p.ghost);
+  const long long g2 = 2LL * p.ghost;
+  if (p.sy < p.n[0] + g2 || p.sz < p.sy * (p.n[1] + g2) || p.sf < p.sz * (p.n[2] + g2))
+    return set_error(SF_EINVAL, "strides too small for the ghosted box");
+  if (p.sf > (1LL << 40)) return set_error(SF_EINVAL, "field stride too large");
+  const size_t es = p.precision == SF_FP64 ? 8 : 4;
+  if (!p.u_stage || !aligned(p.u_stage, es)) return set_error(SF_EINVAL, "u_stage NULL or misaligned");
+  if (need_stage_arrays) {
+    if (prm->rk != SF_RK4 && prm->rk != SF_SSPRK3) return set_error(SF_EINVAL, "unknown rk %d", prm->rk);
+    const int nst = prm->rk == SF_RK4 ? 4 : 3;
+    if (stage < 0 || stage >= nst) return set_error(SF_EINVAL, "stage %d out of range [0,%d)", stage, nst);
+    if (!p.u_n || !aligned(p.u_n, es)) return set_error(SF_EINVAL, "u_n NULL or misaligned");
+    if (!p.u_next || !aligned(p.u_next, es)) return set_error(SF_EINVAL, "u_next NULL or misaligned");
+    const bool last = stage == nst - 1;
+    if (p.u_next == p.u_stage || p.u_next == p.acc || (p.u_next == p.u_n && !last))
+      return set_error(SF_EINVAL,
+                       "u_next must not alias u_stage or acc, nor u_n before the last stage");
+    if (prm->rk == SF_RK4 && (!p.acc || !aligned(p.acc, es)))
+      return set_error(SF_EINVAL, "RK4 needs an acc array");
+    if (prm->rk == SF_RK4 && p.precision == SF_FP32_BULK && (!p.kahan || !aligned(p.kahan, es)))
+      return set_error(SF_EINVAL, "FP32_BULK RK4 needs a kahan array");
+    if (!(p.dt == p.dt) || p.dt < 0) return set_error(SF_EINVAL, "dt must be >= 0");
+    if (prm->ghosts == SF_GHOSTS_PERIODIC)
+      for (int d = 0; d < 3; ++d)
+        if (p.n[d] < p.ghost)
+          return set_error(SF_EINVAL, "fused periodic ghosts need n[%d] >= ghost; use sf_fill_ghosts_periodic", d);
+  }
+  if (!(prm->sigma_ko >= 0)) return set_error(SF_EINVAL, "sigma_ko must be >= 0");
+  return SF_OK;
+}
+
+// ---------------------------------------------------------------- ghosts
+template <typename T>
+__global__ void ghost_fill_kernel(T* u, int nf, int nx, int ny, int nz, int g, long long sy,
+                                  long long sz, long long sf) {
+  const long long NX = nx + 2 * g, NY = ny + 2 * g, NZ = nz + 2 * g;
+  const long long total = NX * NY * NZ * nf;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long r = t;
+    const int x = (int)(r % NX); r /= NX;
+    const int y = (int)(r % NY); r /= NY;
+    const int z = (int)(r % NZ); r /= NZ;
+    const int f = (int)r;
+    const int i = x - g, j = y - g, k = z - g;
+    if (i >= 0 && i < nx && j >= 0 && j < ny && k >= 0 && k < nz) continue;
+    const int ii = ((i % nx) + nx) % nx, jj = ((j % ny) + ny) % ny, kk = ((k % nz) + nz) % nz;
+    u[f * sf + (long long)z * sz + (long long)y * sy + x] =
+        u[f * sf + (long long)(kk + g) * sz + (long long)(jj + g) * sy + (ii + g)];
+  }
+}
+
+// ---------------------------------------------------------------- observers
+template <typename T>
+__global__ void gather_kernel(const T* a, long long off, int nx, int ny, int g, long long sy,
+                              long long sz, long long total, const int64_t* obs, int nobs, T* out) {
+  int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nobs) return;
+  long long lin = obs[o];
+  if (lin < 0 || lin >= total) return;  // out-of-range observer: skipped
+  int i = (int)(lin % nx);
+  int j = (int)((lin / nx) % ny);
+  int k = (int)(lin / ((long long)nx * ny));
+  out[o] = a[off + (long long)(k + g) * sz + (long long)(j + g) * sy + (i + g)];
+}
+
+template <typename T>
+__global__ void scatter_add_kernel(T* a, long long off, int nx, int ny, int g, long long sy,
+                                   long long sz, long long total, const int64_t* obs, int nobs,
+                                   const T* vals) {
+  int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nobs) return;
+  long long lin = obs[o];
+  if (lin < 0 || lin >= total) return;  // out-of-range observer: skipped
+  int i = (int)(lin % nx);
+  int j = (int)((lin / nx) % ny);
+  int k = (int)(lin / ((long long)nx * ny));
+  a[off + (long long)(k + g) * sz + (long long)(j + g) * sy + (i + g)] += vals[o];
+}
+
+static StageArgs stage_args(const sf_params& prm, const sf_patch& p, int stage, int mode) {
+  StageArgs s;
+  s.mode = mode;
+  s.rk = prm.rk;
+  s.stage = stage;
+  s.kahan = (p.precision == SF_FP32_BULK && prm.rk == SF_RK4) ? 1 : 0;
+  s.un_alias = p.u_n == p.u_stage ? 1 : 0;
+  s.ghosts = prm.ghosts == SF_GHOSTS_PERIODIC ? 1 : 0;
+  s.check_finite = prm.check_finite;
+  s.status = status_ptr();
+  return s;
+}
+
+static sf_status dispatch(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
+                          void* rhs_out, bool adjoint, cudaStream_t st) {
+  if (!s.status) return set_error(SF_ECUDA, "no CUDA device / status word unavailable");
+  switch (p.system) {
+    case SF_WAVE: return launch_wave(prm, p, s, stage, rhs_out, adjoint, st);
+    case SF_Z4: return launch_z4(prm, p, s, stage, rhs_out, st);
+    case SF_MHD: return launch_mhd(prm, p, s, stage, rhs_out, st);
+  }
+  return set_error(SF_EINVAL, "unknown system");
+}
+
+}  // namespace sf
+
+using namespace sf;
+
+extern "C" {
+
+int32_t sf_nfields(int32_t system) {
+  switch (system) {
+    case SF_WAVE: return 5;
+    case SF_MHD: return 8;
+    case SF_Z4: return 25;
+  }
+  return -1;
+}
+
+const char* sf_last_error(void) { return t_err; }
+
+int64_t sf_launch_count(void) { return g_launches.load(); }
+
+sf_status sf_substep(const sf_params* prm, const sf_patch* patches, int32_t npatch, int32_t stage,
+                     void* stream) {
+  t_err[0] = 0;
+  if (!patches || npatch < 0) return set_error(SF_EINVAL, "patches NULL or npatch < 0");
+  if (!prm) return set_error(SF_EINVAL, "params is NULL");
+  for (int q = 0; q < npatch; ++q) {
+    sf_patch p = patches[q];
+    normalise_strides(p, sf_nfields(p.system));
+    sf_status e = check_patch(prm, p, 1, stage);
+    if (e) return e;
+    if (q > 0 && (p.system != patches[0].system || p.precision != patches[0].precision))
+      return set_error(SF_EINVAL, "sf_substep needs one system and precision; use sf_batch");
+  }
+  for (int q = 0; q < npatch; ++q) {
+    sf_patch p = patches[q];
+    normalise_strides(p, sf_nfields(p.system));
+    StageArgs s = stage_args(*prm, p, stage, 0);
+    sf_status e = dispatch(*prm, p, s, stage, nullptr, false, (cudaStream_t)stream);
+    if (e) return e;
+  }
+  return SF_OK;
+}
+
+sf_status sf_adjoint_substep(const sf_params* prm, const sf_patch* adj, int32_t npatch,
+                             int32_t stage, void* stream) {
+  t_err[0] = 0;
+  if (!adj || npatch < 0) return set_error(SF_EINVAL, "patches NULL or npatch < 0");
+  for (int q = 0; q < npatch; ++q) {
+    sf_patch p = adj[q];
+    normalise_strides(p, 5);
+    sf_status e = check_patch(prm, p, 1, stage);
+    if (e) return e;
+    if (p.system != SF_WAVE) return set_error(SF_ENOTSUP, "adjoint substep exists for SF_WAVE only");
+  }
+  for (int q = 0; q < npatch; ++q) {
+    sf_patch p = adj[q];
+    normalise_strides(p, 5);
+    StageArgs s = stage_args(*prm, p, stage, 0);
+    if (!s.status) return set_error(SF_ECUDA, "no CUDA device");
+    sf_status e = launch_wave(*prm, p, s, stage, nullptr, true, (cudaStream_t)stream);
+    if (e) return e;
+  }
+  return SF_OK;
+}
+
+sf_status sf_rhs(const sf_params* prm, const sf_patch* patch, void* rhs_out, void* stream) {
+  t_err[0] = 0;
+  if (!patch || !rhs_out) return set_error(SF_EINVAL, "patch or rhs_out NULL");
+  sf_patch p = *patch;
+  normalise_strides(p, sf_nfields(p.system));
+  sf_status e = check_patch(prm, p, 0, 0);
+  if (e) return e;
+  const size_t es = p.precision == SF_FP64 ? 8 : 4;
+  if (!aligned(rhs_out, es)) return set_error(SF_EINVAL, "rhs_out misaligned");
+  sf_params q = *prm;
+  q.rk = SF_RK4;
+  StageArgs s = stage_args(q, p, 0, 1);
+  s.ghosts = 0;
+  return dispatch(q, p, s, 0, rhs_out, false, (cudaStream_t)stream);
+}
+
+sf_status sf_fill_ghosts_periodic(const sf_patch* patch, void* array, int32_t nf, void* stream) {
+  t_err[0] = 0;
+  if (!patch || !array || nf < 1) return set_error(SF_EINVAL, "patch/array NULL or nf < 1");
+  sf_patch p = *patch;
+  normalise_strides(p, nf);
+  sf_params dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  p.u_stage = array;
+  sf_status e = check_patch(&dummy, p, 0, 0);
+  if (e) return e;
+  const long long total = (long long)(p.n[0] + 2 * p.ghost) * (p.n[1] + 2 * p.ghost) *
+                          (p.n[2] + 2 * p.ghost) * nf;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (p.precision == SF_FP64)
+    ghost_fill_kernel<double><<<blocks, 256, 0, (cudaStream_t)stream>>>(
+        (double*)array, nf, p.n[0], p.n[1], p.n[2], p.ghost, p.sy, p.sz, p.sf);
+  else
+    ghost_fill_kernel<float><<<blocks, 256, 0, (cudaStream_t)stream>>>(
+        (float*)array, nf, p.n[0], p.n[1], p.n[2], p.ghost, p.sy, p.sz, p.sf);
+  return after_launch("ghost_fill_kernel");
+}
+
+static sf_status obs_check(const sf_patch* patch, const void* array, int32_t field,
+                           const int64_t* obs, int32_t nobs, const void* other, sf_patch& p) {
+  if (!patch || !array || !obs || !other || nobs < 0) return set_error(SF_EINVAL, "NULL argument");
+  p = *patch;
+  normalise_strides(p, sf_nfields(p.system));
+  if (field < 0 || field >= sf_nfields(p.system)) return set_error(SF_EINVAL, "field out of range");
+  sf_params dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  p.u_stage = const_cast<void*>(array);
+  return check_patch(&dummy, p, 0, 0);
+}
+
+sf_status sf_gather(const sf_patch* patch, const void* array, int32_t field, const int64_t* obs,
+                    int32_t nobs, void* out, void* stream) {
+  t_err[0] = 0;
+  sf_patch p;
+  sf_status e = obs_check(patch, array, field, obs, nobs, out, p);
+  if (e) return e;
+  if (nobs == 0) return SF_OK;
+  int blocks = (nobs + 127) / 128;
+  if (p.precision == SF_FP64)
+    gather_kernel<double><<<blocks, 128, 0, (cudaStream_t)stream>>>(
+        (const double*)array, field * p.sf, p.n[0], p.n[1], p.ghost, p.sy, p.sz,
+        (long long)p.n[0] * p.n[1] * p.n[2], obs, nobs, (double*)out);
+  else
+    gather_kernel<float><<<blocks, 128, 0, (cudaStream_t)stream>>>(
+        (const float*)array, field * p.sf, p.n[0], p.n[1], p.ghost, p.sy, p.sz,
+        (long long)p.n[0] * p.n[1] * p.n[2], obs, nobs, (float*)out);
+  return after_launch("gather_kernel");
+}
+
+sf_status sf_scatter_add(const sf_patch* patch, void* array, int32_t field, const int64_t* obs,
+                         int32_t nobs, const void* vals, void* stream) {
+  t_err[0] = 0;
+  sf_patch p;
+  sf_status e = obs_check(patch, array, field, obs, nobs, vals, p);
+  if (e) return e;
+  if (nobs == 0) return SF_OK;
+  int blocks = (nobs + 127) / 128;
+  if (p.precision == SF_FP64)
+    scatter_add_kernel<double><<<blocks, 128, 0, (cudaStream_t)stream>>>(
+        (double*)array, field * p.sf, p.n[0], p.n[1], p.ghost, p.sy, p.sz,
+        (long long)p.n[0] * p.n[1] * p.n[2], obs, nobs, (const double*)vals);
+  else
+    scatter_add_kernel<float><<<blocks, 128, 0, (cudaStream_t)stream>>>(
+        (float*)array, field * p.sf, p.n[0], p.n[1], p.ghost, p.sy, p.sz,
+        (long long)p.n[0] * p.n[1] * p.n[2], obs, nobs, (const float*)vals);
+  return after_launch("scatter_add_kernel");
+}
+
+sf_status sf_get_device_status(void* stream) {
+  t_err[0] = 0;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return set_error(SF_ECUDA, "sync: %s", cudaGetErrorString(e));
+  unsigned int* p = status_ptr();
+  if (!p) return set_error(SF_ECUDA, "no status word");
+  unsigned int v = 0;
+  e = cudaMemcpy(&v, p, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return set_error(SF_ECUDA, "status read: %s", cudaGetErrorString(e));
+  unsigned int zero = 0;
+  e = cudaMemcpy(p, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return set_error(SF_ECUDA, "status reset: %s", cudaGetErrorString(e));
+  if (v & ST_TIMEOUT) return set_error(SF_ETIMEOUT, "a device wait timed out");
+  if (v & ST_NONFINITE) return set_error(SF_ENONFINITE, "non-finite value written");
+  return SF_OK;
+}
+
+}  // extern "C"

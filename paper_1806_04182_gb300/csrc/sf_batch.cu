@@ -1,0 +1,373 @@
+// Batched AMR-patch dispatch.  A table of patches of mixed systems (wave,
+// CCZ4) and sizes, each with its own dx and dt (the level loop of Sec. III
+// runs every patch of every level through "calculate rhs" + "integrate
+// time"), is advanced by ONE persistent launch per RK stage.  CTAs pull
+// (patch, tile) work items from a device counter until the list is empty;
+// CCZ4 tiles are queued first so the heavy items start early.  No CTA ever
+// waits on another, so the queue has no spin-waits.
+//
+// Buffer roles per patch (sf_patch fields as passed to sf_batch_create):
+//   u_n = A: the state U^n, updated in place by the last stage
+//   u_stage = B, u_next = C: stage scratch
+//   acc = D: RK4 accumulator, kahan = E (FP32_BULK)
+// stage 0: A -> B, stage 1: B -> C, stage 2: C -> B, stage 3: B -> A.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "sf_internal.cuh"
+#include "sf_wave.cuh"
+#include "sf_z4.cuh"
+
+namespace sf {
+
+// tile shapes (TX, TY, TZ); blockDim is always 128 = TX * TY
+struct Shape {
+  int tx, ty, tz;
+};
+static const Shape kShapes[] = {{32, 4, 1}, {32, 4, 2}, {32, 4, 4}, {64, 2, 1},
+                                {64, 2, 2}, {16, 8, 1}, {16, 8, 2}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+constexpr int kClasses = 4;  // (wave, z4) x (small: max n <= 32, large)
+
+struct Item {
+  int patch, x0, y0, z0;
+};
+
+template <typename T, typename H>
+__global__ void __launch_bounds__(128) batch_stage_kernel(const PatchArgs<T>* __restrict__ pa,
+                                                          const int* __restrict__ psys,
+                                                          const int2* __restrict__ pshape,
+                                                          const Item* __restrict__ items, int nitems,
+                                                          unsigned int* counter, StageArgs s,
+                                                          Z4Coef<T> zc) {
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= nitems) return;
+    const Item w = items[it];
+    const PatchArgs<T>& a = pa[w.patch];
+    const int2 sh = pshape[w.patch];  // (tx, tz)
+    const int lx = threadIdx.x % sh.x, ly = threadIdx.x / sh.x;
+    const int i = w.x0 + lx, j = w.y0 + ly;
+    if (i >= a.n[0] || j >= a.n[1]) continue;
+    const int g = a.g;
+    const int zend = min(w.z0 + sh.y, a.n[2]);
+    const int system = psys[w.patch];
+    for (int k = w.z0; k < zend; ++k) {
+      const long long c = (long long)(k + g) * a.sz + (long long)(j + g) * a.sy + (i + g);
+      if (system == SF_Z4) {
+        T v[25], r[25];
+        z4_point<T, H>(a, zc, a.us + c, v, r);
+#pragma unroll
+        for (int f = 0; f < 25; ++f) stage_write(a, s, f, c, i, j, k, v[f], r[f]);
+      } else {
+        T v[5], r[5];
+        wave_point<T, false>(a, a.us + c, v, r);
+#pragma unroll
+        for (int f = 0; f < 5; ++f) stage_write(a, s, f, c, i, j, k, v[f], r[f]);
+      }
+    }
+  }
+}
+
+}  // namespace sf
+
+using namespace sf;
+
+struct sf_batch {
+  sf_params prm;
+  int precision;
+  int npatch;
+  std::vector<sf_patch> patches;
+  int shape_of_class[kClasses];
+  int device;
+  int grid[2];            // persistent grid size (FP64, FP32 kernels)
+  void* d_args = nullptr; // PatchArgs<T>[4][npatch]
+  int* d_sys = nullptr;
+  int2* d_shape = nullptr;
+  Item* d_items = nullptr;
+  int nitems = 0;
+  unsigned int* d_counter = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+int class_of(const sf_patch& p) {
+  const int m = std::max(p.n[0], std::max(p.n[1], p.n[2]));
+  return (p.system == SF_Z4 ? 2 : 0) + (m > 32 ? 1 : 0);
+}
+
+template <typename T>
+sf_status upload_args(sf_batch* b) {
+  const int np = b->npatch;
+  std::vector<PatchArgs<T>> h(4 * (size_t)np);
+  for (int st = 0; st < 4; ++st)
+    for (int q = 0; q < np; ++q) {
+      sf_patch p = b->patches[q];
+      void* A = p.u_n;
+      void* B = p.u_stage;
+      void* C = p.u_next;
+      void* us[4] = {A, B, C, B};
+      void* nx[4] = {B, C, B, A};
+      p.u_stage = us[st];
+      p.u_n = A;
+      p.u_next = nx[st];
+      h[(size_t)st * np + q] = make_args<T>(b->prm, p, st, sf_nfields(p.system), nullptr);
+    }
+  if (!b->d_args && cudaMalloc(&b->d_args, h.size() * sizeof(PatchArgs<T>)) != cudaSuccess)
+    return set_error(SF_ECUDA, "batch: cudaMalloc of patch table failed");
+  if (cudaMemcpy(b->d_args, h.data(), h.size() * sizeof(PatchArgs<T>), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return set_error(SF_ECUDA, "batch: upload of patch table failed");
+  return SF_OK;
+}
+
+// Work list for the current shape choice; CCZ4 items first.  If `only_class`
+// >= 0, only patches of that class are listed (tuning).
+sf_status build_items(sf_batch* b, int only_class) {
+  std::vector<Item> items;
+  std::vector<int2> shapes(b->npatch);
+  for (int pass = 0; pass < 2; ++pass)
+    for (int q = 0; q < b->npatch; ++q) {
+      const sf_patch& p = b->patches[q];
+      const bool z4 = p.system == SF_Z4;
+      if ((pass == 0) != z4) continue;
+      const int cls = class_of(p);
+      const Shape sh = kShapes[b->shape_of_class[cls]];
+      shapes[q] = make_int2(sh.tx, sh.tz);
+      if (only_class >= 0 && cls != only_class) continue;
+      for (int z = 0; z < p.n[2]; z += sh.tz)
+        for (int y = 0; y < p.n[1]; y += sh.ty)
+          for (int x = 0; x < p.n[0]; x += sh.tx) items.push_back(Item{q, x, y, z});
+    }
+  if (b->d_items) cudaFree(b->d_items);
+  b->d_items = nullptr;
+  b->nitems = (int)items.size();
+  if (!items.empty()) {
+    if (cudaMalloc(&b->d_items, items.size() * sizeof(Item)) != cudaSuccess)
+      return set_error(SF_ECUDA, "batch: cudaMalloc of work list failed");
+    if (cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return set_error(SF_ECUDA, "batch: upload of work list failed");
+  }
+  if (cudaMemcpy(b->d_shape, shapes.data(), shapes.size() * sizeof(int2), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return set_error(SF_ECUDA, "batch: upload of shapes failed");
+  return SF_OK;
+}
+
+StageArgs batch_stage_args(const sf_batch* b, int stage, unsigned int* status) {
+  StageArgs s;
+  s.mode = 0;
+  s.rk = SF_RK4;
+  s.stage = stage;
+  s.kahan = b->precision == SF_FP32_BULK ? 1 : 0;
+  s.un_alias = stage == 0 ? 1 : 0;
+  s.ghosts = 1;
+  s.check_finite = b->prm.check_finite;
+  s.status = status;
+  return s;
+}
+
+template <typename T>
+sf_status launch_stage(sf_batch* b, int stage, cudaStream_t st, unsigned int* status) {
+  if (cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), st) != cudaSuccess)
+    return set_error(SF_ECUDA, "batch: counter reset failed");
+  Z4Coef<T> zc;
+  zc.kappa_z = T(b->prm.kappa_z);
+  zc.kappa_c = T(b->prm.kappa_c);
+  zc.eta = T(b->prm.eta);
+  zc.g_shift = T(b->prm.g_shift);
+  zc.slicing = b->prm.slicing;
+  zc.shift_frozen = b->prm.shift_frozen;
+  const PatchArgs<T>* args = static_cast<const PatchArgs<T>*>(b->d_args) + (size_t)stage * b->npatch;
+  const int grid = b->grid[b->precision == SF_FP64 ? 0 : 1];
+  batch_stage_kernel<T, double><<<grid, 128, 0, st>>>(args, b->d_sys, b->d_shape, b->d_items,
+                                                      b->nitems, b->d_counter,
+                                                      batch_stage_args(b, stage, status), zc);
+  return after_launch("batch_stage_kernel");
+}
+
+}  // namespace
+
+extern "C" {
+
+sf_status sf_batch_create(const sf_params* prm, const sf_patch* patches, int32_t npatch,
+                          sf_batch** out) {
+  if (!prm || !patches || !out || npatch < 1) return set_error(SF_EINVAL, "NULL argument or npatch < 1");
+  if (prm->rk != SF_RK4) return set_error(SF_ENOTSUP, "sf_batch runs RK4");
+  *out = nullptr;
+  sf_batch* b = new sf_batch();
+  b->prm = *prm;
+  b->prm.ghosts = SF_GHOSTS_PERIODIC;
+  b->npatch = npatch;
+  b->precision = patches[0].precision;
+  b->patches.assign(patches, patches + npatch);
+  for (int q = 0; q < npatch; ++q) {
+    sf_patch& p = b->patches[q];
+    normalise_strides(p, sf_nfields(p.system));
+    if (p.system != SF_WAVE && p.system != SF_Z4) {
+      delete b;
+      return set_error(SF_ENOTSUP, "sf_batch takes SF_WAVE and SF_Z4 patches");
+    }
+    if (p.precision != b->precision) {
+      delete b;
+      return set_error(SF_EINVAL, "all patches of a batch need one precision");
+    }
+    // the four stage roles must be valid sf_substep patches
+    for (int st = 0; st < 4; ++st) {
+      sf_patch r = p;
+      void* us[4] = {p.u_n, p.u_stage, p.u_next, p.u_stage};
+      void* nx[4] = {p.u_stage, p.u_next, p.u_stage, p.u_n};
+      r.u_stage = us[st];
+      r.u_next = nx[st];
+      sf_status e = check_patch(&b->prm, r, 1, st);
+      if (e) {
+        delete b;
+        return e;
+      }
+    }
+    if (p.u_stage == p.u_next || p.u_stage == p.u_n || p.u_next == p.u_n) {
+      delete b;
+      return set_error(SF_EINVAL, "batch patches need distinct u_n, u_stage and u_next buffers");
+    }
+  }
+  for (int c = 0; c < kClasses; ++c) b->shape_of_class[c] = 0;
+  cudaGetDevice(&b->device);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  int occ64 = 0, occ32 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, batch_stage_kernel<double, double>, 128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, batch_stage_kernel<float, double>, 128, 0);
+  b->grid[0] = std::max(1, sms * std::max(1, occ64));
+  b->grid[1] = std::max(1, sms * std::max(1, occ32));
+  std::vector<int> sys(npatch);
+  for (int q = 0; q < npatch; ++q) sys[q] = b->patches[q].system;
+  if (cudaMalloc(&b->d_sys, npatch * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&b->d_shape, npatch * sizeof(int2)) != cudaSuccess ||
+      cudaMalloc(&b->d_counter, sizeof(unsigned int)) != cudaSuccess) {
+    sf_batch_destroy(b);
+    return set_error(SF_ECUDA, "batch: cudaMalloc failed");
+  }
+  cudaMemcpy(b->d_sys, sys.data(), npatch * sizeof(int), cudaMemcpyHostToDevice);
+  sf_status e = b->precision == SF_FP64 ? upload_args<double>(b) : upload_args<float>(b);
+  if (!e) e = build_items(b, -1);
+  if (e) {
+    sf_batch_destroy(b);
+    return e;
+  }
+  *out = b;
+  return SF_OK;
+}
+
+sf_status sf_batch_substep(sf_batch* b, int32_t stage, void* stream) {
+  if (!b) return set_error(SF_EINVAL, "batch is NULL");
+  if (stage < 0 || stage > 3) return set_error(SF_EINVAL, "stage %d out of range [0,4)", stage);
+  unsigned int* status = status_ptr();
+  if (!status) return set_error(SF_ECUDA, "no status word");
+  if (b->precision == SF_FP64) return launch_stage<double>(b, stage, (cudaStream_t)stream, status);
+  return launch_stage<float>(b, stage, (cudaStream_t)stream, status);
+}
+
+sf_status sf_batch_tune(sf_batch* b, void* stream) {
+  if (!b) return set_error(SF_EINVAL, "batch is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  sf_status err = SF_OK;
+  for (int cls = 0; cls < kClasses && !err; ++cls) {
+    bool any = false;
+    for (const auto& p : b->patches) any |= class_of(p) == cls;
+    if (!any) continue;
+    float best = 1e30f;
+    int best_shape = 0;
+    for (int s = 0; s < kNumShapes && !err; ++s) {
+      b->shape_of_class[cls] = s;
+      if ((err = build_items(b, cls))) break;
+      // stage 1 writes only scratch (u_next role C and acc), never U^n
+      for (int rep = 0; rep < 2 && !err; ++rep) err = sf_batch_substep(b, 1, stream);
+      cudaEventRecord(e0, st);
+      for (int rep = 0; rep < 3 && !err; ++rep) err = sf_batch_substep(b, 1, stream);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_shape = s;
+      }
+    }
+    b->shape_of_class[cls] = best_shape;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!err) err = build_items(b, -1);
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+  }
+  return err;
+}
+
+sf_status sf_batch_capture(sf_batch* b, void* stream) {
+  if (!b) return set_error(SF_EINVAL, "batch is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!st) return set_error(SF_EINVAL, "graph capture needs a non-default stream");
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+  }
+  status_ptr();  // resolve the symbol address before capture
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return set_error(SF_ECUDA, "begin capture failed");
+  sf_status err = SF_OK;
+  for (int s = 0; s < 4 && !err; ++s) err = sf_batch_substep(b, s, stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(st, &g);
+  if (err) {
+    if (g) cudaGraphDestroy(g);
+    return err;
+  }
+  if (ce != cudaSuccess) return set_error(SF_ECUDA, "end capture: %s", cudaGetErrorString(ce));
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return set_error(SF_ECUDA, "graph instantiate failed");
+  }
+  b->graph = g;
+  return SF_OK;
+}
+
+sf_status sf_batch_launch(sf_batch* b, void* stream) {
+  if (!b || !b->exec) return set_error(SF_EINVAL, "batch NULL or not captured");
+  cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return set_error(SF_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+  return after_launch("batch graph");
+}
+
+int32_t sf_batch_launches_per_step(const sf_batch* b) { return b ? 4 : 0; }
+
+sf_status sf_batch_destroy(sf_batch* b) {
+  if (!b) return SF_OK;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->d_args) cudaFree(b->d_args);
+  if (b->d_sys) cudaFree(b->d_sys);
+  if (b->d_shape) cudaFree(b->d_shape);
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_counter) cudaFree(b->d_counter);
+  delete b;
+  return SF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,198 @@
+// Shared device/host pieces of the GB300 substep library: patch layout
+// passed to kernels, the 4th-order stencils of Sec. II.B.1, the RK stage
+// combination of Sec. II.C / App. C-D, fused periodic ghost writes and the
+// device status word.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sf.h"
+
+namespace sf {
+
+// ------------------------------------------------------------ status word
+// bit 0: non-finite output, bit 1: work-queue time-out.  The word lives in
+// sf_api.cu; kernels get its device address through StageArgs::status.
+constexpr unsigned int ST_NONFINITE = 1u;
+constexpr unsigned int ST_TIMEOUT = 2u;
+
+// ------------------------------------------------------------ kernel args
+// Everything a stage kernel needs about one patch, by value.
+template <typename T>
+struct PatchArgs {
+  int n[3];
+  int g;
+  long long sy, sz, sf;
+  long long ninterior;
+  const T* __restrict__ us;  // stage input (ghosted)
+  const T* __restrict__ un;  // U^n (ghosted)
+  T* acc;
+  T* nx;                     // next stage / U^{n+1}, or the RHS output (unghosted)
+  T* kh;
+  // precomputed coefficients
+  T i12h[3];    // 1 / (12 dx_d)
+  T i12h2[3];   // 1 / (12 dx_d^2)
+  T i144hh[3];  // 1 / (144 dx_a dx_b) for (xy, xz, yz)
+  T ko[3];      // sigma / (64 dx_d)
+  T c_next;     // u_next = un + c_next * r   (or ssp weights)
+  T c_acc;      // acc += c_acc * r
+  T dt;
+};
+
+// RK stage selection, uniform over a launch
+struct StageArgs {
+  int mode;        // 0: stage update, 1: write RHS only
+  int rk;          // SF_RK4 / SF_SSPRK3
+  int stage;
+  int kahan;       // FP32_BULK compensated last stage
+  int un_alias;    // u_n == u_stage: reuse the centre value
+  int ghosts;      // SF_GHOSTS_PERIODIC: also write the periodic ghost shell
+  int check_finite;
+  unsigned int* status;  // device status word
+};
+
+// ------------------------------------------------------------ stencils
+// Sec. II.B.1.  `p` points at the centre value, `s` is the element stride
+// of the direction.
+template <typename T>
+__device__ __forceinline__ T d1(const T* __restrict__ p, long long s, T i12h) {
+  return ((__ldg(p - 2 * s) - __ldg(p + 2 * s)) + T(8) * (__ldg(p + s) - __ldg(p - s))) * i12h;
+}
+
+template <typename T>
+__device__ __forceinline__ T d2(const T* __restrict__ p, long long s, T c0, T i12h2) {
+  return (T(16) * (__ldg(p - s) + __ldg(p + s)) - (__ldg(p - 2 * s) + __ldg(p + 2 * s)) - T(30) * c0) *
+         i12h2;
+}
+
+// D_b(D_a U): tensor product of two first-derivative stencils (16 points)
+template <typename T>
+__device__ __forceinline__ T dmix(const T* __restrict__ p, long long sa, long long sb, T i144) {
+  auto row = [&](long long o) {
+    const T* q = p + o;
+    return (__ldg(q - 2 * sa) - __ldg(q + 2 * sa)) + T(8) * (__ldg(q + sa) - __ldg(q - sa));
+  };
+  return ((row(-2 * sb) - row(2 * sb)) + T(8) * (row(sb) - row(-sb))) * i144;
+}
+
+// 6th difference along one direction: U-3 - 6U-2 + 15U-1 - 20U0 + 15U+1 - 6U+2 + U+3
+template <typename T>
+__device__ __forceinline__ T delta6(const T* __restrict__ p, long long s, T c0) {
+  return (__ldg(p - 3 * s) + __ldg(p + 3 * s)) - T(6) * (__ldg(p - 2 * s) + __ldg(p + 2 * s)) +
+         T(15) * (__ldg(p - s) + __ldg(p + s)) - T(20) * c0;
+}
+
+template <typename T>
+__device__ __forceinline__ T ko_all(const T* __restrict__ p, long long sy, long long sz, T c0,
+                                    const T* kc) {
+  return kc[0] * delta6(p, 1, c0) + kc[1] * delta6(p, sy, c0) + kc[2] * delta6(p, sz, c0);
+}
+
+__device__ __forceinline__ bool finite_(double v) { return isfinite(v); }
+__device__ __forceinline__ bool finite_(float v) { return isfinite(v); }
+
+// ------------------------------------------------------------ stage write
+// Writes one field value of the stage update at ghosted offset `c`
+// (interior point i,j,k).  `centre` is u_stage at c; `r` = (L + Q_d)(u_stage).
+template <typename T>
+__device__ __forceinline__ void stage_write(const PatchArgs<T>& a, const StageArgs& s, int f,
+                                            long long c, int i, int j, int k, T centre, T r) {
+  if (s.mode == 1) {
+    a.nx[f * a.ninterior + ((long long)k * a.n[1] + j) * a.n[0] + i] = r;
+    return;
+  }
+  const long long o = f * a.sf + c;
+  T un = s.un_alias ? centre : a.un[o];
+  T out;
+  if (s.rk == SF_RK4) {
+    if (s.stage == 0) {
+      a.acc[o] = (s.kahan ? T(0) : un) + a.c_acc * r;
+      out = un + a.c_next * r;
+    } else if (s.stage < 3) {
+      a.acc[o] = a.acc[o] + a.c_acc * r;
+      out = un + a.c_next * r;
+    } else if (!s.kahan) {
+      out = a.acc[o] + a.c_next * r;
+    } else {
+      // U^{n+1} = U^n + inc with Kahan compensation carried in kh
+      T inc = a.acc[o] + a.c_next * r;
+      T y = inc - a.kh[o];
+      T t = un + y;
+      a.kh[o] = (t - un) - y;
+      out = t;
+    }
+  } else {
+    if (s.stage == 0) out = un + a.dt * r;
+    else if (s.stage == 1) out = T(0.75) * un + T(0.25) * (centre + a.dt * r);
+    else out = un * T(1.0 / 3.0) + T(2.0 / 3.0) * (centre + a.dt * r);
+  }
+  a.nx[o] = out;
+  if (s.check_finite && !finite_(out)) atomicOr(s.status, ST_NONFINITE);
+  if (s.ghosts) {
+    // periodic images of (i,j,k) inside the ghost shell (n >= g is checked on the host)
+    const int g = a.g;
+    int xs[3] = {0, 0, 0}, ys[3] = {0, 0, 0}, zs[3] = {0, 0, 0};
+    int nxs = 1, nys = 1, nzs = 1;
+    if (i < g) xs[nxs++] = a.n[0];
+    if (i >= a.n[0] - g) xs[nxs++] = -a.n[0];
+    if (j < g) ys[nys++] = a.n[1];
+    if (j >= a.n[1] - g) ys[nys++] = -a.n[1];
+    if (k < g) zs[nzs++] = a.n[2];
+    if (k >= a.n[2] - g) zs[nzs++] = -a.n[2];
+    if (nxs + nys + nzs > 3) {
+      for (int p = 0; p < nzs; ++p)
+        for (int q = 0; q < nys; ++q)
+          for (int w = 0; w < nxs; ++w) {
+            if (p == 0 && q == 0 && w == 0) continue;
+            a.nx[o + zs[p] * a.sz + ys[q] * a.sy + xs[w]] = out;
+          }
+    }
+  }
+}
+
+// ------------------------------------------------------------ launch plumbing
+struct Launch {
+  dim3 grid, block;
+};
+
+// Host-side construction of PatchArgs from the ABI structs.
+template <typename T>
+PatchArgs<T> make_args(const sf_params& prm, const sf_patch& p, int stage, int nf,
+                       void* rhs_out) {
+  PatchArgs<T> a;
+  for (int d = 0; d < 3; ++d) a.n[d] = p.n[d];
+  a.g = p.ghost;
+  a.sy = p.sy;
+  a.sz = p.sz;
+  a.sf = p.sf;
+  a.ninterior = (long long)p.n[0] * p.n[1] * p.n[2];
+  a.us = static_cast<const T*>(p.u_stage);
+  a.un = static_cast<const T*>(p.u_n);
+  a.acc = static_cast<T*>(p.acc);
+  a.nx = static_cast<T*>(rhs_out ? rhs_out : p.u_next);
+  a.kh = static_cast<T*>(p.kahan);
+  for (int d = 0; d < 3; ++d) {
+    a.i12h[d] = T(1.0 / (12.0 * p.dx[d]));
+    a.i12h2[d] = T(1.0 / (12.0 * p.dx[d] * p.dx[d]));
+    a.ko[d] = T(prm.sigma_ko / (64.0 * p.dx[d]));
+  }
+  a.i144hh[0] = T(1.0 / (144.0 * p.dx[0] * p.dx[1]));
+  a.i144hh[1] = T(1.0 / (144.0 * p.dx[0] * p.dx[2]));
+  a.i144hh[2] = T(1.0 / (144.0 * p.dx[1] * p.dx[2]));
+  const double dt = p.dt;
+  a.dt = T(dt);
+  double cn = 0.0, ca = 0.0;
+  if (prm.rk == SF_RK4) {
+    const double cnext[4] = {0.5, 0.5, 1.0, 1.0 / 6.0};
+    const double cacc[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 0.0};
+    cn = cnext[stage] * dt;
+    ca = cacc[stage] * dt;
+  }
+  a.c_next = T(cn);
+  a.c_acc = T(ca);
+  (void)nf;
+  return a;
+}
+
+}  // namespace sf

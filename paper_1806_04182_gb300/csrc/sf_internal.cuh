@@ -1,0 +1,26 @@
+// Internal declarations shared by the translation units of libsf.so.
+#pragma once
+
+#include "sf_common.cuh"
+
+namespace sf {
+
+// thread-local error message + launch bookkeeping (sf_api.cu)
+sf_status set_error(sf_status code, const char* fmt, ...);
+sf_status after_launch(const char* what);
+// device address of the status word on the current device (nullptr if none)
+unsigned int* status_ptr();
+
+// per-system stage launchers; rhs_out != nullptr selects "RHS only" output
+sf_status launch_wave(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
+                      void* rhs_out, bool adjoint, cudaStream_t st);
+sf_status launch_z4(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
+                    void* rhs_out, cudaStream_t st);
+sf_status launch_mhd(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
+                     void* rhs_out, cudaStream_t st);
+
+// argument validation shared by the entry points (sf_api.cu)
+sf_status check_patch(const sf_params* prm, const sf_patch& p, int need_stage_arrays, int stage);
+void normalise_strides(sf_patch& p, int nf);
+
+}  // namespace sf

@@ -1,0 +1,243 @@
+// Ideal Newtonian MHD (Sec. IV.B), 8 conserved fields
+//   U = (rho, S_x, S_y, S_z, E, B^x, B^y, B^z),
+// in conservative form L(U)_i = -sum_d (F_{i+1/2} - F_{i-1/2}) / dx_d (Eq. 5).
+// Interface fluxes: WENO5 reconstruction of the evolved fields from the left
+// and right (App. B; JS or Z weights), physical fluxes of both states and the
+// local Lax-Friedrichs formula (Eq. LLF) with the largest fast magnetosonic
+// signal speed of the two states.  Fused with the RK stage update.
+#include "sf_internal.cuh"
+
+namespace sf {
+
+template <typename T>
+struct MhdCoef {
+  T gamma;
+  T eps[3];   // WENO epsilon per direction
+  T q;        // WENO-Z exponent
+  int variant;
+  T idx[3];   // 1/dx_d
+};
+
+template <typename T>
+__device__ __forceinline__ T wz_pow(T x, T q) {
+  return q == T(2) ? x * x : (q == T(1) ? x : pow(x, q));
+}
+
+// App. B: left state at i+1/2 from w[0..4] = U_{i-2..i+2}
+template <typename T>
+__device__ __forceinline__ T weno_left(const T* w, T eps, const MhdCoef<T>& mc) {
+  const T c0 = (T(2) * w[2] + T(5) * w[3] - w[4]) * T(1.0 / 6.0);
+  const T c1 = (-w[1] + T(5) * w[2] + T(2) * w[3]) * T(1.0 / 6.0);
+  const T c2 = (T(2) * w[0] - T(7) * w[1] + T(11) * w[2]) * T(1.0 / 6.0);
+  const T a0 = w[2] - T(2) * w[3] + w[4], b0 = T(3) * w[2] - T(4) * w[3] + w[4];
+  const T a1 = w[1] - T(2) * w[2] + w[3], b1 = w[1] - w[3];
+  const T a2 = w[0] - T(2) * w[1] + w[2], b2 = w[0] - T(4) * w[1] + T(3) * w[2];
+  const T be0 = T(13.0 / 12.0) * a0 * a0 + T(0.25) * b0 * b0;
+  const T be1 = T(13.0 / 12.0) * a1 * a1 + T(0.25) * b1 * b1;
+  const T be2 = T(13.0 / 12.0) * a2 * a2 + T(0.25) * b2 * b2;
+  T al0, al1, al2;
+  if (mc.variant == 1) {
+    const T tau = fabs(be0 - be2);
+    al0 = T(0.3) * (T(1) + wz_pow(tau / (eps + be0), mc.q));
+    al1 = T(0.6) * (T(1) + wz_pow(tau / (eps + be1), mc.q));
+    al2 = T(0.1) * (T(1) + wz_pow(tau / (eps + be2), mc.q));
+  } else {
+    const T e0 = eps + be0, e1 = eps + be1, e2 = eps + be2;
+    al0 = T(0.3) / (e0 * e0);
+    al1 = T(0.6) / (e1 * e1);
+    al2 = T(0.1) / (e2 * e2);
+  }
+  return (al0 * c0 + al1 * c1 + al2 * c2) / (al0 + al1 + al2);
+}
+
+// App. B: right state at i-1/2 from w[0..4] = U_{i-2..i+2}
+template <typename T>
+__device__ __forceinline__ T weno_right(const T* w, T eps, const MhdCoef<T>& mc) {
+  const T c0 = (T(2) * w[4] - T(7) * w[3] + T(11) * w[2]) * T(1.0 / 6.0);
+  const T c1 = (-w[3] + T(5) * w[2] + T(2) * w[1]) * T(1.0 / 6.0);
+  const T c2 = (T(2) * w[2] + T(5) * w[1] - w[0]) * T(1.0 / 6.0);
+  const T a0 = w[4] - T(2) * w[3] + w[2], b0 = w[4] - T(4) * w[3] + T(3) * w[2];
+  const T a1 = w[3] - T(2) * w[2] + w[1], b1 = w[3] - w[1];
+  const T a2 = w[2] - T(2) * w[1] + w[0], b2 = T(3) * w[2] - T(4) * w[1] + w[0];
+  const T be0 = T(13.0 / 12.0) * a0 * a0 + T(0.25) * b0 * b0;
+  const T be1 = T(13.0 / 12.0) * a1 * a1 + T(0.25) * b1 * b1;
+  const T be2 = T(13.0 / 12.0) * a2 * a2 + T(0.25) * b2 * b2;
+  T al0, al1, al2;
+  if (mc.variant == 1) {
+    const T tau = fabs(be0 - be2);
+    al0 = T(0.1) * (T(1) + wz_pow(tau / (eps + be0), mc.q));
+    al1 = T(0.6) * (T(1) + wz_pow(tau / (eps + be1), mc.q));
+    al2 = T(0.3) * (T(1) + wz_pow(tau / (eps + be2), mc.q));
+  } else {
+    const T e0 = eps + be0, e1 = eps + be1, e2 = eps + be2;
+    al0 = T(0.1) / (e0 * e0);
+    al1 = T(0.6) / (e1 * e1);
+    al2 = T(0.3) / (e2 * e2);
+  }
+  return (al0 * c0 + al1 * c1 + al2 * c2) / (al0 + al1 + al2);
+}
+
+// physical flux along d and the largest signal speed |v_d| + c_fast,d
+template <typename T>
+__device__ __forceinline__ T flux_speed(const T* q, int d, const MhdCoef<T>& mc, T* F) {
+  const T rho = q[0], irho = T(1) / rho;
+  const T v[3] = {q[1] * irho, q[2] * irho, q[3] * irho};
+  const T B[3] = {q[5], q[6], q[7]};
+  const T B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+  const T S2v = q[1] * v[0] + q[2] * v[1] + q[3] * v[2];
+  const T pr = (mc.gamma - T(1)) * (q[4] - T(0.5) * S2v - T(0.5) * B2);
+  const T ptot = pr + T(0.5) * B2;
+  const T vB = v[0] * B[0] + v[1] * B[1] + v[2] * B[2];
+  const T vd = v[d], Bd = B[d];
+  F[0] = q[1 + d];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) F[1 + a] = q[1 + d] * v[a] - Bd * B[a] + (a == d ? ptot : T(0));
+  F[4] = (q[4] + ptot) * vd - vB * Bd;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) F[5 + a] = vd * B[a] - v[a] * Bd;
+  const T a2 = mc.gamma * pr * irho, b2 = B2 * irho, bd2 = Bd * Bd * irho;
+  const T s = a2 + b2;
+  const T cf2 = T(0.5) * (s + sqrt(s * s - T(4) * a2 * bd2));
+  return fabs(vd) + sqrt(cf2);
+}
+
+// LLF flux through the face between the cell at p and its +d neighbour
+template <typename T>
+__device__ __forceinline__ void face_flux(const T* __restrict__ p, long long F, long long s, int d,
+                                          const MhdCoef<T>& mc, T* Fout) {
+  T UL[8], UR[8];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    const T* q = p + f * F;
+    T w[6];
+#pragma unroll
+    for (int o = 0; o < 6; ++o) w[o] = __ldg(q + (o - 2) * s);
+    UL[f] = weno_left(w, mc.eps[d], mc);
+    UR[f] = weno_right(w + 1, mc.eps[d], mc);
+  }
+  T FL[8], FR[8];
+  const T sl = flux_speed(UL, d, mc, FL);
+  const T sr = flux_speed(UR, d, mc, FR);
+  const T S = sl > sr ? sl : sr;
+#pragma unroll
+  for (int f = 0; f < 8; ++f) Fout[f] = T(0.5) * (FL[f] + FR[f] - S * (UR[f] - UL[f]));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) mhd_stage_kernel(PatchArgs<T> a, StageArgs s, MhdCoef<T> mc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= a.n[0] || j >= a.n[1]) return;
+  const int g = a.g;
+  const long long c = (long long)(k + g) * a.sz + (long long)(j + g) * a.sy + (i + g);
+  const T* __restrict__ u = a.us + c;
+  const long long st[3] = {1, a.sy, a.sz};
+  T r[8];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) r[f] = T(0);
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    T Fp[8], Fm[8];
+    face_flux(u, a.sf, st[d], d, mc, Fp);
+    face_flux(u - st[d], a.sf, st[d], d, mc, Fm);
+#pragma unroll
+    for (int f = 0; f < 8; ++f) r[f] -= (Fp[f] - Fm[f]) * mc.idx[d];
+  }
+#pragma unroll
+  for (int f = 0; f < 8; ++f) stage_write(a, s, f, c, i, j, k, __ldg(u + f * a.sf), r[f]);
+}
+
+// CFL rate: max over cells and d of (|v_d| + c_fast,d) / dx_d
+template <typename T>
+__global__ void __launch_bounds__(256) mhd_rate_kernel(const T* __restrict__ u0, int nx, int ny,
+                                                       int nz, int g, long long sy, long long sz,
+                                                       long long F, MhdCoef<T> mc,
+                                                       unsigned long long* out) {
+  const long long total = (long long)nx * ny * nz;
+  double best = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % nx);
+    const int j = (int)((t / nx) % ny);
+    const int k = (int)(t / ((long long)nx * ny));
+    const T* p = u0 + (long long)(k + g) * sz + (long long)(j + g) * sy + (i + g);
+    T q[8], Fd[8];
+#pragma unroll
+    for (int f = 0; f < 8; ++f) q[f] = __ldg(p + f * F);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double r = double(flux_speed(q, d, mc, Fd)) * double(mc.idx[d]);
+      best = r > best ? r : best;
+    }
+  }
+  // block max, then one atomic per block (non-negative doubles order like their bits)
+  __shared__ double sm[256];
+  sm[threadIdx.x] = best;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(sm[0]));
+}
+
+template <typename T>
+static MhdCoef<T> coef(const sf_params& prm, const sf_patch& p) {
+  MhdCoef<T> mc;
+  mc.gamma = T(prm.gamma_eos);
+  for (int d = 0; d < 3; ++d) {
+    const double h = p.dx[d];
+    mc.eps[d] = T(prm.weno_eps > 0 ? prm.weno_eps : h * h * h * h);
+    mc.idx[d] = T(1.0 / h);
+  }
+  mc.q = T(prm.weno_q);
+  mc.variant = prm.weno_variant;
+  return mc;
+}
+
+template <typename T>
+static sf_status launch(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
+                        void* rhs_out, cudaStream_t st) {
+  PatchArgs<T> a = make_args<T>(prm, p, stage, 8, rhs_out);
+  dim3 block(32, 4, 1);
+  dim3 grid((p.n[0] + 31) / 32, (p.n[1] + 3) / 4, p.n[2]);
+  mhd_stage_kernel<T><<<grid, block, 0, st>>>(a, s, coef<T>(prm, p));
+  return after_launch("mhd_stage_kernel");
+}
+
+sf_status launch_mhd(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
+                     void* rhs_out, cudaStream_t st) {
+  if (p.precision == SF_FP64) return launch<double>(prm, p, s, stage, rhs_out, st);
+  return launch<float>(prm, p, s, stage, rhs_out, st);
+}
+
+}  // namespace sf
+
+using namespace sf;
+
+extern "C" sf_status sf_mhd_max_rate(const sf_params* prm, const sf_patch* patch,
+                                     const void* array, double* d_rate, void* stream) {
+  if (!patch || !array || !d_rate) return set_error(SF_EINVAL, "NULL argument");
+  sf_patch p = *patch;
+  normalise_strides(p, 8);
+  p.u_stage = const_cast<void*>(array);
+  sf_status e = check_patch(prm, p, 0, 0);
+  if (e) return e;
+  if (p.system != SF_MHD) return set_error(SF_EINVAL, "sf_mhd_max_rate needs an SF_MHD patch");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(d_rate, 0, sizeof(double), st) != cudaSuccess)
+    return set_error(SF_ECUDA, "memset of d_rate failed");
+  const long long total = (long long)p.n[0] * p.n[1] * p.n[2];
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (p.precision == SF_FP64)
+    mhd_rate_kernel<double><<<blocks, 256, 0, st>>>((const double*)array, p.n[0], p.n[1], p.n[2],
+                                                    p.ghost, p.sy, p.sz, p.sf, coef<double>(*prm, p),
+                                                    (unsigned long long*)d_rate);
+  else
+    mhd_rate_kernel<float><<<blocks, 256, 0, st>>>((const float*)array, p.n[0], p.n[1], p.n[2],
+                                                   p.ghost, p.sy, p.sz, p.sf, coef<float>(*prm, p),
+                                                   (unsigned long long*)d_rate);
+  return after_launch("mhd_rate_kernel");
+}

@@ -250,6 +250,24 @@ def z4_gauge_wave(n, amp: float = 0.01, t: float = 0.0):
     return U, dx
 
 
+def z4_perturbed(n, seed: int = 0, amp: float = 0.05):
+    """Minkowski plus smooth periodic perturbations of every field: each field
+    gets amp * sum of three Fourier modes with seeded integer wave vectors in
+    {1,2}^3 and seeded phases.  Exercises every term of the right-hand side
+    (non-zero shift, curvature, Theta, Z).  Returns (U, dx)."""
+    nx, ny, nz = n
+    dx = (1.0 / nx, 1.0 / ny, 1.0 / nz)
+    Z, Y, X = coords(n, dx)
+    U = z4_minkowski(n)
+    r = uniform(seed, Z4_NF * 3 * 4, offset=30000).reshape(Z4_NF, 3, 4)
+    for f in range(Z4_NF):
+        for m in range(3):
+            kx, ky, kz = (1 + int(2 * r[f, m, q]) for q in range(3))
+            ph = 2.0 * math.pi * (kx * X + ky * Y + kz * Z + r[f, m, 3])
+            U[f] += amp / 3.0 * np.sin(ph)
+    return U, dx
+
+
 # ------------------------------------------------------------------- batches
 def amr_patch_table(npatch: int = 512, seed: int = 0, lo: int = 16, hi: int = 64):
     """Seeded patch descriptors for the batched AMR step: sizes (nx, ny, nz)

@@ -1,0 +1,142 @@
+"""Device buffers of one ghosted patch and its RK stepping through the C ABI.
+
+PyTorch only allocates the device arrays and supplies the stream; every
+stage runs in libsf.so.  Buffer roles (all with the layout of include/sf.h):
+  A  the state U^n (updated in place by the last stage)
+  B, C  stage scratch
+  D  RK4 accumulator
+  E  Kahan compensation (FP32_BULK only)
+RK4:    stage 0: A -> B, 1: B -> C, 2: C -> B, 3: B -> A.
+SSP-RK3: stage 0: A -> B, 1: B -> C, 2: C -> A.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import capi
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class PatchState:
+    def __init__(self, system: int, n, dx, dt: float, precision: int = capi.SF_FP64,
+                 prm: capi.sf_params | None = None, ghost: int = 3, device="cuda"):
+        self.system = system
+        self.n = tuple(int(v) for v in n)
+        self.dx = tuple(float(v) for v in dx)
+        self.dt = float(dt)
+        self.precision = precision
+        self.prm = prm if prm is not None else capi.params(
+            rk=capi.SF_SSPRK3 if system == capi.SF_MHD else capi.SF_RK4)
+        self.g = ghost
+        self.nf = capi.sf_nfields(system)
+        self.dtype = torch.float64 if precision == capi.SF_FP64 else torch.float32
+        nx, ny, nz = self.n
+        g = ghost
+        self.shape = (self.nf, nz + 2 * g, ny + 2 * g, nx + 2 * g)
+        kw = dict(dtype=self.dtype, device=device)
+        self.A = torch.zeros(self.shape, **kw)
+        self.B = torch.zeros(self.shape, **kw)
+        self.C = torch.zeros(self.shape, **kw)
+        self.D = torch.zeros(self.shape, **kw) if self.prm.rk == capi.SF_RK4 else None
+        self.E = (torch.zeros(self.shape, **kw)
+                  if precision == capi.SF_FP32_BULK and self.prm.rk == capi.SF_RK4 else None)
+
+    # ------------------------------------------------------------------ ABI
+    def patch(self, u_stage, u_n, u_next) -> capi.sf_patch:
+        p = capi.sf_patch()
+        p.n[:] = self.n
+        p.ghost = self.g
+        p.dx[:] = self.dx
+        p.dt = self.dt
+        p.system = self.system
+        p.precision = self.precision
+        p.sy = p.sz = p.sf = 0
+        p.u_stage = u_stage.data_ptr()
+        p.u_n = u_n.data_ptr()
+        p.acc = self.D.data_ptr() if self.D is not None else None
+        p.u_next = u_next.data_ptr()
+        p.kahan = self.E.data_ptr() if self.E is not None else None
+        return p
+
+    def roles(self, stage: int):
+        if self.prm.rk == capi.SF_RK4:
+            return [(self.A, self.B), (self.B, self.C), (self.C, self.B), (self.B, self.A)][stage]
+        return [(self.A, self.B), (self.B, self.C), (self.C, self.A)][stage]
+
+    def stage_patch(self, stage: int) -> capi.sf_patch:
+        us, nx = self.roles(stage)
+        return self.patch(us, self.A, nx)
+
+    @property
+    def nstages(self) -> int:
+        return 4 if self.prm.rk == capi.SF_RK4 else 3
+
+    # ------------------------------------------------------------------ data
+    def upload(self, interior, stream=None) -> None:
+        """Set U^n from an interior array (nf, nz, ny, nx) and fill periodic ghosts."""
+        g = self.g
+        t = torch.as_tensor(np.ascontiguousarray(interior) if isinstance(interior, np.ndarray)
+                            else interior)
+        self.A[:, g:self.shape[1] - g, g:self.shape[2] - g, g:self.shape[3] - g].copy_(
+            t.to(self.dtype))
+        if self.E is not None:
+            self.E.zero_()
+        self.fill_ghosts(self.A, stream)
+
+    def fill_ghosts(self, array: torch.Tensor, stream=None) -> None:
+        capi.sf_fill_ghosts_periodic(self.patch(array, array, array), array.data_ptr(), self.nf,
+                                     _stream_handle(stream))
+
+    def interior(self, array: torch.Tensor | None = None) -> torch.Tensor:
+        a = self.A if array is None else array
+        g = self.g
+        return a[:, g:self.shape[1] - g, g:self.shape[2] - g, g:self.shape[3] - g]
+
+    # ------------------------------------------------------------------ stepping
+    def stage(self, s: int, stream=None) -> torch.Tensor:
+        """Run RK stage s; returns the array holding its output."""
+        capi.sf_substep(self.prm, self.stage_patch(s), s, _stream_handle(stream))
+        return self.roles(s)[1]
+
+    def step(self, nsteps: int = 1, stream=None) -> None:
+        h = _stream_handle(stream)
+        for _ in range(nsteps):
+            for s in range(self.nstages):
+                capi.sf_substep(self.prm, self.stage_patch(s), s, h)
+
+    def adjoint_step(self, nsteps: int = 1, stream=None) -> None:
+        """RK4 steps of the transposed wave operator on A (adjoint fields)."""
+        h = _stream_handle(stream)
+        for _ in range(nsteps):
+            for s in range(4):
+                capi.sf_adjoint_substep(self.prm, self.stage_patch(s), s, h)
+
+    def rhs(self, array: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """(L + Q_d)(array) on the interior, shape (nf, nz, ny, nx)."""
+        a = self.A if array is None else array
+        nx, ny, nz = self.n
+        out = torch.empty((self.nf, nz, ny, nx), dtype=self.dtype, device=a.device)
+        capi.sf_rhs(self.prm, self.patch(a, a, self.B), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def diagnostics(self, array: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        a = self.A if array is None else array
+        out = torch.empty(5, dtype=torch.float64, device=a.device)
+        capi.sf_diagnostics(self.prm, self.patch(a, a, self.B), a.data_ptr(), out.data_ptr(),
+                            _stream_handle(stream))
+        return out
+
+    def mhd_max_rate(self, array: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        a = self.A if array is None else array
+        out = torch.empty(1, dtype=torch.float64, device=a.device)
+        capi.sf_mhd_max_rate(self.prm, self.patch(a, a, self.B), a.data_ptr(), out.data_ptr(),
+                             _stream_handle(stream))
+        return out

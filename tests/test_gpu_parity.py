@@ -1,0 +1,252 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerance (FP64): max over fields of ||gpu - oracle||_inf / max(||oracle||_inf, floor)
+<= 1e-12 per substep, the bound stated for this path.  Summation order differs
+between the two (the kernels fuse and reorder sums), so bit equality is not
+expected except where the result is exactly zero.  FP32-bulk results are
+checked against the same oracle with per-field bounds derived from float
+rounding (stated at each test).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1806_04182_gb300 import build, capi, inputs
+from paper_1806_04182_gb300.state import PatchState
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    build.build()
+    return capi.lib()
+
+
+def rel_err(got, want, floor=1e-300):
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    errs = []
+    for f in range(want.shape[0]):
+        scale = max(np.abs(want[f]).max(), floor)
+        errs.append(np.abs(got[f] - want[f]).max() / scale)
+    return np.array(errs)
+
+
+def oracle_params(prm: capi.sf_params):
+    return oracle.params(sigma=prm.sigma_ko, gamma_eos=prm.gamma_eos, weno_eps=prm.weno_eps,
+                         weno_q=prm.weno_q, kappa_z=prm.kappa_z, kappa_c=prm.kappa_c, eta=prm.eta,
+                         g_shift=prm.g_shift, weno_variant=prm.weno_variant, slicing=prm.slicing,
+                         shift_frozen=prm.shift_frozen)
+
+
+def run_stages(system, U0, dx, dt, prm, precision=capi.SF_FP64):
+    """GPU stage outputs (interior, numpy float64) of one full step."""
+    n = (U0.shape[3], U0.shape[2], U0.shape[1])
+    st = PatchState(system, n, dx, dt, precision=precision, prm=prm)
+    st.upload(U0)
+    outs = []
+    for s in range(st.nstages):
+        arr = st.stage(s)
+        outs.append(st.interior(arr).double().cpu().numpy().copy())
+    torch.cuda.synchronize()
+    return outs
+
+
+def oracle_stages(system, U0, dx, dt, prm):
+    G = oracle.ghosted(U0.copy())
+    if prm.rk == capi.SF_RK4:
+        return list(oracle.rk4_step(system, G, dx, dt, oracle_params(prm), stages=True))
+    return list(oracle.ssprk3_step(system, G, dx, dt, oracle_params(prm), stages=True))
+
+
+# ------------------------------------------------------------------ wave
+@pytest.mark.parametrize("n", [(37, 13, 11), (5, 6, 4), (64, 9, 3)])
+def test_wave_fp64_stages(n):
+    U0, dx = inputs.wave_plane(n, seed=2)
+    U0 = U0 + inputs.wave_noise(n, seed=3, amp=0.3)
+    prm = capi.params()
+    dt = 0.25 * min(dx)
+    got = run_stages(capi.SF_WAVE, U0, dx, dt, prm)
+    want = oracle_stages(oracle.WAVE, U0, dx, dt, prm)
+    for s in range(4):
+        assert rel_err(got[s], want[s]).max() < TOL64, s
+
+
+def test_wave_rhs_and_ghost_fill():
+    n = (21, 10, 7)
+    U0, dx = inputs.wave_plane(n, seed=4)
+    U0 = U0 + inputs.wave_noise(n, seed=5, amp=0.5)
+    st = PatchState(capi.SF_WAVE, n, dx, 0.01)
+    st.upload(U0)
+    G = oracle.ghosted(U0)
+    # periodic ghost fill is a copy: bit-exact
+    np.testing.assert_array_equal(st.A.cpu().numpy(), G)
+    r = st.rhs().cpu().numpy()
+    want = oracle.rhs(oracle.WAVE, G, dx)
+    assert rel_err(r, want).max() < TOL64
+
+
+def test_wave_adjoint_step():
+    n = (19, 11, 9)
+    dx = (1 / 19, 1 / 11, 1 / 9)
+    L0 = inputs.wave_noise(n, seed=8)
+    dt = 0.2 * min(dx)
+    prm = capi.params()
+    st = PatchState(capi.SF_WAVE, n, dx, dt, prm=prm)
+    st.upload(L0)
+    st.adjoint_step(1)
+    got = st.interior().cpu().numpy()
+    G = oracle.ghosted(L0.copy())
+    oracle.rk4_step(oracle.WAVE_ADJ, G, dx, dt, oracle_params(prm))
+    assert rel_err(got, oracle.interior(G)).max() < TOL64
+
+
+def test_wave_fp32_bulk_step():
+    # float storage: relative error ~ a few ulp of float per stage
+    n = (33, 10, 9)
+    U0, dx = inputs.wave_plane(n, seed=6)
+    prm = capi.params()
+    dt = 0.25 * min(dx)
+    got = run_stages(capi.SF_WAVE, U0, dx, dt, prm, precision=capi.SF_FP32_BULK)
+    want = oracle_stages(oracle.WAVE, U0, dx, dt, prm)
+    assert rel_err(got[3], want[3]).max() < 2e-6
+
+
+# ------------------------------------------------------------------ Z4
+@pytest.mark.parametrize("slicing,frozen", [(0, 0), (1, 1)])
+def test_z4_fp64_stages(slicing, frozen):
+    n = (35, 9, 6)
+    U0, dx = inputs.z4_perturbed(n, seed=1, amp=0.05)
+    prm = capi.params(slicing=slicing, shift_frozen=frozen)
+    dt = 0.25 * min(dx)
+    got = run_stages(capi.SF_Z4, U0, dx, dt, prm)
+    want = oracle_stages(oracle.Z4, U0, dx, dt, prm)
+    for s in range(4):
+        e = rel_err(got[s], want[s], floor=1e-3)
+        assert e.max() < TOL64, (s, e)
+
+
+def test_z4_rhs_matches_oracle():
+    n = (17, 12, 8)
+    U0, dx = inputs.z4_perturbed(n, seed=3, amp=0.08)
+    prm = capi.params()
+    st = PatchState(capi.SF_Z4, n, dx, 0.01, prm=prm)
+    st.upload(U0)
+    r = st.rhs().cpu().numpy()
+    want = oracle.rhs(oracle.Z4, oracle.ghosted(U0), dx, oracle_params(prm))
+    e = rel_err(r, want, floor=1e-3)
+    assert e.max() < TOL64, e
+
+
+def test_z4_minkowski_rhs_is_exactly_zero():
+    n = (12, 8, 8)
+    U0 = inputs.z4_minkowski(n)
+    for prec in (capi.SF_FP64, capi.SF_FP32_BULK):
+        st = PatchState(capi.SF_Z4, n, (0.1, 0.1, 0.1), 0.01, precision=prec)
+        st.upload(U0)
+        assert torch.count_nonzero(st.rhs()).item() == 0
+
+
+def test_z4_fp32_bulk_step():
+    # float storage and stencils: per-field error relative to the field's own
+    # scale (floor 1e-2) stays within ~1e-5 for one step on smooth data
+    n = (33, 8, 8)
+    U0, dx = inputs.z4_perturbed(n, seed=2, amp=0.05)
+    prm = capi.params()
+    dt = 0.25 * min(dx)
+    got = run_stages(capi.SF_Z4, U0, dx, dt, prm, precision=capi.SF_FP32_BULK)
+    want = oracle_stages(oracle.Z4, U0, dx, dt, prm)
+    e = rel_err(got[3], want[3], floor=1e-2)
+    assert e.max() < 1e-5, e
+
+
+# ------------------------------------------------------------------ MHD
+@pytest.mark.parametrize("variant", [0, 1])
+def test_mhd_fp64_stages(variant):
+    n = (35, 10, 7)
+    U0, dx = inputs.mhd_blast(n, seed=4, radius=0.3)
+    prm = capi.params(rk=capi.SF_SSPRK3, weno_variant=variant)
+    rate = oracle.mhd_max_rate(oracle.ghosted(U0), dx)
+    dt = 0.3 / rate
+    got = run_stages(capi.SF_MHD, U0, dx, dt, prm)
+    want = oracle_stages(oracle.MHD, U0, dx, dt, prm)
+    for s in range(3):
+        e = rel_err(got[s], want[s], floor=1e-3)
+        assert e.max() < TOL64, (s, e)
+
+
+def test_mhd_max_rate_and_rhs():
+    n = (20, 9, 8)
+    U0, dx = inputs.mhd_blast(n, seed=5, radius=0.3)
+    prm = capi.params(rk=capi.SF_SSPRK3)
+    st = PatchState(capi.SF_MHD, n, dx, 0.001, prm=prm)
+    st.upload(U0)
+    G = oracle.ghosted(U0)
+    assert st.mhd_max_rate().item() == pytest.approx(oracle.mhd_max_rate(G, dx), rel=1e-13)
+    e = rel_err(st.rhs().cpu().numpy(), oracle.rhs(oracle.MHD, G, dx), floor=1e-3)
+    assert e.max() < TOL64, e
+
+
+def test_mhd_uniform_rhs_exactly_zero():
+    n = (9, 8, 7)
+    st = PatchState(capi.SF_MHD, n, (0.1, 0.1, 0.1), 0.01, prm=capi.params(rk=capi.SF_SSPRK3))
+    st.upload(inputs.mhd_uniform(n))
+    assert torch.count_nonzero(st.rhs()).item() == 0
+
+
+# ------------------------------------------------------------------ diagnostics, status
+def test_diagnostics_match_oracle():
+    n = (16, 12, 10)
+    U0, dx = inputs.wave_plane(n, seed=1)
+    st = PatchState(capi.SF_WAVE, n, dx, 0.01)
+    st.upload(U0)
+    d = st.diagnostics().cpu().numpy()
+    assert d[0] == pytest.approx(oracle.wave_energy(oracle.ghosted(U0), dx), rel=1e-12)
+    assert d[4] == 0
+    U0, dx = inputs.z4_perturbed(n, seed=2, amp=0.03)
+    st = PatchState(capi.SF_Z4, n, dx, 0.01)
+    st.upload(U0)
+    d = st.diagnostics().cpu().numpy()
+    m = oracle.z4_monitors(oracle.ghosted(U0), dx)
+    N = np.prod(n)
+    np.testing.assert_allclose(np.sqrt(d[:4] / N), m, rtol=1e-10)
+
+
+def test_nonfinite_output_is_flagged():
+    n = (8, 8, 8)
+    U0, dx = inputs.wave_plane(n, seed=1)
+    U0[1, 3, 4, 5] = np.nan
+    prm = capi.params(check_finite=1)
+    st = PatchState(capi.SF_WAVE, n, dx, 0.01, prm=prm)
+    st.upload(U0)
+    capi.sf_get_device_status()  # clear
+    st.step(1)
+    assert capi.sf_get_device_status() == capi.SF_ENONFINITE
+    assert capi.sf_get_device_status() == capi.SF_OK  # cleared by the read
+
+
+# ------------------------------------------------------------------ full size, sampled
+def test_z4_full_size_sampled_parity():
+    # the benchmark's 96^3 Z4 workload in its launch configuration: sampled
+    # points of the RHS and of the first stage output against the oracle
+    n = (96, 96, 96)
+    U0, dx = inputs.z4_minkowski_noise(n, seed=0, amp=1e-10)
+    pert, _ = inputs.z4_perturbed(n, seed=7, amp=0.02)
+    U0 = U0 + (pert - inputs.z4_minkowski(n))
+    prm = capi.params()
+    dt = 0.25 * dx[0]
+    st = PatchState(capi.SF_Z4, n, dx, dt, prm=prm)
+    st.upload(U0)
+    r = st.rhs().cpu().numpy().reshape(25, -1)
+    out = st.interior(st.stage(0)).cpu().numpy().reshape(25, -1)
+    pts = inputs.observers(n, 2000, seed=11)
+    want = oracle.rhs_points(oracle.Z4, oracle.ghosted(U0), dx, pts, oracle_params(prm))
+    assert rel_err(r[:, pts], want, floor=1e-3).max() < TOL64
+    want_out = U0.reshape(25, -1)[:, pts] + 0.5 * dt * want
+    assert rel_err(out[:, pts], want_out, floor=1e-3).max() < TOL64
