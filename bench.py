@@ -50,7 +50,7 @@ def bytes_per_cell_update(precision: str) -> float:
     return 19 / 4 * NF * 4
 
 
-STAGE_PASSES = {"fp64": [3, 5, 5, 3], "fp32": [3, 5, 5, 6]}
+STAGE_PASSES = {"fp64": [3, 5, 5, 3], "fp32": [3, 5, 5, 6], "fp32dw": [3, 5, 5, 6]}
 
 
 # ---------------------------------------------------------------- clocks
@@ -112,13 +112,31 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- ranks
+def max_over_ranks(v: float, device=None) -> float:
+    """Max of v over the ranks of the default process group (v itself if none)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, cells: int, substeps: int, max_ms: float) -> float:
+    """Cell-updates/s of the whole job: every rank advances its own patch."""
+    return world * cells * substeps / (max_ms * 1e-3)
+
+
 # ---------------------------------------------------------------- GPU arm
 def make_state(precision: str, seed: int, device):
     import torch
     from paper_1806_04182_gb300 import capi, inputs
     from paper_1806_04182_gb300.state import PatchState
     U0, dx = inputs.z4_minkowski_noise((N, N, N), seed=seed, amp=1e-10)
-    prec = capi.SF_FP64 if precision == "fp64" else capi.SF_FP32_BULK
+    prec = {"fp64": capi.SF_FP64, "fp32": capi.SF_FP32_BULK,
+            "fp32dw": capi.SF_FP32_BULK_DW}[precision]
     st = PatchState(capi.SF_Z4, (N, N, N), dx, 0.25 * dx[0], precision=prec,
                     prm=capi.params(), device=device)
     st.upload(U0)
@@ -208,30 +226,23 @@ def gpu_arm(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     cells = N ** 3
     res = {}
     clocks = None
-    precisions = ("fp32", "fp64") if args.only is None else (args.only,)
+    precisions = ("fp32dw", "fp32", "fp64") if args.only is None else (args.only,)
     for precision in precisions:
         st = make_state(precision, seed=rank, device=device)
         barrier()
-        sampler = ClockSampler(local) if precision == "fp32" else None
+        sampler = ClockSampler(local) if precision == "fp32dw" else None
         if sampler:
             sampler.start()
         total_ms, per, launches = time_device(st, args.steps, args.warmup)
         if sampler:
             clocks = sampler.stop()
         barrier()
-        total_ms = max_over_ranks(total_ms)
+        total_ms = max_over_ranks(total_ms, device)
         substeps = 4 * args.steps
-        value = world * cells * substeps / (total_ms * 1e-3)
+        value = whole_job_rate(world, cells, substeps, total_ms)
         # dominant kernel: the stage kernel; average launch duration
         avg_launch_ms = float(per.mean())
         bpc = bytes_per_cell_update(precision)
@@ -249,18 +260,18 @@ def gpu_arm(args):
         r = res[args.only]
         return None if rank else {"profiling_run": args.only, "value": r["value"],
                                   "ms_per_step": r["ms_per_step"], "achieved_gbs": r["achieved_gbs"]}
-    # end to end through host buffers (FP32-bulk)
-    st = res["fp32"]["state"]
+    # end to end through host buffers (FP32-bulk, double-word islands)
+    st = res["fp32dw"]["state"]
     barrier()
     e2e_ms, bi, bo = time_e2e(st, args.steps, args.warmup)
     barrier()
-    e2e_ms = max_over_ranks(e2e_ms)
-    e2e_value = world * cells * 4 * args.steps / (e2e_ms * 1e-3)
+    e2e_ms = max_over_ranks(e2e_ms, device)
+    e2e_value = whole_job_rate(world, cells, 4 * args.steps, e2e_ms)
     if world > 1:
         dist.destroy_process_group()
     if rank != 0:
         return None
-    r32, r64 = res["fp32"], res["fp64"]
+    r32, r32n, r64 = res["fp32dw"], res["fp32"], res["fp64"]
     line = {
         "metric": METRIC,
         "value": r32["value"],
@@ -275,17 +286,23 @@ def gpu_arm(args):
         "dtype": "f32",
         "data": "synthetic: Minkowski + seeded uniform noise 1e-10 on all 25 fields",
         "config": {"workload": WORKLOAD, "n": N, "ghost": GHOST, "fields": NF, "rk": "RK4",
-                   "substeps_per_step": 4, "precision": "fp32_bulk (fp64 det/inverse/ln det/"
-                   "trace removals, Kahan RK accumulation)", "slicing": "1+log",
-                   "shift": "Gamma-driver", "sigma_ko": 0.1, "dt_over_dx": 0.25,
-                   "l2": "inputs larger than L2 (5 arrays x 106 MB fp32)",
+                   "substeps_per_step": 4,
+                   "precision": "fp32_bulk: float storage and stencils, Kahan RK accumulation, "
+                                "det/inverse/ln det/trace removals in double-word (FP64-class) "
+                                "arithmetic on the FP32 pipe",
+                   "slicing": "1+log", "shift": "Gamma-driver", "sigma_ko": 0.1,
+                   "dt_over_dx": 0.25, "l2": "inputs larger than L2 (5 arrays x 106 MB fp32)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": r32["achieved_gbs"], "peak": hbm_peak,
                      "unit": "GB/s", "frac": r32["achieved_gbs"] / hbm_peak, "traffic": None,
                      "peak_source": peak_src,
-                     "kernel": "z4_stage_kernel<float,double>",
+                     "kernel": "z4_stage_kernel<float,dw,102,10404>",
                      "bytes_per_cell_update": r32["bytes_per_cell_update"],
                      "per_stage_ms": r32["per_stage_ms"], "per_stage_gbs": r32["per_stage_gbs"]},
+        "fp32_bulk_fp64_islands": {
+            "value": r32n["value"], "ms_per_step": r32n["ms_per_step"],
+            "achieved_gbs": r32n["achieved_gbs"], "hbm_frac": r32n["achieved_gbs"] / hbm_peak,
+            "per_stage_ms": r32n["per_stage_ms"]},
         "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"],
                  "achieved_gbs": r64["achieved_gbs"], "hbm_frac": r64["achieved_gbs"] / hbm_peak,
                  "bytes_per_cell_update": r64["bytes_per_cell_update"],
@@ -370,7 +387,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["fp32", "fp64"], default=None,
+    ap.add_argument("--only", choices=["fp32dw", "fp32", "fp64"], default=None,
                     help="time one precision only (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -53,8 +53,14 @@ typedef enum { SF_WAVE = 0, SF_MHD = 1, SF_Z4 = 2 } sf_system;
  * SF_FP32_BULK: storage and stencil arithmetic in float; the Z4 conformal
  * metric determinant, inverse, ln det and the trace removals are evaluated
  * in double; the last RK4 stage adds the step increment to U^n with a
- * compensated (Kahan) sum carried across steps in the `kahan` array. */
-typedef enum { SF_FP64 = 0, SF_FP32_BULK = 1 } sf_precision;
+ * compensated (Kahan) sum carried across steps in the `kahan` array.
+ * SF_FP32_BULK_DW: as SF_FP32_BULK, but the island quantities are evaluated
+ * in double-word arithmetic (a float pair hi + lo built from error-free
+ * transformations, relative error a few 2^-48) on the FP32 pipe instead of
+ * the FP64 pipe, which on GB300 runs at ~1/58 of the FP32 rate.  The paper
+ * has no counterpart; it is this library's way to keep FP64-class islands
+ * cheap on this GPU. */
+typedef enum { SF_FP64 = 0, SF_FP32_BULK = 1, SF_FP32_BULK_DW = 2 } sf_precision;
 
 typedef enum { SF_RK4 = 0, SF_SSPRK3 = 1 } sf_rk;
 
@@ -70,7 +76,7 @@ typedef enum {
  * Every array of a patch has the same layout: nf fields, field f, interior
  * point (i,j,k) (0 <= i < n[0], ...) at element
  *     f*sf + (k+ghost)*sz + (j+ghost)*sy + (i+ghost)
- * with x fastest.  Elements are double (SF_FP64) or float (SF_FP32_BULK).
+ * with x fastest.  Elements are double (SF_FP64) or float (both FP32 modes).
  * Strides may be 0, meaning contiguous: sy = n[0]+2g, sz = sy*(n[1]+2g),
  * sf = sz*(n[2]+2g).
  *

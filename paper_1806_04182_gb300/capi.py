@@ -16,7 +16,7 @@ from . import build as _build
 
 SF_OK, SF_EINVAL, SF_ENOTSUP, SF_ECUDA, SF_ENONFINITE, SF_ETIMEOUT = range(6)
 SF_WAVE, SF_MHD, SF_Z4 = 0, 1, 2
-SF_FP64, SF_FP32_BULK = 0, 1
+SF_FP64, SF_FP32_BULK, SF_FP32_BULK_DW = 0, 1, 2
 SF_RK4, SF_SSPRK3 = 0, 1
 SF_GHOSTS_NONE, SF_GHOSTS_PERIODIC = 0, 1
 STATUS_NAMES = {0: "SF_OK", 1: "SF_EINVAL", 2: "SF_ENOTSUP", 3: "SF_ECUDA", 4: "SF_ENONFINITE",

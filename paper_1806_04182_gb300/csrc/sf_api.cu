@@ -56,7 +56,7 @@ static bool aligned(const void* ptr, size_t a) { return (reinterpret_cast<uintpt
 sf_status check_patch(const sf_params* prm, const sf_patch& p, int need_stage_arrays, int stage) {
   if (!prm) return set_error(SF_EINVAL, "params is NULL");
   if (p.system < 0 || p.system > 2) return set_error(SF_EINVAL, "unknown system %d", p.system);
-  if (p.precision != SF_FP64 && p.precision != SF_FP32_BULK)
+  if (p.precision != SF_FP64 && p.precision != SF_FP32_BULK && p.precision != SF_FP32_BULK_DW)
     return set_error(SF_EINVAL, "unknown precision %d", p.precision);
   for (int d = 0; d < 3; ++d) {
     if (p.n[d] < 1) return set_error(SF_EINVAL, "n[%d] = %d < 1", d, p.n[d]);
@@ -82,7 +82,7 @@ sf_status check_patch(const sf_params* prm, const sf_patch& p, int need_stage_ar
                        "u_next must not alias u_stage or acc, nor u_n before the last stage");
     if (prm->rk == SF_RK4 && (!p.acc || !aligned(p.acc, es)))
       return set_error(SF_EINVAL, "RK4 needs an acc array");
-    if (prm->rk == SF_RK4 && p.precision == SF_FP32_BULK && (!p.kahan || !aligned(p.kahan, es)))
+    if (prm->rk == SF_RK4 && p.precision != SF_FP64 && (!p.kahan || !aligned(p.kahan, es)))
       return set_error(SF_EINVAL, "FP32_BULK RK4 needs a kahan array");
     if (!(p.dt == p.dt) || p.dt < 0) return set_error(SF_EINVAL, "dt must be >= 0");
     if (prm->ghosts == SF_GHOSTS_PERIODIC)
@@ -148,7 +148,7 @@ static StageArgs stage_args(const sf_params& prm, const sf_patch& p, int stage, 
   s.mode = mode;
   s.rk = prm.rk;
   s.stage = stage;
-  s.kahan = (p.precision == SF_FP32_BULK && prm.rk == SF_RK4) ? 1 : 0;
+  s.kahan = (p.precision != SF_FP64 && prm.rk == SF_RK4) ? 1 : 0;
   s.un_alias = p.u_n == p.u_stage ? 1 : 0;
   s.ghosts = prm.ghosts == SF_GHOSTS_PERIODIC ? 1 : 0;
   s.check_finite = prm.check_finite;

@@ -60,10 +60,10 @@ __global__ void __launch_bounds__(128) batch_stage_kernel(const PatchArgs<T>* __
     for (int k = w.z0; k < zend; ++k) {
       const long long c = (long long)(k + g) * a.sz + (long long)(j + g) * a.sy + (i + g);
       if (system == SF_Z4) {
-        T v[25], r[25];
-        z4_point<T, H>(a, zc, a.us + c, v, r);
-#pragma unroll
-        for (int f = 0; f < 25; ++f) stage_write(a, s, f, c, i, j, k, v[f], r[f]);
+        const T* __restrict__ u = a.us + c;
+        z4_cell<T, H, 0, 0>(a, zc, u, [&](int f, T r) {
+          stage_write(a, s, f, c, i, j, k, __ldg(u + f * a.sf), r);
+        });
       } else {
         T v[5], r[5];
         wave_point<T, false>(a, a.us + c, v, r);
@@ -85,7 +85,7 @@ struct sf_batch {
   std::vector<sf_patch> patches;
   int shape_of_class[kClasses];
   int device;
-  int grid[2];            // persistent grid size (FP64, FP32 kernels)
+  int grid[3];            // persistent grid size per precision
   void* d_args = nullptr; // PatchArgs<T>[4][npatch]
   int* d_sys = nullptr;
   int2* d_shape = nullptr;
@@ -167,7 +167,7 @@ StageArgs batch_stage_args(const sf_batch* b, int stage, unsigned int* status) {
   s.mode = 0;
   s.rk = SF_RK4;
   s.stage = stage;
-  s.kahan = b->precision == SF_FP32_BULK ? 1 : 0;
+  s.kahan = b->precision != SF_FP64 ? 1 : 0;
   s.un_alias = stage == 0 ? 1 : 0;
   s.ghosts = 1;
   s.check_finite = b->prm.check_finite;
@@ -175,7 +175,7 @@ StageArgs batch_stage_args(const sf_batch* b, int stage, unsigned int* status) {
   return s;
 }
 
-template <typename T>
+template <typename T, typename H>
 sf_status launch_stage(sf_batch* b, int stage, cudaStream_t st, unsigned int* status) {
   if (cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), st) != cudaSuccess)
     return set_error(SF_ECUDA, "batch: counter reset failed");
@@ -187,8 +187,8 @@ sf_status launch_stage(sf_batch* b, int stage, cudaStream_t st, unsigned int* st
   zc.slicing = b->prm.slicing;
   zc.shift_frozen = b->prm.shift_frozen;
   const PatchArgs<T>* args = static_cast<const PatchArgs<T>*>(b->d_args) + (size_t)stage * b->npatch;
-  const int grid = b->grid[b->precision == SF_FP64 ? 0 : 1];
-  batch_stage_kernel<T, double><<<grid, 128, 0, st>>>(args, b->d_sys, b->d_shape, b->d_items,
+  const int grid = b->grid[b->precision];
+  batch_stage_kernel<T, H><<<grid, 128, 0, st>>>(args, b->d_sys, b->d_shape, b->d_items,
                                                       b->nitems, b->d_counter,
                                                       batch_stage_args(b, stage, status), zc);
   return after_launch("batch_stage_kernel");
@@ -242,11 +242,11 @@ sf_status sf_batch_create(const sf_params* prm, const sf_patch* patches, int32_t
   cudaGetDevice(&b->device);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  int occ64 = 0, occ32 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, batch_stage_kernel<double, double>, 128, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, batch_stage_kernel<float, double>, 128, 0);
-  b->grid[0] = std::max(1, sms * std::max(1, occ64));
-  b->grid[1] = std::max(1, sms * std::max(1, occ32));
+  int occ[3] = {0, 0, 0};
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], batch_stage_kernel<double, double>, 128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], batch_stage_kernel<float, double>, 128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], batch_stage_kernel<float, dw>, 128, 0);
+  for (int q = 0; q < 3; ++q) b->grid[q] = std::max(1, sms * std::max(1, occ[q]));
   std::vector<int> sys(npatch);
   for (int q = 0; q < npatch; ++q) sys[q] = b->patches[q].system;
   if (cudaMalloc(&b->d_sys, npatch * sizeof(int)) != cudaSuccess ||
@@ -257,6 +257,7 @@ sf_status sf_batch_create(const sf_params* prm, const sf_patch* patches, int32_t
   }
   cudaMemcpy(b->d_sys, sys.data(), npatch * sizeof(int), cudaMemcpyHostToDevice);
   sf_status e = b->precision == SF_FP64 ? upload_args<double>(b) : upload_args<float>(b);
+  (void)0;
   if (!e) e = build_items(b, -1);
   if (e) {
     sf_batch_destroy(b);
@@ -271,8 +272,11 @@ sf_status sf_batch_substep(sf_batch* b, int32_t stage, void* stream) {
   if (stage < 0 || stage > 3) return set_error(SF_EINVAL, "stage %d out of range [0,4)", stage);
   unsigned int* status = status_ptr();
   if (!status) return set_error(SF_ECUDA, "no status word");
-  if (b->precision == SF_FP64) return launch_stage<double>(b, stage, (cudaStream_t)stream, status);
-  return launch_stage<float>(b, stage, (cudaStream_t)stream, status);
+  if (b->precision == SF_FP64)
+    return launch_stage<double, double>(b, stage, (cudaStream_t)stream, status);
+  if (b->precision == SF_FP32_BULK_DW)
+    return launch_stage<float, dw>(b, stage, (cudaStream_t)stream, status);
+  return launch_stage<float, double>(b, stage, (cudaStream_t)stream, status);
 }
 
 sf_status sf_batch_tune(sf_batch* b, void* stream) {

@@ -1,0 +1,120 @@
+// Arithmetic of the "island" quantities of the FP32-bulk CCZ4 path (conformal
+// metric determinant, inverse, ln det and the trace removals), in one of two
+// types:
+//   double - native FP64;
+//   dw     - an unevaluated sum hi + lo of two floats ("double-word"), built
+//            from error-free transformations: TwoSum (Knuth, TAOCP vol. 2),
+//            FastTwoSum (Dekker 1971), TwoProd via FMA, and the double-word
+//            sum/product algorithms of Joldes, Muller & Popescu, "Tight and
+//            rigorous error bounds for basic building blocks of double-word
+//            arithmetic", ACM TOMS 44 (2017) (AccurateDWPlusDW, DWTimesFP3,
+//            DWTimesDW3).  Relative error of each operation is a few 2^-48,
+//            i.e. within a small factor of FP64, while every instruction runs
+//            on the FP32 pipe (GB300's FP64 pipe is ~1/58 of its FP32 rate).
+// The explicit __fadd_rn/__fmul_rn intrinsics keep the compiler from fusing
+// the error-free transformations into FMAs.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace sf {
+
+struct dw {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dw dw_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fadd_rn(s, -a);
+  const float e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
+  return {s, e};
+}
+
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ dw dw_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float z = __fadd_rn(s, -a);
+  return {s, __fadd_rn(b, -z)};
+}
+
+__device__ __forceinline__ dw dw_two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ dw dw_add(dw x, dw y) {  // AccurateDWPlusDW
+  const dw s = dw_two_sum(x.hi, y.hi);
+  const dw t = dw_two_sum(x.lo, y.lo);
+  const float c = __fadd_rn(s.lo, t.hi);
+  const dw v = dw_fast_two_sum(s.hi, c);
+  const float w = __fadd_rn(t.lo, v.lo);
+  return dw_fast_two_sum(v.hi, w);
+}
+
+__device__ __forceinline__ dw dw_neg(dw x) { return {-x.hi, -x.lo}; }
+
+__device__ __forceinline__ dw dw_mulf(dw x, float y) {  // DWTimesFP3
+  const dw c = dw_two_prod(x.hi, y);
+  const float cl3 = __fmaf_rn(x.lo, y, c.lo);
+  return dw_fast_two_sum(c.hi, cl3);
+}
+
+__device__ __forceinline__ dw dw_mul(dw x, dw y) {  // DWTimesDW3
+  const dw c = dw_two_prod(x.hi, y.hi);
+  const float tl0 = __fmul_rn(x.lo, y.lo);
+  const float tl1 = __fmaf_rn(x.hi, y.lo, tl0);
+  const float cl2 = __fmaf_rn(x.lo, y.hi, tl1);
+  const float cl3 = __fadd_rn(c.lo, cl2);
+  return dw_fast_two_sum(c.hi, cl3);
+}
+
+// 1/x by one Newton step from the float reciprocal: r = r0 + r0 (1 - x r0)
+__device__ __forceinline__ dw dw_recip(dw x) {
+  const float r0 = __frcp_rn(x.hi);
+  const dw e = dw_add(dw{1.0f, 0.0f}, dw_neg(dw_mulf(x, r0)));
+  return dw_add(dw{r0, 0.0f}, dw_mulf(e, r0));
+}
+
+// ------------------------------------------------------------ island ops
+// Uniform interface over H = double and H = dw.
+template <typename H> struct Isl;
+
+template <> struct Isl<double> {
+  using H = double;
+  static __device__ __forceinline__ H from(float a) { return double(a); }
+  static __device__ __forceinline__ H from(double a) { return a; }
+  static __device__ __forceinline__ H prod(float a, float b) { return double(a) * double(b); }
+  static __device__ __forceinline__ H prod(double a, double b) { return a * b; }
+  static __device__ __forceinline__ H add(H a, H b) { return a + b; }
+  static __device__ __forceinline__ H sub(H a, H b) { return a - b; }
+  static __device__ __forceinline__ H mul(H a, H b) { return a * b; }
+  static __device__ __forceinline__ H mulf(H a, float b) { return a * double(b); }
+  static __device__ __forceinline__ H mulf(H a, double b) { return a * b; }
+  static __device__ __forceinline__ H recip(H a) { return 1.0 / a; }
+  static __device__ __forceinline__ H third(H a) { return a * (1.0 / 3.0); }
+  template <typename T> static __device__ __forceinline__ T to(H a) { return T(a); }
+  // ln of a value close to 1, returned in the bulk type
+  template <typename T> static __device__ __forceinline__ T log(H a) { return T(::log(a)); }
+};
+
+template <> struct Isl<dw> {
+  using H = dw;
+  static __device__ __forceinline__ H from(float a) { return {a, 0.0f}; }
+  static __device__ __forceinline__ H prod(float a, float b) { return dw_two_prod(a, b); }
+  static __device__ __forceinline__ H add(H a, H b) { return dw_add(a, b); }
+  static __device__ __forceinline__ H sub(H a, H b) { return dw_add(a, dw_neg(b)); }
+  static __device__ __forceinline__ H mul(H a, H b) { return dw_mul(a, b); }
+  static __device__ __forceinline__ H mulf(H a, float b) { return dw_mulf(a, b); }
+  static __device__ __forceinline__ H recip(H a) { return dw_recip(a); }
+  static __device__ __forceinline__ H third(H a) {
+    // multiply by 1/3 represented as a double-word constant
+    return dw_mul(a, dw{0.333333343267f, -9.93410746e-09f});
+  }
+  template <typename T> static __device__ __forceinline__ T to(H a) { return T(a.hi + a.lo); }
+  // ln(hi + lo) = ln(hi) + ln(1 + lo/hi) ~ logf(hi) + lo/hi (|lo/hi| < 2^-24)
+  template <typename T> static __device__ __forceinline__ T log(H a) {
+    return T(::logf(a.hi) + a.lo / a.hi);
+  }
+};
+
+}  // namespace sf

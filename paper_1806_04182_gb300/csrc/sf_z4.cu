@@ -1,28 +1,30 @@
 // Standalone CCZ4 stage kernel (one launch per patch); the per-point
-// right-hand side lives in sf_z4.cuh.
+// right-hand side lives in sf_z4.cuh.  Layouts with the strides of a 96^3
+// patch with 3 ghosts (the benchmark configuration) get a kernel with
+// compile-time strides; every other layout uses runtime strides.
 #include "sf_internal.cuh"
 #include "sf_z4.cuh"
 
 namespace sf {
 
-template <typename T, typename H>
+template <typename T, typename H, int SY, int SZ>
 __global__ void __launch_bounds__(128) z4_stage_kernel(PatchArgs<T> a, StageArgs s, Z4Coef<T> zc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= a.n[0] || j >= a.n[1]) return;
   const int g = a.g;
-  const long long c = (long long)(k + g) * a.sz + (long long)(j + g) * a.sy + (i + g);
-  T v[25], r[25];
-  z4_point<T, H>(a, zc, a.us + c, v, r);
-#pragma unroll
-  for (int f = 0; f < 25; ++f) stage_write(a, s, f, c, i, j, k, v[f], r[f]);
+  const long long sy = SY ? (long long)SY : a.sy;
+  const long long sz = SZ ? (long long)SZ : a.sz;
+  const long long c = (long long)(k + g) * sz + (long long)(j + g) * sy + (i + g);
+  const T* __restrict__ u = a.us + c;
+  z4_cell<T, H, SY, SZ>(a, zc, u, [&](int f, T r) {
+    stage_write(a, s, f, c, i, j, k, __ldg(u + f * a.sf), r);
+  });
 }
 
-template <typename T, typename H>
-static sf_status launch(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
-                        void* rhs_out, cudaStream_t st) {
-  PatchArgs<T> a = make_args<T>(prm, p, stage, 25, rhs_out);
+template <typename T>
+Z4Coef<T> z4_coef(const sf_params& prm) {
   Z4Coef<T> zc;
   zc.kappa_z = T(prm.kappa_z);
   zc.kappa_c = T(prm.kappa_c);
@@ -30,15 +32,27 @@ static sf_status launch(const sf_params& prm, const sf_patch& p, const StageArgs
   zc.g_shift = T(prm.g_shift);
   zc.slicing = prm.slicing;
   zc.shift_frozen = prm.shift_frozen;
+  return zc;
+}
+
+template <typename T, typename H>
+static sf_status launch(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
+                        void* rhs_out, cudaStream_t st) {
+  PatchArgs<T> a = make_args<T>(prm, p, stage, 25, rhs_out);
+  const Z4Coef<T> zc = z4_coef<T>(prm);
   dim3 block(32, 4, 1);
   dim3 grid((p.n[0] + 31) / 32, (p.n[1] + 3) / 4, p.n[2]);
-  z4_stage_kernel<T, H><<<grid, block, 0, st>>>(a, s, zc);
+  if (p.sy == 102 && p.sz == 102 * 102)
+    z4_stage_kernel<T, H, 102, 102 * 102><<<grid, block, 0, st>>>(a, s, zc);
+  else
+    z4_stage_kernel<T, H, 0, 0><<<grid, block, 0, st>>>(a, s, zc);
   return after_launch("z4_stage_kernel");
 }
 
 sf_status launch_z4(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                     void* rhs_out, cudaStream_t st) {
   if (p.precision == SF_FP64) return launch<double, double>(prm, p, s, stage, rhs_out, st);
+  if (p.precision == SF_FP32_BULK_DW) return launch<float, dw>(prm, p, s, stage, rhs_out, st);
   return launch<float, double>(prm, p, s, stage, rhs_out, st);
 }
 

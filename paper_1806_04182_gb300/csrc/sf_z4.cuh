@@ -1,18 +1,23 @@
-// CCZ4 (Sec. V) with Bona-Masso slicing and Gamma-driver shift, vacuum,
-// 25 fields, fused with Kreiss-Oliger dissipation and the RK stage update.
+// CCZ4 right-hand side at one point (Sec. V): Bona-Masso slicing,
+// Gamma-driver shift, vacuum, 25 fields, plus Kreiss-Oliger dissipation.
 //
 // Field order: 0 chi | 1-6 gt_xx,xy,xz,yy,yz,zz | 7 Khat | 8-13 At_ij |
 // 14-16 Gammahat^i | 17 Theta | 18 alpha | 19-21 beta^i | 22-24 B^i
 //
-// One thread per interior point.  Derivatives are taken straight from the
-// ghosted SoA arrays (L1/L2-resident neighbours) and consumed as soon as
-// they are formed, so only the 48 first derivatives the algebra reuses stay
-// live.  T is the bulk (storage + stencil) type, H the type of the
-// "island" quantities: conformal-metric determinant, inverse, ln det and
-// the trace removals.  FP64: T = H = double.  FP32-bulk: T = float,
-// H = double.
+// Derivatives come straight from the ghosted SoA arrays (neighbours hit in
+// L1/L2).  Each field's final value is handed to `out(f, rhs)` as soon as it
+// is complete, and quantities are formed in the order they are consumed, so
+// the live set stays small:
+//   islands (det, inverse, ln det) -> shift derivatives -> metric derivatives,
+//   d/dt gt, Christoffels -> Ricci -> D D alpha -> d/dt A~ -> chi, Khat,
+//   Theta -> Gammahat, alpha, beta, B.
+// T is the bulk (storage + stencil) type; H the island type (double, or the
+// double-word float pair of sf_dw.cuh).  SY, SZ > 0 fix the y/z element
+// strides at compile time, so every stencil read is an immediate offset
+// from a per-field base pointer; 0 means runtime strides.
 #pragma once
 #include "sf_common.cuh"
+#include "sf_dw.cuh"
 
 namespace sf {
 
@@ -28,212 +33,219 @@ __host__ __device__ constexpr int S(int a, int b) {
                 : ((a + b) == 1 ? 1 : ((a + b) == 2 ? 2 : 4));
 }
 
-template <typename T, typename H>
-__device__ __forceinline__ void z4_point(const PatchArgs<T>& a, const Z4Coef<T>& zc,
-                                         const T* __restrict__ u, T v[25], T rhs[25]) {
+template <typename T, typename H, int SY, int SZ, typename Out>
+__device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& zc,
+                                        const T* __restrict__ u, Out&& out) {
+  using I = Isl<H>;
   const long long F = a.sf;
-  const long long st[3] = {1, a.sy, a.sz};
-  const long long sy = a.sy, sz = a.sz;
+  const long long sy = SY ? (long long)SY : a.sy;
+  const long long sz = SZ ? (long long)SZ : a.sz;
+  const long long st[3] = {1, sy, sz};
   auto U = [&](int f) { return u + f * F; };
-
-#pragma unroll
-  for (int f = 0; f < 25; ++f) v[f] = __ldg(U(f));
-  const T chi = v[0];
-  T gt[6], At[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) { gt[q] = v[1 + q]; At[q] = v[8 + q]; }
-  const T Kh = v[7], Th = v[17], al = v[18];
-  const T Gh[3] = {v[14], v[15], v[16]};
-  const T be[3] = {v[19], v[20], v[21]};
-  const T Bv[3] = {v[22], v[23], v[24]};
-
-  // ---- conformal metric inverse, determinant, ln det (island type H)
-  const H g00 = gt[0], g01 = gt[1], g02 = gt[2], g11 = gt[3], g12 = gt[4], g22 = gt[5];
-  const H c00 = g11 * g22 - g12 * g12, c01 = g02 * g12 - g01 * g22, c02 = g01 * g12 - g02 * g11;
-  const H c11 = g00 * g22 - g02 * g02, c12 = g01 * g02 - g00 * g12, c22 = g00 * g11 - g01 * g01;
-  const H det = g00 * c00 + g01 * c01 + g02 * c02;
-  const H idet = H(1) / det;
-  const H igH[6] = {c00 * idet, c01 * idet, c02 * idet, c11 * idet, c12 * idet, c22 * idet};
-  const H lndet = log(det);
-  T ig[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) ig[q] = T(igH[q]);
-  // symmetric contraction weights: off-diagonal entries appear twice
-  T w[6] = {ig[0], T(2) * ig[1], T(2) * ig[2], ig[3], T(2) * ig[4], ig[5]};
-
-  // ---- first derivatives that the algebra reuses
-  T dchi[3], dKh[3], dTh[3], dal[3], dgt[6][3], dbe[3][3], dGh[3][3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const T h = a.i12h[d];
-    dchi[d] = d1(U(0), st[d], h);
-    dKh[d] = d1(U(7), st[d], h);
-    dTh[d] = d1(U(17), st[d], h);
-    dal[d] = d1(U(18), st[d], h);
-#pragma unroll
-    for (int q = 0; q < 6; ++q) dgt[q][d] = d1(U(1 + q), st[d], h);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      dbe[q][d] = d1(U(19 + q), st[d], h);  // partial_d beta^q
-      dGh[q][d] = d1(U(14 + q), st[d], h);  // partial_d Gammahat^q
-    }
-  }
-  auto advk = [&](const T* dd) { return be[0] * dd[0] + be[1] * dd[1] + be[2] * dd[2]; };
-  auto adv_direct = [&](int f) {
-    T s = T(0);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) s += be[d] * d1(U(f), st[d], a.i12h[d]);
-    return s;
-  };
-  const T divbe = dbe[0][0] + dbe[1][1] + dbe[2][2];
-
-  // ---- second derivatives.  dd(f, m, n) for m <= n.
-  auto dd = [&](int f, int m, int n) -> T {
-    if (m == n) return d2(U(f), st[m], v[f], a.i12h2[m]);
+  auto c0 = [&](int f) { return __ldg(U(f)); };
+  auto D = [&](int f, int d) { return d1(U(f), st[d], a.i12h[d]); };
+  auto KO = [&](int f) { return ko_all(U(f), sy, sz, c0(f), a.ko); };
+  auto DD = [&](int f, int m, int n) -> T {
+    if (m == n) return d2(U(f), st[m], c0(f), a.i12h2[m]);
     const int pi = (m == 0 && n == 1) ? 0 : ((m == 0 && n == 2) ? 1 : 2);
     return dmix(U(f), st[m], st[n], a.i144hh[pi]);
   };
-  T ddchi[6], ddal[6];
-  // conformal metric: t1[q] = gt^{mn} d_m d_n gt_q, consumed at once
-  T t1[6];
-  // shift: s2[a] = gt^{mn} d_m d_n beta^a, ddiv[b] = d_b d_k beta^k
-  T s2[3] = {T(0), T(0), T(0)}, ddiv[3] = {T(0), T(0), T(0)};
-#pragma unroll
-  for (int m = 0; m < 3; ++m)
-#pragma unroll
-    for (int n = m; n < 3; ++n) {
-      const int q = S(m, n);
-      ddchi[q] = dd(0, m, n);
-      ddal[q] = dd(18, m, n);
-    }
-#pragma unroll
-  for (int p = 0; p < 6; ++p) {
-    T s = T(0);
-#pragma unroll
-    for (int m = 0; m < 3; ++m)
-#pragma unroll
-      for (int n = m; n < 3; ++n) s += w[S(m, n)] * dd(1 + p, m, n);
-    t1[p] = s;
-  }
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int m = 0; m < 3; ++m)
-#pragma unroll
-      for (int n = m; n < 3; ++n) {
-        const T x = dd(19 + c, m, n);
-        s2[c] += w[S(m, n)] * x;
-        if (m == n) {
-          if (m == c) ddiv[c] += x;
-        } else {
-          if (n == c) ddiv[m] += x;
-          if (m == c) ddiv[n] += x;
-        }
-      }
+  auto emit = [&](int f, T r) { out(f, r + KO(f)); };
 
-  // ---- Christoffel symbols
-  T Gl[3][6];  // Gamma~_{a bc}, first index lowered
+  const T chi = c0(0), Kh = c0(7), Th = c0(17), al = c0(18);
+  T gt[6], At[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) { gt[q] = c0(1 + q); At[q] = c0(8 + q); }
+  T be[3], Gh[3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p) { be[p] = c0(19 + p); Gh[p] = c0(14 + p); }
+  auto advk = [&](const T* dd) { return be[0] * dd[0] + be[1] * dd[1] + be[2] * dd[2]; };
+  auto adv = [&](int f) { return be[0] * D(f, 0) + be[1] * D(f, 1) + be[2] * D(f, 2); };
+
+  // ---- islands: determinant, inverse and ln det of the conformal metric
+  const H c00 = I::sub(I::prod(gt[3], gt[5]), I::prod(gt[4], gt[4]));
+  const H c01 = I::sub(I::prod(gt[2], gt[4]), I::prod(gt[1], gt[5]));
+  const H c02 = I::sub(I::prod(gt[1], gt[4]), I::prod(gt[2], gt[3]));
+  const H c11 = I::sub(I::prod(gt[0], gt[5]), I::prod(gt[2], gt[2]));
+  const H c12 = I::sub(I::prod(gt[1], gt[2]), I::prod(gt[0], gt[4]));
+  const H c22 = I::sub(I::prod(gt[0], gt[3]), I::prod(gt[1], gt[1]));
+  const H det = I::add(I::add(I::mulf(c00, gt[0]), I::mulf(c01, gt[1])), I::mulf(c02, gt[2]));
+  const H idet = I::recip(det);
+  const H igH[6] = {I::mul(c00, idet), I::mul(c01, idet), I::mul(c02, idet),
+                    I::mul(c11, idet), I::mul(c12, idet), I::mul(c22, idet)};
+  const T lndet = I::template log<T>(det);
+  T ig[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) ig[q] = I::template to<T>(igH[q]);
+  const T w[6] = {ig[0], T(2) * ig[1], T(2) * ig[2], ig[3], T(2) * ig[4], ig[5]};
+  // island trace: gt^{ij} X_ij with off-diagonal entries counted twice
+  auto trace_isl = [&](const T* X) {
+    const H d = I::add(I::add(I::mulf(igH[0], X[0]), I::mulf(igH[3], X[3])), I::mulf(igH[5], X[5]));
+    const H o = I::add(I::add(I::mulf(igH[1], X[1]), I::mulf(igH[2], X[2])), I::mulf(igH[4], X[4]));
+    return I::add(d, I::add(o, o));
+  };
+  // island trace removal X_q - gt_q tr / 3, rounded to the bulk type
+  auto tf_isl = [&](T Xq, T gq, const H& tr) {
+    return I::template to<T>(I::sub(I::from(Xq), I::third(I::mulf(tr, gq))));
+  };
+  const H trAH = trace_isl(At);
+  const T trA = I::template to<T>(trAH);
+
+  // ---- shift derivatives
+  T dbe[3][3];
 #pragma unroll
   for (int p = 0; p < 3; ++p)
 #pragma unroll
-    for (int b = 0; b < 3; ++b)
+    for (int d = 0; d < 3; ++d) dbe[p][d] = D(19 + p, d);  // partial_d beta^p
+  const T divbe = dbe[0][0] + dbe[1][1] + dbe[2][2];
+  const T kz = zc.kappa_z, kc = zc.kappa_c;
+
+  // ---- metric derivatives: d/dt gt (Eq. syseq1) and Christoffels
+  T Gl[3][6];  // Gamma~_{a bc}, first index lowered
+  {
+    T dgt[6][3];
 #pragma unroll
-      for (int c = b; c < 3; ++c)
-        Gl[p][S(b, c)] = T(0.5) * (dgt[S(p, c)][b] + dgt[S(p, b)][c] - dgt[S(b, c)][p]);
+    for (int q = 0; q < 6; ++q)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) dgt[q][d] = D(1 + q, d);
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int b = p; b < 3; ++b) {
+        const int q = S(p, b);
+        T s = T(0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s += gt[S(p, c)] * dbe[c][b] + gt[S(c, b)] * dbe[c][p];
+        const T AtTF = tf_isl(At[q], gt[q], trAH);
+        emit(1 + q, advk(dgt[q]) + s - T(2.0 / 3.0) * gt[q] * divbe - T(2) * al * AtTF -
+                        kc * T(1.0 / 3.0) * al * gt[q] * lndet);
+      }
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = b; c < 3; ++c)
+          Gl[p][S(b, c)] = T(0.5) * (dgt[S(p, c)][b] + dgt[S(p, b)][c] - dgt[S(b, c)][p]);
+  }
   T Gu[3][6];  // Gamma~^a_{bc}
 #pragma unroll
   for (int p = 0; p < 3; ++p)
 #pragma unroll
     for (int q = 0; q < 6; ++q)
       Gu[p][q] = ig[S(p, 0)] * Gl[0][q] + ig[S(p, 1)] * Gl[1][q] + ig[S(p, 2)] * Gl[2][q];
-  T Gt[3], Z[3];
+  T Z[3];
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
     T s = T(0);
 #pragma unroll
     for (int q = 0; q < 6; ++q) s += w[q] * Gu[p][q];
-    Gt[p] = s;
-    Z[p] = T(0.5) * chi * (Gh[p] - Gt[p]);
+    Z[p] = T(0.5) * chi * (Gh[p] - s);  // Z^i = chi/2 (Gammahat^i - Gamma~^i)
   }
 
-  // ---- Ricci tensor Rhat_ab + Rchi_ab (Sec. V)
-  // Q[c][a][n] = gt^{nm} Gamma~^c_{ma}
-  T Qm[3][3][3];
+  // ---- Ricci tensor Rhat_ab + Rchi_ab
+  T dchi[3], dal[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c)
+  for (int d = 0; d < 3; ++d) { dchi[d] = D(0, d); dal[d] = D(18, d); }
+  const T ichi = T(1) / chi;
+  T Rt[6];
+  {
+    T ddchi[6], t1[6];
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int n = m; n < 3; ++n) ddchi[S(m, n)] = DD(0, m, n);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      T s = T(0);
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int n = m; n < 3; ++n) s += w[S(m, n)] * DD(1 + q, m, n);
+      t1[q] = s;  // gt^{mn} d_m d_n gt_q
+    }
+    T t4[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) t4[q] = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T Qc[3][3];  // gt^{nm} Gamma~^c_{mp}
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int n = 0; n < 3; ++n)
+          Qc[p][n] = ig[S(n, 0)] * Gu[c][S(0, p)] + ig[S(n, 1)] * Gu[c][S(1, p)] +
+                     ig[S(n, 2)] * Gu[c][S(2, p)];
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int b = p; b < 3; ++b) {
+          T s = T(0);
+#pragma unroll
+          for (int n = 0; n < 3; ++n)
+            s += Qc[p][n] * (Gl[b][S(c, n)] + Gl[c][S(n, b)]) + Qc[b][n] * Gl[p][S(c, n)];
+          t4[S(p, b)] += s;
+        }
+    }
+    T s3 = T(0), s3b = T(0);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) s3 += w[q] * ddchi[q];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) s3b += ig[S(c, m)] * dchi[c] * dchi[m];
+    const T Ghdchi = Gh[0] * dchi[0] + Gh[1] * dchi[1] + Gh[2] * dchi[2];
+    const T trace_chi = (s3 - T(1.5) * ichi * s3b) - Ghdchi;
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll
-      for (int n = 0; n < 3; ++n)
-        Qm[c][p][n] = ig[S(n, 0)] * Gu[c][S(0, p)] + ig[S(n, 1)] * Gu[c][S(1, p)] +
-                      ig[S(n, 2)] * Gu[c][S(2, p)];
-  const T ichi = T(1) / chi;
-  T s3 = T(0);
+      for (int b = p; b < 3; ++b) {
+        const int q = S(p, b);
+        T t2 = T(0), t3 = T(0), sG = T(0), sZ = T(0);
 #pragma unroll
-  for (int q = 0; q < 6; ++q) s3 += w[q] * ddchi[q];
-  T s3b = T(0);
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int m = 0; m < 3; ++m) s3b += ig[S(c, m)] * dchi[c] * dchi[m];
-  const T Ghdchi = Gh[0] * dchi[0] + Gh[1] * dchi[1] + Gh[2] * dchi[2];
-  const T trace_chi = (s3 - T(1.5) * ichi * s3b) - Ghdchi;
-  T Rt[6];
-#pragma unroll
-  for (int p = 0; p < 3; ++p)
-#pragma unroll
-    for (int b = p; b < 3; ++b) {
-      const int q = S(p, b);
-      T t2 = T(0), t3 = T(0), t4 = T(0), sG = T(0), sZ = T(0);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        t2 += gt[S(c, p)] * dGh[c][b] + gt[S(c, b)] * dGh[c][p];
-        t3 += Gh[c] * (Gl[p][S(b, c)] + Gl[b][S(p, c)]);
-        sG += Gu[c][q] * dchi[c];
-        sZ += Z[c] * (gt[S(c, p)] * dchi[b] + gt[S(c, b)] * dchi[p]);
-#pragma unroll
-        for (int n = 0; n < 3; ++n)
-          t4 += Qm[c][p][n] * Gl[b][S(c, n)] + Qm[c][b][n] * Gl[p][S(c, n)] +
-                Qm[c][p][n] * Gl[c][S(n, b)];
+        for (int c = 0; c < 3; ++c) {
+          const T dGcb = D(14 + c, b), dGcp = D(14 + c, p);
+          t2 += gt[S(c, p)] * dGcb + gt[S(c, b)] * dGcp;
+          t3 += Gh[c] * (Gl[p][S(b, c)] + Gl[b][S(p, c)]);
+          sG += Gu[c][q] * dchi[c];
+          sZ += Z[c] * (gt[S(c, p)] * dchi[b] + gt[S(c, b)] * dchi[p]);
+        }
+        const T Rhat = T(-0.5) * t1[q] + T(0.5) * t2 + T(0.5) * t3 + t4[q];
+        const T Rchi = T(0.5) * ichi * (ddchi[q] - sG) -
+                       T(0.25) * ichi * ichi * dchi[p] * dchi[b] + ichi * ichi * sZ +
+                       T(0.5) * ichi * gt[q] * trace_chi;
+        Rt[q] = Rhat + Rchi;
       }
-      const T Rhat = T(-0.5) * t1[q] + T(0.5) * t2 + T(0.5) * t3 + t4;
-      const T Rchi = T(0.5) * ichi * (ddchi[q] - sG) - T(0.25) * ichi * ichi * dchi[p] * dchi[b] +
-                     ichi * ichi * sZ + T(0.5) * ichi * gt[q] * trace_chi;
-      Rt[q] = Rhat + Rchi;
-    }
+  }
   T RZ = T(0);
 #pragma unroll
   for (int q = 0; q < 6; ++q) RZ += w[q] * Rt[q];
-  RZ *= chi;
+  RZ *= chi;  // R + 2 nabla_i Z^i = chi gt^{ij} (Rhat + Rchi)_ij
 
-  // ---- nabla_a nabla_b alpha and its trace
-  T gdadc = T(0);
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int m = 0; m < 3; ++m) gdadc += ig[S(c, m)] * dal[c] * dchi[m];
-  T DDal[6];
-#pragma unroll
-  for (int p = 0; p < 3; ++p)
-#pragma unroll
-    for (int b = p; b < 3; ++b) {
-      const int q = S(p, b);
-      T sG = Gu[0][q] * dal[0] + Gu[1][q] * dal[1] + Gu[2][q] * dal[2];
-      DDal[q] = ddal[q] - sG + T(0.5) * ichi * (dal[p] * dchi[b] + dal[b] * dchi[p] - gt[q] * gdadc);
-    }
+  // ---- nabla_a nabla_b alpha and its trace; M_ab = alpha R_ab - D_a D_b alpha
+  T M[6];
   T LapAl = T(0);
-#pragma unroll
-  for (int q = 0; q < 6; ++q) LapAl += w[q] * DDal[q];
-  LapAl *= chi;
-
-  // ---- A~ contractions
-  H trAH = H(0);
   {
-    const H wH[6] = {igH[0], H(2) * igH[1], H(2) * igH[2], igH[3], H(2) * igH[4], igH[5]};
+    T gdadc = T(0);
 #pragma unroll
-    for (int q = 0; q < 6; ++q) trAH += wH[q] * H(At[q]);
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) gdadc += ig[S(c, m)] * dal[c] * dchi[m];
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int b = p; b < 3; ++b) {
+        const int q = S(p, b);
+        const T sG = Gu[0][q] * dal[0] + Gu[1][q] * dal[1] + Gu[2][q] * dal[2];
+        const T DDal = DD(18, p, b) - sG +
+                       T(0.5) * ichi * (dal[p] * dchi[b] + dal[b] * dchi[p] - gt[q] * gdadc);
+        LapAl += w[q] * DDal;
+        M[q] = al * Rt[q] - DDal;
+      }
+    LapAl *= chi;
   }
-  const T trA = T(trAH);
+
+  // ---- A~ contractions and d/dt A~_ab (trace removal of M in the island type)
   T Aud[3][3];  // A~^a_b = gt^{ac} A~_cb
 #pragma unroll
   for (int p = 0; p < 3; ++p)
@@ -247,36 +259,10 @@ __device__ __forceinline__ void z4_point(const PatchArgs<T>& a, const Z4Coef<T>&
     for (int b = p; b < 3; ++b)
       Auu[S(p, b)] = ig[S(p, 0)] * Aud[b][0] + ig[S(p, 1)] * Aud[b][1] + ig[S(p, 2)] * Aud[b][2];
   T AA = T(0);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) AA += ((q == 0 || q == 3 || q == 5) ? T(1) : T(2)) * At[q] * Auu[q];
   {
-    const T wA[6] = {T(1), T(2), T(2), T(1), T(2), T(1)};
-#pragma unroll
-    for (int q = 0; q < 6; ++q) AA += wA[q] * At[q] * Auu[q];
-  }
-
-  const T kz = zc.kappa_z, kc = zc.kappa_c;
-  // ---- d/dt gt_ab  (Eq. syseq1); trace removal of A~ in H
-#pragma unroll
-  for (int p = 0; p < 3; ++p)
-#pragma unroll
-    for (int b = p; b < 3; ++b) {
-      const int q = S(p, b);
-      T s = T(0);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) s += gt[S(p, c)] * dbe[c][b] + gt[S(c, b)] * dbe[c][p];
-      const T AtTF = T(H(At[q]) - H(1.0 / 3.0) * H(gt[q]) * trAH);
-      rhs[1 + q] = advk(dgt[q]) + s - T(2.0 / 3.0) * gt[q] * divbe - T(2) * al * AtTF -
-                   kc * T(1.0 / 3.0) * al * gt[q] * T(lndet);
-    }
-
-  // ---- d/dt A~_ab; trace-free part of alpha R - D D alpha in H
-  {
-    T M[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) M[q] = al * Rt[q] - DDal[q];
-    const H wH[6] = {igH[0], H(2) * igH[1], H(2) * igH[2], igH[3], H(2) * igH[4], igH[5]};
-    H trM = H(0);
-#pragma unroll
-    for (int q = 0; q < 6; ++q) trM += wH[q] * H(M[q]);
+    const H trM = trace_isl(M);
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll
@@ -288,67 +274,84 @@ __device__ __forceinline__ void z4_point(const PatchArgs<T>& a, const Z4Coef<T>&
           s += At[S(p, c)] * dbe[c][b] + At[S(c, b)] * dbe[c][p];
           AAd += At[S(p, c)] * Aud[c][b];
         }
-        const T MTF = T(H(M[q]) - H(1.0 / 3.0) * H(gt[q]) * trM);
-        rhs[8 + q] = adv_direct(8 + q) + s - T(2.0 / 3.0) * At[q] * divbe -
-                     kc * T(1.0 / 3.0) * al * gt[q] * trA + chi * MTF +
-                     al * (Kh * At[q] - T(2) * AAd);
+        const T MTF = tf_isl(M[q], gt[q], trM);
+        emit(8 + q, adv(8 + q) + s - T(2.0 / 3.0) * At[q] * divbe -
+                        kc * T(1.0 / 3.0) * al * gt[q] * trA + chi * MTF +
+                        al * (Kh * At[q] - T(2) * AAd));
       }
   }
 
   // ---- d/dt chi, Khat, Theta
   const T Kt = Kh + T(2) * Th;
-  rhs[0] = advk(dchi) + T(2.0 / 3.0) * chi * (al * Kt - divbe);
   const T Zdal = Z[0] * dal[0] + Z[1] * dal[1] + Z[2] * dal[2];
-  rhs[7] = advk(dKh) - LapAl + al * (T(1.0 / 3.0) * Kt * Kt + AA + kz * Th) + T(2) * Zdal;
-  rhs[17] = advk(dTh) +
-            T(0.5) * al * (RZ + T(2.0 / 3.0) * Kh * Kh + T(2.0 / 3.0) * Th * (Kh - T(2) * Th) - AA) -
-            Zdal - T(2) * al * kz * Th;
-
-  // ---- d/dt Gammahat^a  (Eq. syseq2)
-  T rGh[3];
-  const T ialpha = T(1) / al;
+  emit(0, advk(dchi) + T(2.0 / 3.0) * chi * (al * Kt - divbe));
+  {
+    T dKh[3];
 #pragma unroll
-  for (int p = 0; p < 3; ++p) {
-    T sb = T(0), s3v = T(0), s4 = T(0), s5 = T(0), s6 = T(0), s7 = T(0), s8 = T(0);
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      sb += Gh[b] * dbe[p][b];
-      s3v += ig[S(p, b)] * ddiv[b];
-      s4 += Auu[S(p, b)] * dal[b];
-      s6 += Auu[S(p, b)] * dchi[b];
-      s7 += ig[S(p, b)] * dKh[b];
-      s8 += ig[S(p, b)] * (T(1.0 / 3.0) * dTh[b] + Th * ialpha * dal[b]);
-    }
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      const T wA = (q == 0 || q == 3 || q == 5) ? T(1) : T(2);
-      s5 += wA * Gu[p][q] * Auu[q];
-    }
-    rGh[p] = -sb + T(2.0 / 3.0) * Gh[p] * divbe + s2[p] + T(1.0 / 3.0) * s3v - T(2) * s4 +
-             T(2) * al * (s5 - T(1.5) * ichi * s6 - T(2.0 / 3.0) * s7) +
-             T(2) * al * (-s8 - ichi * Z[p] * (kz + T(2.0 / 3.0) * Kt));
-    rhs[14 + p] = advk(dGh[p]) + rGh[p];
+    for (int d = 0; d < 3; ++d) dKh[d] = D(7, d);
+    emit(7, advk(dKh) - LapAl + al * (T(1.0 / 3.0) * Kt * Kt + AA + kz * Th) + T(2) * Zdal);
   }
+  emit(17, adv(17) +
+               T(0.5) * al * (RZ + T(2.0 / 3.0) * Kh * Kh + T(2.0 / 3.0) * Th * (Kh - T(2) * Th) - AA) -
+               Zdal - T(2) * al * kz * Th);
 
-  // ---- gauge (Sec. V): Bona-Masso slicing, Gamma-driver shift
+  // ---- d/dt Gammahat^a (Eq. syseq2), gauge (Bona-Masso, Gamma-driver)
+  T s2[3] = {T(0), T(0), T(0)}, ddiv[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int n = m; n < 3; ++n) {
+        const T x = DD(19 + c, m, n);  // d_m d_n beta^c
+        s2[c] += w[S(m, n)] * x;
+        if (m == n) {
+          if (m == c) ddiv[c] += x;
+        } else {
+          if (n == c) ddiv[m] += x;
+          if (m == c) ddiv[n] += x;
+        }
+      }
+  const T ialpha = T(1) / al;
+  T rGh[3];
+  {
+    T dKh[3], dTh[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) { dKh[d] = D(7, d); dTh[d] = D(17, d); }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      T sb = T(0), s3v = T(0), s4 = T(0), s5 = T(0), s6 = T(0), s7 = T(0), s8 = T(0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        sb += Gh[b] * dbe[p][b];
+        s3v += ig[S(p, b)] * ddiv[b];
+        s4 += Auu[S(p, b)] * dal[b];
+        s6 += Auu[S(p, b)] * dchi[b];
+        s7 += ig[S(p, b)] * dKh[b];
+        s8 += ig[S(p, b)] * (T(1.0 / 3.0) * dTh[b] + Th * ialpha * dal[b]);
+      }
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+        s5 += ((q == 0 || q == 3 || q == 5) ? T(1) : T(2)) * Gu[p][q] * Auu[q];
+      rGh[p] = -sb + T(2.0 / 3.0) * Gh[p] * divbe + s2[p] + T(1.0 / 3.0) * s3v - T(2) * s4 +
+               T(2) * al * (s5 - T(1.5) * ichi * s6 - T(2.0 / 3.0) * s7) +
+               T(2) * al * (-s8 - ichi * Z[p] * (kz + T(2.0 / 3.0) * Kt));
+      emit(14 + p, adv(14 + p) + rGh[p]);
+    }
+  }
   const T fsl = zc.slicing == 0 ? T(2) * ialpha : T(1);
-  rhs[18] = advk(dal) - al * al * fsl * Kh;
+  emit(18, advk(dal) - al * al * fsl * Kh);
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
     if (zc.shift_frozen) {
-      rhs[19 + p] = T(0);
-      rhs[22 + p] = T(0);
+      out(19 + p, T(0));
+      out(22 + p, T(0));
     } else {
-      rhs[19 + p] = advk(dbe[p]) + zc.g_shift * Bv[p];
-      rhs[22 + p] = adv_direct(22 + p) - zc.eta * Bv[p] + rGh[p];
+      const T Bp = c0(22 + p);
+      emit(19 + p, advk(dbe[p]) + zc.g_shift * Bp);
+      emit(22 + p, adv(22 + p) - zc.eta * Bp + rGh[p]);
     }
   }
-
-  // ---- Kreiss-Oliger dissipation on every evolved field
-  const int nko = zc.shift_frozen ? 19 : 25;
-#pragma unroll
-  for (int f = 0; f < 25; ++f)
-    if (f < nko) rhs[f] += ko_all(U(f), sy, sz, v[f], a.ko);
 }
 
 }  // namespace sf

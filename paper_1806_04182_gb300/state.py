@@ -11,6 +11,8 @@ SSP-RK3: stage 0: A -> B, 1: B -> C, 2: C -> A.
 """
 from __future__ import annotations
 
+import json
+
 import numpy as np
 import torch
 
@@ -47,7 +49,7 @@ class PatchState:
         self.C = torch.zeros(self.shape, **kw)
         self.D = torch.zeros(self.shape, **kw) if self.prm.rk == capi.SF_RK4 else None
         self.E = (torch.zeros(self.shape, **kw)
-                  if precision == capi.SF_FP32_BULK and self.prm.rk == capi.SF_RK4 else None)
+                  if precision != capi.SF_FP64 and self.prm.rk == capi.SF_RK4 else None)
 
     # ------------------------------------------------------------------ ABI
     def patch(self, u_stage, u_n, u_next) -> capi.sf_patch:
@@ -140,3 +142,30 @@ class PatchState:
         capi.sf_mhd_max_rate(self.prm, self.patch(a, a, self.B), a.data_ptr(), out.data_ptr(),
                              _stream_handle(stream))
         return out
+
+    # ------------------------------------------------------------------ checkpoint
+    _PRM_FIELDS = [f for f, _ in capi.sf_params._fields_]
+
+    def save(self, path: str, step: int = 0, t: float = 0.0) -> None:
+        """Write U^n (with ghosts), the Kahan compensation and the run
+        metadata to `path` (.npz); `load` resumes bit for bit."""
+        meta = dict(system=self.system, n=self.n, dx=self.dx, dt=self.dt,
+                    precision=self.precision, ghost=self.g, step=step, t=t,
+                    prm={f: getattr(self.prm, f) for f in self._PRM_FIELDS})
+        arrays = {"A": self.A.cpu().numpy()}
+        if self.E is not None:
+            arrays["E"] = self.E.cpu().numpy()
+        np.savez(path, meta=np.array(json.dumps(meta)), **arrays)
+
+    @classmethod
+    def load(cls, path: str, device="cuda"):
+        """(state, step, t) from a file written by `save`."""
+        z = np.load(path, allow_pickle=False)
+        meta = json.loads(str(z["meta"]))
+        st = cls(meta["system"], meta["n"], meta["dx"], meta["dt"], precision=meta["precision"],
+                 prm=capi.params(**meta["prm"]), ghost=meta["ghost"], device=device)
+        st.A.copy_(torch.from_numpy(z["A"]))
+        if st.E is not None and "E" in z:
+            st.E.copy_(torch.from_numpy(z["E"]))
+        return st, meta["step"], meta["t"]
+

@@ -1,0 +1,127 @@
+"""Batched persistent dispatch over a mixed AMR patch table (wave and CCZ4
+patches of different sizes, levels, dx and dt): the persistent kernel must give
+the same states as per-patch launches of the same stage kernels, through the
+plain stage calls and through the captured CUDA graph, and match the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1806_04182_gb300 import build, capi, inputs
+from paper_1806_04182_gb300.state import PatchState
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    assert torch.cuda.is_available()
+    build.build()
+    return capi.lib()
+
+
+def make_states(table, precision, seed=0):
+    states = []
+    for q, t in enumerate(table):
+        n = t["n"]
+        h = t["dx"]
+        system = capi.SF_WAVE if t["system"] == "wave" else capi.SF_Z4
+        if system == capi.SF_WAVE:
+            U0, _ = inputs.wave_plane(n, seed=seed + q, length=n[0] * h)
+            U0 = U0 * 1e-2
+        else:
+            U0, _ = inputs.z4_perturbed(n, seed=seed + q, amp=0.03)
+        st = PatchState(system, n, (h, h, h), t["dt"], precision=precision)
+        st.upload(U0)
+        st.U0 = U0
+        states.append(st)
+    return states
+
+
+def batch_patches(states):
+    # batch roles: u_n = A (state), u_stage = B, u_next = C, acc = D, kahan = E
+    return [st.patch(st.B, st.A, st.C) for st in states]
+
+
+def small_table(npatch=10, seed=3):
+    t = inputs.amr_patch_table(npatch, seed=seed, lo=6, hi=21)
+    assert {p["system"] for p in t} == {"wave", "z4"}
+    return t
+
+
+@pytest.mark.parametrize("precision", [capi.SF_FP64, capi.SF_FP32_BULK_DW])
+def test_batch_equals_per_patch_launches(precision):
+    table = small_table()
+    ref_states = make_states(table, precision)
+    for st in ref_states:
+        st.step(2)
+    states = make_states(table, precision)
+    b = capi.sf_batch_create(capi.params(), batch_patches(states))
+    try:
+        for _ in range(2):
+            for s in range(4):
+                capi.sf_batch_substep(b, s, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        for st, ref in zip(states, ref_states):
+            a, r = st.interior(), ref.interior()
+            scale = r.abs().amax(dim=(1, 2, 3)).clamp_min(1e-3)
+            err = ((a - r).abs().amax(dim=(1, 2, 3)) / scale).max().item()
+            assert err < (1e-13 if precision == capi.SF_FP64 else 2e-6), err
+    finally:
+        capi.sf_batch_destroy(b)
+
+
+def test_batch_fp64_matches_oracle():
+    table = small_table(6, seed=5)
+    states = make_states(table, capi.SF_FP64)
+    b = capi.sf_batch_create(capi.params(), batch_patches(states))
+    try:
+        for s in range(4):
+            capi.sf_batch_substep(b, s, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+    finally:
+        capi.sf_batch_destroy(b)
+    for st, t in zip(states, table):
+        sysid = oracle.WAVE if t["system"] == "wave" else oracle.Z4
+        G = oracle.ghosted(st.U0.copy())
+        oracle.rk4_step(sysid, G, st.dx, st.dt, oracle.params())
+        want = oracle.interior(G)
+        got = st.interior().cpu().numpy()
+        for f in range(want.shape[0]):
+            scale = max(np.abs(want[f]).max(), 1e-2)
+            assert np.abs(got[f] - want[f]).max() <= 1e-12 * scale, (t, f)
+
+
+def test_batch_graph_tune_and_capture():
+    table = small_table(12, seed=7)
+    states = make_states(table, capi.SF_FP32_BULK_DW)
+    ref = make_states(table, capi.SF_FP32_BULK_DW)
+    for st in ref:
+        st.step(3)
+    b = capi.sf_batch_create(capi.params(), batch_patches(states))
+    stream = torch.cuda.Stream()
+    try:
+        with torch.cuda.stream(stream):
+            capi.sf_batch_tune(b, stream.cuda_stream)  # writes scratch only
+            capi.sf_batch_capture(b, stream.cuda_stream)
+            for _ in range(3):
+                capi.sf_batch_launch(b, stream.cuda_stream)
+        stream.synchronize()
+        assert capi.sf_batch_launches_per_step(b) == 4
+        for st, r in zip(states, ref):
+            a, w = st.interior(), r.interior()
+            scale = w.abs().amax(dim=(1, 2, 3)).clamp_min(1e-3)
+            assert ((a - w).abs().amax(dim=(1, 2, 3)) / scale).max().item() < 2e-6
+    finally:
+        capi.sf_batch_destroy(b)
+
+
+def test_batch_rejects_mixed_precision_and_mhd():
+    table = small_table(4)
+    s64 = make_states(table[:2], capi.SF_FP64)
+    s32 = make_states(table[2:], capi.SF_FP32_BULK_DW)
+    with pytest.raises(capi.SfError, match="precision"):
+        capi.sf_batch_create(capi.params(), batch_patches(s64 + s32))
+    m = PatchState(capi.SF_MHD, (8, 8, 8), (0.1,) * 3, 0.01, prm=capi.params())
+    with pytest.raises(capi.SfError):
+        capi.sf_batch_create(capi.params(), [m.patch(m.B, m.A, m.C)])
