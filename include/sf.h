@@ -216,6 +216,30 @@ int32_t sf_batch_launches_per_step(const sf_batch* b);
 sf_status sf_batch_destroy(sf_batch* b);
 
 /*
+ * Allocation-free form of sf_batch_substep (the paper has no counterpart).
+ * For callers that cannot call cudaMalloc when they advance their patches:
+ * codes that give all device memory to their own pool or arena up front, and
+ * codes that must not allocate while other work is in flight (cudaMalloc may
+ * synchronise the device; cudaFree always does).  One RK4 stage of the
+ * batched persistent kernel over `patches` (same buffer roles as sf_batch:
+ * u_n = state, u_stage and u_next = scratch, acc, kahan), with the kernel's
+ * scratch (queue counter, per-patch stage table, work list) kept in a
+ * file-scope device array of 145,408 bytes that every GPU loading the
+ * library holds until the process exits.  The call allocates nothing; it
+ * copies the stage table from a static host buffer and clears the queue
+ * counter on `stream` before the launch.
+ * Limits: at most 64 patches and 8192 work items of 32x4x4 points per call;
+ * larger requests return SF_EINVAL and enqueue nothing.
+ * The first call on a device looks up the scratch address and the grid size
+ * (with that device current); make that first call before any stream
+ * capture.  All calls share the one scratch array, which keeps the last
+ * call's contents: calls that overlap on the GPU (different streams, or
+ * other host threads' streams) race; issue them in order on one stream.
+ */
+sf_status sf_batch_substep_static(const sf_params* prm, const sf_patch* patches, int32_t npatch,
+                                  int32_t stage, void* stream);
+
+/*
  * Synchronises `stream`, returns and clears the device status word:
  * SF_OK, SF_ENONFINITE or SF_ETIMEOUT.
  */

@@ -26,6 +26,7 @@ EXPORTS = ["sf_nfields", "sf_substep", "sf_rhs", "sf_fill_ghosts_periodic", "sf_
            "sf_adjoint_substep", "sf_gather", "sf_scatter_add", "sf_diagnostics",
            "sf_batch_create", "sf_batch_substep", "sf_batch_tune", "sf_batch_capture",
            "sf_batch_launch", "sf_batch_launches_per_step", "sf_batch_destroy",
+           "sf_batch_substep_static",
            "sf_get_device_status", "sf_last_error", "sf_launch_count"]
 
 
@@ -115,6 +116,7 @@ def lib() -> ctypes.CDLL:
         L.sf_batch_launches_per_step.argtypes = [vp]
         L.sf_batch_launches_per_step.restype = i32
         L.sf_batch_destroy.argtypes = [vp]
+        L.sf_batch_substep_static.argtypes = [P(sf_params), P(sf_patch), i32, i32, vp]
         L.sf_get_device_status.argtypes = [vp]
         L.sf_last_error.argtypes = []
         L.sf_last_error.restype = ctypes.c_char_p
@@ -123,7 +125,8 @@ def lib() -> ctypes.CDLL:
         for name in ("sf_substep", "sf_rhs", "sf_fill_ghosts_periodic", "sf_mhd_max_rate",
                      "sf_adjoint_substep", "sf_gather", "sf_scatter_add", "sf_diagnostics",
                      "sf_batch_create", "sf_batch_substep", "sf_batch_tune", "sf_batch_capture",
-                     "sf_batch_launch", "sf_batch_destroy", "sf_get_device_status"):
+                     "sf_batch_launch", "sf_batch_destroy", "sf_get_device_status",
+                     "sf_batch_substep_static"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -214,6 +217,13 @@ def sf_batch_launches_per_step(batch: int) -> int:
 
 def sf_batch_destroy(batch: int) -> None:
     _check(lib().sf_batch_destroy(batch), "sf_batch_destroy")
+
+
+def sf_batch_substep_static(prm: sf_params, patches, stage: int, stream: int = 0) -> None:
+    """Allocation-free batched RK4 stage (scratch in a fixed device array)."""
+    arr, n = _patches(patches)
+    _check(lib().sf_batch_substep_static(ctypes.byref(prm), arr, n, stage, stream),
+           "sf_batch_substep_static")
 
 
 def sf_get_device_status(stream: int = 0) -> int:

@@ -13,6 +13,7 @@
 // stage 0: A -> B, stage 1: B -> C, stage 2: C -> B, stage 3: B -> A.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "sf_internal.cuh"
@@ -375,3 +376,172 @@ sf_status sf_batch_destroy(sf_batch* b) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free batched stage.  Some callers cannot call cudaMalloc at the
+// point where they advance their patches: codes that hand all device memory
+// to their own pool or arena up front, and codes that must not allocate
+// while other work is in flight (cudaMalloc may synchronise the device and
+// cudaFree always does).  sf_batch_substep_static serves them: it runs the
+// same persistent kernel as sf_batch_substep, but keeps the kernel's scratch
+// (queue counter, per-patch stage table, work list) in one file-scope
+// device array of fixed size instead of memory from sf_batch_create.
+namespace {
+
+constexpr int kStaticMaxPatches = 64;
+constexpr int kStaticMaxItems = 8192;
+constexpr Shape kStaticShape = {32, 4, 4};
+constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+constexpr size_t kArgsBytes = align256(kStaticMaxPatches * (sizeof(PatchArgs<double>) > sizeof(PatchArgs<float>)
+                                                               ? sizeof(PatchArgs<double>)
+                                                               : sizeof(PatchArgs<float>)));
+constexpr size_t kOffArgs = 256;  // [0, 256): queue counter
+constexpr size_t kOffSys = kOffArgs + kArgsBytes;
+constexpr size_t kOffShape = kOffSys + align256(kStaticMaxPatches * sizeof(int));
+constexpr size_t kOffItems = kOffShape + align256(kStaticMaxPatches * sizeof(int2));
+constexpr size_t kStaticBytes = kOffItems + align256(kStaticMaxItems * sizeof(Item));
+
+}  // namespace
+
+// Scratch of sf_batch_substep_static: 145,408 bytes (about 142 KB).  Every GPU that loads
+// the library holds one copy until the process exits.  Host code must not
+// use this name as a device address; it asks the runtime for the address.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+namespace {
+
+std::mutex g_static_mu;                            // guards the host staging copy
+alignas(256) unsigned char g_static_host[kStaticBytes];  // host image of the scratch
+unsigned char* g_static_dev[64] = {nullptr};       // device address per device
+int g_static_grid[64][3] = {{0}};
+
+// Per-device set-up, done once with that device current: the device address
+// of the scratch array and the persistent grid sizes.
+sf_status static_setup(int dev) {
+  if (g_static_dev[dev]) return SF_OK;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess) return set_error(SF_ECUDA, "scratch address: %s", cudaGetErrorString(e));
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return set_error(SF_ECUDA, "SM count query failed");
+  int occ[3] = {0, 0, 0};
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], batch_stage_kernel<double, double>, 128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], batch_stage_kernel<float, double>, 128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], batch_stage_kernel<float, dw>, 128, 0);
+  for (int q = 0; q < 3; ++q) g_static_grid[dev][q] = std::max(1, sms * std::max(1, occ[q]));
+  g_static_dev[dev] = static_cast<unsigned char*>(p);
+  return SF_OK;
+}
+
+template <typename T, typename H>
+sf_status static_stage(const sf_params& prm, const sf_patch* pin, int np, int stage, int dev,
+                       cudaStream_t st) {
+  unsigned char* d = g_static_dev[dev];
+  PatchArgs<T>* hargs = reinterpret_cast<PatchArgs<T>*>(g_static_host + kOffArgs);
+  int* hsys = reinterpret_cast<int*>(g_static_host + kOffSys);
+  int2* hshape = reinterpret_cast<int2*>(g_static_host + kOffShape);
+  Item* hitems = reinterpret_cast<Item*>(g_static_host + kOffItems);
+  int nitems = 0;
+  for (int pass = 0; pass < 2; ++pass)  // CCZ4 items first, as in sf_batch_substep
+    for (int q = 0; q < np; ++q) {
+      const sf_patch& p = pin[q];
+      if ((pass == 0) != (p.system == SF_Z4)) continue;
+      for (int z = 0; z < p.n[2]; z += kStaticShape.tz)
+        for (int y = 0; y < p.n[1]; y += kStaticShape.ty)
+          for (int x = 0; x < p.n[0]; x += kStaticShape.tx) hitems[nitems++] = Item{q, x, y, z};
+    }
+  for (int q = 0; q < np; ++q) {
+    sf_patch p = pin[q];
+    void* A = p.u_n;
+    void* us[4] = {A, p.u_stage, p.u_next, p.u_stage};
+    void* nx[4] = {p.u_stage, p.u_next, p.u_stage, A};
+    p.u_stage = us[stage];
+    p.u_next = nx[stage];
+    hargs[q] = make_args<T>(prm, p, stage, sf_nfields(p.system), nullptr);
+    hsys[q] = p.system;
+    hshape[q] = make_int2(kStaticShape.tx, kStaticShape.tz);
+  }
+  // pageable source: the copies have left g_static_host when they return
+  if (cudaMemcpyAsync(d + kOffArgs, g_static_host + kOffArgs, np * sizeof(PatchArgs<T>),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(d + kOffSys, g_static_host + kOffSys, np * sizeof(int),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(d + kOffShape, g_static_host + kOffShape, np * sizeof(int2),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(d + kOffItems, g_static_host + kOffItems, nitems * sizeof(Item),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return set_error(SF_ECUDA, "upload of the stage table failed");
+  // the queue counter must start at zero on every call
+  if (cudaMemsetAsync(d, 0, sizeof(unsigned int), st) != cudaSuccess)
+    return set_error(SF_ECUDA, "queue counter reset failed");
+  sf_batch tmp;  // only carries the fields batch_stage_args reads
+  tmp.prm = prm;
+  tmp.precision = pin[0].precision;
+  Z4Coef<T> zc;
+  zc.kappa_z = T(prm.kappa_z);
+  zc.kappa_c = T(prm.kappa_c);
+  zc.eta = T(prm.eta);
+  zc.g_shift = T(prm.g_shift);
+  zc.slicing = prm.slicing;
+  zc.shift_frozen = prm.shift_frozen;
+  batch_stage_kernel<T, H><<<g_static_grid[dev][pin[0].precision], 128, 0, st>>>(
+      reinterpret_cast<const PatchArgs<T>*>(d + kOffArgs), reinterpret_cast<const int*>(d + kOffSys),
+      reinterpret_cast<const int2*>(d + kOffShape), reinterpret_cast<const Item*>(d + kOffItems),
+      nitems, reinterpret_cast<unsigned int*>(d), batch_stage_args(&tmp, stage, status_ptr()), zc);
+  return after_launch("batch_stage_kernel (static scratch)");
+}
+
+}  // namespace
+
+extern "C" sf_status sf_batch_substep_static(const sf_params* prm, const sf_patch* patches,
+                                             int32_t npatch, int32_t stage, void* stream) {
+  if (!prm || !patches) return set_error(SF_EINVAL, "NULL argument");
+  if (npatch < 1 || npatch > kStaticMaxPatches)
+    return set_error(SF_EINVAL, "npatch = %d outside [1, %d], the static scratch maximum", npatch,
+                     kStaticMaxPatches);
+  if (stage < 0 || stage > 3) return set_error(SF_EINVAL, "stage %d out of range [0,4)", stage);
+  if (prm->rk != SF_RK4) return set_error(SF_ENOTSUP, "sf_batch_substep_static runs RK4");
+  sf_params q = *prm;
+  q.ghosts = SF_GHOSTS_PERIODIC;
+  sf_patch local[kStaticMaxPatches];
+  long long items = 0;
+  for (int i = 0; i < npatch; ++i) {
+    sf_patch p = patches[i];
+    normalise_strides(p, sf_nfields(p.system));
+    if (p.system != SF_WAVE && p.system != SF_Z4)
+      return set_error(SF_ENOTSUP, "sf_batch_substep_static takes SF_WAVE and SF_Z4 patches");
+    if (p.precision != patches[0].precision)
+      return set_error(SF_EINVAL, "all patches of a call need one precision");
+    if (p.u_stage == p.u_next || p.u_stage == p.u_n || p.u_next == p.u_n)
+      return set_error(SF_EINVAL, "patches need distinct u_n, u_stage and u_next buffers");
+    void* us[4] = {p.u_n, p.u_stage, p.u_next, p.u_stage};
+    void* nx[4] = {p.u_stage, p.u_next, p.u_stage, p.u_n};
+    sf_patch r = p;
+    r.u_stage = us[stage];
+    r.u_next = nx[stage];
+    sf_status e = check_patch(&q, r, 1, stage);
+    if (e) return e;
+    items += (long long)((p.n[0] + kStaticShape.tx - 1) / kStaticShape.tx) *
+             ((p.n[1] + kStaticShape.ty - 1) / kStaticShape.ty) *
+             ((p.n[2] + kStaticShape.tz - 1) / kStaticShape.tz);
+    local[i] = p;
+  }
+  if (items > kStaticMaxItems)
+    return set_error(SF_EINVAL,
+                     "%lld work items of 32x4x4 points exceed the static scratch maximum of %d",
+                     items, kStaticMaxItems);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+    return set_error(SF_ECUDA, "no usable CUDA device");
+  if (!status_ptr()) return set_error(SF_ECUDA, "no status word");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  sf_status e = static_setup(dev);
+  if (e) return e;
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (local[0].precision) {
+    case SF_FP64: return static_stage<double, double>(q, local, npatch, stage, dev, st);
+    case SF_FP32_BULK_DW: return static_stage<float, dw>(q, local, npatch, stage, dev, st);
+    default: return static_stage<float, double>(q, local, npatch, stage, dev, st);
+  }
+}
