@@ -318,6 +318,156 @@ def gpu_arm(args):
     return line
 
 
+# ---------------------------------------------------------------- other rows
+def _events_time(fn, steps: int, warmup: int) -> float:
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def suite(args, hbm_peak: float) -> list[dict]:
+    """The remaining workloads, each timed on the device with CUDA events."""
+    import torch
+    from paper_1806_04182_gb300 import adjoint, capi, inputs
+    from paper_1806_04182_gb300.state import PatchState
+    rows = set(args.rows.split(",")) if args.rows else {"wave", "mhd", "batch", "adjoint"}
+    out = []
+    # wave 64^3 FP64 and FP32, RK4, CFL 0.25
+    for prec, name, bpc in (() if "wave" not in rows else ((capi.SF_FP64, "fp64", 16 / 4 * 5 * 8),
+                            (capi.SF_FP32_BULK, "fp32", 19 / 4 * 5 * 4))):
+        n = (64, 64, 64)
+        U0, dx = inputs.wave_plane(n, seed=0)
+        st = PatchState(capi.SF_WAVE, n, dx, 0.25 * dx[0], precision=prec)
+        st.upload(U0)
+        ms = _events_time(lambda: st.step(1), 20, 3)
+        cells = 64 ** 3
+        rate = cells * 4 * 20 / (ms * 1e-3)
+        out.append({"workload": f"wave_64cubed_rk4_{name}", "value": rate, "unit": UNIT,
+                    "ms_per_step": ms / 20, "bytes_per_cell_update": bpc,
+                    "hbm_frac": rate * bpc / 1e9 / hbm_peak})
+    if "mhd" in rows:
+        out += _mhd_row(hbm_peak)
+    if "batch" in rows:
+        out += _batch_rows(hbm_peak)
+    if "adjoint" in rows:
+        out += _adjoint_rows()
+    return out
+
+
+def _mhd_row(hbm_peak: float) -> list[dict]:
+    import torch
+    from paper_1806_04182_gb300 import capi, inputs
+    from paper_1806_04182_gb300.state import PatchState
+    out = []
+    # MHD 128^3 FP64, SSP-RK3, CFL 0.3 with the rate recomputed every step
+    n = (128, 128, 128)
+    U0, dx = inputs.mhd_blast(n, seed=0)
+    prm = capi.params(rk=capi.SF_SSPRK3)
+    st = PatchState(capi.SF_MHD, n, dx, 1e-3, prm=prm)
+    st.upload(U0)
+    ms = _events_time(lambda: st.step_cfl(1, cfl=0.3), 10, 3)
+    rate = 128 ** 3 * 3 * 10 / (ms * 1e-3)
+    out.append({"workload": "mhd_128cubed_weno5_llf_ssprk3_fp64", "value": rate, "unit": UNIT,
+                "ms_per_step": ms / 10, "bytes_per_cell_update": 8 / 3 * 8 * 8,
+                "hbm_frac": rate * 8 / 3 * 8 * 8 / 1e9 / hbm_peak,
+                "note": "dt = 0.3 / max signal rate: sf_mhd_max_rate once, then the rate "
+                        "fused into each step's last stage, read back every step"})
+    return out
+
+
+def _batch_rows(hbm_peak: float) -> list[dict]:
+    import torch
+    from paper_1806_04182_gb300 import capi, inputs
+    from paper_1806_04182_gb300.state import PatchState
+    out = []
+    # batched AMR step: 512 patches, one persistent launch per stage in a CUDA graph
+    table = inputs.amr_patch_table(512, seed=0)
+
+    def states(precision):
+        sts = []
+        for q, t in enumerate(table):
+            h = t["dx"]
+            system = capi.SF_WAVE if t["system"] == "wave" else capi.SF_Z4
+            if system == capi.SF_WAVE:
+                U0, _ = inputs.wave_plane(t["n"], seed=q, length=t["n"][0] * h)
+            else:
+                U0, _ = inputs.z4_minkowski_noise(t["n"], seed=q)
+            sts.append(PatchState(system, t["n"], (h, h, h), t["dt"], precision=precision))
+            sts[-1].upload(U0)
+        return sts
+
+    cells = sum(t["n"][0] * t["n"][1] * t["n"][2] for t in table)
+    bytes_step = sum(t["n"][0] * t["n"][1] * t["n"][2] * (19 * (25 if t["system"] == "z4" else 5) * 4)
+                     for t in table)
+    sts = states(capi.SF_FP32_BULK_DW)
+    stream = torch.cuda.Stream()
+    b = capi.sf_batch_create(capi.params(), [s_.patch(s_.B, s_.A, s_.C) for s_ in sts])
+    with torch.cuda.stream(stream):
+        capi.sf_batch_tune(b, stream.cuda_stream)
+        capi.sf_batch_capture(b, stream.cuda_stream)
+        ms = _events_time(lambda: capi.sf_batch_launch(b, stream.cuda_stream), 10, 3)
+    capi.sf_batch_destroy(b)
+    batch_rate = cells * 4 * 10 / (ms * 1e-3)
+    out.append({"workload": "amr_batch_512_patches_fp32_bulk_dw_graph", "value": batch_rate,
+                "unit": UNIT, "ms_per_step": ms / 10, "cells": cells,
+                "hbm_frac": bytes_step * 10 / (ms * 1e-3) / 1e9 / hbm_peak})
+    del sts
+    sts = states(capi.SF_FP64)
+    z4p = [s_ for s_ in sts if s_.system == capi.SF_Z4]
+    wvp = [s_ for s_ in sts if s_.system == capi.SF_WAVE]
+
+    def per_patch_step():
+        h = torch.cuda.current_stream().cuda_stream
+        for stg in range(4):
+            capi.sf_substep(z4p[0].prm, [s_.stage_patch(stg) for s_ in z4p], stg, h)
+            capi.sf_substep(wvp[0].prm, [s_.stage_patch(stg) for s_ in wvp], stg, h)
+
+    ms = _events_time(per_patch_step, 3, 1)
+    pp_rate = cells * 4 * 3 / (ms * 1e-3)
+    out.append({"workload": "amr_512_patches_fp64_per_patch_launches", "value": pp_rate,
+                "unit": UNIT, "ms_per_step": ms / 3,
+                "batched_fp32_speedup": batch_rate / pp_rate})
+    return out
+
+
+def _adjoint_rows() -> list[dict]:
+    import torch
+    from paper_1806_04182_gb300 import adjoint, capi, inputs
+    out = []
+    # adjoint: 128^3 wave, 200 RK4 steps, 64 observers, checkpoints every 20 steps
+    for prec, name in ((capi.SF_FP64, "fp64"), (capi.SF_FP32_BULK, "fp32")):
+        n = (128, 128, 128)
+        U0, dx = inputs.wave_plane(n, seed=0)
+        dt = 0.25 * dx[0]
+        dtype = torch.float64 if prec == capi.SF_FP64 else torch.float32
+        phi0 = torch.tensor(U0[0], device="cuda", dtype=dtype)
+        Pi0 = torch.tensor(U0[1], device="cuda", dtype=dtype)
+        obs = torch.tensor(inputs.observers(n, 64, seed=1), device="cuda")
+        bump = torch.tensor(1e-3 * inputs.smooth_bump(n, seed=2), device="cuda", dtype=dtype)
+        ref = adjoint.observe(phi0 + bump, Pi0, obs, dx, dt, 200, precision=prec)
+
+        def grad_eval():
+            p = phi0.clone().requires_grad_(True)
+            q = Pi0.clone().requires_grad_(True)
+            adjoint.misfit(p, q, obs, ref, dx, dt, 200, precision=prec, checkpoint_every=20).backward()
+
+        ms = _events_time(grad_eval, 1, 1)
+        out.append({"workload": f"wave_adjoint_128cubed_200steps_{name}", "value": 1e3 / ms,
+                    "unit": "gradients/s", "ms_per_gradient": ms,
+                    "cell_updates_per_s": 128 ** 3 * 4 * 200 * 3 / (ms * 1e-3),
+                    "note": "forward + recompute + adjoint = 3 x 200 RK4 steps"})
+    return out
+
+
 # ---------------------------------------------------------------- oracle arm
 def cpu_baseline(seconds: float = 15.0, nz: int = 4) -> dict:
     """The FP64 oracle as it stands (OpenMP over z) on a bounded sample of the
@@ -387,11 +537,25 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--suite", action="store_true",
+                    help="time every workload row (one JSON line each) instead of the headline")
+    ap.add_argument("--rows", default=None,
+                    help="comma-separated subset of wave,mhd,batch,adjoint for --suite")
     ap.add_argument("--only", choices=["fp32dw", "fp32", "fp64"], default=None,
                     help="time one precision only (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.suite:
+        import torch
+        from paper_1806_04182_gb300 import build as sfbuild
+        sfbuild.build()
+        torch.cuda.set_device(0)
+        pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        hbm = json.load(open(pk)).get("hbm_gbs", 6800.0) if os.path.exists(pk) else 6800.0
+        for row in suite(args, hbm):
+            print(json.dumps(row), flush=True)
+        return
     line = reference_arm(args) if args.impl == "reference" else gpu_arm(args)
     if line is not None:
         print(json.dumps(line), flush=True)

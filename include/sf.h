@@ -59,7 +59,11 @@ typedef enum { SF_WAVE = 0, SF_MHD = 1, SF_Z4 = 2 } sf_system;
  * transformations, relative error a few 2^-48) on the FP32 pipe instead of
  * the FP64 pipe, which on GB300 runs at ~1/58 of the FP32 rate.  The paper
  * has no counterpart; it is this library's way to keep FP64-class islands
- * cheap on this GPU. */
+ * cheap on this GPU.
+ * In both FP32 modes the SF_Z4 arrays store chi, gt_xx, gt_yy, gt_zz and alpha
+ * MINUS their flat-space value 1 (fields 0, 1, 4, 6 and 18), so that small
+ * deviations from flat space (noise of 1e-10, say) survive float storage;
+ * all other fields, and every field in SF_FP64, are stored as they are. */
 typedef enum { SF_FP64 = 0, SF_FP32_BULK = 1, SF_FP32_BULK_DW = 2 } sf_precision;
 
 typedef enum { SF_RK4 = 0, SF_SSPRK3 = 1 } sf_rk;
@@ -111,6 +115,10 @@ typedef struct {
   void* acc;         /* in/out: RK4 accumulator (unused by SSP-RK3) */
   void* u_next;      /* out: next stage input, or U^{n+1} after the last stage */
   void* kahan;       /* in/out: FP32_BULK compensation (NULL otherwise) */
+  double* cfl_rate;  /* SF_MHD only, optional (NULL = off): device double that the
+                        LAST stage sets to max over interior points and directions
+                        d of (|v_d| + c_fast,d)/dx_d of u_next (Sec. II.A footnote),
+                        so the next step's dt = cfl / rate needs no extra sweep */
 } sf_patch;
 
 typedef struct {

@@ -71,6 +71,7 @@ class sf_patch(ctypes.Structure):
         ("acc", ctypes.c_void_p),
         ("u_next", ctypes.c_void_p),
         ("kahan", ctypes.c_void_p),
+        ("cfl_rate", ctypes.c_void_p),
     ]
 
 

@@ -36,7 +36,7 @@ struct Item {
 };
 
 template <typename T, typename H>
-__global__ void __launch_bounds__(128) batch_stage_kernel(const PatchArgs<T>* __restrict__ pa,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) batch_stage_kernel(const PatchArgs<T>* __restrict__ pa,
                                                           const int* __restrict__ psys,
                                                           const int2* __restrict__ pshape,
                                                           const Item* __restrict__ items, int nitems,
@@ -62,8 +62,9 @@ __global__ void __launch_bounds__(128) batch_stage_kernel(const PatchArgs<T>* __
       const long long c = (long long)(k + g) * a.sz + (long long)(j + g) * a.sy + (i + g);
       if (system == SF_Z4) {
         const T* __restrict__ u = a.us + c;
-        z4_cell<T, H, 0, 0>(a, zc, u, [&](int f, T r) {
-          stage_write(a, s, f, c, i, j, k, __ldg(u + f * a.sf), r);
+        const Images im = ghost_images(a, s, i, j, k);
+        z4_cell<T, H, 0, 0>(a, zc, u, [&](int f, T r, T centre) {
+          write_field(a, s, im, f, c, i, j, k, centre, r);
         });
       } else {
         T v[5], r[5];

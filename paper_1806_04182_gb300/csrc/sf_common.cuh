@@ -30,6 +30,7 @@ struct PatchArgs {
   T* acc;
   T* nx;                     // next stage / U^{n+1}, or the RHS output (unghosted)
   T* kh;
+  double* rate;  // MHD: max signal rate of u_next (last stage only), or nullptr
   // precomputed coefficients
   T i12h[3];    // 1 / (12 dx_d)
   T i12h2[3];   // 1 / (12 dx_d^2)
@@ -151,6 +152,79 @@ __device__ __forceinline__ void stage_write(const PatchArgs<T>& a, const StageAr
   }
 }
 
+// ------------------------------------------------------------ split stage write
+// The same stage combination as stage_write, for kernels that compute the
+// periodic ghost images of a point once (ghost_images) and reuse them for
+// every field (write_field).
+struct Images {
+  int n;
+  int off[7];  // element offsets of the periodic images (|off| < 2^31 is checked on the host)
+};
+
+template <typename T>
+__device__ __forceinline__ Images ghost_images(const PatchArgs<T>& a, const StageArgs& s, int i,
+                                               int j, int k) {
+  Images im;
+  im.n = 0;
+  if (!s.ghosts || s.mode == 1) return im;
+  const int g = a.g;
+  int xs[3] = {0, 0, 0}, ys[3] = {0, 0, 0}, zs[3] = {0, 0, 0};
+  int nxs = 1, nys = 1, nzs = 1;
+  if (i < g) xs[nxs++] = a.n[0];
+  if (i >= a.n[0] - g) xs[nxs++] = -a.n[0];
+  if (j < g) ys[nys++] = a.n[1];
+  if (j >= a.n[1] - g) ys[nys++] = -a.n[1];
+  if (k < g) zs[nzs++] = a.n[2];
+  if (k >= a.n[2] - g) zs[nzs++] = -a.n[2];
+  if (nxs + nys + nzs == 3) return im;
+  for (int p = 0; p < nzs; ++p)
+    for (int q = 0; q < nys; ++q)
+      for (int w = 0; w < nxs; ++w) {
+        if (p == 0 && q == 0 && w == 0) continue;
+        im.off[im.n++] = (int)(zs[p] * a.sz + ys[q] * a.sy + xs[w]);
+      }
+  return im;
+}
+
+// Returns the value written to u_next (r itself in RHS-only mode).
+template <typename T>
+__device__ __forceinline__ T write_field(const PatchArgs<T>& a, const StageArgs& s,
+                                         const Images& im, int f, long long c, int i, int j,
+                                         int k, T centre, T r) {
+  if (s.mode == 1) {
+    a.nx[f * a.ninterior + ((long long)k * a.n[1] + j) * a.n[0] + i] = r;
+    return r;
+  }
+  const long long o = f * a.sf + c;
+  const T un = s.un_alias ? centre : a.un[o];
+  T out;
+  if (s.rk == SF_RK4) {
+    if (s.stage == 0) {
+      a.acc[o] = (s.kahan ? T(0) : un) + a.c_acc * r;
+      out = un + a.c_next * r;
+    } else if (s.stage < 3) {
+      a.acc[o] = a.acc[o] + a.c_acc * r;
+      out = un + a.c_next * r;
+    } else if (!s.kahan) {
+      out = a.acc[o] + a.c_next * r;
+    } else {
+      const T inc = a.acc[o] + a.c_next * r;
+      const T y = inc - a.kh[o];
+      const T t = un + y;
+      a.kh[o] = (t - un) - y;
+      out = t;
+    }
+  } else {
+    if (s.stage == 0) out = un + a.dt * r;
+    else if (s.stage == 1) out = T(0.75) * un + T(0.25) * (centre + a.dt * r);
+    else out = un * T(1.0 / 3.0) + T(2.0 / 3.0) * (centre + a.dt * r);
+  }
+  a.nx[o] = out;
+  if (s.check_finite && !finite_(out)) atomicOr(s.status, ST_NONFINITE);
+  for (int q = 0; q < im.n; ++q) a.nx[o + im.off[q]] = out;
+  return out;
+}
+
 // ------------------------------------------------------------ launch plumbing
 struct Launch {
   dim3 grid, block;
@@ -172,6 +246,7 @@ PatchArgs<T> make_args(const sf_params& prm, const sf_patch& p, int stage, int n
   a.acc = static_cast<T*>(p.acc);
   a.nx = static_cast<T*>(rhs_out ? rhs_out : p.u_next);
   a.kh = static_cast<T*>(p.kahan);
+  a.rate = nullptr;
   for (int d = 0; d < 3; ++d) {
     a.i12h[d] = T(1.0 / (12.0 * p.dx[d]));
     a.i12h2[d] = T(1.0 / (12.0 * p.dx[d] * p.dx[d]));

@@ -32,8 +32,13 @@ __global__ void __launch_bounds__(256) diag_kernel(const T* __restrict__ u0, int
       }
       acc[0] += e * hx * hy * hz;
     } else if (system == SF_Z4) {
+      // float arrays hold chi, gt_ii and alpha minus 1 (flat-space offset)
+      const double off = sizeof(T) == 4 ? 1.0 : 0.0;
       double gt[6], At[6];
-      for (int q = 0; q < 6; ++q) { gt[q] = double(p[(1 + q) * F]); At[q] = double(p[(8 + q) * F]); }
+      for (int q = 0; q < 6; ++q) {
+        gt[q] = double(p[(1 + q) * F]) + ((q == 0 || q == 3 || q == 5) ? off : 0.0);
+        At[q] = double(p[(8 + q) * F]);
+      }
       const double c00 = gt[3] * gt[5] - gt[4] * gt[4], c01 = gt[2] * gt[4] - gt[1] * gt[5],
                    c02 = gt[1] * gt[4] - gt[2] * gt[3], c11 = gt[0] * gt[5] - gt[2] * gt[2],
                    c12 = gt[1] * gt[2] - gt[0] * gt[4], c22 = gt[0] * gt[3] - gt[1] * gt[1];
@@ -47,7 +52,7 @@ __global__ void __launch_bounds__(256) diag_kernel(const T* __restrict__ u0, int
           const long long s = st[d];
           dg[q][d] = (double(c[-2 * s]) - double(c[2 * s]) + 8.0 * (double(c[s]) - double(c[-s]))) * ih[d];
         }
-      const double chi = double(p[0]);
+      const double chi = double(p[0]) + off;
       double Z2 = 0.0;
       for (int a = 0; a < 3; ++a) {
         double Gt = 0.0;

@@ -123,29 +123,90 @@ __device__ __forceinline__ void face_flux(const T* __restrict__ p, long long F, 
   for (int f = 0; f < 8; ++f) Fout[f] = T(0.5) * (FL[f] + FR[f] - S * (UR[f] - UL[f]));
 }
 
+// Stage kernel.  Each interface flux is evaluated once: a block of 32 x 8
+// threads owns 31 x 7 output cells of a plane; thread (tx, ty) evaluates the
+// x-face at i - 1/2 and the y-face at j - 1/2 of its column, so the +1/2
+// faces of the output cells come from lane tx + 1 (warp shuffle) and row
+// ty + 1 (shared memory).  Each thread marches MZ planes in z and carries the
+// z-face below the current plane in registers.  Faces are only evaluated at
+// positions 0..n along their direction, whose WENO stencils (cells p-3..p+2)
+// lie inside the 3-point ghost zone.
+constexpr int MX = 32, MY = 8, MZ = 16;
+
 template <typename T>
-__global__ void __launch_bounds__(128) mhd_stage_kernel(PatchArgs<T> a, StageArgs s, MhdCoef<T> mc) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  if (i >= a.n[0] || j >= a.n[1]) return;
+__global__ void __launch_bounds__(MX * MY) mhd_stage_kernel(PatchArgs<T> a, StageArgs s,
+                                                           MhdCoef<T> mc) {
+  __shared__ T fy[MY][MX][8];
+  __shared__ double s_rate[MX * MY / 32];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  double rate = 0.0;  // max signal rate of this thread's outputs (fused CFL reduction)
+  const int i = blockIdx.x * (MX - 1) + tx;
+  const int j = blockIdx.y * (MY - 1) + ty;
+  const int k0 = blockIdx.z * MZ;
+  const int k1 = min(k0 + MZ, a.n[2]);
   const int g = a.g;
-  const long long c = (long long)(k + g) * a.sz + (long long)(j + g) * a.sy + (i + g);
-  const T* __restrict__ u = a.us + c;
-  const long long st[3] = {1, a.sy, a.sz};
-  T r[8];
+  const bool out = tx < MX - 1 && ty < MY - 1 && i < a.n[0] && j < a.n[1];
+  const bool xface = i <= a.n[0] && j < a.n[1];
+  const bool yface = j <= a.n[1] && i < a.n[0];
+  auto at = [&](int ii, int jj, int kk) {
+    return a.us + (long long)(kk + g) * a.sz + (long long)(jj + g) * a.sy + (ii + g);
+  };
+  T Fzm[8];
+  if (out) face_flux(at(i, j, k0 - 1), a.sf, a.sz, 2, mc, Fzm);
+  for (int k = k0; k < k1; ++k) {
+    T Fx[8], Fy[8], Fz[8];
+    if (xface) {
+      face_flux(at(i - 1, j, k), a.sf, 1, 0, mc, Fx);
+    } else {
 #pragma unroll
-  for (int f = 0; f < 8; ++f) r[f] = T(0);
-#pragma unroll 1
-  for (int d = 0; d < 3; ++d) {
-    T Fp[8], Fm[8];
-    face_flux(u, a.sf, st[d], d, mc, Fp);
-    face_flux(u - st[d], a.sf, st[d], d, mc, Fm);
+      for (int f = 0; f < 8; ++f) Fx[f] = T(0);
+    }
+    if (yface) {
+      face_flux(at(i, j - 1, k), a.sf, a.sy, 1, mc, Fy);
+    } else {
 #pragma unroll
-    for (int f = 0; f < 8; ++f) r[f] -= (Fp[f] - Fm[f]) * mc.idx[d];
+      for (int f = 0; f < 8; ++f) Fy[f] = T(0);
+    }
+#pragma unroll
+    for (int f = 0; f < 8; ++f) fy[ty][tx][f] = Fy[f];
+    if (out) face_flux(at(i, j, k), a.sf, a.sz, 2, mc, Fz);
+    T Fxp[8];
+#pragma unroll
+    for (int f = 0; f < 8; ++f) Fxp[f] = __shfl_down_sync(0xffffffffu, Fx[f], 1);
+    __syncthreads();
+    if (out) {
+      const long long c = (long long)(k + g) * a.sz + (long long)(j + g) * a.sy + (i + g);
+      const Images im = ghost_images(a, s, i, j, k);
+      T q[8];
+#pragma unroll
+      for (int f = 0; f < 8; ++f) {
+        T r = T(0);
+        r -= (Fxp[f] - Fx[f]) * mc.idx[0];
+        r -= (fy[ty + 1][tx][f] - Fy[f]) * mc.idx[1];
+        r -= (Fz[f] - Fzm[f]) * mc.idx[2];
+        q[f] = write_field(a, s, im, f, c, i, j, k, __ldg(a.us + f * a.sf + c), r);
+        Fzm[f] = Fz[f];
+      }
+      if (a.rate) {
+        T Fd[8];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) rate = fmax(rate, double(flux_speed(q, d, mc, Fd) * mc.idx[d]));
+      }
+    }
+    __syncthreads();
   }
+  if (a.rate) {  // block max, then one atomic per block (non-negative doubles order as their bits)
 #pragma unroll
-  for (int f = 0; f < 8; ++f) stage_write(a, s, f, c, i, j, k, __ldg(u + f * a.sf), r[f]);
+    for (int o = 16; o > 0; o >>= 1) rate = fmax(rate, __shfl_down_sync(0xffffffffu, rate, o));
+    const int lin = ty * MX + tx;
+    if ((lin & 31) == 0) s_rate[lin >> 5] = rate;
+    __syncthreads();
+    if (lin == 0) {
+      double m = 0.0;
+      for (int w = 0; w < MX * MY / 32; ++w) m = fmax(m, s_rate[w]);
+      atomicMax(reinterpret_cast<unsigned long long*>(a.rate), (unsigned long long)__double_as_longlong(m));
+    }
+  }
 }
 
 // CFL rate: max over cells and d of (|v_d| + c_fast,d) / dx_d
@@ -200,8 +261,14 @@ template <typename T>
 static sf_status launch(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                         void* rhs_out, cudaStream_t st) {
   PatchArgs<T> a = make_args<T>(prm, p, stage, 8, rhs_out);
-  dim3 block(32, 4, 1);
-  dim3 grid((p.n[0] + 31) / 32, (p.n[1] + 3) / 4, p.n[2]);
+  const int last = prm.rk == SF_RK4 ? 3 : 2;
+  if (p.cfl_rate && !rhs_out && stage == last) {
+    if (cudaMemsetAsync(p.cfl_rate, 0, sizeof(double), st) != cudaSuccess)
+      return set_error(SF_ECUDA, "reset of cfl_rate failed");
+    a.rate = p.cfl_rate;
+  }
+  dim3 block(MX, MY, 1);
+  dim3 grid((p.n[0] + MX - 2) / (MX - 1), (p.n[1] + MY - 2) / (MY - 1), (p.n[2] + MZ - 1) / MZ);
   mhd_stage_kernel<T><<<grid, block, 0, st>>>(a, s, coef<T>(prm, p));
   return after_launch("mhd_stage_kernel");
 }

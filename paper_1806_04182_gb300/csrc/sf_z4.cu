@@ -7,8 +7,12 @@
 
 namespace sf {
 
+// 128 threads and at least 3 CTAs per SM for the float kernels (<= 168
+// registers): on the 96^3 benchmark patch this measured faster than 2 CTAs
+// (255 registers) and than 4+ CTAs (128 registers or fewer, with spills).
 template <typename T, typename H, int SY, int SZ>
-__global__ void __launch_bounds__(128) z4_stage_kernel(PatchArgs<T> a, StageArgs s, Z4Coef<T> zc) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2)
+    z4_stage_kernel(PatchArgs<T> a, StageArgs s, Z4Coef<T> zc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
@@ -18,8 +22,9 @@ __global__ void __launch_bounds__(128) z4_stage_kernel(PatchArgs<T> a, StageArgs
   const long long sz = SZ ? (long long)SZ : a.sz;
   const long long c = (long long)(k + g) * sz + (long long)(j + g) * sy + (i + g);
   const T* __restrict__ u = a.us + c;
-  z4_cell<T, H, SY, SZ>(a, zc, u, [&](int f, T r) {
-    stage_write(a, s, f, c, i, j, k, __ldg(u + f * a.sf), r);
+  const Images im = ghost_images(a, s, i, j, k);
+  z4_cell<T, H, SY, SZ>(a, zc, u, [&](int f, T r, T centre) {
+    write_field(a, s, im, f, c, i, j, k, centre, r);
   });
 }
 

@@ -4,17 +4,22 @@
 // Field order: 0 chi | 1-6 gt_xx,xy,xz,yy,yz,zz | 7 Khat | 8-13 At_ij |
 // 14-16 Gammahat^i | 17 Theta | 18 alpha | 19-21 beta^i | 22-24 B^i
 //
-// Derivatives come straight from the ghosted SoA arrays (neighbours hit in
-// L1/L2).  Each field's final value is handed to `out(f, rhs)` as soon as it
-// is complete, and quantities are formed in the order they are consumed, so
-// the live set stays small:
-//   islands (det, inverse, ln det) -> shift derivatives -> metric derivatives,
-//   d/dt gt, Christoffels -> Ricci -> D D alpha -> d/dt A~ -> chi, Khat,
-//   Theta -> Gammahat, alpha, beta, B.
+// Each field's 19-point cross (centre and +-1..3 along x, y, z) is read once
+// and gives its three first derivatives D_i, its KO term and, for the fields
+// that need them, its pure second derivatives D_ii (Sec. II.B.1); mixed
+// derivatives D_ij = D_j(D_i) read their 16 off-axis points.  Quantities are
+// formed in the order they are consumed and every field is handed to
+// `out(f, rhs, centre)` as soon as its right-hand side is complete:
+//   islands (det, inverse, ln det) -> shift -> metric + d/dt gt ->
+//   Christoffels -> chi, alpha -> Ricci -> D D alpha -> Khat, Theta ->
+//   A~ -> Gammahat, beta, B.
 // T is the bulk (storage + stencil) type; H the island type (double, or the
-// double-word float pair of sf_dw.cuh).  SY, SZ > 0 fix the y/z element
-// strides at compile time, so every stencil read is an immediate offset
-// from a per-field base pointer; 0 means runtime strides.
+// double-word float pair of sf_dw.cuh).  With T = float the arrays store
+// chi - 1, gt_xx - 1, gt_yy - 1, gt_zz - 1 and alpha - 1, so that values
+// near flat space keep their small deviations (e.g. 1e-10 noise) in float.
+// SY, SZ > 0 fix the y/z element strides at compile time, so every stencil
+// read is an immediate offset from a per-field base pointer; 0 means
+// runtime strides.
 #pragma once
 #include "sf_common.cuh"
 #include "sf_dw.cuh"
@@ -33,6 +38,14 @@ __host__ __device__ constexpr int S(int a, int b) {
                 : ((a + b) == 1 ? 1 : ((a + b) == 2 ? 2 : 4));
 }
 
+template <typename T>
+struct Cross {
+  T c;      // centre value
+  T d[3];   // D_x, D_y, D_z
+  T dd[3];  // D_xx, D_yy, D_zz (when requested)
+  T ko;     // sum_d sigma/(64 dx_d) delta^6_d
+};
+
 template <typename T, typename H, int SY, int SZ, typename Out>
 __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& zc,
                                         const T* __restrict__ u, Out&& out) {
@@ -43,33 +56,61 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
   const long long st[3] = {1, sy, sz};
   auto U = [&](int f) { return u + f * F; };
   auto c0 = [&](int f) { return __ldg(U(f)); };
-  auto D = [&](int f, int d) { return d1(U(f), st[d], a.i12h[d]); };
-  auto KO = [&](int f) { return ko_all(U(f), sy, sz, c0(f), a.ko); };
-  auto DD = [&](int f, int m, int n) -> T {
-    if (m == n) return d2(U(f), st[m], c0(f), a.i12h2[m]);
+  // 19-point cross of field f: first derivatives, KO, optional D_ii
+  auto cross = [&](int f, bool second) {
+    const T* p = U(f);
+    Cross<T> x;
+    x.c = __ldg(p);
+    x.ko = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const long long s = st[d];
+      const T m1 = __ldg(p - s), p1 = __ldg(p + s);
+      const T m2 = __ldg(p - 2 * s), p2 = __ldg(p + 2 * s);
+      const T m3 = __ldg(p - 3 * s), p3 = __ldg(p + 3 * s);
+      x.d[d] = ((m2 - p2) + T(8) * (p1 - m1)) * a.i12h[d];
+      x.dd[d] = second ? (T(16) * (m1 + p1) - (m2 + p2) - T(30) * x.c) * a.i12h2[d] : T(0);
+      x.ko += a.ko[d] * ((m3 + p3) - T(6) * (m2 + p2) + T(15) * (m1 + p1) - T(20) * x.c);
+    }
+    return x;
+  };
+  auto MIX = [&](int f, int m, int n) -> T {
     const int pi = (m == 0 && n == 1) ? 0 : ((m == 0 && n == 2) ? 1 : 2);
     return dmix(U(f), st[m], st[n], a.i144hh[pi]);
   };
-  auto emit = [&](int f, T r) { out(f, r + KO(f)); };
 
-  const T chi = c0(0), Kh = c0(7), Th = c0(17), al = c0(18);
+  // float storage holds chi, gt_xx, gt_yy, gt_zz and alpha minus their flat
+  // value 1 (every stencil's weights sum to zero, so derivatives are the
+  // same; only the point values used in the algebra get the 1 back)
+  const T off = sizeof(T) == 4 ? T(1) : T(0);
+  const T chi = c0(0) + off, Kh = c0(7), Th = c0(17), al = c0(18) + off;
   T gt[6], At[6];
 #pragma unroll
-  for (int q = 0; q < 6; ++q) { gt[q] = c0(1 + q); At[q] = c0(8 + q); }
+  for (int q = 0; q < 6; ++q) {
+    gt[q] = c0(1 + q) + ((q == 0 || q == 3 || q == 5) ? off : T(0));
+    At[q] = c0(8 + q);
+  }
   T be[3], Gh[3];
 #pragma unroll
   for (int p = 0; p < 3; ++p) { be[p] = c0(19 + p); Gh[p] = c0(14 + p); }
   auto advk = [&](const T* dd) { return be[0] * dd[0] + be[1] * dd[1] + be[2] * dd[2]; };
-  auto adv = [&](int f) { return be[0] * D(f, 0) + be[1] * D(f, 1) + be[2] * D(f, 2); };
+  const T kz = zc.kappa_z, kc = zc.kappa_c;
 
-  // ---- islands: determinant, inverse and ln det of the conformal metric
-  const H c00 = I::sub(I::prod(gt[3], gt[5]), I::prod(gt[4], gt[4]));
-  const H c01 = I::sub(I::prod(gt[2], gt[4]), I::prod(gt[1], gt[5]));
-  const H c02 = I::sub(I::prod(gt[1], gt[4]), I::prod(gt[2], gt[3]));
-  const H c11 = I::sub(I::prod(gt[0], gt[5]), I::prod(gt[2], gt[2]));
-  const H c12 = I::sub(I::prod(gt[1], gt[2]), I::prod(gt[0], gt[4]));
-  const H c22 = I::sub(I::prod(gt[0], gt[3]), I::prod(gt[1], gt[1]));
-  const H det = I::add(I::add(I::mulf(c00, gt[0]), I::mulf(c01, gt[1])), I::mulf(c02, gt[2]));
+  // ---- islands: determinant, inverse and ln det of the conformal metric,
+  // from the exact stored value + offset (not its rounding to the bulk type)
+  H gH[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const T sq = c0(1 + q);
+    gH[q] = (q == 0 || q == 3 || q == 5) ? I::add(I::from(sq), I::from(off)) : I::from(sq);
+  }
+  const H c00 = I::sub(I::mul(gH[3], gH[5]), I::mul(gH[4], gH[4]));
+  const H c01 = I::sub(I::mul(gH[2], gH[4]), I::mul(gH[1], gH[5]));
+  const H c02 = I::sub(I::mul(gH[1], gH[4]), I::mul(gH[2], gH[3]));
+  const H c11 = I::sub(I::mul(gH[0], gH[5]), I::mul(gH[2], gH[2]));
+  const H c12 = I::sub(I::mul(gH[1], gH[2]), I::mul(gH[0], gH[4]));
+  const H c22 = I::sub(I::mul(gH[0], gH[3]), I::mul(gH[1], gH[1]));
+  const H det = I::add(I::add(I::mul(c00, gH[0]), I::mul(c01, gH[1])), I::mul(c02, gH[2]));
   const H idet = I::recip(det);
   const H igH[6] = {I::mul(c00, idet), I::mul(c01, idet), I::mul(c02, idet),
                     I::mul(c11, idet), I::mul(c12, idet), I::mul(c22, idet)};
@@ -78,7 +119,7 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
 #pragma unroll
   for (int q = 0; q < 6; ++q) ig[q] = I::template to<T>(igH[q]);
   const T w[6] = {ig[0], T(2) * ig[1], T(2) * ig[2], ig[3], T(2) * ig[4], ig[5]};
-  // island trace: gt^{ij} X_ij with off-diagonal entries counted twice
+  // island trace gt^{ij} X_ij (off-diagonal entries counted twice)
   auto trace_isl = [&](const T* X) {
     const H d = I::add(I::add(I::mulf(igH[0], X[0]), I::mulf(igH[3], X[3])), I::mulf(igH[5], X[5]));
     const H o = I::add(I::add(I::mulf(igH[1], X[1]), I::mulf(igH[2], X[2])), I::mulf(igH[4], X[4]));
@@ -91,34 +132,61 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
   const H trAH = trace_isl(At);
   const T trA = I::template to<T>(trAH);
 
-  // ---- shift derivatives
-  T dbe[3][3];
+  // ---- shift: first derivatives, gt^{mn} d_m d_n beta^c and d_b d_k beta^k
+  T dbe[3][3], koBe[3];
+  T s2[3] = {T(0), T(0), T(0)}, ddiv[3] = {T(0), T(0), T(0)};
 #pragma unroll
-  for (int p = 0; p < 3; ++p)
+  for (int c = 0; c < 3; ++c) {
+    const Cross<T> x = cross(19 + c, true);
+    koBe[c] = x.ko;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) dbe[p][d] = D(19 + p, d);  // partial_d beta^p
+    for (int d = 0; d < 3; ++d) {
+      dbe[c][d] = x.d[d];  // partial_d beta^c
+      s2[c] += w[S(d, d)] * x.dd[d];
+    }
+    ddiv[c] += x.dd[c];
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int n = m + 1; n < 3; ++n) {
+        const T y = MIX(19 + c, m, n);
+        s2[c] += w[S(m, n)] * y;
+        if (n == c) ddiv[m] += y;
+        if (m == c) ddiv[n] += y;
+      }
+  }
   const T divbe = dbe[0][0] + dbe[1][1] + dbe[2][2];
-  const T kz = zc.kappa_z, kc = zc.kappa_c;
 
-  // ---- metric derivatives: d/dt gt (Eq. syseq1) and Christoffels
+  // ---- conformal metric: derivatives, gt^{mn} d_m d_n gt_q, d/dt gt (Eq. syseq1)
   T Gl[3][6];  // Gamma~_{a bc}, first index lowered
+  T t1[6];
   {
     T dgt[6][3];
-#pragma unroll
-    for (int q = 0; q < 6; ++q)
-#pragma unroll
-      for (int d = 0; d < 3; ++d) dgt[q][d] = D(1 + q, d);
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll
       for (int b = p; b < 3; ++b) {
         const int q = S(p, b);
+        const Cross<T> x = cross(1 + q, true);
+        T s1 = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          dgt[q][d] = x.d[d];
+          s1 += w[S(d, d)] * x.dd[d];
+        }
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+          for (int n = m + 1; n < 3; ++n) s1 += w[S(m, n)] * MIX(1 + q, m, n);
+        t1[q] = s1;
         T s = T(0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) s += gt[S(p, c)] * dbe[c][b] + gt[S(c, b)] * dbe[c][p];
         const T AtTF = tf_isl(At[q], gt[q], trAH);
-        emit(1 + q, advk(dgt[q]) + s - T(2.0 / 3.0) * gt[q] * divbe - T(2) * al * AtTF -
-                        kc * T(1.0 / 3.0) * al * gt[q] * lndet);
+        out(1 + q,
+            advk(x.d) + s - T(2.0 / 3.0) * gt[q] * divbe - T(2) * al * AtTF -
+                kc * T(1.0 / 3.0) * al * gt[q] * lndet + x.ko,
+            x.c);
       }
 #pragma unroll
     for (int p = 0; p < 3; ++p)
@@ -142,28 +210,43 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
     for (int q = 0; q < 6; ++q) s += w[q] * Gu[p][q];
     Z[p] = T(0.5) * chi * (Gh[p] - s);  // Z^i = chi/2 (Gammahat^i - Gamma~^i)
   }
+  const T Kt = Kh + T(2) * Th;
+
+  // ---- chi and alpha: derivatives; their right-hand sides are complete here
+  T dchi[3], ddchi[6], dal[3], ddal[6];
+  {
+    const Cross<T> x = cross(0, true);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) { dchi[d] = x.d[d]; ddchi[S(d, d)] = x.dd[d]; }
+    ddchi[1] = MIX(0, 0, 1);
+    ddchi[2] = MIX(0, 0, 2);
+    ddchi[4] = MIX(0, 1, 2);
+    out(0, advk(dchi) + T(2.0 / 3.0) * chi * (al * Kt - divbe) + x.ko, x.c);
+  }
+  const T ialpha = T(1) / al;
+  {
+    const Cross<T> x = cross(18, true);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) { dal[d] = x.d[d]; ddal[S(d, d)] = x.dd[d]; }
+    ddal[1] = MIX(18, 0, 1);
+    ddal[2] = MIX(18, 0, 2);
+    ddal[4] = MIX(18, 1, 2);
+    const T fsl = zc.slicing == 0 ? T(2) * ialpha : T(1);
+    out(18, advk(dal) - al * al * fsl * Kh + x.ko, x.c);
+  }
 
   // ---- Ricci tensor Rhat_ab + Rchi_ab
-  T dchi[3], dal[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) { dchi[d] = D(0, d); dal[d] = D(18, d); }
   const T ichi = T(1) / chi;
   T Rt[6];
+  T dGh[3][3], koGh[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const Cross<T> x = cross(14 + c, false);
+    koGh[c] = x.ko;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dGh[c][d] = x.d[d];  // partial_d Gammahat^c
+  }
   {
-    T ddchi[6], t1[6];
-#pragma unroll
-    for (int m = 0; m < 3; ++m)
-#pragma unroll
-      for (int n = m; n < 3; ++n) ddchi[S(m, n)] = DD(0, m, n);
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      T s = T(0);
-#pragma unroll
-      for (int m = 0; m < 3; ++m)
-#pragma unroll
-        for (int n = m; n < 3; ++n) s += w[S(m, n)] * DD(1 + q, m, n);
-      t1[q] = s;  // gt^{mn} d_m d_n gt_q
-    }
     T t4[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) t4[q] = T(0);
@@ -204,8 +287,7 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
         T t2 = T(0), t3 = T(0), sG = T(0), sZ = T(0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const T dGcb = D(14 + c, b), dGcp = D(14 + c, p);
-          t2 += gt[S(c, p)] * dGcb + gt[S(c, b)] * dGcp;
+          t2 += gt[S(c, p)] * dGh[c][b] + gt[S(c, b)] * dGh[c][p];
           t3 += Gh[c] * (Gl[p][S(b, c)] + Gl[b][S(p, c)]);
           sG += Gu[c][q] * dchi[c];
           sZ += Z[c] * (gt[S(c, p)] * dchi[b] + gt[S(c, b)] * dchi[p]);
@@ -237,7 +319,7 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
       for (int b = p; b < 3; ++b) {
         const int q = S(p, b);
         const T sG = Gu[0][q] * dal[0] + Gu[1][q] * dal[1] + Gu[2][q] * dal[2];
-        const T DDal = DD(18, p, b) - sG +
+        const T DDal = ddal[q] - sG +
                        T(0.5) * ichi * (dal[p] * dchi[b] + dal[b] * dchi[p] - gt[q] * gdadc);
         LapAl += w[q] * DDal;
         M[q] = al * Rt[q] - DDal;
@@ -245,7 +327,7 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
     LapAl *= chi;
   }
 
-  // ---- A~ contractions and d/dt A~_ab (trace removal of M in the island type)
+  // ---- A~ contractions
   T Aud[3][3];  // A~^a_b = gt^{ac} A~_cb
 #pragma unroll
   for (int p = 0; p < 3; ++p)
@@ -261,6 +343,29 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
   T AA = T(0);
 #pragma unroll
   for (int q = 0; q < 6; ++q) AA += ((q == 0 || q == 3 || q == 5) ? T(1) : T(2)) * At[q] * Auu[q];
+
+  // ---- Khat and Theta
+  const T Zdal = Z[0] * dal[0] + Z[1] * dal[1] + Z[2] * dal[2];
+  T dKh[3], dTh[3];
+  {
+    const Cross<T> x = cross(7, false);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dKh[d] = x.d[d];
+    out(7, advk(dKh) - LapAl + al * (T(1.0 / 3.0) * Kt * Kt + AA + kz * Th) + T(2) * Zdal + x.ko,
+        Kh);
+  }
+  {
+    const Cross<T> x = cross(17, false);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dTh[d] = x.d[d];
+    out(17,
+        advk(dTh) +
+            T(0.5) * al * (RZ + T(2.0 / 3.0) * Kh * Kh + T(2.0 / 3.0) * Th * (Kh - T(2) * Th) - AA) -
+            Zdal - T(2) * al * kz * Th + x.ko,
+        Th);
+  }
+
+  // ---- d/dt A~_ab (trace removal of M in the island type)
   {
     const H trM = trace_isl(M);
 #pragma unroll
@@ -268,6 +373,7 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
 #pragma unroll
       for (int b = p; b < 3; ++b) {
         const int q = S(p, b);
+        const Cross<T> x = cross(8 + q, false);
         T s = T(0), AAd = T(0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -275,81 +381,44 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
           AAd += At[S(p, c)] * Aud[c][b];
         }
         const T MTF = tf_isl(M[q], gt[q], trM);
-        emit(8 + q, adv(8 + q) + s - T(2.0 / 3.0) * At[q] * divbe -
-                        kc * T(1.0 / 3.0) * al * gt[q] * trA + chi * MTF +
-                        al * (Kh * At[q] - T(2) * AAd));
+        out(8 + q,
+            advk(x.d) + s - T(2.0 / 3.0) * At[q] * divbe - kc * T(1.0 / 3.0) * al * gt[q] * trA +
+                chi * MTF + al * (Kh * At[q] - T(2) * AAd) + x.ko,
+            x.c);
       }
   }
 
-  // ---- d/dt chi, Khat, Theta
-  const T Kt = Kh + T(2) * Th;
-  const T Zdal = Z[0] * dal[0] + Z[1] * dal[1] + Z[2] * dal[2];
-  emit(0, advk(dchi) + T(2.0 / 3.0) * chi * (al * Kt - divbe));
-  {
-    T dKh[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) dKh[d] = D(7, d);
-    emit(7, advk(dKh) - LapAl + al * (T(1.0 / 3.0) * Kt * Kt + AA + kz * Th) + T(2) * Zdal);
-  }
-  emit(17, adv(17) +
-               T(0.5) * al * (RZ + T(2.0 / 3.0) * Kh * Kh + T(2.0 / 3.0) * Th * (Kh - T(2) * Th) - AA) -
-               Zdal - T(2) * al * kz * Th);
-
-  // ---- d/dt Gammahat^a (Eq. syseq2), gauge (Bona-Masso, Gamma-driver)
-  T s2[3] = {T(0), T(0), T(0)}, ddiv[3] = {T(0), T(0), T(0)};
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int m = 0; m < 3; ++m)
-#pragma unroll
-      for (int n = m; n < 3; ++n) {
-        const T x = DD(19 + c, m, n);  // d_m d_n beta^c
-        s2[c] += w[S(m, n)] * x;
-        if (m == n) {
-          if (m == c) ddiv[c] += x;
-        } else {
-          if (n == c) ddiv[m] += x;
-          if (m == c) ddiv[n] += x;
-        }
-      }
-  const T ialpha = T(1) / al;
+  // ---- d/dt Gammahat^a (Eq. syseq2), shift and B (Gamma-driver)
   T rGh[3];
-  {
-    T dKh[3], dTh[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) { dKh[d] = D(7, d); dTh[d] = D(17, d); }
+  for (int p = 0; p < 3; ++p) {
+    T sb = T(0), s3v = T(0), s4 = T(0), s5 = T(0), s6 = T(0), s7 = T(0), s8 = T(0);
 #pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      T sb = T(0), s3v = T(0), s4 = T(0), s5 = T(0), s6 = T(0), s7 = T(0), s8 = T(0);
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        sb += Gh[b] * dbe[p][b];
-        s3v += ig[S(p, b)] * ddiv[b];
-        s4 += Auu[S(p, b)] * dal[b];
-        s6 += Auu[S(p, b)] * dchi[b];
-        s7 += ig[S(p, b)] * dKh[b];
-        s8 += ig[S(p, b)] * (T(1.0 / 3.0) * dTh[b] + Th * ialpha * dal[b]);
-      }
-#pragma unroll
-      for (int q = 0; q < 6; ++q)
-        s5 += ((q == 0 || q == 3 || q == 5) ? T(1) : T(2)) * Gu[p][q] * Auu[q];
-      rGh[p] = -sb + T(2.0 / 3.0) * Gh[p] * divbe + s2[p] + T(1.0 / 3.0) * s3v - T(2) * s4 +
-               T(2) * al * (s5 - T(1.5) * ichi * s6 - T(2.0 / 3.0) * s7) +
-               T(2) * al * (-s8 - ichi * Z[p] * (kz + T(2.0 / 3.0) * Kt));
-      emit(14 + p, adv(14 + p) + rGh[p]);
+    for (int b = 0; b < 3; ++b) {
+      sb += Gh[b] * dbe[p][b];
+      s3v += ig[S(p, b)] * ddiv[b];
+      s4 += Auu[S(p, b)] * dal[b];
+      s6 += Auu[S(p, b)] * dchi[b];
+      s7 += ig[S(p, b)] * dKh[b];
+      s8 += ig[S(p, b)] * (T(1.0 / 3.0) * dTh[b] + Th * ialpha * dal[b]);
     }
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      s5 += ((q == 0 || q == 3 || q == 5) ? T(1) : T(2)) * Gu[p][q] * Auu[q];
+    rGh[p] = -sb + T(2.0 / 3.0) * Gh[p] * divbe + s2[p] + T(1.0 / 3.0) * s3v - T(2) * s4 +
+             T(2) * al * (s5 - T(1.5) * ichi * s6 - T(2.0 / 3.0) * s7) +
+             T(2) * al * (-s8 - ichi * Z[p] * (kz + T(2.0 / 3.0) * Kt));
+    out(14 + p, advk(dGh[p]) + rGh[p] + koGh[p], Gh[p]);
   }
-  const T fsl = zc.slicing == 0 ? T(2) * ialpha : T(1);
-  emit(18, advk(dal) - al * al * fsl * Kh);
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
     if (zc.shift_frozen) {
-      out(19 + p, T(0));
-      out(22 + p, T(0));
+      out(19 + p, T(0), be[p]);
+      out(22 + p, T(0), c0(22 + p));
     } else {
-      const T Bp = c0(22 + p);
-      emit(19 + p, advk(dbe[p]) + zc.g_shift * Bp);
-      emit(22 + p, adv(22 + p) - zc.eta * Bp + rGh[p]);
+      const Cross<T> x = cross(22 + p, false);
+      out(19 + p, advk(dbe[p]) + zc.g_shift * x.c + koBe[p], be[p]);
+      out(22 + p, advk(x.d) - zc.eta * x.c + rGh[p] + x.ko, x.c);
     }
   }
 }

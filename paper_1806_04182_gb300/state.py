@@ -50,6 +50,7 @@ class PatchState:
         self.D = torch.zeros(self.shape, **kw) if self.prm.rk == capi.SF_RK4 else None
         self.E = (torch.zeros(self.shape, **kw)
                   if precision != capi.SF_FP64 and self.prm.rk == capi.SF_RK4 else None)
+        self._rate = None  # MHD: device rate of the current U^n, if known
 
     # ------------------------------------------------------------------ ABI
     def patch(self, u_stage, u_n, u_next) -> capi.sf_patch:
@@ -66,6 +67,7 @@ class PatchState:
         p.acc = self.D.data_ptr() if self.D is not None else None
         p.u_next = u_next.data_ptr()
         p.kahan = self.E.data_ptr() if self.E is not None else None
+        p.cfl_rate = None
         return p
 
     def roles(self, stage: int):
@@ -82,15 +84,31 @@ class PatchState:
         return 4 if self.prm.rk == capi.SF_RK4 else 3
 
     # ------------------------------------------------------------------ data
+    # fields stored minus their flat value 1 in the float CCZ4 arrays
+    Z4_OFFSET_FIELDS = (0, 1, 4, 6, 18)
+
+    @property
+    def offset_fields(self):
+        if self.system == capi.SF_Z4 and self.precision != capi.SF_FP64:
+            return self.Z4_OFFSET_FIELDS
+        return ()
+
     def upload(self, interior, stream=None) -> None:
-        """Set U^n from an interior array (nf, nz, ny, nx) and fill periodic ghosts."""
+        """Set U^n from an interior array (nf, nz, ny, nx) of field values and
+        fill periodic ghosts (float CCZ4 arrays get the flat-space offset
+        subtracted in double precision before rounding to float)."""
         g = self.g
         t = torch.as_tensor(np.ascontiguousarray(interior) if isinstance(interior, np.ndarray)
-                            else interior)
+                            else interior).double()
+        if self.offset_fields:
+            t = t.clone()
+            for f in self.offset_fields:
+                t[f] -= 1.0
         self.A[:, g:self.shape[1] - g, g:self.shape[2] - g, g:self.shape[3] - g].copy_(
             t.to(self.dtype))
         if self.E is not None:
             self.E.zero_()
+        self._rate = None
         self.fill_ghosts(self.A, stream)
 
     def fill_ghosts(self, array: torch.Tensor, stream=None) -> None:
@@ -98,21 +116,54 @@ class PatchState:
                                      _stream_handle(stream))
 
     def interior(self, array: torch.Tensor | None = None) -> torch.Tensor:
+        """Interior view of the stored values (float CCZ4: with offsets)."""
         a = self.A if array is None else array
         g = self.g
         return a[:, g:self.shape[1] - g, g:self.shape[2] - g, g:self.shape[3] - g]
 
+    def fields(self, array: torch.Tensor | None = None) -> torch.Tensor:
+        """Interior field values in float64 (flat-space offsets added back)."""
+        v = self.interior(array).double().clone()
+        for f in self.offset_fields:
+            v[f] += 1.0
+        return v
+
     # ------------------------------------------------------------------ stepping
     def stage(self, s: int, stream=None) -> torch.Tensor:
         """Run RK stage s; returns the array holding its output."""
+        self._rate = None
         capi.sf_substep(self.prm, self.stage_patch(s), s, _stream_handle(stream))
         return self.roles(s)[1]
 
     def step(self, nsteps: int = 1, stream=None) -> None:
+        self._rate = None
         h = _stream_handle(stream)
         for _ in range(nsteps):
             for s in range(self.nstages):
                 capi.sf_substep(self.prm, self.stage_patch(s), s, h)
+
+    def step_cfl(self, nsteps: int = 1, cfl: float = 0.3, stream=None) -> list[float]:
+        """MHD steps with dt = cfl / rate, the rate of U^n coming from the
+        previous step's last stage (the first from sf_mhd_max_rate).  Returns
+        the rate used by every step (one device-to-host read per step)."""
+        if self.system != capi.SF_MHD:
+            raise ValueError("step_cfl is for SF_MHD patches")
+        h = _stream_handle(stream)
+        # the rate of the current U^n: kept from the previous call's last
+        # stage, else one sf_mhd_max_rate sweep
+        rate = self._rate if self._rate is not None else self.mhd_max_rate(stream=stream)
+        self._rate = rate
+        rates = []
+        for _ in range(nsteps):
+            r = rate.item()
+            rates.append(r)
+            self.dt = cfl / r
+            for s in range(self.nstages):
+                p = self.stage_patch(s)
+                if s == self.nstages - 1:
+                    p.cfl_rate = rate.data_ptr()
+                capi.sf_substep(self.prm, p, s, h)
+        return rates
 
     def adjoint_step(self, nsteps: int = 1, stream=None) -> None:
         """RK4 steps of the transposed wave operator on A (adjoint fields)."""

@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(L):
 def test_struct_layouts_match_header():
     # sizes follow from the C declaration order with natural alignment
     assert ctypes.sizeof(capi.sf_params) == 4 + 4 + 8 * 4 + 4 * 4 + 8 * 4
-    assert ctypes.sizeof(capi.sf_patch) == 12 + 4 + 24 + 8 + 4 + 4 + 24 + 5 * 8
+    assert ctypes.sizeof(capi.sf_patch) == 12 + 4 + 24 + 8 + 4 + 4 + 24 + 5 * 8 + 8
 
 
 def test_nfields(L):
@@ -99,6 +99,13 @@ def test_in_place_only_in_last_stage(L):
 def test_fused_periodic_ghosts_need_n_at_least_ghost(L):
     with pytest.raises(capi.SfError, match="ghost"):
         capi.sf_substep(capi.params(), fake_patch(n=(2, 8, 8)), 0)
+
+
+def test_cfl_rate_only_for_mhd(L):
+    p = fake_patch()
+    p.cfl_rate = 1 << 24
+    with pytest.raises(capi.SfError, match="cfl_rate"):
+        capi.sf_substep(capi.params(), p, 0)
 
 
 def test_adjoint_only_for_wave(L):

@@ -43,6 +43,19 @@ def batch_patches(states):
     return [st.patch(st.B, st.A, st.C) for st in states]
 
 
+def fp_bound(precision, st, steps=2):
+    """FP64: summation-order rounding.  FP32: the two kernels are compiled
+    separately (FMA contraction may differ), so they differ by the float
+    rounding of the O(1) metric's second-derivative stencils, ~64/12 eps32
+    / dx^2 per evaluation, times dt per stage, four stages per step, relative
+    to the 1e-2 floor of the comparison."""
+    if precision == capi.SF_FP64:
+        return 1e-13
+    eps32 = float(np.finfo(np.float32).eps)
+    h = min(st.dx)
+    return 2 * steps * 4 * 64 / 12 * eps32 * st.dt / h ** 2 / 1e-2
+
+
 def small_table(npatch=10, seed=3):
     t = inputs.amr_patch_table(npatch, seed=seed, lo=6, hi=21)
     assert {p["system"] for p in t} == {"wave", "z4"}
@@ -64,9 +77,9 @@ def test_batch_equals_per_patch_launches(precision):
         torch.cuda.synchronize()
         for st, ref in zip(states, ref_states):
             a, r = st.interior(), ref.interior()
-            scale = r.abs().amax(dim=(1, 2, 3)).clamp_min(1e-3)
+            scale = r.abs().amax(dim=(1, 2, 3)).clamp_min(1e-2)
             err = ((a - r).abs().amax(dim=(1, 2, 3)) / scale).max().item()
-            assert err < (1e-13 if precision == capi.SF_FP64 else 2e-6), err
+            assert err < fp_bound(precision, st), err
     finally:
         capi.sf_batch_destroy(b)
 
@@ -110,8 +123,9 @@ def test_batch_graph_tune_and_capture():
         assert capi.sf_batch_launches_per_step(b) == 4
         for st, r in zip(states, ref):
             a, w = st.interior(), r.interior()
-            scale = w.abs().amax(dim=(1, 2, 3)).clamp_min(1e-3)
-            assert ((a - w).abs().amax(dim=(1, 2, 3)) / scale).max().item() < 2e-6
+            scale = w.abs().amax(dim=(1, 2, 3)).clamp_min(1e-2)
+            err = ((a - w).abs().amax(dim=(1, 2, 3)) / scale).max().item()
+            assert err < fp_bound(capi.SF_FP32_BULK_DW, st, steps=3), err
     finally:
         capi.sf_batch_destroy(b)
 

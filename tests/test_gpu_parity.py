@@ -55,7 +55,7 @@ def run_stages(system, U0, dx, dt, prm, precision=capi.SF_FP64):
     outs = []
     for s in range(st.nstages):
         arr = st.stage(s)
-        outs.append(st.interior(arr).double().cpu().numpy().copy())
+        outs.append(st.fields(arr).cpu().numpy())
     torch.cuda.synchronize()
     return outs
 
@@ -202,6 +202,23 @@ def test_mhd_max_rate_and_rhs():
     assert st.mhd_max_rate().item() == pytest.approx(oracle.mhd_max_rate(G, dx), rel=1e-13)
     e = rel_err(st.rhs().cpu().numpy(), oracle.rhs(oracle.MHD, G, dx), floor=1e-3)
     assert e.max() < TOL64, e
+
+
+def test_mhd_fused_cfl_rate_equals_separate_reduction():
+    # the last SSP-RK3 stage reduces the signal rate of its output; it must equal
+    # sf_mhd_max_rate of the new state exactly (max is order independent)
+    n = (40, 17, 11)
+    U0, dx = inputs.mhd_blast(n, seed=6, radius=0.3)
+    st = PatchState(capi.SF_MHD, n, dx, 1e-3, prm=capi.params(rk=capi.SF_SSPRK3))
+    st.upload(U0)
+    rates = st.step_cfl(3, cfl=0.3)
+    assert rates[0] == pytest.approx(oracle.mhd_max_rate(oracle.ghosted(U0), dx), rel=1e-13)
+    st2 = PatchState(capi.SF_MHD, n, dx, 1e-3, prm=capi.params(rk=capi.SF_SSPRK3))
+    st2.upload(U0)
+    for r in rates[:-1]:
+        st2.dt = 0.3 / r
+        st2.step(1)
+    assert st2.mhd_max_rate().item() == rates[-1]
 
 
 def test_mhd_uniform_rhs_exactly_zero():

@@ -35,8 +35,10 @@ def states_for(table, precision):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision,tol", [(capi.SF_FP64, 1e-13), (capi.SF_FP32_BULK_DW, 2e-6)])
+@pytest.mark.parametrize("precision,tol", [(capi.SF_FP64, 1e-13), (capi.SF_FP32_BULK_DW, 0.0)])
 def test_static_scratch_batch_matches_allocating_batch(precision, tol):
+    # Both paths launch the same compiled persistent kernel, so for FP64 they
+    # agree to rounding and for FP32 bit for bit (tolerance 0).
     table = inputs.amr_patch_table(10, seed=3, lo=6, hi=21)
     a = states_for(table, precision)
     b = states_for(table, precision)
