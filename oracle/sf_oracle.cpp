@@ -34,7 +34,7 @@ extern "C" {
 typedef struct {
   double sigma;       // KO strength (Sec. II.B.1)
   double gamma_eos;   // ideal-gas adiabatic index (Sec. IV.B)
-  double weno_eps;    // WENO epsilon; <= 0 means dx_d^4 per direction (App. B)
+  double weno_eps;    // WENO epsilon; <= 0 means dx_d^4 (WENO5, App. B) or dx_d^2 (WENO3, App. A)
   double weno_q;      // WENO-Z exponent q (App. B)
   double kappa_z;     // Z4 damping (Sec. V)
   double kappa_c;     // conformal-constraint damping (Sec. V)
@@ -42,7 +42,7 @@ typedef struct {
   double g_shift;     // Gamma-driver coefficient g (Sec. V)
   double ch;          // GLM cleaning speed (Sec. IV.B)
   double kappa_psi;   // GLM damping (Sec. IV.B)
-  int32_t weno_variant;  // 0: WENO5-JS, 1: WENO5-Z
+  int32_t weno_variant;  // 0: WENO5-JS, 1: WENO5-Z, 2: WENO3 (App. A)
   int32_t slicing;       // 0: 1+log (f = 2/alpha), 1: harmonic (f = 1)
   int32_t shift_frozen;  // 1: d/dt beta = d/dt B = 0
   int32_t mhd_glm;       // 1: 9th MHD field psi
@@ -316,12 +316,39 @@ T weno5_right(const or_params& p, const T* w, double eps) {
   return (al[0] * c0 + al[1] * c1 + al[2] * c2) / sum;
 }
 
-// LLF flux at the interface x_{i+1/2} along d (Eq. LLF), from the WENO5 left
+// App. A: WENO3 left state U^L_{i+1/2} from U_{i-1..i+1} (w[1..3] of w[0..4]).
+template <class T>
+T weno3_left(const T* w, double eps) {
+  const T& um1 = w[1]; const T& u0 = w[2]; const T& up1 = w[3];
+  T c0 = T(0.5) * u0 + T(0.5) * up1;
+  T c1 = T(-0.5) * um1 + T(1.5) * u0;
+  T b0 = (up1 - u0) * (up1 - u0);
+  T b1 = (u0 - um1) * (u0 - um1);
+  T e0 = T(eps) + b0, e1 = T(eps) + b1;
+  T a0 = T(2.0 / 3.0) / (e0 * e0), a1 = T(1.0 / 3.0) / (e1 * e1);
+  return (a0 * c0 + a1 * c1) / (a0 + a1);
+}
+
+// App. A: WENO3 right state U^R_{i-1/2} from U_{i-1..i+1}.
+template <class T>
+T weno3_right(const T* w, double eps) {
+  const T& um1 = w[1]; const T& u0 = w[2]; const T& up1 = w[3];
+  T c0 = T(-0.5) * up1 + T(1.5) * u0;
+  T c1 = T(0.5) * u0 + T(0.5) * um1;
+  T b0 = (u0 - up1) * (u0 - up1);
+  T b1 = (um1 - u0) * (um1 - u0);
+  T e0 = T(eps) + b0, e1 = T(eps) + b1;
+  T a0 = T(1.0 / 3.0) / (e0 * e0), a1 = T(2.0 / 3.0) / (e1 * e1);
+  return (a0 * c0 + a1 * c1) / (a0 + a1);
+}
+
+// LLF flux at the interface x_{i+1/2} along d (Eq. LLF), from the WENO left
 // state (stencil centred at i) and right state (stencil centred at i+1).
 template <class T>
 void mhd_interface_flux(const or_params& p, const double* u, const Grid& G, const double* dx,
                         int nf, int i, int j, int k, int d, T* Fout) {
-  double eps = p.weno_eps > 0 ? p.weno_eps : dx[d] * dx[d] * dx[d] * dx[d];
+  double eps = p.weno_eps > 0 ? p.weno_eps
+                              : (p.weno_variant == 2 ? dx[d] * dx[d] : dx[d] * dx[d] * dx[d] * dx[d]);
   T UL[9], UR[9];
   for (int f = 0; f < nf; ++f) {
     T wl[5], wr[5];
@@ -329,8 +356,13 @@ void mhd_interface_flux(const or_params& p, const double* u, const Grid& G, cons
       wl[s + 2] = U_off<T>(u, G, f, i, j, k, d, s);
       wr[s + 2] = U_off<T>(u, G, f, i, j, k, d, s + 1);
     }
-    UL[f] = weno5_left<T>(p, wl, eps);
-    UR[f] = weno5_right<T>(p, wr, eps);
+    if (p.weno_variant == 2) {
+      UL[f] = weno3_left<T>(wl, eps);
+      UR[f] = weno3_right<T>(wr, eps);
+    } else {
+      UL[f] = weno5_left<T>(p, wl, eps);
+      UR[f] = weno5_right<T>(p, wr, eps);
+    }
   }
   T FL[9], FR[9];
   mhd_flux<T>(p, UL, d, nf, FL);
