@@ -70,6 +70,8 @@ class Params(ctypes.Structure):
         ("slicing", ctypes.c_int32),
         ("shift_frozen", ctypes.c_int32),
         ("mhd_glm", ctypes.c_int32),
+        ("lopsided", ctypes.c_int32),
+        ("pad_", ctypes.c_int32),
     ]
 
 
@@ -78,7 +80,7 @@ def params(**kw) -> Params:
     kappa_z = kappa_c = 1, eta = 2, g = 3/4, 1+log slicing (Sec. V with M = 1)."""
     d = dict(sigma=0.1, gamma_eos=5.0 / 3.0, weno_eps=0.0, weno_q=2.0, kappa_z=1.0,
              kappa_c=1.0, eta=2.0, g_shift=0.75, ch=0.0, kappa_psi=0.0, weno_variant=0,
-             slicing=0, shift_frozen=0, mhd_glm=0)
+             slicing=0, shift_frozen=0, mhd_glm=0, lopsided=0, pad_=0)
     d.update(kw)
     return Params(**d)
 
@@ -246,7 +248,7 @@ def misfit_gradient(phi0: np.ndarray, Pi0: np.ndarray, dx, dt: float, nsteps: in
     return J, gphi, gPi
 
 
-D1, D2, DMIX, KO = 0, 1, 2, 3
+D1, D2, DMIX, KO, DLOP = 0, 1, 2, 3, 4
 
 
 def stencil(op: int, U: np.ndarray, dx, f: int, i: int, j: int, k: int, d1: int = 0,

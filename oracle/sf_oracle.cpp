@@ -46,6 +46,8 @@ typedef struct {
   int32_t slicing;       // 0: 1+log (f = 2/alpha), 1: harmonic (f = 1)
   int32_t shift_frozen;  // 1: d/dt beta = d/dt B = 0
   int32_t mhd_glm;       // 1: 9th MHD field psi
+  int32_t lopsided;      // 1: CCZ4 advection beta^k d_k with the one-sided stencils (Sec. II.B.1)
+  int32_t pad_;
 } or_params;
 }
 
@@ -163,6 +165,24 @@ T Dmix(const double* u, const Grid& G, int f, int i, int j, int k, int d1, int d
     acc = acc + T(c[s + 2]) * D1<T>(u, G, f, ii, jj, kk, d1, dx);
   }
   return acc * T(1.0 / (12.0 * dx[d2]));
+}
+
+// Sec. II.B.1: one-sided ("lopsided") advection derivative along d for an
+// advecting velocity of sign `sgn`:
+//   beta > 0: ( U_{+3} - 6 U_{+2} + 18 U_{+1} - 10 U_0 - 3 U_{-1}) / (12 dx_d)
+//   beta < 0: (-U_{-3} + 6 U_{-2} - 18 U_{-1} + 10 U_0 + 3 U_{+1}) / (12 dx_d)
+template <class T>
+T Dlop(const double* u, const Grid& G, int f, int i, int j, int k, int d, double sgn,
+       const double* dx) {
+  T u0 = U_<T>(u, G, f, i, j, k);
+  if (sgn > 0) {
+    T a = U_off<T>(u, G, f, i, j, k, d, 3), b = U_off<T>(u, G, f, i, j, k, d, 2);
+    T c = U_off<T>(u, G, f, i, j, k, d, 1), e = U_off<T>(u, G, f, i, j, k, d, -1);
+    return (a - T(6.0) * b + T(18.0) * c - T(10.0) * u0 - T(3.0) * e) * T(1.0 / (12.0 * dx[d]));
+  }
+  T a = U_off<T>(u, G, f, i, j, k, d, -3), b = U_off<T>(u, G, f, i, j, k, d, -2);
+  T c = U_off<T>(u, G, f, i, j, k, d, -1), e = U_off<T>(u, G, f, i, j, k, d, 1);
+  return (-a + T(6.0) * b - T(18.0) * c + T(10.0) * u0 + T(3.0) * e) * T(1.0 / (12.0 * dx[d]));
 }
 
 // Sec. II.B.1: Q_d U = sum_d sigma/(64 dx_d) (U_{-3} - 6U_{-2} + 15U_{-1} - 20U_0 + 15U_{+1} - 6U_{+2} + U_{+3})
@@ -575,7 +595,16 @@ void z4_cell(const or_params& p, const double* u, const Grid& G, const double* d
     for (int b = 0; b < 3; ++b) AA = AA + At[a][b] * Auu[a][b];
 
   T divbe = dbe[0][0] + dbe[1][1] + dbe[2][2];
-  auto adv = [&](int f) -> T { return be[0] * d1[f][0] + be[1] * d1[f][1] + be[2] * d1[f][2]; };
+  // advection beta^k d_k U_f: centred D_k, or the one-sided stencil chosen by the sign of beta^k
+  auto adv = [&](int f) -> T {
+    if (!p.lopsided) return be[0] * d1[f][0] + be[1] * d1[f][1] + be[2] * d1[f][2];
+    T s(0.0);
+    for (int c = 0; c < 3; ++c) {
+      const double b = val_(be[c]);
+      if (b != 0.0) s = s + be[c] * Dlop<T>(u, G, f, i, j, k, c, b, dx);
+    }
+    return s;
+  };
   const T kz(p.kappa_z), kc(p.kappa_c);
 
   // --- d/dt gt_ij  (Eq. syseq1)
@@ -1005,7 +1034,8 @@ int or_rhs_points(int system, const or_params* p, const int* n, int g, const dou
 
 // One stencil of Sec. II.B.1 at interior point (i,j,k) of field f of a
 // ghost-filled array: op 0 = D_d1, 1 = D_d1d1, 2 = D_d2(D_d1) (d1 != d2),
-// 3 = Q_d with strength sigma (all three directions).
+// 3 = Q_d with strength sigma (all three directions), 4 = one-sided D_d1 for
+// an advecting velocity of sign d2 (> 0 or <= 0).
 double or_stencil(int op, const int* n, int g, const double* dx, const double* u, int f, int i,
                   int j, int k, int d1, int d2, double sigma) {
   Grid G(n, g);
@@ -1014,6 +1044,7 @@ double or_stencil(int op, const int* n, int g, const double* dx, const double* u
     case 1: return D2<double>(u, G, f, i, j, k, d1, dx);
     case 2: return Dmix<double>(u, G, f, i, j, k, d1, d2, dx);
     case 3: return KO<double>(u, G, f, i, j, k, dx, sigma);
+    case 4: return Dlop<double>(u, G, f, i, j, k, d1, d2 > 0 ? 1.0 : -1.0, dx);
   }
   return 0.0;
 }

@@ -123,3 +123,36 @@ def test_fourier_symbols(m):
         assert oracle.stencil(oracle.D1, U, dx, 0, i, 0, 0, d1=0) == pytest.approx(d1, abs=1e-12)
         assert oracle.stencil(oracle.D2, U, dx, 0, i, 0, 0, d1=0) == pytest.approx(d2, abs=1e-10)
         assert oracle.stencil(oracle.KO, U, dx, 0, i, 0, 0, sigma=sigma) == pytest.approx(ko, abs=1e-12)
+
+
+def test_lopsided_advection_stencils():
+    # Sec. II.B.1 one-sided stencils: exact on quartics in both orientations,
+    # each reads only the points on its side (i-1..i+3 for beta > 0, i-3..i+1 for
+    # beta < 0), and the two mirror stencils share the leading truncation term
+    # +h^4/20 u^(5) (sum of coefficient x offset^5 = 72 for both)
+    c = [2, -1, 3, 1, -2]
+    for d in range(3):
+        fn = lambda x, y, z, d=d: sum(Fraction(c[p]) * (x, y, z)[d] ** p for p in range(5))
+        dfn = lambda x, y, z, d=d: sum(Fraction(p * c[p]) * (x, y, z)[d] ** (p - 1) for p in range(1, 5))
+        U = poly_field(fn)
+        for sgn in (1, -1):
+            for (i, j, k) in [(1, 1, 1), (3, 4, 2)]:
+                got = oracle.stencil(oracle.DLOP, U, H, 0, i, j, k, d1=d, d2=sgn)
+                want = dfn(coord(0, i, j, k), coord(1, i, j, k), coord(2, i, j, k))
+                assert got == pytest.approx(float(want), rel=1e-13, abs=1e-11)
+    # one-sidedness: a spike 2 points behind the upwind side is invisible
+    U = np.zeros((1, N[2] + 2 * G, N[1] + 2 * G, N[0] + 2 * G))
+    U[0, G + 2, G + 3, G + 3 - 2] = 1.0  # x offset -2 from (3, 3, 2)
+    assert oracle.stencil(oracle.DLOP, U, H, 0, 3, 3, 2, d1=0, d2=1) == 0.0
+    assert oracle.stencil(oracle.DLOP, U, H, 0, 3, 3, 2, d1=0, d2=-1) != 0.0
+    U[...] = 0.0
+    U[0, G + 2, G + 3, G + 3 + 2] = 1.0  # x offset +2
+    assert oracle.stencil(oracle.DLOP, U, H, 0, 3, 3, 2, d1=0, d2=-1) == 0.0
+    assert oracle.stencil(oracle.DLOP, U, H, 0, 3, 3, 2, d1=0, d2=1) != 0.0
+    # 4th order: the truncation term h^4/20 * 5! is visible on x^5, equal for both
+    U = poly_field(lambda x, y, z: x ** 5)
+    x = Fraction(3) * Fraction(H[0])
+    plus = oracle.stencil(oracle.DLOP, U, H, 0, 3, 1, 1, d1=0, d2=1) - float(5 * x ** 4)
+    minus = oracle.stencil(oracle.DLOP, U, H, 0, 3, 1, 1, d1=0, d2=-1) - float(5 * x ** 4)
+    assert plus == pytest.approx(H[0] ** 4 * 120 / 20, rel=1e-10)
+    assert minus == pytest.approx(plus, rel=1e-10)

@@ -181,3 +181,16 @@ def test_monitors_on_exact_data():
     assert m[2] < 1e-15         # ln det gt = 0 analytically
     assert m[3] < 1e-15         # tr A~ = 0 analytically
     assert 0 < m[1] < 1e-4      # Z ~ truncation error of Gamma~
+
+
+def test_lopsided_advection_converges_to_centred():
+    # with a non-zero shift, one-sided and centred advection differ by the
+    # stencils' truncation only: the RHS difference falls at 4th order
+    errs = []
+    for N in (16, 32):
+        U0, dx = inputs.z4_perturbed((N, N, N), seed=9, amp=0.05)
+        G = oracle.ghosted(U0)
+        a = oracle.rhs(oracle.Z4, G, dx, oracle.params(lopsided=0))
+        b = oracle.rhs(oracle.Z4, G, dx, oracle.params(lopsided=1))
+        errs.append(np.abs(a - b).max())
+    assert errs[0] > 0 and errs[0] / errs[1] > 13.0, errs
