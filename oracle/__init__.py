@@ -123,6 +123,8 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(ctypes.c_long)]
         L.or_rhs_points.argtypes = [ctypes.c_int, pp, ip, ctypes.c_int, dp, dp, ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_int64), dp]
+        L.or_prolong.argtypes = [ctypes.c_int, ip, ctypes.c_int, dp, ctypes.c_int, ip, ip, dp]
+        L.or_restrict.argtypes = [ctypes.c_int, ip, ctypes.c_int, dp, ctypes.c_int, ip, ip, dp]
         L.or_stencil.argtypes = [ctypes.c_int, ip, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_double]
@@ -182,6 +184,27 @@ def rhs_points(system: int, U: np.ndarray, dx, pts: np.ndarray, p: Params | None
                              pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(out))
     if rc:
         raise ValueError("oracle rhs_points: bad arguments")
+    return out
+
+
+def prolong(Uc: np.ndarray, ratio: int, origin, ext, g: int = 3) -> np.ndarray:
+    """Sec. III.A quintic Lagrange prolongation of a ghost-filled coarse array
+    onto fine points origin..origin+ext-1 (fine index R*i = coarse point i)."""
+    nf, n = shape_info(Uc, g)
+    out = np.zeros((nf, ext[2], ext[1], ext[0]))
+    rc = lib().or_prolong(nf, _ivec(n), g, _dp(Uc), ratio, _ivec(origin), _ivec(ext), _dp(out))
+    if rc:
+        raise ValueError("oracle prolong: stencil leaves the coarse box")
+    return out
+
+
+def restrict(Uf: np.ndarray, ratio: int, origin, ext, g: int = 3) -> np.ndarray:
+    """Sec. III.A injection of fine point R*i into coarse points origin..origin+ext-1."""
+    nf, n = shape_info(Uf, g)
+    out = np.zeros((nf, ext[2], ext[1], ext[0]))
+    rc = lib().or_restrict(nf, _ivec(n), g, _dp(Uf), ratio, _ivec(origin), _ivec(ext), _dp(out))
+    if rc:
+        raise ValueError("oracle restrict: out of the fine box")
     return out
 
 

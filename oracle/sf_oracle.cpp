@@ -1032,6 +1032,77 @@ int or_rhs_points(int system, const or_params* p, const int* n, int g, const dou
   return 0;
 }
 
+// Sec. III.A prolongation: 6-point (5th-order) Lagrange interpolation in each
+// direction, p(x) = sum_j U_j l_j(x), l_j(x) = prod_{m != j} (x - x_m)/(x_j - x_m),
+// applied as a tensor product.  Fine point F (fine index, where fine index
+// R*i sits on coarse interior point i) has coarse coordinate X = F/R; the
+// nodes are the coarse points floor(X)-2 .. floor(X)+3.  `cu` is a ghost-filled
+// coarse array (nf fields, interior n, ghost g); `out` is a dense array
+// nf x ext[2] x ext[1] x ext[0] of the fine points origin .. origin+ext-1.
+int or_prolong(int nf, const int* n, int g, const double* cu, int ratio, const int* origin,
+               const int* ext, double* out) {
+  Grid G(n, g);
+  auto weights = [&](long F, int& base, double w[6]) {
+    // floor division for negative fine indices
+    long q = F >= 0 ? F / ratio : -((-F + ratio - 1) / ratio);
+    base = (int)q;
+    const double X = (double)F / (double)ratio;
+    for (int j = 0; j < 6; ++j) {
+      const double xj = (double)(base - 2 + j);
+      double l = 1.0;
+      for (int m = 0; m < 6; ++m) {
+        if (m == j) continue;
+        const double xm = (double)(base - 2 + m);
+        l *= (X - xm) / (xj - xm);
+      }
+      w[j] = l;
+    }
+  };
+  for (int k = 0; k < ext[2]; ++k)
+    for (int jj = 0; jj < ext[1]; ++jj)
+      for (int i = 0; i < ext[0]; ++i) {
+        int bx, by, bz;
+        double wx[6], wy[6], wz[6];
+        weights(origin[0] + i, bx, wx);
+        weights(origin[1] + jj, by, wy);
+        weights(origin[2] + k, bz, wz);
+        for (int a = 0; a < 3; ++a) {
+          const int b = a == 0 ? bx : (a == 1 ? by : bz);
+          if (b - 2 < -g || b + 3 > n[a] + g - 1) return 1;  // stencil leaves the coarse box
+        }
+        for (int f = 0; f < nf; ++f) {
+          double acc = 0.0;
+          for (int c = 0; c < 6; ++c)
+            for (int bq = 0; bq < 6; ++bq)
+              for (int a = 0; a < 6; ++a)
+                acc += wz[c] * wy[bq] * wx[a] *
+                       cu[G.at(f, bx - 2 + a, by - 2 + bq, bz - 2 + c)];
+          out[(((long)f * ext[2] + k) * ext[1] + jj) * ext[0] + i] = acc;
+        }
+      }
+  return 0;
+}
+
+// Sec. III.A restriction by injection: coarse interior point i takes the fine
+// value at fine interior point R*i.  Coarse points origin .. origin+ext-1 are
+// written into the dense array `out` (nf x ext).
+int or_restrict(int nf, const int* nfine, int gf, const double* fu, int ratio, const int* origin,
+                const int* ext, double* out) {
+  Grid G(nfine, gf);
+  for (int f = 0; f < nf; ++f)
+    for (int k = 0; k < ext[2]; ++k)
+      for (int j = 0; j < ext[1]; ++j)
+        for (int i = 0; i < ext[0]; ++i) {
+          const int I = ratio * (origin[0] + i), J = ratio * (origin[1] + j),
+                    K = ratio * (origin[2] + k);
+          if (I < -gf || I >= nfine[0] + gf || J < -gf || J >= nfine[1] + gf || K < -gf ||
+              K >= nfine[2] + gf)
+            return 1;
+          out[(((long)f * ext[2] + k) * ext[1] + j) * ext[0] + i] = fu[G.at(f, I, J, K)];
+        }
+  return 0;
+}
+
 // One stencil of Sec. II.B.1 at interior point (i,j,k) of field f of a
 // ghost-filled array: op 0 = D_d1, 1 = D_d1d1, 2 = D_d2(D_d1) (d1 != d2),
 // 3 = Q_d with strength sigma (all three directions), 4 = one-sided D_d1 for
