@@ -112,6 +112,36 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- traffic
+# DRAM traffic of the headline kernel comes from one ncu capture summarised in
+# profiles/; it is reported only while the kernel sources still hash to the
+# value recorded there (null once the kernel has changed).
+PROFILE = os.path.join(ROOT, "profiles", "z4_stage_fp32dw_96cubed.md")
+KERNEL_SOURCES = ["sf_common.cuh", "sf_dw.cuh", "sf_z4.cuh", "sf_z4.cu"]
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1806_04182_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """(bytes per launch, source hash) from the profile summary, or (None, None)."""
+    if not os.path.exists(PROFILE):
+        return None, None
+    traffic = src = None
+    for line in open(PROFILE):
+        if line.startswith("traffic_bytes_per_launch:"):
+            traffic = float(line.split(":")[1])
+        if line.startswith("kernel_source_sha256_16:"):
+            src = line.split(":")[1].strip()
+    return traffic, src
+
+
 # ---------------------------------------------------------------- ranks
 def max_over_ranks(v: float, device=None) -> float:
     """Max of v over the ranks of the default process group (v itself if none)."""
@@ -272,6 +302,7 @@ def gpu_arm(args):
     if rank != 0:
         return None
     r32, r32n, r64 = res["fp32dw"], res["fp32"], res["fp64"]
+    traffic, traffic_src = profiled_traffic()
     line = {
         "metric": METRIC,
         "value": r32["value"],
@@ -294,7 +325,9 @@ def gpu_arm(args):
                    "dt_over_dx": 0.25, "l2": "inputs larger than L2 (5 arrays x 106 MB fp32)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": r32["achieved_gbs"], "peak": hbm_peak,
-                     "unit": "GB/s", "frac": r32["achieved_gbs"] / hbm_peak, "traffic": None,
+                     "unit": "GB/s", "frac": r32["achieved_gbs"] / hbm_peak,
+                     "traffic": traffic if traffic_src == kernel_source_hash() else None,
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read+write, mean of the 4 stages)",
                      "peak_source": peak_src,
                      "kernel": "z4_stage_kernel<float,dw,102,10404>",
                      "bytes_per_cell_update": r32["bytes_per_cell_update"],
@@ -356,41 +389,43 @@ def suite(args, hbm_peak: float) -> list[dict]:
                     "hbm_frac": rate * bpc / 1e9 / hbm_peak})
     if "mhd" in rows:
         out += _mhd_row(hbm_peak)
-    if "batch" in rows:
-        out += _batch_rows(hbm_peak)
+    if "batch" in rows or "batch_graph" in rows:
+        out += _batch_rows(hbm_peak, npatch=args.npatch, per_patch="batch" in rows)
     if "adjoint" in rows:
         out += _adjoint_rows()
     return out
 
 
 def _mhd_row(hbm_peak: float) -> list[dict]:
-    import torch
     from paper_1806_04182_gb300 import capi, inputs
     from paper_1806_04182_gb300.state import PatchState
     out = []
-    # MHD 128^3 FP64, SSP-RK3, CFL 0.3 with the rate recomputed every step
+    # MHD 128^3, SSP-RK3, CFL 0.3 with the rate fused into each step's last stage
     n = (128, 128, 128)
     U0, dx = inputs.mhd_blast(n, seed=0)
     prm = capi.params(rk=capi.SF_SSPRK3)
-    st = PatchState(capi.SF_MHD, n, dx, 1e-3, prm=prm)
-    st.upload(U0)
-    ms = _events_time(lambda: st.step_cfl(1, cfl=0.3), 10, 3)
-    rate = 128 ** 3 * 3 * 10 / (ms * 1e-3)
-    out.append({"workload": "mhd_128cubed_weno5_llf_ssprk3_fp64", "value": rate, "unit": UNIT,
-                "ms_per_step": ms / 10, "bytes_per_cell_update": 8 / 3 * 8 * 8,
-                "hbm_frac": rate * 8 / 3 * 8 * 8 / 1e9 / hbm_peak,
-                "note": "dt = 0.3 / max signal rate: sf_mhd_max_rate once, then the rate "
-                        "fused into each step's last stage, read back every step"})
+    for prec, name, es in ((capi.SF_FP64, "fp64", 8), (capi.SF_FP32_BULK, "fp32", 4)):
+        st = PatchState(capi.SF_MHD, n, dx, 1e-3, precision=prec, prm=prm)
+        st.upload(U0)
+        steps = 10 if prec == capi.SF_FP64 else 50
+        ms = _events_time(lambda: st.step_cfl(1, cfl=0.3), steps, 3)
+        rate = 128 ** 3 * 3 * steps / (ms * 1e-3)
+        bpc = 8 / 3 * 8 * es
+        out.append({"workload": f"mhd_128cubed_weno5_llf_ssprk3_{name}", "value": rate,
+                    "unit": UNIT, "ms_per_step": ms / steps, "bytes_per_cell_update": bpc,
+                    "hbm_frac": rate * bpc / 1e9 / hbm_peak,
+                    "note": "dt = 0.3 / max signal rate: sf_mhd_max_rate once, then the rate "
+                            "fused into each step's last stage, read back every step"})
     return out
 
 
-def _batch_rows(hbm_peak: float) -> list[dict]:
+def _batch_rows(hbm_peak: float, npatch: int = 512, per_patch: bool = True) -> list[dict]:
     import torch
     from paper_1806_04182_gb300 import capi, inputs
     from paper_1806_04182_gb300.state import PatchState
     out = []
-    # batched AMR step: 512 patches, one persistent launch per stage in a CUDA graph
-    table = inputs.amr_patch_table(512, seed=0)
+    # batched AMR step: npatch patches, one persistent launch per stage in a CUDA graph
+    table = inputs.amr_patch_table(npatch, seed=0)
 
     def states(precision):
         sts = []
@@ -417,10 +452,12 @@ def _batch_rows(hbm_peak: float) -> list[dict]:
         ms = _events_time(lambda: capi.sf_batch_launch(b, stream.cuda_stream), 10, 3)
     capi.sf_batch_destroy(b)
     batch_rate = cells * 4 * 10 / (ms * 1e-3)
-    out.append({"workload": "amr_batch_512_patches_fp32_bulk_dw_graph", "value": batch_rate,
+    out.append({"workload": f"amr_batch_{npatch}_patches_fp32_bulk_dw_graph", "value": batch_rate,
                 "unit": UNIT, "ms_per_step": ms / 10, "cells": cells,
                 "hbm_frac": bytes_step * 10 / (ms * 1e-3) / 1e9 / hbm_peak})
     del sts
+    if not per_patch:
+        return out
     sts = states(capi.SF_FP64)
     z4p = [s_ for s_ in sts if s_.system == capi.SF_Z4]
     wvp = [s_ for s_ in sts if s_.system == capi.SF_WAVE]
@@ -433,7 +470,7 @@ def _batch_rows(hbm_peak: float) -> list[dict]:
 
     ms = _events_time(per_patch_step, 3, 1)
     pp_rate = cells * 4 * 3 / (ms * 1e-3)
-    out.append({"workload": "amr_512_patches_fp64_per_patch_launches", "value": pp_rate,
+    out.append({"workload": f"amr_{npatch}_patches_fp64_per_patch_launches", "value": pp_rate,
                 "unit": UNIT, "ms_per_step": ms / 3,
                 "batched_fp32_speedup": batch_rate / pp_rate})
     return out
@@ -519,7 +556,7 @@ def reference_arm(args):
     value = cells * 4 * args.steps / el
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     sample = f"each step: one RK4 step of a 96x96x{nz} periodic slab of the 96^3 workload"
-    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic: Minkowski + seeded uniform noise 1e-10",
@@ -540,7 +577,8 @@ def main():
     ap.add_argument("--suite", action="store_true",
                     help="time every workload row (one JSON line each) instead of the headline")
     ap.add_argument("--rows", default=None,
-                    help="comma-separated subset of wave,mhd,batch,adjoint for --suite")
+                    help="comma-separated subset of wave,mhd,batch,batch_graph,adjoint for --suite")
+    ap.add_argument("--npatch", type=int, default=512, help="patches of the batch rows")
     ap.add_argument("--only", choices=["fp32dw", "fp32", "fp64"], default=None,
                     help="time one precision only (profiling runs)")
     args = ap.parse_args()

@@ -126,9 +126,9 @@ typedef struct {
   int32_t ghosts;       /* sf_ghosts */
   double sigma_ko;      /* KO strength sigma (Sec. II.B.1), >= 0 */
   double gamma_eos;     /* MHD adiabatic index (Sec. IV.B) */
-  double weno_eps;      /* WENO epsilon; <= 0 means dx_d^4 (App. B) */
+  double weno_eps;      /* WENO epsilon; <= 0 means dx_d^4 (WENO5, App. B) or dx_d^2 (WENO3, App. A) */
   double weno_q;        /* WENO-Z exponent (App. B) */
-  int32_t weno_variant; /* 0: WENO5-JS, 1: WENO5-Z */
+  int32_t weno_variant; /* 0: WENO5-JS, 1: WENO5-Z, 2: WENO3 (App. A) */
   int32_t slicing;      /* 0: 1+log (f = 2/alpha), 1: harmonic (f = 1) (Sec. V) */
   int32_t shift_frozen; /* 1: d/dt beta = d/dt B = 0 */
   int32_t check_finite; /* 1: flag NaN/Inf written to u_next in the status word */
@@ -136,6 +136,10 @@ typedef struct {
   double kappa_c;       /* conformal-constraint damping kappa_c (Sec. V) */
   double eta;           /* Gamma-driver damping eta (Sec. V) */
   double g_shift;       /* Gamma-driver coefficient g (Sec. V) */
+  int32_t lopsided;     /* SF_Z4: 1 = advection terms beta^k d_k with the 4th-order
+                           one-sided stencils of Sec. II.B.1, chosen by the sign
+                           of beta^k; 0 = centred D_k */
+  int32_t reserved;     /* set to 0 */
 } sf_params;
 
 /* Number of evolved fields of a system (5, 8 or 25); -1 if unknown. */
@@ -202,6 +206,46 @@ sf_status sf_scatter_add(const sf_patch* patch, void* array, int32_t field, cons
  */
 sf_status sf_diagnostics(const sf_params* prm, const sf_patch* patch, const void* array,
                          double* d_out, void* stream);
+
+/*
+ * Box copies between patch arrays, for the AMR level loop (Sec. III): same-
+ * level ghost synchronisation between neighbouring patches, and, with
+ * src_step = R, restriction by injection (Sec. III.A: coarse point i takes
+ * the fine value at fine point R i).  Box point (x, y, z) of field f is read
+ * at  src_off + f*src_sf + R*(z*src_sz + y*src_sy + x)  and written at
+ *      dst_off + f*dst_sf + z*dst_sz + y*dst_sy + x  (element offsets; the
+ * element type follows `precision`).  The caller guarantees both ranges lie
+ * inside its arrays and that destination boxes do not overlap sources or each
+ * other.  One launch per 16 boxes; nothing is allocated.
+ */
+typedef struct {
+  const void* src;
+  void* dst;
+  int64_t src_off, src_sy, src_sz, src_sf;
+  int64_t dst_off, dst_sy, dst_sz, dst_sf;
+  int32_t ext[3];    /* box extent x, y, z (>= 0) */
+  int32_t nf;        /* fields (>= 1) */
+  int32_t src_step;  /* 1: copy; R: injection from a level R times finer */
+  int32_t reserved;  /* set to 0 */
+} sf_box_copy;
+
+sf_status sf_copy_boxes(const sf_box_copy* boxes, int32_t nbox, int32_t precision, void* stream);
+
+/*
+ * Prolongation (Sec. III.A): 6-point (5th-order) Lagrange interpolation of
+ * `coarse_array` (layout of `coarse`, nf fields, ghost-filled) onto the fine
+ * points origin .. origin+ext-1 of a level `ratio` times finer, where fine
+ * index R i coincides with coarse interior point i.  In each direction the
+ * nodes are the coarse points floor(F/R)-2 .. floor(F/R)+3 and the weights
+ * are the Lagrange basis l_j at the fractional position (F mod R)/R; 3D is
+ * the tensor product.  Coincident points reduce to injection.  The result
+ * goes to fine_out with element strides (out_sy, out_sz, out_sf), for example
+ * straight into a fine patch's ghost zone.  SF_EINVAL if a stencil node falls
+ * outside the ghosted coarse box.  ratio in [1, 8].
+ */
+sf_status sf_prolong(const sf_patch* coarse, const void* coarse_array, int32_t nf, int32_t ratio,
+                     const int32_t* origin, const int32_t* ext, void* fine_out, int64_t out_sy,
+                     int64_t out_sz, int64_t out_sf, void* stream);
 
 /*
  * Batched AMR-patch dispatch: one persistent launch per stage over a table of

@@ -26,7 +26,7 @@ EXPORTS = ["sf_nfields", "sf_substep", "sf_rhs", "sf_fill_ghosts_periodic", "sf_
            "sf_adjoint_substep", "sf_gather", "sf_scatter_add", "sf_diagnostics",
            "sf_batch_create", "sf_batch_substep", "sf_batch_tune", "sf_batch_capture",
            "sf_batch_launch", "sf_batch_launches_per_step", "sf_batch_destroy",
-           "sf_batch_substep_static",
+           "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong",
            "sf_get_device_status", "sf_last_error", "sf_launch_count"]
 
 
@@ -52,6 +52,8 @@ class sf_params(ctypes.Structure):
         ("kappa_c", ctypes.c_double),
         ("eta", ctypes.c_double),
         ("g_shift", ctypes.c_double),
+        ("lopsided", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -75,13 +77,29 @@ class sf_patch(ctypes.Structure):
     ]
 
 
+class sf_box_copy(ctypes.Structure):
+    _fields_ = [
+        ("src", ctypes.c_void_p),
+        ("dst", ctypes.c_void_p),
+        ("src_off", ctypes.c_int64), ("src_sy", ctypes.c_int64), ("src_sz", ctypes.c_int64),
+        ("src_sf", ctypes.c_int64),
+        ("dst_off", ctypes.c_int64), ("dst_sy", ctypes.c_int64), ("dst_sz", ctypes.c_int64),
+        ("dst_sf", ctypes.c_int64),
+        ("ext", ctypes.c_int32 * 3),
+        ("nf", ctypes.c_int32),
+        ("src_step", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
 def params(**kw) -> sf_params:
     """Defaults: RK4, periodic ghosts written by the substep, sigma = 0.1,
     Gamma = 5/3, eps = dx^4, WENO5-JS, kappa_z = kappa_c = 1, eta = 2,
     g = 3/4, 1+log slicing (Sec. V with M = 1)."""
     d = dict(rk=SF_RK4, ghosts=SF_GHOSTS_PERIODIC, sigma_ko=0.1, gamma_eos=5.0 / 3.0,
              weno_eps=0.0, weno_q=2.0, weno_variant=0, slicing=0, shift_frozen=0,
-             check_finite=0, kappa_z=1.0, kappa_c=1.0, eta=2.0, g_shift=0.75)
+             check_finite=0, kappa_z=1.0, kappa_c=1.0, eta=2.0, g_shift=0.75, lopsided=0,
+             reserved=0)
     d.update(kw)
     return sf_params(**d)
 
@@ -118,6 +136,8 @@ def lib() -> ctypes.CDLL:
         L.sf_batch_launches_per_step.restype = i32
         L.sf_batch_destroy.argtypes = [vp]
         L.sf_batch_substep_static.argtypes = [P(sf_params), P(sf_patch), i32, i32, vp]
+        L.sf_copy_boxes.argtypes = [P(sf_box_copy), i32, i32, vp]
+        L.sf_prolong.argtypes = [P(sf_patch), vp, i32, i32, P(i32), P(i32), vp, i64, i64, i64, vp]
         L.sf_get_device_status.argtypes = [vp]
         L.sf_last_error.argtypes = []
         L.sf_last_error.restype = ctypes.c_char_p
@@ -127,7 +147,7 @@ def lib() -> ctypes.CDLL:
                      "sf_adjoint_substep", "sf_gather", "sf_scatter_add", "sf_diagnostics",
                      "sf_batch_create", "sf_batch_substep", "sf_batch_tune", "sf_batch_capture",
                      "sf_batch_launch", "sf_batch_destroy", "sf_get_device_status",
-                     "sf_batch_substep_static"):
+                     "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -225,6 +245,19 @@ def sf_batch_substep_static(prm: sf_params, patches, stage: int, stream: int = 0
     arr, n = _patches(patches)
     _check(lib().sf_batch_substep_static(ctypes.byref(prm), arr, n, stage, stream),
            "sf_batch_substep_static")
+
+
+def sf_copy_boxes(boxes, precision: int, stream: int = 0) -> None:
+    arr = (sf_box_copy * max(1, len(boxes)))(*boxes)
+    _check(lib().sf_copy_boxes(arr, len(boxes), precision, stream), "sf_copy_boxes")
+
+
+def sf_prolong(coarse: sf_patch, coarse_array: int, nf: int, ratio: int, origin, ext,
+               fine_out: int, out_sy: int, out_sz: int, out_sf: int, stream: int = 0) -> None:
+    o = (ctypes.c_int32 * 3)(*origin)
+    e = (ctypes.c_int32 * 3)(*ext)
+    _check(lib().sf_prolong(ctypes.byref(coarse), coarse_array, nf, ratio, o, e, fine_out, out_sy,
+                            out_sz, out_sf, stream), "sf_prolong")
 
 
 def sf_get_device_status(stream: int = 0) -> int:

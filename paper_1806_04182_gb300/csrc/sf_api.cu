@@ -68,8 +68,6 @@ sf_status check_patch(const sf_params* prm, const sf_patch& p, int need_stage_ar
   if (p.sy < p.n[0] + g2 || p.sz < p.sy * (p.n[1] + g2) || p.sf < p.sz * (p.n[2] + g2))
     return set_error(SF_EINVAL, "strides too small for the ghosted box");
   if (p.sf > (1LL << 40)) return set_error(SF_EINVAL, "field stride too large");
-  if ((long long)p.n[2] * p.sz >= (1LL << 31))
-    return set_error(SF_EINVAL, "one field's z extent must span < 2^31 elements");
   const size_t es = p.precision == SF_FP64 ? 8 : 4;
   if (!p.u_stage || !aligned(p.u_stage, es)) return set_error(SF_EINVAL, "u_stage NULL or misaligned");
   if (need_stage_arrays) {
@@ -93,6 +91,8 @@ sf_status check_patch(const sf_params* prm, const sf_patch& p, int need_stage_ar
           return set_error(SF_EINVAL, "fused periodic ghosts need n[%d] >= ghost; use sf_fill_ghosts_periodic", d);
   }
   if (!(prm->sigma_ko >= 0)) return set_error(SF_EINVAL, "sigma_ko must be >= 0");
+  if (prm->weno_variant < 0 || prm->weno_variant > 2)
+    return set_error(SF_EINVAL, "weno_variant %d not in {0, 1, 2}", prm->weno_variant);
   if (p.cfl_rate && p.system != SF_MHD)
     return set_error(SF_EINVAL, "cfl_rate is an SF_MHD output");
   if (p.cfl_rate && !aligned(p.cfl_rate, 8)) return set_error(SF_EINVAL, "cfl_rate misaligned");

@@ -35,8 +35,8 @@ struct Item {
   int patch, x0, y0, z0;
 };
 
-template <typename T, typename H>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) batch_stage_kernel(const PatchArgs<T>* __restrict__ pa,
+template <typename T, typename H, bool LOP>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) batch_stage_kernel(const PatchArgs<T>* __restrict__ pa,
                                                           const int* __restrict__ psys,
                                                           const int2* __restrict__ pshape,
                                                           const Item* __restrict__ items, int nitems,
@@ -61,16 +61,17 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) batch_stage_kerne
     for (int k = w.z0; k < zend; ++k) {
       const long long c = (long long)(k + g) * a.sz + (long long)(j + g) * a.sy + (i + g);
       if (system == SF_Z4) {
-        const T* __restrict__ u = a.us + c;
+        GlobalSrc<T, 0, 0> src{a.us + c, a.sf, a.sy, a.sz};
         const Images im = ghost_images(a, s, i, j, k);
-        z4_cell<T, H, 0, 0>(a, zc, u, [&](int f, T r, T centre) {
+        z4_cell<T, H, LOP>(a, zc, src, [&](int f, T r, T centre) {
           write_field(a, s, im, f, c, i, j, k, centre, r);
         });
       } else {
         T v[5], r[5];
         wave_point<T, false>(a, a.us + c, v, r);
+        const Images im = ghost_images(a, s, i, j, k);
 #pragma unroll
-        for (int f = 0; f < 5; ++f) stage_write(a, s, f, c, i, j, k, v[f], r[f]);
+        for (int f = 0; f < 5; ++f) write_field(a, s, im, f, c, i, j, k, v[f], r[f]);
       }
     }
   }
@@ -188,11 +189,16 @@ sf_status launch_stage(sf_batch* b, int stage, cudaStream_t st, unsigned int* st
   zc.g_shift = T(b->prm.g_shift);
   zc.slicing = b->prm.slicing;
   zc.shift_frozen = b->prm.shift_frozen;
+  zc.lopsided = b->prm.lopsided;
   const PatchArgs<T>* args = static_cast<const PatchArgs<T>*>(b->d_args) + (size_t)stage * b->npatch;
   const int grid = b->grid[b->precision];
-  batch_stage_kernel<T, H><<<grid, 128, 0, st>>>(args, b->d_sys, b->d_shape, b->d_items,
-                                                      b->nitems, b->d_counter,
-                                                      batch_stage_args(b, stage, status), zc);
+  const StageArgs sa = batch_stage_args(b, stage, status);
+  if (b->prm.lopsided)
+    batch_stage_kernel<T, H, true><<<grid, 128, 0, st>>>(args, b->d_sys, b->d_shape, b->d_items,
+                                                         b->nitems, b->d_counter, sa, zc);
+  else
+    batch_stage_kernel<T, H, false><<<grid, 128, 0, st>>>(args, b->d_sys, b->d_shape, b->d_items,
+                                                          b->nitems, b->d_counter, sa, zc);
   return after_launch("batch_stage_kernel");
 }
 
@@ -245,9 +251,9 @@ sf_status sf_batch_create(const sf_params* prm, const sf_patch* patches, int32_t
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
   int occ[3] = {0, 0, 0};
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], batch_stage_kernel<double, double>, 128, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], batch_stage_kernel<float, double>, 128, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], batch_stage_kernel<float, dw>, 128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], batch_stage_kernel<double, double, false>, 128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], batch_stage_kernel<float, double, false>, 128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], batch_stage_kernel<float, dw, false>, 128, 0);
   for (int q = 0; q < 3; ++q) b->grid[q] = std::max(1, sms * std::max(1, occ[q]));
   std::vector<int> sys(npatch);
   for (int q = 0; q < npatch; ++q) sys[q] = b->patches[q].system;
@@ -427,9 +433,9 @@ sf_status static_setup(int dev) {
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return set_error(SF_ECUDA, "SM count query failed");
   int occ[3] = {0, 0, 0};
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], batch_stage_kernel<double, double>, 128, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], batch_stage_kernel<float, double>, 128, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], batch_stage_kernel<float, dw>, 128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], batch_stage_kernel<double, double, false>, 128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], batch_stage_kernel<float, double, false>, 128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], batch_stage_kernel<float, dw, false>, 128, 0);
   for (int q = 0; q < 3; ++q) g_static_grid[dev][q] = std::max(1, sms * std::max(1, occ[q]));
   g_static_dev[dev] = static_cast<unsigned char*>(p);
   return SF_OK;
@@ -486,10 +492,20 @@ sf_status static_stage(const sf_params& prm, const sf_patch* pin, int np, int st
   zc.g_shift = T(prm.g_shift);
   zc.slicing = prm.slicing;
   zc.shift_frozen = prm.shift_frozen;
-  batch_stage_kernel<T, H><<<g_static_grid[dev][pin[0].precision], 128, 0, st>>>(
-      reinterpret_cast<const PatchArgs<T>*>(d + kOffArgs), reinterpret_cast<const int*>(d + kOffSys),
-      reinterpret_cast<const int2*>(d + kOffShape), reinterpret_cast<const Item*>(d + kOffItems),
-      nitems, reinterpret_cast<unsigned int*>(d), batch_stage_args(&tmp, stage, status_ptr()), zc);
+  zc.lopsided = prm.lopsided;
+  const StageArgs sa = batch_stage_args(&tmp, stage, status_ptr());
+  const int grid = g_static_grid[dev][pin[0].precision];
+  const PatchArgs<T>* targs = reinterpret_cast<const PatchArgs<T>*>(d + kOffArgs);
+  const int* tsys = reinterpret_cast<const int*>(d + kOffSys);
+  const int2* tshape = reinterpret_cast<const int2*>(d + kOffShape);
+  const Item* titems = reinterpret_cast<const Item*>(d + kOffItems);
+  unsigned int* tcounter = reinterpret_cast<unsigned int*>(d);
+  if (prm.lopsided)
+    batch_stage_kernel<T, H, true><<<grid, 128, 0, st>>>(targs, tsys, tshape, titems, nitems,
+                                                         tcounter, sa, zc);
+  else
+    batch_stage_kernel<T, H, false><<<grid, 128, 0, st>>>(targs, tsys, tshape, titems, nitems,
+                                                          tcounter, sa, zc);
   return after_launch("batch_stage_kernel (static scratch)");
 }
 

@@ -1,7 +1,7 @@
 // Shared device/host pieces of the GB300 substep library: patch layout
 // passed to kernels, the 4th-order stencils of Sec. II.B.1, the RK stage
 // combination of Sec. II.C / App. C-D, fused periodic ghost writes and the
-// device status word.
+// status-word bits.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -94,99 +94,29 @@ __device__ __forceinline__ bool finite_(double v) { return isfinite(v); }
 __device__ __forceinline__ bool finite_(float v) { return isfinite(v); }
 
 // ------------------------------------------------------------ stage write
-// Writes one field value of the stage update at ghosted offset `c`
-// (interior point i,j,k).  `centre` is u_stage at c; `r` = (L + Q_d)(u_stage).
-template <typename T>
-__device__ __forceinline__ void stage_write(const PatchArgs<T>& a, const StageArgs& s, int f,
-                                            long long c, int i, int j, int k, T centre, T r) {
-  if (s.mode == 1) {
-    a.nx[f * a.ninterior + ((long long)k * a.n[1] + j) * a.n[0] + i] = r;
-    return;
-  }
-  const long long o = f * a.sf + c;
-  T un = s.un_alias ? centre : a.un[o];
-  T out;
-  if (s.rk == SF_RK4) {
-    if (s.stage == 0) {
-      a.acc[o] = (s.kahan ? T(0) : un) + a.c_acc * r;
-      out = un + a.c_next * r;
-    } else if (s.stage < 3) {
-      a.acc[o] = a.acc[o] + a.c_acc * r;
-      out = un + a.c_next * r;
-    } else if (!s.kahan) {
-      out = a.acc[o] + a.c_next * r;
-    } else {
-      // U^{n+1} = U^n + inc with Kahan compensation carried in kh
-      T inc = a.acc[o] + a.c_next * r;
-      T y = inc - a.kh[o];
-      T t = un + y;
-      a.kh[o] = (t - un) - y;
-      out = t;
-    }
-  } else {
-    if (s.stage == 0) out = un + a.dt * r;
-    else if (s.stage == 1) out = T(0.75) * un + T(0.25) * (centre + a.dt * r);
-    else out = un * T(1.0 / 3.0) + T(2.0 / 3.0) * (centre + a.dt * r);
-  }
-  a.nx[o] = out;
-  if (s.check_finite && !finite_(out)) atomicOr(s.status, ST_NONFINITE);
-  if (s.ghosts) {
-    // periodic images of (i,j,k) inside the ghost shell (n >= g is checked on the host)
-    const int g = a.g;
-    int xs[3] = {0, 0, 0}, ys[3] = {0, 0, 0}, zs[3] = {0, 0, 0};
-    int nxs = 1, nys = 1, nzs = 1;
-    if (i < g) xs[nxs++] = a.n[0];
-    if (i >= a.n[0] - g) xs[nxs++] = -a.n[0];
-    if (j < g) ys[nys++] = a.n[1];
-    if (j >= a.n[1] - g) ys[nys++] = -a.n[1];
-    if (k < g) zs[nzs++] = a.n[2];
-    if (k >= a.n[2] - g) zs[nzs++] = -a.n[2];
-    if (nxs + nys + nzs > 3) {
-      for (int p = 0; p < nzs; ++p)
-        for (int q = 0; q < nys; ++q)
-          for (int w = 0; w < nxs; ++w) {
-            if (p == 0 && q == 0 && w == 0) continue;
-            a.nx[o + zs[p] * a.sz + ys[q] * a.sy + xs[w]] = out;
-          }
-    }
-  }
-}
-
-// ------------------------------------------------------------ split stage write
-// The same stage combination as stage_write, for kernels that compute the
-// periodic ghost images of a point once (ghost_images) and reuse them for
-// every field (write_field).
+// RK stage combination of one field value at ghosted offset c (interior
+// point i,j,k); `centre` is u_stage there and r = (L + Q_d)(u_stage).  The
+// periodic ghost images of the point are computed once (ghost_images) and
+// reused for every field (write_field).
 struct Images {
-  int n;
-  int off[7];  // element offsets of the periodic images (|off| < 2^31 is checked on the host)
+  // bit 2d: the point lies within `ghost` of the low end of axis d (its image
+  // shifted by +n_d is a ghost point); bit 2d+1: of the high end (shift -n_d).
+  // Both bits of one axis are set when n_d < 2 ghost; up to 26 images.
+  unsigned mask;
 };
 
 template <typename T>
 __device__ __forceinline__ Images ghost_images(const PatchArgs<T>& a, const StageArgs& s, int i,
                                                int j, int k) {
   Images im;
-  im.n = 0;
+  im.mask = 0;
   if (!s.ghosts || s.mode == 1) return im;
   const int g = a.g;
-  int xs[3] = {0, 0, 0}, ys[3] = {0, 0, 0}, zs[3] = {0, 0, 0};
-  int nxs = 1, nys = 1, nzs = 1;
-  if (i < g) xs[nxs++] = a.n[0];
-  if (i >= a.n[0] - g) xs[nxs++] = -a.n[0];
-  if (j < g) ys[nys++] = a.n[1];
-  if (j >= a.n[1] - g) ys[nys++] = -a.n[1];
-  if (k < g) zs[nzs++] = a.n[2];
-  if (k >= a.n[2] - g) zs[nzs++] = -a.n[2];
-  if (nxs + nys + nzs == 3) return im;
-  for (int p = 0; p < nzs; ++p)
-    for (int q = 0; q < nys; ++q)
-      for (int w = 0; w < nxs; ++w) {
-        if (p == 0 && q == 0 && w == 0) continue;
-        im.off[im.n++] = (int)(zs[p] * a.sz + ys[q] * a.sy + xs[w]);
-      }
+  im.mask = (i < g ? 1u : 0u) | (i >= a.n[0] - g ? 2u : 0u) | (j < g ? 4u : 0u) |
+            (j >= a.n[1] - g ? 8u : 0u) | (k < g ? 16u : 0u) | (k >= a.n[2] - g ? 32u : 0u);
   return im;
 }
 
-// Returns the value written to u_next (r itself in RHS-only mode).
 template <typename T>
 __device__ __forceinline__ T write_field(const PatchArgs<T>& a, const StageArgs& s,
                                          const Images& im, int f, long long c, int i, int j,
@@ -221,7 +151,25 @@ __device__ __forceinline__ T write_field(const PatchArgs<T>& a, const StageArgs&
   }
   a.nx[o] = out;
   if (s.check_finite && !finite_(out)) atomicOr(s.status, ST_NONFINITE);
-  for (int q = 0; q < im.n; ++q) a.nx[o + im.off[q]] = out;
+  if (im.mask) {
+    // shift index 0: none, 1: +n_d (point near the low end), 2: -n_d
+    const unsigned m = im.mask;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      if (p && !(m & (p == 1 ? 16u : 32u))) continue;
+      const long long oz = p == 0 ? 0 : (p == 1 ? 1 : -1) * (long long)a.n[2] * a.sz;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (q && !(m & (q == 1 ? 4u : 8u))) continue;
+        const long long oy = q == 0 ? 0 : (q == 1 ? 1 : -1) * (long long)a.n[1] * a.sy;
+#pragma unroll
+        for (int w = 0; w < 3; ++w) {
+          if (w && !(m & (w == 1 ? 1u : 2u))) continue;
+          if (p | q | w) a.nx[o + oz + oy + (w == 0 ? 0 : (w == 1 ? a.n[0] : -a.n[0]))] = out;
+        }
+      }
+    }
+  }
   return out;
 }
 

@@ -1,8 +1,9 @@
 // Ideal Newtonian MHD (Sec. IV.B), 8 conserved fields
 //   U = (rho, S_x, S_y, S_z, E, B^x, B^y, B^z),
 // in conservative form L(U)_i = -sum_d (F_{i+1/2} - F_{i-1/2}) / dx_d (Eq. 5).
-// Interface fluxes: WENO5 reconstruction of the evolved fields from the left
-// and right (App. B; JS or Z weights), physical fluxes of both states and the
+// Interface fluxes: WENO reconstruction of the evolved fields from the left
+// and right (WENO5 with JS or Z weights, App. B; WENO3, App. A), physical
+// fluxes of both states and the
 // local Lax-Friedrichs formula (Eq. LLF) with the largest fast magnetosonic
 // signal speed of the two states.  Fused with the RK stage update.
 #include "sf_internal.cuh"
@@ -77,6 +78,30 @@ __device__ __forceinline__ T weno_right(const T* w, T eps, const MhdCoef<T>& mc)
   return (al0 * c0 + al1 * c1 + al2 * c2) / (al0 + al1 + al2);
 }
 
+// App. A: WENO3 left state at i+1/2 from w[1..3] = U_{i-1..i+1}
+template <typename T>
+__device__ __forceinline__ T weno3_left(const T* w, T eps) {
+  const T c0 = T(0.5) * w[2] + T(0.5) * w[3];
+  const T c1 = T(-0.5) * w[1] + T(1.5) * w[2];
+  const T b0 = (w[3] - w[2]) * (w[3] - w[2]);
+  const T b1 = (w[2] - w[1]) * (w[2] - w[1]);
+  const T e0 = eps + b0, e1 = eps + b1;
+  const T a0 = T(2.0 / 3.0) / (e0 * e0), a1 = T(1.0 / 3.0) / (e1 * e1);
+  return (a0 * c0 + a1 * c1) / (a0 + a1);
+}
+
+// App. A: WENO3 right state at i-1/2 from w[1..3] = U_{i-1..i+1}
+template <typename T>
+__device__ __forceinline__ T weno3_right(const T* w, T eps) {
+  const T c0 = T(-0.5) * w[3] + T(1.5) * w[2];
+  const T c1 = T(0.5) * w[2] + T(0.5) * w[1];
+  const T b0 = (w[2] - w[3]) * (w[2] - w[3]);
+  const T b1 = (w[1] - w[2]) * (w[1] - w[2]);
+  const T e0 = eps + b0, e1 = eps + b1;
+  const T a0 = T(1.0 / 3.0) / (e0 * e0), a1 = T(2.0 / 3.0) / (e1 * e1);
+  return (a0 * c0 + a1 * c1) / (a0 + a1);
+}
+
 // physical flux along d and the largest signal speed |v_d| + c_fast,d
 template <typename T>
 __device__ __forceinline__ T flux_speed(const T* q, int d, const MhdCoef<T>& mc, T* F) {
@@ -112,8 +137,13 @@ __device__ __forceinline__ void face_flux(const T* __restrict__ p, long long F, 
     T w[6];
 #pragma unroll
     for (int o = 0; o < 6; ++o) w[o] = __ldg(q + (o - 2) * s);
-    UL[f] = weno_left(w, mc.eps[d], mc);
-    UR[f] = weno_right(w + 1, mc.eps[d], mc);
+    if (mc.variant == 2) {
+      UL[f] = weno3_left(w, mc.eps[d]);
+      UR[f] = weno3_right(w + 1, mc.eps[d]);
+    } else {
+      UL[f] = weno_left(w, mc.eps[d], mc);
+      UR[f] = weno_right(w + 1, mc.eps[d], mc);
+    }
   }
   T FL[8], FR[8];
   const T sl = flux_speed(UL, d, mc, FL);
@@ -249,7 +279,8 @@ static MhdCoef<T> coef(const sf_params& prm, const sf_patch& p) {
   mc.gamma = T(prm.gamma_eos);
   for (int d = 0; d < 3; ++d) {
     const double h = p.dx[d];
-    mc.eps[d] = T(prm.weno_eps > 0 ? prm.weno_eps : h * h * h * h);
+    mc.eps[d] = T(prm.weno_eps > 0 ? prm.weno_eps
+                                   : (prm.weno_variant == 2 ? h * h : h * h * h * h));
     mc.idx[d] = T(1.0 / h);
   }
   mc.q = T(prm.weno_q);

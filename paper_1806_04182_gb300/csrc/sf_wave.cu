@@ -15,8 +15,9 @@ __global__ void __launch_bounds__(128) wave_stage_kernel(PatchArgs<T> a, StageAr
   const long long c = (long long)(k + g) * a.sz + (long long)(j + g) * a.sy + (i + g);
   T v[5], r[5];
   wave_point<T, ADJ>(a, a.us + c, v, r);
+  const Images im = ghost_images(a, s, i, j, k);
 #pragma unroll
-  for (int f = 0; f < 5; ++f) stage_write(a, s, f, c, i, j, k, v[f], r[f]);
+  for (int f = 0; f < 5; ++f) write_field(a, s, im, f, c, i, j, k, v[f], r[f]);
 }
 
 template <typename T>

@@ -1,7 +1,8 @@
 // Standalone CCZ4 stage kernel (one launch per patch); the per-point
 // right-hand side lives in sf_z4.cuh.  Layouts with the strides of a 96^3
 // patch with 3 ghosts (the benchmark configuration) get a kernel with
-// compile-time strides; every other layout uses runtime strides.
+// compile-time strides; every other layout, and one-sided advection, uses
+// runtime strides.
 #include "sf_internal.cuh"
 #include "sf_z4.cuh"
 
@@ -10,7 +11,7 @@ namespace sf {
 // 128 threads and at least 3 CTAs per SM for the float kernels (<= 168
 // registers): on the 96^3 benchmark patch this measured faster than 2 CTAs
 // (255 registers) and than 4+ CTAs (128 registers or fewer, with spills).
-template <typename T, typename H, int SY, int SZ>
+template <typename T, typename H, int SY, int SZ, bool LOP>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2)
     z4_stage_kernel(PatchArgs<T> a, StageArgs s, Z4Coef<T> zc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -21,9 +22,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2)
   const long long sy = SY ? (long long)SY : a.sy;
   const long long sz = SZ ? (long long)SZ : a.sz;
   const long long c = (long long)(k + g) * sz + (long long)(j + g) * sy + (i + g);
-  const T* __restrict__ u = a.us + c;
+  GlobalSrc<T, SY, SZ> src{a.us + c, a.sf, a.sy, a.sz};
   const Images im = ghost_images(a, s, i, j, k);
-  z4_cell<T, H, SY, SZ>(a, zc, u, [&](int f, T r, T centre) {
+  z4_cell<T, H, LOP>(a, zc, src, [&](int f, T r, T centre) {
     write_field(a, s, im, f, c, i, j, k, centre, r);
   });
 }
@@ -37,6 +38,7 @@ Z4Coef<T> z4_coef(const sf_params& prm) {
   zc.g_shift = T(prm.g_shift);
   zc.slicing = prm.slicing;
   zc.shift_frozen = prm.shift_frozen;
+  zc.lopsided = prm.lopsided;
   return zc;
 }
 
@@ -47,10 +49,12 @@ static sf_status launch(const sf_params& prm, const sf_patch& p, const StageArgs
   const Z4Coef<T> zc = z4_coef<T>(prm);
   dim3 block(32, 4, 1);
   dim3 grid((p.n[0] + 31) / 32, (p.n[1] + 3) / 4, p.n[2]);
-  if (p.sy == 102 && p.sz == 102 * 102)
-    z4_stage_kernel<T, H, 102, 102 * 102><<<grid, block, 0, st>>>(a, s, zc);
+  if (prm.lopsided)
+    z4_stage_kernel<T, H, 0, 0, true><<<grid, block, 0, st>>>(a, s, zc);
+  else if (p.sy == 102 && p.sz == 102 * 102)
+    z4_stage_kernel<T, H, 102, 102 * 102, false><<<grid, block, 0, st>>>(a, s, zc);
   else
-    z4_stage_kernel<T, H, 0, 0><<<grid, block, 0, st>>>(a, s, zc);
+    z4_stage_kernel<T, H, 0, 0, false><<<grid, block, 0, st>>>(a, s, zc);
   return after_launch("z4_stage_kernel");
 }
 

@@ -31,6 +31,7 @@ struct Z4Coef {
   T kappa_z, kappa_c, eta, g_shift;
   int slicing;       // 0: 1+log, 1: harmonic
   int shift_frozen;
+  int lopsided;      // 1: one-sided advection stencils (Sec. II.B.1); picks the LOP instance
 };
 
 __host__ __device__ constexpr int S(int a, int b) {
@@ -44,39 +45,77 @@ struct Cross {
   T d[3];   // D_x, D_y, D_z
   T dd[3];  // D_xx, D_yy, D_zz (when requested)
   T ko;     // sum_d sigma/(64 dx_d) delta^6_d
+  T adv;    // beta^k d_k U: centred D_k, or one-sided by the sign of beta^k
 };
 
-template <typename T, typename H, int SY, int SZ, typename Out>
-__device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& zc,
-                                        const T* __restrict__ u, Out&& out) {
+// Stencil source reading the ghosted SoA arrays in global memory.
+template <typename T, int SY, int SZ>
+struct GlobalSrc {
+  const T* __restrict__ u;  // centre of field 0
+  long long F, sy_, sz_;
+  __device__ __forceinline__ long long sy() const { return SY ? (long long)SY : sy_; }
+  __device__ __forceinline__ long long sz() const { return SZ ? (long long)SZ : sz_; }
+  __device__ __forceinline__ const T* p(int f) const { return u + f * F; }
+  __device__ __forceinline__ T ld(const T* q) const { return __ldg(q); }
+  __device__ __forceinline__ T centre(int f) const { return __ldg(u + f * F); }
+  __device__ __forceinline__ void begin(int) {}   // called before field f's first stencil
+  __device__ __forceinline__ void finish() {}     // called once at the end
+};
+
+// LOP: one-sided advection stencils compiled in (Z4Coef::lopsided selects
+// the instance at launch, so the centred instance carries no extra code).
+template <typename T, typename H, bool LOP, typename Src, typename Out>
+__device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& zc, Src& src,
+                                        Out&& out) {
   using I = Isl<H>;
-  const long long F = a.sf;
-  const long long sy = SY ? (long long)SY : a.sy;
-  const long long sz = SZ ? (long long)SZ : a.sz;
+  const long long sy = src.sy();
+  const long long sz = src.sz();
   const long long st[3] = {1, sy, sz};
-  auto U = [&](int f) { return u + f * F; };
-  auto c0 = [&](int f) { return __ldg(U(f)); };
+  auto U = [&](int f) { return src.p(f); };
+  auto c0 = [&](int f) { return src.centre(f); };
+  T be[3], Gh[3];  // loaded with the other centre values below
   // 19-point cross of field f: first derivatives, KO, optional D_ii
   auto cross = [&](int f, bool second) {
+    src.begin(f);
     const T* p = U(f);
     Cross<T> x;
-    x.c = __ldg(p);
+    x.c = src.ld(p);
     x.ko = T(0);
+    x.adv = T(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const long long s = st[d];
-      const T m1 = __ldg(p - s), p1 = __ldg(p + s);
-      const T m2 = __ldg(p - 2 * s), p2 = __ldg(p + 2 * s);
-      const T m3 = __ldg(p - 3 * s), p3 = __ldg(p + 3 * s);
+      const T m1 = src.ld(p - s), p1 = src.ld(p + s);
+      const T m2 = src.ld(p - 2 * s), p2 = src.ld(p + 2 * s);
+      const T m3 = src.ld(p - 3 * s), p3 = src.ld(p + 3 * s);
       x.d[d] = ((m2 - p2) + T(8) * (p1 - m1)) * a.i12h[d];
       x.dd[d] = second ? (T(16) * (m1 + p1) - (m2 + p2) - T(30) * x.c) * a.i12h2[d] : T(0);
       x.ko += a.ko[d] * ((m3 + p3) - T(6) * (m2 + p2) + T(15) * (m1 + p1) - T(20) * x.c);
+      // advection along d (Sec. II.B.1), one-sided on the side the
+      // characteristic comes from; the centred instance forms beta^k D_k at
+      // the point of use instead (advk)
+      if (LOP) {
+        T ad = x.d[d];
+        if (be[d] != T(0))
+          ad = (be[d] > T(0) ? (p3 - T(6) * p2 + T(18) * p1 - T(10) * x.c - T(3) * m1)
+                             : (-m3 + T(6) * m2 - T(18) * m1 + T(10) * x.c + T(3) * p1)) *
+               a.i12h[d];
+        x.adv += be[d] * ad;
+      }
     }
     return x;
   };
+  auto advk = [&](const T* dd) { return be[0] * dd[0] + be[1] * dd[1] + be[2] * dd[2]; };
+  auto adv = [&](const Cross<T>& x) { return LOP ? x.adv : advk(x.d); };
   auto MIX = [&](int f, int m, int n) -> T {
     const int pi = (m == 0 && n == 1) ? 0 : ((m == 0 && n == 2) ? 1 : 2);
-    return dmix(U(f), st[m], st[n], a.i144hh[pi]);
+    const T* p = U(f);
+    const long long sa = st[m], sb = st[n];
+    auto row = [&](long long o) {
+      const T* q = p + o;
+      return (src.ld(q - 2 * sa) - src.ld(q + 2 * sa)) + T(8) * (src.ld(q + sa) - src.ld(q - sa));
+    };
+    return ((row(-2 * sb) - row(2 * sb)) + T(8) * (row(sb) - row(-sb))) * a.i144hh[pi];
   };
 
   // float storage holds chi, gt_xx, gt_yy, gt_zz and alpha minus their flat
@@ -90,10 +129,8 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
     gt[q] = c0(1 + q) + ((q == 0 || q == 3 || q == 5) ? off : T(0));
     At[q] = c0(8 + q);
   }
-  T be[3], Gh[3];
 #pragma unroll
   for (int p = 0; p < 3; ++p) { be[p] = c0(19 + p); Gh[p] = c0(14 + p); }
-  auto advk = [&](const T* dd) { return be[0] * dd[0] + be[1] * dd[1] + be[2] * dd[2]; };
   const T kz = zc.kappa_z, kc = zc.kappa_c;
 
   // ---- islands: determinant, inverse and ln det of the conformal metric,
@@ -133,12 +170,13 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
   const T trA = I::template to<T>(trAH);
 
   // ---- shift: first derivatives, gt^{mn} d_m d_n beta^c and d_b d_k beta^k
-  T dbe[3][3], koBe[3];
+  T dbe[3][3], koBe[3], advBe[3];
   T s2[3] = {T(0), T(0), T(0)}, ddiv[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const Cross<T> x = cross(19 + c, true);
     koBe[c] = x.ko;
+    if (LOP) advBe[c] = x.adv;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       dbe[c][d] = x.d[d];  // partial_d beta^c
@@ -184,7 +222,7 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
         for (int c = 0; c < 3; ++c) s += gt[S(p, c)] * dbe[c][b] + gt[S(c, b)] * dbe[c][p];
         const T AtTF = tf_isl(At[q], gt[q], trAH);
         out(1 + q,
-            advk(x.d) + s - T(2.0 / 3.0) * gt[q] * divbe - T(2) * al * AtTF -
+            adv(x) + s - T(2.0 / 3.0) * gt[q] * divbe - T(2) * al * AtTF -
                 kc * T(1.0 / 3.0) * al * gt[q] * lndet + x.ko,
             x.c);
       }
@@ -221,7 +259,7 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
     ddchi[1] = MIX(0, 0, 1);
     ddchi[2] = MIX(0, 0, 2);
     ddchi[4] = MIX(0, 1, 2);
-    out(0, advk(dchi) + T(2.0 / 3.0) * chi * (al * Kt - divbe) + x.ko, x.c);
+    out(0, adv(x) + T(2.0 / 3.0) * chi * (al * Kt - divbe) + x.ko, x.c);
   }
   const T ialpha = T(1) / al;
   {
@@ -232,17 +270,18 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
     ddal[2] = MIX(18, 0, 2);
     ddal[4] = MIX(18, 1, 2);
     const T fsl = zc.slicing == 0 ? T(2) * ialpha : T(1);
-    out(18, advk(dal) - al * al * fsl * Kh + x.ko, x.c);
+    out(18, adv(x) - al * al * fsl * Kh + x.ko, x.c);
   }
 
   // ---- Ricci tensor Rhat_ab + Rchi_ab
   const T ichi = T(1) / chi;
   T Rt[6];
-  T dGh[3][3], koGh[3];
+  T dGh[3][3], koGh[3], advGh[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const Cross<T> x = cross(14 + c, false);
     koGh[c] = x.ko;
+    if (LOP) advGh[c] = x.adv;
 #pragma unroll
     for (int d = 0; d < 3; ++d) dGh[c][d] = x.d[d];  // partial_d Gammahat^c
   }
@@ -351,7 +390,7 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
     const Cross<T> x = cross(7, false);
 #pragma unroll
     for (int d = 0; d < 3; ++d) dKh[d] = x.d[d];
-    out(7, advk(dKh) - LapAl + al * (T(1.0 / 3.0) * Kt * Kt + AA + kz * Th) + T(2) * Zdal + x.ko,
+    out(7, adv(x) - LapAl + al * (T(1.0 / 3.0) * Kt * Kt + AA + kz * Th) + T(2) * Zdal + x.ko,
         Kh);
   }
   {
@@ -359,7 +398,7 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
 #pragma unroll
     for (int d = 0; d < 3; ++d) dTh[d] = x.d[d];
     out(17,
-        advk(dTh) +
+        adv(x) +
             T(0.5) * al * (RZ + T(2.0 / 3.0) * Kh * Kh + T(2.0 / 3.0) * Th * (Kh - T(2) * Th) - AA) -
             Zdal - T(2) * al * kz * Th + x.ko,
         Th);
@@ -382,7 +421,7 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
         }
         const T MTF = tf_isl(M[q], gt[q], trM);
         out(8 + q,
-            advk(x.d) + s - T(2.0 / 3.0) * At[q] * divbe - kc * T(1.0 / 3.0) * al * gt[q] * trA +
+            adv(x) + s - T(2.0 / 3.0) * At[q] * divbe - kc * T(1.0 / 3.0) * al * gt[q] * trA +
                 chi * MTF + al * (Kh * At[q] - T(2) * AAd) + x.ko,
             x.c);
       }
@@ -408,7 +447,7 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
     rGh[p] = -sb + T(2.0 / 3.0) * Gh[p] * divbe + s2[p] + T(1.0 / 3.0) * s3v - T(2) * s4 +
              T(2) * al * (s5 - T(1.5) * ichi * s6 - T(2.0 / 3.0) * s7) +
              T(2) * al * (-s8 - ichi * Z[p] * (kz + T(2.0 / 3.0) * Kt));
-    out(14 + p, advk(dGh[p]) + rGh[p] + koGh[p], Gh[p]);
+    out(14 + p, (LOP ? advGh[p] : advk(dGh[p])) + rGh[p] + koGh[p], Gh[p]);
   }
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
@@ -417,10 +456,11 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
       out(22 + p, T(0), c0(22 + p));
     } else {
       const Cross<T> x = cross(22 + p, false);
-      out(19 + p, advk(dbe[p]) + zc.g_shift * x.c + koBe[p], be[p]);
-      out(22 + p, advk(x.d) - zc.eta * x.c + rGh[p] + x.ko, x.c);
+      out(19 + p, (LOP ? advBe[p] : advk(dbe[p])) + zc.g_shift * x.c + koBe[p], be[p]);
+      out(22 + p, adv(x) - zc.eta * x.c + rGh[p] + x.ko, x.c);
     }
   }
+  src.finish();
 }
 
 }  // namespace sf

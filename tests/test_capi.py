@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(L):
 
 def test_struct_layouts_match_header():
     # sizes follow from the C declaration order with natural alignment
-    assert ctypes.sizeof(capi.sf_params) == 4 + 4 + 8 * 4 + 4 * 4 + 8 * 4
+    assert ctypes.sizeof(capi.sf_params) == 4 + 4 + 8 * 4 + 4 * 4 + 8 * 4 + 4 + 4
     assert ctypes.sizeof(capi.sf_patch) == 12 + 4 + 24 + 8 + 4 + 4 + 24 + 5 * 8 + 8
 
 

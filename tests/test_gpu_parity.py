@@ -44,7 +44,7 @@ def oracle_params(prm: capi.sf_params):
     return oracle.params(sigma=prm.sigma_ko, gamma_eos=prm.gamma_eos, weno_eps=prm.weno_eps,
                          weno_q=prm.weno_q, kappa_z=prm.kappa_z, kappa_c=prm.kappa_c, eta=prm.eta,
                          g_shift=prm.g_shift, weno_variant=prm.weno_variant, slicing=prm.slicing,
-                         shift_frozen=prm.shift_frozen)
+                         shift_frozen=prm.shift_frozen, lopsided=prm.lopsided)
 
 
 def run_stages(system, U0, dx, dt, prm, precision=capi.SF_FP64):
@@ -121,17 +121,40 @@ def test_wave_fp32_bulk_step():
 
 
 # ------------------------------------------------------------------ Z4
-@pytest.mark.parametrize("slicing,frozen", [(0, 0), (1, 1)])
-def test_z4_fp64_stages(slicing, frozen):
+@pytest.mark.parametrize("slicing,frozen,lop", [(0, 0, 0), (1, 1, 0), (0, 0, 1)])
+def test_z4_fp64_stages(slicing, frozen, lop):
     n = (35, 9, 6)
     U0, dx = inputs.z4_perturbed(n, seed=1, amp=0.05)
-    prm = capi.params(slicing=slicing, shift_frozen=frozen)
+    prm = capi.params(slicing=slicing, shift_frozen=frozen, lopsided=lop)
     dt = 0.25 * min(dx)
     got = run_stages(capi.SF_Z4, U0, dx, dt, prm)
     want = oracle_stages(oracle.Z4, U0, dx, dt, prm)
     for s in range(4):
         e = rel_err(got[s], want[s], floor=1e-3)
         assert e.max() < TOL64, (s, e)
+
+
+@pytest.mark.parametrize("n", [(3, 5, 4), (7, 3, 5)])
+def test_small_boxes_all_systems(n):
+    # ghost <= n < 2 ghost: a point near both ends of an axis has periodic
+    # images on both sides (up to 26 ghost copies per point)
+    for system, osys, data, prm in (
+            (capi.SF_WAVE, oracle.WAVE, inputs.wave_plane(n, seed=3), capi.params()),
+            (capi.SF_Z4, oracle.Z4, inputs.z4_perturbed(n, seed=3, amp=0.03), capi.params()),
+            (capi.SF_MHD, oracle.MHD, inputs.mhd_blast(n, seed=3, radius=0.4),
+             capi.params(rk=capi.SF_SSPRK3))):
+        U0, dx = data
+        dt = 0.1 * min(dx)
+        got = run_stages(system, U0, dx, dt, prm)
+        want = oracle_stages(osys, U0, dx, dt, prm)
+        for s_ in range(len(want)):
+            assert rel_err(got[s_], want[s_], floor=1e-2).max() < TOL64, (system, s_)
+        # the ghost shell written by the last stage equals a periodic fill
+        st = PatchState(system, n, dx, dt, prm=prm)
+        st.upload(U0)
+        st.step(1)
+        G = oracle.ghosted(st.interior().cpu().numpy().copy())
+        np.testing.assert_array_equal(st.A.cpu().numpy(), G)
 
 
 def test_z4_rhs_matches_oracle():
@@ -178,7 +201,7 @@ def test_z4_fp32_bulk_step():
 
 
 # ------------------------------------------------------------------ MHD
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_mhd_fp64_stages(variant):
     n = (35, 10, 7)
     U0, dx = inputs.mhd_blast(n, seed=4, radius=0.3)
