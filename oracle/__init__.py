@@ -32,6 +32,21 @@ Functions and what pins them (tests/test_oracle_*.py):
                    Shu-Osher form.
   misfit_gradient  discrete adjoint of the RK4 wave evolution.  Pinned:
                    central finite differences (exact for the quadratic misfit).
+  stencil(DLOP)    Sec. II.B.1 one-sided advection stencils.  Pinned:
+                   exactness on quartics, one-sidedness, truncation term.
+  prolong          Sec. III.A quintic Lagrange prolongation.  Pinned:
+                   exactness on quintic polynomials, injection at coincident
+                   points, 6th-order convergence on smooth data.
+  restrict         Sec. III.A injection.  Pinned: brute-force copy.
+  dense_output     App. C interpolators.  Pinned: theta = 0 and 1 give U^n
+                   and U^{n+1}; exact on polynomial-in-time solutions of the
+                   interpolator's order; derivatives against finite
+                   differences in theta.
+  bor_fine_stages  App. D (BOR).  Pinned: with R = 1 the fine stages equal
+                   the coarse RK4 stages for any increments; for a forcing
+                   f(t) of degree 2 (RK4) or 1 (SSP-RK3) the fine stages equal
+                   those of a fine RK step; 4th-order (RK4) error of the
+                   sub-cycled solution of a linear ODE system.
 """
 from __future__ import annotations
 
@@ -43,6 +58,7 @@ import threading
 import numpy as np
 
 WAVE, MHD, Z4, WAVE_ADJ = 0, 1, 2, 3
+RK4, SSPRK3 = 0, 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sf_oracle.cpp")
@@ -129,6 +145,10 @@ def lib() -> ctypes.CDLL:
                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_double]
         L.or_stencil.restype = ctypes.c_double
+        L.or_bor_fine_stages.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double,
+                                         ctypes.c_int, ctypes.c_int, dp]
+        L.or_dense_output.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int, dp]
         _lib = L
     return _lib
 
@@ -206,6 +226,33 @@ def restrict(Uf: np.ndarray, ratio: int, origin, ext, g: int = 3) -> np.ndarray:
     if rc:
         raise ValueError("oracle restrict: out of the fine box")
     return out
+
+
+def bor_fine_stages(rk: int, Un: np.ndarray, k: np.ndarray, dt: float, R: int, r: int) -> np.ndarray:
+    """Sec. III.B / App. D (BOR): fine stage inputs U^(1..s) and the end value
+    U^{n+(r+1)/R} of fine step r of R, from the coarse U^n (any shape) and the
+    coarse increments k (s x Un.shape), s = 4 (RK4, rk = 0) or 3 (SSP-RK3).
+    Returns an array (s + 1) x Un.shape."""
+    s = 4 if rk == RK4 else 3
+    un = np.ascontiguousarray(Un, dtype=np.float64).ravel()
+    kk = np.ascontiguousarray(k, dtype=np.float64).reshape(s, un.size)
+    out = np.zeros((s + 1, un.size))
+    rc = lib().or_bor_fine_stages(rk, un.size, _dp(un), _dp(kk), dt, R, r, _dp(out))
+    if rc:
+        raise ValueError("oracle bor_fine_stages: bad arguments")
+    return out.reshape((s + 1,) + np.shape(Un))
+
+
+def dense_output(rk: int, Un: np.ndarray, k: np.ndarray, dt: float, theta: float, m: int = 0) -> np.ndarray:
+    """App. C dense output (m = 0) or its m-th time derivative at t^n + theta dt."""
+    s = 4 if rk == RK4 else 3
+    un = np.ascontiguousarray(Un, dtype=np.float64).ravel()
+    kk = np.ascontiguousarray(k, dtype=np.float64).reshape(s, un.size)
+    out = np.zeros(un.size)
+    rc = lib().or_dense_output(rk, un.size, _dp(un), _dp(kk), dt, theta, m, _dp(out))
+    if rc:
+        raise ValueError("oracle dense_output: bad arguments")
+    return out.reshape(np.shape(Un))
 
 
 def rk4_step(system: int, U: np.ndarray, dx, dt: float, p: Params | None = None, g: int = 3,

@@ -1103,6 +1103,125 @@ int or_restrict(int nf, const int* nfine, int gf, const double* fu, int ratio, c
   return 0;
 }
 
+// ---------------------------------------------------------------- sub-cycling
+// App. C dense output of one coarse RK step, U(t^n + theta dt) =
+// U^n + sum_j b_j(theta) k_j, and its theta-derivatives d^m b_j / d theta^m
+// (m = 0..3) written out from the polynomials.
+//   RK(4,4):    b_1 = theta - 3/2 theta^2 + 2/3 theta^3,
+//               b_2 = b_3 = theta^2 - 2/3 theta^3,
+//               b_4 = -1/2 theta^2 + 2/3 theta^3   (sign of the cubic term read
+//               so that b_4(1) = 1/6, the RK weight);
+//   SSP-RK(3,3): b_1 = theta - 5/6 theta^2, b_2 = 1/6 theta^2, b_3 = 4/6 theta^2.
+static void dense_b(int rk, double th, int m, double b[4]) {
+  const double t2 = th * th, t3 = t2 * th;
+  if (rk == 0) {
+    switch (m) {
+      case 0: b[0] = th - 1.5 * t2 + (2.0 / 3.0) * t3; b[1] = t2 - (2.0 / 3.0) * t3;
+              b[3] = -0.5 * t2 + (2.0 / 3.0) * t3; break;
+      case 1: b[0] = 1.0 - 3.0 * th + 2.0 * t2; b[1] = 2.0 * th - 2.0 * t2; b[3] = -th + 2.0 * t2; break;
+      case 2: b[0] = -3.0 + 4.0 * th; b[1] = 2.0 - 4.0 * th; b[3] = -1.0 + 4.0 * th; break;
+      default: b[0] = 4.0; b[1] = -4.0; b[3] = 4.0; break;
+    }
+    b[2] = b[1];
+  } else {
+    switch (m) {
+      case 0: b[0] = th - (5.0 / 6.0) * t2; b[1] = t2 / 6.0; b[2] = (4.0 / 6.0) * t2; break;
+      case 1: b[0] = 1.0 - (5.0 / 3.0) * th; b[1] = th / 3.0; b[2] = (4.0 / 3.0) * th; break;
+      case 2: b[0] = -5.0 / 3.0; b[1] = 1.0 / 3.0; b[2] = 4.0 / 3.0; break;
+      default: b[0] = b[1] = b[2] = 0.0; break;
+    }
+    b[3] = 0.0;
+  }
+}
+
+// Sec. III.B / App. D, Berger-Oliger without order reduction, for one fine
+// step r (0 <= r < R) of the R fine steps inside one coarse step of size dt.
+// Inputs per point q: the coarse U^n (un[q]) and the coarse stage increments
+// k_j = dt L(U^(j)) (k[j*npts + q], j < s; s = 4 for RK4, 3 for SSP-RK3).
+// Steps, in the order of App. D:
+//   1. U_{n+r/R} from the dense output at theta = r/R;
+//   2. the first three time derivatives of U from the theta-derivatives of
+//      the dense output, d^m U/dt^m = dt^-m sum_j k_j b_j^(m)(theta), and
+//      (RK4 only) the Jacobian term f_U U_tt = 4 (k_3 - k_2) / dt^3;
+//   3. the fine increments with dt_F = dt / R (RK4: the four fine-grid
+//      increments of App. D; SSP-RK3: k_1 = dt_F U_t, k_2 = dt_F U_t +
+//      dt_F^2 U_tt, k_3 = dt_F U_t + dt_F^2 U_tt / 2);
+//   4. the fine stage inputs and the end-of-step value: RK4 U^(1) = U_{n+r/R},
+//      U^(2) = U^(1) + k_1/2, U^(3) = U^(1) + k_2/2, U^(4) = U^(1) + k_3,
+//      U^{n+(r+1)/R} = U^(1) + (k_1 + 2k_2 + 2k_3 + k_4)/6; SSP-RK3 U^(1),
+//      U^(2) = U^(1) + k_1, U^(3) = U^(1) + k_1/4 + k_2/4 (the printed
+//      k_2/4 + k_3/4 read as the scheme's own third stage, as in the coarse
+//      step), U^{n+(r+1)/R} = U^(1) + (k_1 + k_2 + 4 k_3)/6.
+// out[m*npts + q], m = 0..s: U^(1..s) then U^{n+(r+1)/R}.
+int or_bor_fine_stages(int rk, int npts, const double* un, const double* k, double dt, int R,
+                       int r, double* out) {
+  if ((rk != 0 && rk != 1) || R < 1 || r < 0 || r >= R || npts < 0) return 1;
+  const int s = rk == 0 ? 4 : 3;
+  const double th = (double)r / (double)R;
+  const double dtF = dt / (double)R;
+  double b0[4], b1[4], b2[4], b3[4];
+  dense_b(rk, th, 0, b0);
+  dense_b(rk, th, 1, b1);
+  dense_b(rk, th, 2, b2);
+  dense_b(rk, th, 3, b3);
+  for (int q = 0; q < npts; ++q) {
+    double kk[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = 0; j < s; ++j) kk[j] = k[(size_t)j * npts + q];
+    // step 1
+    double U = un[q];
+    for (int j = 0; j < s; ++j) U += b0[j] * kk[j];
+    // step 2
+    double d1 = 0.0, d2 = 0.0, d3 = 0.0;
+    for (int j = 0; j < s; ++j) {
+      d1 += b1[j] * kk[j];
+      d2 += b2[j] * kk[j];
+      d3 += b3[j] * kk[j];
+    }
+    const double Ut = d1 / dt, Utt = d2 / (dt * dt), Uttt = d3 / (dt * dt * dt);
+    double* o = out + q;
+    if (rk == 0) {
+      const double fUtt = 4.0 * (kk[2] - kk[1]) / (dt * dt * dt);
+      // step 3
+      const double f1 = dtF * Ut;
+      const double f2 = dtF * Ut + 0.5 * dtF * dtF * Utt + 0.125 * dtF * dtF * dtF * (Uttt - fUtt);
+      const double f3 = dtF * Ut + 0.5 * dtF * dtF * Utt + 0.125 * dtF * dtF * dtF * (Uttt + fUtt);
+      const double f4 = dtF * Ut + dtF * dtF * Utt + 0.5 * dtF * dtF * dtF * Uttt;
+      // step 4
+      o[0] = U;
+      o[(size_t)npts] = U + 0.5 * f1;
+      o[2 * (size_t)npts] = U + 0.5 * f2;
+      o[3 * (size_t)npts] = U + f3;
+      o[4 * (size_t)npts] = U + (f1 + 2.0 * f2 + 2.0 * f3 + f4) / 6.0;
+    } else {
+      const double f1 = dtF * Ut;
+      const double f2 = dtF * Ut + dtF * dtF * Utt;
+      const double f3 = dtF * Ut + 0.5 * dtF * dtF * Utt;
+      o[0] = U;
+      o[(size_t)npts] = U + f1;
+      o[2 * (size_t)npts] = U + 0.25 * f1 + 0.25 * f2;
+      o[3 * (size_t)npts] = U + (f1 + f2 + 4.0 * f3) / 6.0;
+    }
+  }
+  return 0;
+}
+
+// Dense output U(t^n + theta dt) and its time derivatives (App. C):
+// out[q] = dt^-m sum_j k_j b_j^(m)(theta) (+ U^n for m = 0).
+int or_dense_output(int rk, int npts, const double* un, const double* k, double dt, double theta,
+                    int m, double* out) {
+  if ((rk != 0 && rk != 1) || m < 0 || m > 3) return 1;
+  const int s = rk == 0 ? 4 : 3;
+  double b[4];
+  dense_b(rk, theta, m, b);
+  const double scale = std::pow(dt, -(double)m);
+  for (int q = 0; q < npts; ++q) {
+    double v = 0.0;
+    for (int j = 0; j < s; ++j) v += b[j] * k[(size_t)j * npts + q];
+    out[q] = (m == 0 ? un[q] : 0.0) + scale * v;
+  }
+  return 0;
+}
+
 // One stencil of Sec. II.B.1 at interior point (i,j,k) of field f of a
 // ghost-filled array: op 0 = D_d1, 1 = D_d1d1, 2 = D_d2(D_d1) (d1 != d2),
 // 3 = Q_d with strength sigma (all three directions), 4 = one-sided D_d1 for
