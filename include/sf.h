@@ -248,6 +248,33 @@ sf_status sf_prolong(const sf_patch* coarse, const void* coarse_array, int32_t n
                      int64_t out_sz, int64_t out_sf, void* stream);
 
 /*
+ * Sub-cycling in time by Berger-Oliger without order reduction (Sec. III.B;
+ * dense output App. C; BOR App. D), fused with the prolongation above: the
+ * fine-grid value needed at fine points origin .. origin+ext-1 for fine step
+ * r (0 <= r < ratio) of the `ratio` fine steps (dt_F = dt / ratio) inside
+ * one coarse step.
+ *   rk = SF_RK4:    states[0..4] = coarse U^n, U^(2) = U^n + k_1/2,
+ *                   U^(3) = U^n + k_2/2, U^(4) = U^n + k_3, U^{n+1};
+ *   rk = SF_SSPRK3: states[0..3] = coarse U^n, U^(2) = U^n + k_1,
+ *                   U^(3) = U^n + (k_1 + k_2)/4, U^{n+1}
+ * (the stage inputs the coarse substeps produce, each ghost-filled, layout
+ * of `coarse`).  The coarse increments k_j follow from them exactly; the
+ * value is that of App. D: the dense output at theta = r/ratio, its time
+ * derivatives, the fine increments with dt_F, and the fine RK formula:
+ *   stage = 0 .. s-1  ->  fine stage input U^(stage+1) of fine step r,
+ *   stage = s         ->  U^{n+(r+1)/ratio},
+ * with s = 4 (RK4) or 3 (SSP-RK3).  The result is then prolonged in space as
+ * sf_prolong does (ratio 1: a copy) and written to fine_out.  Every value is
+ * formed in double precision and stored in the coarse element type.
+ * SF_EINVAL for a NULL or misaligned state, stage or r out of range, or a
+ * stencil node outside the ghosted coarse box.
+ */
+sf_status sf_bor_prolong(const sf_patch* coarse, int32_t rk, const void* const* states, int32_t nf,
+                         int32_t ratio, int32_t r, int32_t stage, const int32_t* origin,
+                         const int32_t* ext, void* fine_out, int64_t out_sy, int64_t out_sz,
+                         int64_t out_sf, void* stream);
+
+/*
  * Batched AMR-patch dispatch: one persistent launch per stage over a table of
  * patches of mixed systems (SF_WAVE and SF_Z4) and sizes, each with its own
  * dx and dt.  CTAs take (patch, tile) work items from a device queue.

@@ -1,14 +1,24 @@
 """Host-side bookkeeping of the AMR level loop (Sec. III) over the C ABI.
 
-A periodic box tiled by a regular grid of equal patches exchanges its ghost
-shells with ``sf_copy_boxes`` (same-level synchronisation): for each patch
-and each of its 26 neighbours, the neighbour's interior slab next to the
-shared face, edge or corner is copied into this patch's ghost zone.  Every
-copy is a box descriptor; the kernels run in libsf.so.
+* Same-level synchronisation: a periodic box tiled by a regular grid of equal
+  patches exchanges its ghost shells with ``sf_copy_boxes``; for each patch
+  and each of its 26 neighbours, the neighbour's interior slab next to the
+  shared face, edge or corner is copied into this patch's ghost zone.
+* Restriction by injection (``restrict_box``).
+* Sub-cycling in time (``SubcycledPair``): a periodic coarse patch and one
+  fine patch R times finer in space and time; the fine ghost zone at every
+  fine RK stage is filled by Berger-Oliger without order reduction
+  (Sec. III.B, App. D) fused with the quintic prolongation
+  (``sf_bor_prolong``), and the fine solution is injected back into the
+  coarse level after the R fine steps.
+Every copy and every interpolation runs in libsf.so; this module only builds
+descriptors and orders the calls.
 """
 from __future__ import annotations
 
 import itertools
+
+import torch
 
 from . import capi
 from .state import PatchState
@@ -75,9 +85,10 @@ def halo_boxes(grid: dict, which: str = "A") -> list:
 
 
 def restrict_box(fine: PatchState, coarse: PatchState, ratio: int, coarse_origin, ext,
-                 fine_array=None, coarse_array=None) -> capi.sf_box_copy:
-    """Box copy injecting fine point R*i into coarse points origin..origin+ext-1
-    (both patches share the origin of their interior index spaces)."""
+                 fine_array=None, coarse_array=None, fine_at=(0, 0, 0)) -> capi.sf_box_copy:
+    """Box copy injecting fine values into coarse points origin..origin+ext-1.
+    Fine interior point 0 sits on coarse interior point `fine_at`, so coarse
+    point i takes fine point R*(i - fine_at)."""
     fa = fine.A if fine_array is None else fine_array
     ca = coarse.A if coarse_array is None else coarse_array
     fsy, fsz, fsf = _strides(fine)
@@ -85,7 +96,7 @@ def restrict_box(fine: PatchState, coarse: PatchState, ratio: int, coarse_origin
     bx = capi.sf_box_copy()
     bx.src = fa.data_ptr()
     bx.dst = ca.data_ptr()
-    bx.src_off = _off(fine, *(ratio * o for o in coarse_origin))
+    bx.src_off = _off(fine, *(ratio * (o - a) for o, a in zip(coarse_origin, fine_at)))
     bx.dst_off = _off(coarse, *coarse_origin)
     bx.src_sy, bx.src_sz, bx.src_sf = fsy, fsz, fsf
     bx.dst_sy, bx.dst_sz, bx.dst_sf = csy, csz, csf
@@ -94,3 +105,116 @@ def restrict_box(fine: PatchState, coarse: PatchState, ratio: int, coarse_origin
     bx.src_step = ratio
     bx.reserved = 0
     return bx
+
+
+def whole_array_box(st: PatchState, src, dst) -> capi.sf_box_copy:
+    """Box copy of a complete ghosted array (all fields, ghosts included)."""
+    sy, sz, sf = _strides(st)
+    nx, ny, nz = st.n
+    g = st.g
+    bx = capi.sf_box_copy()
+    bx.src = src.data_ptr()
+    bx.dst = dst.data_ptr()
+    bx.src_off = bx.dst_off = 0
+    bx.src_sy = bx.dst_sy = sy
+    bx.src_sz = bx.dst_sz = sz
+    bx.src_sf = bx.dst_sf = sf
+    bx.ext[:] = (nx + 2 * g, ny + 2 * g, nz + 2 * g)
+    bx.nf = st.nf
+    bx.src_step = 1
+    bx.reserved = 0
+    return bx
+
+
+def ghost_shell_boxes(st: PatchState):
+    """The ghost shell of a patch as six disjoint boxes (local interior
+    coordinates of the lower corner, extent): z slabs over the full x-y
+    extent, then y slabs, then x slabs."""
+    nx, ny, nz = st.n
+    g = st.g
+    X, Y = nx + 2 * g, ny + 2 * g
+    return [((-g, -g, -g), (X, Y, g)), ((-g, -g, nz), (X, Y, g)),
+            ((-g, -g, 0), (X, g, nz)), ((-g, ny, 0), (X, g, nz)),
+            ((-g, 0, 0), (g, ny, nz)), ((nx, 0, 0), (g, ny, nz))]
+
+
+class SubcycledPair:
+    """A periodic coarse patch and one fine patch, `ratio` times finer in
+    space and time, advanced with sub-cycling (Sec. III.B).
+
+    The fine patch covers coarse interior points at .. at + n_fine/ratio - 1
+    and has no periodic images of its own: before each fine RK stage its
+    ghost zone receives the BOR value of that stage (App. D), prolonged from
+    the coarse stage states.  After the `ratio` fine steps of one coarse step
+    the fine interior is injected into the coarse points it covers.
+
+    The coarse stage states that BOR needs are the stage inputs the coarse
+    substeps leave behind; only those that a later coarse stage overwrites
+    are copied aside (RK4: U^n and U^(2); SSP-RK3: U^n).
+    """
+
+    def __init__(self, coarse: PatchState, fine: PatchState, ratio: int, at):
+        if coarse.prm.rk != fine.prm.rk:
+            raise ValueError("coarse and fine levels must use the same RK scheme")
+        if fine.prm.ghosts != capi.SF_GHOSTS_NONE:
+            raise ValueError("the fine patch must be created with ghosts=SF_GHOSTS_NONE")
+        if any(v % ratio for v in fine.n):
+            raise ValueError("fine patch size must be a multiple of the ratio")
+        self.coarse, self.fine, self.R = coarse, fine, int(ratio)
+        self.at = tuple(int(v) for v in at)
+        self.rk = coarse.prm.rk
+        self.s = 4 if self.rk == capi.SF_RK4 else 3
+        kw = dict(dtype=coarse.dtype, device=coarse.A.device)
+        self.S0 = torch.zeros(coarse.shape, **kw)
+        self.S1 = torch.zeros(coarse.shape, **kw) if self.rk == capi.SF_RK4 else None
+        self._box_S0 = whole_array_box(coarse, coarse.A, self.S0)
+        self._box_S1 = whole_array_box(coarse, coarse.B, self.S1) if self.S1 is not None else None
+        cext = tuple(v // ratio for v in fine.n)
+        self._restrict = restrict_box(fine, coarse, ratio, self.at, cext, fine_at=self.at)
+        self._shell = ghost_shell_boxes(fine)
+
+    def _states(self):
+        c = self.coarse
+        if self.rk == capi.SF_RK4:
+            return [self.S0.data_ptr(), self.S1.data_ptr(), c.C.data_ptr(), c.B.data_ptr(),
+                    c.A.data_ptr()]
+        return [self.S0.data_ptr(), c.B.data_ptr(), c.C.data_ptr(), c.A.data_ptr()]
+
+    def fill_fine_ghosts(self, array, r: int, stage: int, stream=None) -> None:
+        """BOR value of fine step r, fine stage `stage`, into the ghost shell
+        of the fine array `array`."""
+        f, c, R = self.fine, self.coarse, self.R
+        h = _stream(stream)
+        sy, sz, sf = _strides(f)
+        es = array.element_size()
+        states = self._states()
+        cpatch = c.patch(c.A, c.A, c.B)
+        for lo, ext in self._shell:
+            origin = tuple(R * a + l for a, l in zip(self.at, lo))
+            ptr = array.data_ptr() + _off(f, *lo) * es
+            capi.sf_bor_prolong(cpatch, self.rk, states, f.nf, R, r, stage, origin, ext, ptr, sy, sz,
+                                sf, h)
+
+    def step(self, nsteps: int = 1, stream=None) -> None:
+        c, f, R = self.coarse, self.fine, self.R
+        h = _stream(stream)
+        for _ in range(nsteps):
+            capi.sf_copy_boxes([self._box_S0], c.precision, h)
+            for s in range(c.nstages):
+                capi.sf_substep(c.prm, c.stage_patch(s), s, h)
+                if s == 0 and self._box_S1 is not None:
+                    capi.sf_copy_boxes([self._box_S1], c.precision, h)
+            for r in range(R):
+                for s in range(f.nstages):
+                    self.fill_fine_ghosts(f.roles(s)[0], r, s, h)
+                    capi.sf_substep(f.prm, f.stage_patch(s), s, h)
+            capi.sf_copy_boxes([self._restrict], c.precision, h)
+            c.fill_ghosts(c.A, h)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)

@@ -26,7 +26,7 @@ EXPORTS = ["sf_nfields", "sf_substep", "sf_rhs", "sf_fill_ghosts_periodic", "sf_
            "sf_adjoint_substep", "sf_gather", "sf_scatter_add", "sf_diagnostics",
            "sf_batch_create", "sf_batch_substep", "sf_batch_tune", "sf_batch_capture",
            "sf_batch_launch", "sf_batch_launches_per_step", "sf_batch_destroy",
-           "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong",
+           "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong", "sf_bor_prolong",
            "sf_get_device_status", "sf_last_error", "sf_launch_count"]
 
 
@@ -138,6 +138,8 @@ def lib() -> ctypes.CDLL:
         L.sf_batch_substep_static.argtypes = [P(sf_params), P(sf_patch), i32, i32, vp]
         L.sf_copy_boxes.argtypes = [P(sf_box_copy), i32, i32, vp]
         L.sf_prolong.argtypes = [P(sf_patch), vp, i32, i32, P(i32), P(i32), vp, i64, i64, i64, vp]
+        L.sf_bor_prolong.argtypes = [P(sf_patch), i32, P(vp), i32, i32, i32, i32, P(i32), P(i32), vp,
+                                     i64, i64, i64, vp]
         L.sf_get_device_status.argtypes = [vp]
         L.sf_last_error.argtypes = []
         L.sf_last_error.restype = ctypes.c_char_p
@@ -258,6 +260,20 @@ def sf_prolong(coarse: sf_patch, coarse_array: int, nf: int, ratio: int, origin,
     e = (ctypes.c_int32 * 3)(*ext)
     _check(lib().sf_prolong(ctypes.byref(coarse), coarse_array, nf, ratio, o, e, fine_out, out_sy,
                             out_sz, out_sf, stream), "sf_prolong")
+
+
+def sf_bor_prolong(coarse: sf_patch, rk: int, states, nf: int, ratio: int, r: int, stage: int,
+                   origin, ext, fine_out: int, out_sy: int, out_sz: int, out_sf: int,
+                   stream: int = 0) -> None:
+    """Fine-time value of BOR sub-cycling (fine step r, fine stage `stage`, or
+    the end of the fine step for stage = number of RK stages) prolonged onto
+    fine points origin..origin+ext-1.  `states` are device pointers of the
+    coarse stage states (5 for RK4, 4 for SSP-RK3)."""
+    arr = (ctypes.c_void_p * len(states))(*states)
+    o = (ctypes.c_int32 * 3)(*origin)
+    e = (ctypes.c_int32 * 3)(*ext)
+    _check(lib().sf_bor_prolong(ctypes.byref(coarse), rk, arr, nf, ratio, r, stage, o, e, fine_out,
+                                out_sy, out_sz, out_sf, stream), "sf_bor_prolong")
 
 
 def sf_get_device_status(stream: int = 0) -> int:

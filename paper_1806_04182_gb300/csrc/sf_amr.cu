@@ -5,7 +5,12 @@
 //   sf_prolong     - 6-point (5th-order) Lagrange prolongation from a coarse
 //                    patch onto fine points, as a tensor product of 1D
 //                    interpolations whose weights l_j(t) are tabulated on the
-//                    host for the R fractional positions t = r/R.
+//                    host for the R fractional positions t = r/R;
+//   sf_bor_prolong - the same prolongation of the fine-time values of
+//                    Berger-Oliger without order reduction (Sec. III.B,
+//                    App. C-D), a fixed linear combination of the coarse
+//                    stage states whose coefficients the host derives.
+#include <cmath>
 #include <cstring>
 
 #include "sf_internal.cuh"
@@ -52,8 +57,28 @@ struct ProlongArgs {
 
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
+// Value of the coarse data at a node: NS == 0 reads one array; otherwise a
+// fixed linear combination of NS+1 arrays,  S_0 + sum_m c_m (S_m - S_0),
+// formed in double precision (the BOR fine-time values below).
 template <typename T>
-__global__ void __launch_bounds__(128) prolong_kernel(const T* __restrict__ cu, T* out, ProlongArgs p) {
+struct Combo {
+  const T* s[5];
+  double c[4];
+};
+
+template <typename T, int NS>
+__device__ __forceinline__ double node_value(const Combo<T>& cb, long long o) {
+  double v = double(__ldg(cb.s[0] + o));
+  if (NS > 0) {
+    const double u = v;
+#pragma unroll
+    for (int m = 1; m <= NS; ++m) v += cb.c[m - 1] * (double(__ldg(cb.s[m] + o)) - u);
+  }
+  return v;
+}
+
+template <typename T, int NS>
+__global__ void __launch_bounds__(128) prolong_kernel(Combo<T> cb, T* out, ProlongArgs p) {
   const long long vol = (long long)p.ext[0] * p.ext[1] * p.ext[2];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < vol;
        t += (long long)gridDim.x * blockDim.x) {
@@ -71,21 +96,118 @@ __global__ void __launch_bounds__(128) prolong_kernel(const T* __restrict__ cu, 
     const long long c0 = (long long)(base[2] - 2 + p.g) * p.sz + (long long)(base[1] - 2 + p.g) * p.sy +
                          (base[0] - 2 + p.g);
     for (int f = 0; f < p.nf; ++f) {
-      const T* q = cu + f * p.sf + c0;
+      const long long q = f * p.sf + c0;
       double acc = 0.0;
       for (int c = 0; c < 6; ++c) {
         double ay = 0.0;
         for (int b = 0; b < 6; ++b) {
-          const T* row = q + c * p.sz + b * p.sy;
+          const long long row = q + c * p.sz + b * p.sy;
           double ax = 0.0;
 #pragma unroll
-          for (int a = 0; a < 6; ++a) ax += p.w[r[0]][a] * double(__ldg(row + a));
+          for (int a = 0; a < 6; ++a) ax += p.w[r[0]][a] * node_value<T, NS>(cb, row + a);
           ay += p.w[r[1]][b] * ax;
         }
         acc += p.w[r[2]][c] * ay;
       }
       out[f * p.osf + (long long)k * p.osz + (long long)j * p.osy + i] = T(acc);
     }
+  }
+}
+
+// App. C dense-output polynomials b_j(theta) of one coarse step and their
+// theta-derivatives of order m (RK(4,4): the cubic interpolant with b_4's
+// cubic coefficient +2/3, so that b_4(1) = 1/6; SSP-RK(3,3): the quadratic
+// one).  Unused entries are zero.
+static void dense_poly(int rk, double th, int m, double b[4]) {
+  for (int j = 0; j < 4; ++j) b[j] = 0.0;
+  if (rk == SF_RK4) {
+    // coefficients of 1, th, th^2, th^3
+    static const double P[4][4] = {{0.0, 1.0, -1.5, 2.0 / 3.0},
+                                   {0.0, 0.0, 1.0, -2.0 / 3.0},
+                                   {0.0, 0.0, 1.0, -2.0 / 3.0},
+                                   {0.0, 0.0, -0.5, 2.0 / 3.0}};
+    for (int j = 0; j < 4; ++j)
+      for (int e = m; e < 4; ++e) {
+        double fall = 1.0;  // e (e-1) ... (e-m+1)
+        for (int q = 0; q < m; ++q) fall *= double(e - q);
+        b[j] += P[j][e] * fall * std::pow(th, double(e - m));
+      }
+  } else {
+    static const double P[3][3] = {{0.0, 1.0, -5.0 / 6.0}, {0.0, 0.0, 1.0 / 6.0}, {0.0, 0.0, 4.0 / 6.0}};
+    for (int j = 0; j < 3; ++j)
+      for (int e = m; e < 3; ++e) {
+        double fall = 1.0;
+        for (int q = 0; q < m; ++q) fall *= double(e - q);
+        b[j] += P[j][e] * fall * std::pow(th, double(e - m));
+      }
+  }
+}
+
+// BOR (App. D) as a linear map.  Every quantity of the algorithm is a linear
+// combination of the coarse increments k_1..k_s; a[j] is the weight of k_j in
+// the requested fine value minus U^n.  The increments are in turn fixed by
+// the stored stage states, k = T (S - U^n); the result is the coefficient c_m
+// of (S_m - U^n).
+static void bor_coefficients(int rk, int R, int r, int stage, double c[4]) {
+  const int s = rk == SF_RK4 ? 4 : 3;
+  const double th = double(r) / double(R), q = 1.0 / double(R);  // q = dt_F / dt
+  double b0[4], v1[4], v2[4], v3[4];
+  dense_poly(rk, th, 0, b0);  // U_{n+r/R} - U^n
+  dense_poly(rk, th, 1, v1);  // dt U_t
+  dense_poly(rk, th, 2, v2);  // dt^2 U_tt
+  dense_poly(rk, th, 3, v3);  // dt^3 U_ttt
+  double f[4][4] = {};        // fine increments f[i][j]: weight of coarse k_j
+  for (int j = 0; j < 4; ++j) {
+    if (rk == SF_RK4) {
+      const double vf = j == 2 ? 4.0 : (j == 1 ? -4.0 : 0.0);  // dt^3 f_U U_tt = 4 (k_3 - k_2)
+      f[0][j] = q * v1[j];
+      f[1][j] = q * v1[j] + 0.5 * q * q * v2[j] + 0.125 * q * q * q * (v3[j] - vf);
+      f[2][j] = q * v1[j] + 0.5 * q * q * v2[j] + 0.125 * q * q * q * (v3[j] + vf);
+      f[3][j] = q * v1[j] + q * q * v2[j] + 0.5 * q * q * q * v3[j];
+    } else {
+      f[0][j] = q * v1[j];
+      f[1][j] = q * v1[j] + q * q * v2[j];
+      f[2][j] = q * v1[j] + 0.5 * q * q * v2[j];
+    }
+  }
+  double a[4];
+  for (int j = 0; j < 4; ++j) {
+    double w;
+    if (rk == SF_RK4) {
+      switch (stage) {
+        case 0: w = 0.0; break;
+        case 1: w = 0.5 * f[0][j]; break;
+        case 2: w = 0.5 * f[1][j]; break;
+        case 3: w = f[2][j]; break;
+        default: w = (f[0][j] + 2.0 * f[1][j] + 2.0 * f[2][j] + f[3][j]) / 6.0; break;
+      }
+    } else {
+      switch (stage) {
+        case 0: w = 0.0; break;
+        case 1: w = f[0][j]; break;
+        case 2: w = 0.25 * f[0][j] + 0.25 * f[1][j]; break;
+        default: w = (f[0][j] + f[1][j] + 4.0 * f[2][j]) / 6.0; break;
+      }
+    }
+    a[j] = b0[j] + w;
+  }
+  // k in terms of D_m = S_m - U^n (m = 1..s):
+  //   RK4:  k_1 = 2 D_1, k_2 = 2 D_2, k_3 = D_3, k_4 = 6 D_4 - k_1 - 2 k_2 - 2 k_3
+  //   SSP:  k_1 = D_1, k_2 = 4 D_2 - D_1, k_3 = (6 D_3 - k_1 - k_2) / 4
+  double Tm[4][4] = {};
+  if (rk == SF_RK4) {
+    Tm[0][0] = 2.0;
+    Tm[1][1] = 2.0;
+    Tm[2][2] = 1.0;
+    Tm[3][0] = -2.0; Tm[3][1] = -4.0; Tm[3][2] = -2.0; Tm[3][3] = 6.0;
+  } else {
+    Tm[0][0] = 1.0;
+    Tm[1][0] = -1.0; Tm[1][1] = 4.0;
+    Tm[2][1] = -1.0; Tm[2][2] = 1.5;
+  }
+  for (int m = 0; m < 4; ++m) {
+    c[m] = 0.0;
+    for (int j = 0; j < s; ++j) c[m] += a[j] * Tm[j][m];
   }
 }
 
@@ -129,21 +251,29 @@ extern "C" sf_status sf_copy_boxes(const sf_box_copy* boxes, int32_t nbox, int32
   return SF_OK;
 }
 
-extern "C" sf_status sf_prolong(const sf_patch* coarse, const void* coarse_array, int32_t nf,
-                                int32_t ratio, const int32_t* origin, const int32_t* ext,
+// Shared set-up of sf_prolong and sf_bor_prolong: validation of the box
+// against the ghosted coarse layout, the Lagrange weight table, the launch.
+template <int NS>
+static sf_status prolong_launch(const sf_patch* coarse, const void* const* arrays, const double* c,
+                                int32_t nf, int32_t ratio, const int32_t* origin, const int32_t* ext,
                                 void* fine_out, int64_t out_sy, int64_t out_sz, int64_t out_sf,
                                 void* stream) {
-  if (!coarse || !coarse_array || !origin || !ext || !fine_out)
-    return set_error(SF_EINVAL, "NULL argument");
+  if (!coarse || !arrays || !origin || !ext || !fine_out) return set_error(SF_EINVAL, "NULL argument");
   if (ratio < 1 || ratio > 8) return set_error(SF_EINVAL, "ratio %d not in [1, 8]", ratio);
   if (nf < 1) return set_error(SF_EINVAL, "nf < 1");
   sf_patch p = *coarse;
   normalise_strides(p, nf);
+  const size_t es = p.precision == SF_FP64 ? 8 : 4;
+  for (int m = 0; m <= NS; ++m) {
+    if (!arrays[m]) return set_error(SF_EINVAL, "coarse array %d is NULL", m);
+    if (reinterpret_cast<uintptr_t>(arrays[m]) % es) return set_error(SF_EINVAL, "coarse array %d misaligned", m);
+  }
   sf_params dummy;
   memset(&dummy, 0, sizeof(dummy));
-  p.u_stage = const_cast<void*>(coarse_array);
+  p.u_stage = const_cast<void*>(arrays[0]);
   sf_status e = check_patch(&dummy, p, 0, 0);
   if (e) return e;
+  if (reinterpret_cast<uintptr_t>(fine_out) % es) return set_error(SF_EINVAL, "fine_out misaligned");
   for (int d = 0; d < 3; ++d) {
     if (ext[d] < 0) return set_error(SF_EINVAL, "ext[%d] < 0", d);
     if (ext[d] == 0) return SF_OK;
@@ -184,9 +314,44 @@ extern "C" sf_status sf_prolong(const sf_patch* coarse, const void* coarse_array
   int blocks = (int)((vol + 127) / 128);
   if (blocks > 152 * 16) blocks = 152 * 16;
   cudaStream_t st = (cudaStream_t)stream;
-  if (p.precision == SF_FP64)
-    prolong_kernel<double><<<blocks, 128, 0, st>>>((const double*)coarse_array, (double*)fine_out, a);
-  else
-    prolong_kernel<float><<<blocks, 128, 0, st>>>((const float*)coarse_array, (float*)fine_out, a);
+  if (p.precision == SF_FP64) {
+    Combo<double> cb;
+    for (int m = 0; m < 5; ++m) cb.s[m] = m <= NS ? (const double*)arrays[m] : nullptr;
+    for (int m = 0; m < 4; ++m) cb.c[m] = (c && m < NS) ? c[m] : 0.0;
+    prolong_kernel<double, NS><<<blocks, 128, 0, st>>>(cb, (double*)fine_out, a);
+  } else {
+    Combo<float> cb;
+    for (int m = 0; m < 5; ++m) cb.s[m] = m <= NS ? (const float*)arrays[m] : nullptr;
+    for (int m = 0; m < 4; ++m) cb.c[m] = (c && m < NS) ? c[m] : 0.0;
+    prolong_kernel<float, NS><<<blocks, 128, 0, st>>>(cb, (float*)fine_out, a);
+  }
   return after_launch("prolong_kernel");
+}
+
+extern "C" sf_status sf_prolong(const sf_patch* coarse, const void* coarse_array, int32_t nf,
+                                int32_t ratio, const int32_t* origin, const int32_t* ext,
+                                void* fine_out, int64_t out_sy, int64_t out_sz, int64_t out_sf,
+                                void* stream) {
+  const void* arrays[1] = {coarse_array};
+  return prolong_launch<0>(coarse, arrays, nullptr, nf, ratio, origin, ext, fine_out, out_sy, out_sz,
+                           out_sf, stream);
+}
+
+extern "C" sf_status sf_bor_prolong(const sf_patch* coarse, int32_t rk, const void* const* states,
+                                    int32_t nf, int32_t ratio, int32_t r, int32_t stage,
+                                    const int32_t* origin, const int32_t* ext, void* fine_out,
+                                    int64_t out_sy, int64_t out_sz, int64_t out_sf, void* stream) {
+  if (rk != SF_RK4 && rk != SF_SSPRK3) return set_error(SF_EINVAL, "unknown rk %d", rk);
+  if (!states) return set_error(SF_EINVAL, "states NULL");
+  if (ratio < 1 || ratio > 8) return set_error(SF_EINVAL, "ratio %d not in [1, 8]", ratio);
+  if (r < 0 || r >= ratio) return set_error(SF_EINVAL, "fine step r = %d not in [0, %d)", r, ratio);
+  const int s = rk == SF_RK4 ? 4 : 3;
+  if (stage < 0 || stage > s) return set_error(SF_EINVAL, "stage %d not in [0, %d]", stage, s);
+  double c[4];
+  bor_coefficients(rk, ratio, r, stage, c);
+  if (rk == SF_RK4)
+    return prolong_launch<4>(coarse, states, c, nf, ratio, origin, ext, fine_out, out_sy, out_sz,
+                             out_sf, stream);
+  return prolong_launch<3>(coarse, states, c, nf, ratio, origin, ext, fine_out, out_sy, out_sz,
+                           out_sf, stream);
 }
