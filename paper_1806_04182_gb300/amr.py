@@ -25,12 +25,7 @@ from .state import PatchState
 
 
 def _strides(st: PatchState):
-    nx, ny, nz = st.n
-    g = st.g
-    sy = nx + 2 * g
-    sz = sy * (ny + 2 * g)
-    sf = sz * (nz + 2 * g)
-    return sy, sz, sf
+    return st.strides
 
 
 def _off(st: PatchState, i: int, j: int, k: int) -> int:

@@ -16,6 +16,10 @@ sf_status launch_wave(const sf_params& prm, const sf_patch& p, const StageArgs& 
                       void* rhs_out, bool adjoint, cudaStream_t st);
 sf_status launch_z4(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                     void* rhs_out, cudaStream_t st);
+// TMA-staged CCZ4 kernel (sf_z4_tma.cu) and the layouts it serves
+bool z4_tma_eligible(const sf_params& prm, const sf_patch& p);
+sf_status launch_z4_tma(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
+                        void* rhs_out, cudaStream_t st);
 sf_status launch_mhd(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                      void* rhs_out, cudaStream_t st);
 

@@ -34,6 +34,19 @@ struct Z4Coef {
   int lopsided;      // 1: one-sided advection stencils (Sec. II.B.1); picks the LOP instance
 };
 
+template <typename T>
+Z4Coef<T> z4_coef(const sf_params& prm) {
+  Z4Coef<T> zc;
+  zc.kappa_z = T(prm.kappa_z);
+  zc.kappa_c = T(prm.kappa_c);
+  zc.eta = T(prm.eta);
+  zc.g_shift = T(prm.g_shift);
+  zc.slicing = prm.slicing;
+  zc.shift_frozen = prm.shift_frozen;
+  zc.lopsided = prm.lopsided;
+  return zc;
+}
+
 __host__ __device__ constexpr int S(int a, int b) {
   return a == b ? (a == 0 ? 0 : (a == 1 ? 3 : 5))
                 : ((a + b) == 1 ? 1 : ((a + b) == 2 ? 2 : 4));

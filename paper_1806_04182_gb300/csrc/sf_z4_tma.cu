@@ -1,0 +1,321 @@
+// CCZ4 stage kernel with TMA-staged stencils (float storage, centred
+// advection).  The per-point right-hand side is the same z4_cell as the
+// global-load kernel; only its stencil source differs.
+//
+// Each CTA computes a 32 x 12 x 1 tile of points, one warp per row.  The
+// CCZ4 right-hand side consumes the 25 fields' stencils one field at a time in
+// a fixed order (the shift, the conformal metric, chi, alpha, Gammahat, Khat,
+// Theta, A~, B), so the halo box of every field (40 x 18 x 7 floats: the
+// 38 x 18 x 7 the 4th-order and Kreiss-Oliger stencils reach, x rounded up to
+// 16 bytes) is copied into shared memory by a cp.async.bulk.tensor load ahead
+// of its use.  A ring of slots, each with a "full" mbarrier (the TMA
+// transaction count) and an "empty" mbarrier (one arrival per warp), keeps
+// all but two slots in flight: thread 0 issues the load for field use
+// u + slots - 2 when the warps reach field use u.  Warps wait only for the
+// field they need, so there is no CTA-wide barrier after the barrier
+// initialisation.
+//
+// Every wait is bounded (about a second of clock cycles); a wait that gives up
+// sets ST_TIMEOUT in the status word, and the kernel finishes its points with
+// whatever the slot holds, waits (bounded) for its own loads still in flight
+// and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "sf_internal.cuh"
+#include "sf_z4.cuh"
+
+namespace sf {
+namespace {
+
+// A CTA computes a 32 x BY x 1 tile of points (one warp per row); the staged
+// box of a field is TX x (BY + 6) x TZ floats, each slot rounded up to 128 B.
+// Shared memory: KS slots, 2 KS mbarriers, and the 25 right-hand sides of
+// every thread (parked until the RK combination at the end).
+constexpr int TX = 40, TZ = 7;
+constexpr int kSY = 104, kSZ = 104 * 102;         // global strides of the padded 96^3 layout
+constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at GB300 clocks
+
+template <int BY, int KS>
+struct Cfg {
+  static constexpr int TY = BY + 6;
+  static constexpr int kBoxBytes = TX * TY * TZ * 4;
+  static constexpr int kSlotFloats = ((kBoxBytes + 127) / 128) * 32;
+  static constexpr int kSlots = KS;
+  static constexpr int kThreads = 32 * BY;
+  static constexpr int kRbufOffset = KS * kSlotFloats * 4 + 2 * KS * 8;
+  static constexpr int kSmemBytes = kRbufOffset + 25 * kThreads * 4;
+  static constexpr int kMinBlocks = BY <= 4 ? 3 : 1;  // 168 registers a thread
+};
+
+// The configuration in use: one CTA of 12 warps per SM (168 registers x 384
+// threads), a ring of 8 slots (6 fields in flight), 200 KB of shared memory.
+// Measured on the 96^3 patch against 4-warp CTAs (3 per SM) and 6- or
+// 10-slot rings: the 12 warps of one CTA stay within two fields of each
+// other (the ring couples them), so they share the instruction cache, and
+// the kernel is bound by instruction fetch.
+constexpr int kBY = 12, kKS = 8;
+
+// Order in which z4_cell opens the fields' stencils (cross, then the mixed
+// derivatives of the same field).  Without the Gamma-driver (shift frozen)
+// the last three are not used.
+__constant__ signed char kFieldSeq[25] = {19, 20, 21, 1, 2,  3,  4,  5,  6,  0,  18, 14, 15,
+                                          16, 7,  17, 8, 9, 10, 11, 12, 13, 22, 23, 24};
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(saddr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
+  if (mbar_try(b, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(b, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(float* dst, const CUtensorMap* map, int x, int y, int z,
+                                            int f, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(f), "r"(saddr(bar))
+      : "memory");
+}
+
+// Stencil source for z4_cell reading the staged boxes.
+template <int BY, int KS>
+struct TmaSrc {
+  using C = Cfg<BY, KS>;
+  static constexpr int TY = C::TY;
+  static constexpr int kSlots = KS;
+  static constexpr int kSlotFloats = C::kSlotFloats;
+  static constexpr int kBoxBytes = C::kBoxBytes;
+  const float* __restrict__ u;  // global stage input at this point, field 0
+  long long F;
+  float* tiles;
+  uint64_t* full;
+  uint64_t* empty;
+  const CUtensorMap* map;
+  unsigned* status;
+  int local;          // this thread's centre inside a box
+  int use, cur, nuses, issued;
+  int gx, gy, gz;     // ghosted coordinates of the box origin
+  bool leader, lane0, dead;
+
+  __device__ __forceinline__ static constexpr long long sy() { return TX; }
+  __device__ __forceinline__ static constexpr long long sz() { return TX * TY; }
+  __device__ __forceinline__ const float* p(int) const { return tiles + cur * kSlotFloats + local; }
+  __device__ __forceinline__ float ld(const float* q) const { return *q; }
+  __device__ __forceinline__ float centre(int f) const { return __ldg(u + f * F); }
+
+  __device__ __forceinline__ void fail() {
+    if (!dead) atomicOr(status, ST_TIMEOUT);
+    dead = true;
+  }
+
+  // leader: load field use j into its slot once the previous occupant
+  // (use j - kSlots) has been released by every warp
+  __device__ __forceinline__ void issue(int j) {
+    const int sl = j % kSlots;
+    if (j >= kSlots && !dead && !mbar_wait(&empty[sl], ((j / kSlots) - 1) & 1)) fail();
+    if (dead) return;
+    mbar_expect(&full[sl], kBoxBytes);
+    tma_load_4d(tiles + sl * kSlotFloats, map, gx, gy, gz, kFieldSeq[j], &full[sl]);
+    issued = j + 1;
+  }
+
+  __device__ __forceinline__ void prologue() {
+    if (leader)
+      for (int j = 0; j < kSlots - 2 && j < nuses; ++j) issue(j);
+  }
+
+  __device__ __forceinline__ void begin(int) {
+    const int i = use++;
+    if (leader && i + kSlots - 2 < nuses) issue(i + kSlots - 2);
+    if (i > 0) {
+      __syncwarp();
+      if (lane0) mbar_arrive(&empty[(i - 1) % kSlots]);
+    }
+    cur = i % kSlots;
+    if (!dead && !mbar_wait(&full[cur], (i / kSlots) & 1)) fail();
+  }
+
+  // the leader's warp consumed every load it issued unless a wait gave up;
+  // then it waits (bounded) for the loads still in flight before exiting
+  __device__ __forceinline__ void finish() {
+    if (leader && dead)
+      for (int j = use; j < issued; ++j) mbar_wait(&full[j % kSlots], (j / kSlots) & 1);
+  }
+};
+
+}  // namespace
+
+// Bulk L2 prefetch of the 128-byte row segment of every field that the RK
+// combination of this stage reads (U^n, the accumulator, the Kahan term):
+// those reads come late in the point's computation, one field at a time, and
+// would otherwise each wait for DRAM.
+__device__ __forceinline__ void prefetch_rows(const float* base, long long F) {
+#pragma unroll 1
+  for (int f = 0; f < 25; ++f)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], 144;" ::"l"(base + f * F) : "memory");
+}
+
+template <typename H, int BY, int KS>
+__global__ void __launch_bounds__(Cfg<BY, KS>::kThreads, Cfg<BY, KS>::kMinBlocks)
+    z4_tma_kernel(const __grid_constant__ CUtensorMap map, PatchArgs<float> a, StageArgs s,
+                  Z4Coef<float> zc) {
+  using C = Cfg<BY, KS>;
+  constexpr int kSlots = KS;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* tiles = reinterpret_cast<float*>(smem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kSlots * C::kSlotFloats * 4);
+  uint64_t* empty = full + kSlots;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  if (tid == 0) {
+    for (int q = 0; q < kSlots; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], BY);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  // whole tiles only (checked on the host): every thread has a point
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int k = blockIdx.z;
+  const long long c = (long long)(k + 3) * kSZ + (long long)(j + 3) * kSY + (i + 3);
+  if (threadIdx.x == 0 && s.mode == 0) {
+    // the warp's 32 points sit at byte offsets 12 .. 139 from the 16-byte
+    // aligned address of ghosted x = 32 m (row pitch 416 B): prefetch 144 B
+    const long long c0 = c - 3;
+    if (!s.un_alias) prefetch_rows(a.un + c0, a.sf);
+    if (s.rk == SF_RK4 && s.stage > 0) prefetch_rows(a.acc + c0, a.sf);
+    if (s.kahan && s.stage == 3) prefetch_rows(a.kh + c0, a.sf);
+  }
+  TmaSrc<BY, KS> src;
+  src.u = a.us + c;
+  src.F = a.sf;
+  src.tiles = tiles;
+  src.full = full;
+  src.empty = empty;
+  src.map = &map;
+  src.status = s.status;
+  src.local = (3 * C::TY + threadIdx.y + 3) * TX + threadIdx.x + 3;
+  src.use = 0;
+  src.cur = 0;
+  src.nuses = zc.shift_frozen ? 22 : 25;
+  src.issued = 0;
+  src.gx = blockIdx.x * 32;  // interior x0 - 3, in ghosted coordinates
+  src.gy = blockIdx.y * BY;
+  src.gz = k;
+  src.leader = tid == 0;
+  src.lane0 = threadIdx.x == 0;
+  src.dead = false;
+  src.prologue();
+  const Images im = ghost_images(a, s, i, j, k);
+  // right-hand sides parked in shared memory; the RK combination runs once at
+  // the end as a rolled loop over the fields (as in the global-load kernel)
+  float* rbuf = reinterpret_cast<float*>(smem + C::kRbufOffset);
+  z4_cell<float, H, false>(a, zc, src, [&](int f, float r, float) { rbuf[f * C::kThreads + tid] = r; });
+#pragma unroll 1
+  for (int f = 0; f < 25; ++f)
+    write_field(a, s, im, f, c, i, j, k, a.us[f * a.sf + c], rbuf[f * C::kThreads + tid]);
+}
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+template <typename H, int BY, int KS>
+sf_status launch_tma(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
+                     void* rhs_out, cudaStream_t st) {
+  using C = Cfg<BY, KS>;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return set_error(SF_ECUDA, "cuTensorMapEncodeTiled not available");
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  const cuuint64_t dims[4] = {(cuuint64_t)(p.n[0] + 6), (cuuint64_t)(p.n[1] + 6),
+                              (cuuint64_t)(p.n[2] + 6), 25};
+  const cuuint64_t strides[3] = {(cuuint64_t)p.sy * 4, (cuuint64_t)p.sz * 4, (cuuint64_t)p.sf * 4};
+  const cuuint32_t box[4] = {TX, (cuuint32_t)C::TY, TZ, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p.u_stage, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(SF_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(z4_tma_kernel<H, BY, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         C::kSmemBytes);
+  });
+  PatchArgs<float> a = make_args<float>(prm, p, stage, 25, rhs_out);
+  const Z4Coef<float> zc = z4_coef<float>(prm);
+  dim3 block(32, BY, 1);
+  dim3 grid(p.n[0] / 32, p.n[1] / BY, p.n[2]);
+  z4_tma_kernel<H, BY, KS><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc);
+  return after_launch("z4_tma_kernel");
+}
+
+}  // namespace
+
+// The staged kernel serves float storage with centred advection on the
+// padded 96^3 layout: 3 ghosts, row pitch 104 floats (416 bytes), plane
+// pitch 104 x 102, field pitch a multiple of 4 floats, 16-byte aligned
+// arrays, and whole 32 x 12 tiles in x and y.
+bool z4_tma_eligible(const sf_params& prm, const sf_patch& p) {
+  if (p.precision == SF_FP64 || prm.lopsided) return false;
+  if (p.ghost != 3 || p.sy != kSY || p.sz != kSZ || p.sf % 4) return false;
+  if (p.n[0] % 32 || p.n[1] % kBY || p.n[0] + 6 > kSY || p.n[1] + 6 > 102) return false;
+  if (reinterpret_cast<uintptr_t>(p.u_stage) % 16) return false;
+  return true;
+}
+
+sf_status launch_z4_tma(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
+                        void* rhs_out, cudaStream_t st) {
+  if (p.precision == SF_FP32_BULK_DW) return launch_tma<dw, kBY, kKS>(prm, p, s, stage, rhs_out, st);
+  return launch_tma<double, kBY, kKS>(prm, p, s, stage, rhs_out, st);
+}
+
+}  // namespace sf

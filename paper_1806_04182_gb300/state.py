@@ -29,7 +29,12 @@ def _stream_handle(stream) -> int:
 
 class PatchState:
     def __init__(self, system: int, n, dx, dt: float, precision: int = capi.SF_FP64,
-                 prm: capi.sf_params | None = None, ghost: int = 3, device="cuda"):
+                 prm: capi.sf_params | None = None, ghost: int = 3, device="cuda",
+                 x_pitch: int | None = None):
+        """x_pitch: row length of the ghosted arrays in elements (default
+        nx + 2 ghost).  A pitch that makes every row, plane and field start
+        on a 16-byte boundary (a multiple of 4 floats) lets the float CCZ4
+        substep stage its stencils with TMA bulk-tensor copies."""
         self.system = system
         self.n = tuple(int(v) for v in n)
         self.dx = tuple(float(v) for v in dx)
@@ -42,7 +47,10 @@ class PatchState:
         self.dtype = torch.float64 if precision == capi.SF_FP64 else torch.float32
         nx, ny, nz = self.n
         g = ghost
-        self.shape = (self.nf, nz + 2 * g, ny + 2 * g, nx + 2 * g)
+        self.pitch = nx + 2 * g if x_pitch is None else int(x_pitch)
+        if self.pitch < nx + 2 * g:
+            raise ValueError("x_pitch shorter than a ghosted row")
+        self.shape = (self.nf, nz + 2 * g, ny + 2 * g, self.pitch)
         kw = dict(dtype=self.dtype, device=device)
         self.A = torch.zeros(self.shape, **kw)
         self.B = torch.zeros(self.shape, **kw)
@@ -61,7 +69,7 @@ class PatchState:
         p.dt = self.dt
         p.system = self.system
         p.precision = self.precision
-        p.sy = p.sz = p.sf = 0
+        p.sy, p.sz, p.sf = self.strides
         p.u_stage = u_stage.data_ptr()
         p.u_n = u_n.data_ptr()
         p.acc = self.D.data_ptr() if self.D is not None else None
@@ -69,6 +77,13 @@ class PatchState:
         p.kahan = self.E.data_ptr() if self.E is not None else None
         p.cfl_rate = None
         return p
+
+    @property
+    def strides(self):
+        """Element strides (y, z, field) of the ghosted arrays."""
+        sy = self.pitch
+        sz = sy * self.shape[2]
+        return sy, sz, sz * self.shape[1]
 
     def roles(self, stage: int):
         if self.prm.rk == capi.SF_RK4:
@@ -104,8 +119,8 @@ class PatchState:
             t = t.clone()
             for f in self.offset_fields:
                 t[f] -= 1.0
-        self.A[:, g:self.shape[1] - g, g:self.shape[2] - g, g:self.shape[3] - g].copy_(
-            t.to(self.dtype))
+        nx = self.n[0]
+        self.A[:, g:self.shape[1] - g, g:self.shape[2] - g, g:g + nx].copy_(t.to(self.dtype))
         if self.E is not None:
             self.E.zero_()
         self._rate = None
@@ -119,7 +134,7 @@ class PatchState:
         """Interior view of the stored values (float CCZ4: with offsets)."""
         a = self.A if array is None else array
         g = self.g
-        return a[:, g:self.shape[1] - g, g:self.shape[2] - g, g:self.shape[3] - g]
+        return a[:, g:self.shape[1] - g, g:self.shape[2] - g, g:g + self.n[0]]
 
     def fields(self, array: torch.Tensor | None = None) -> torch.Tensor:
         """Interior field values in float64 (flat-space offsets added back)."""
@@ -201,7 +216,7 @@ class PatchState:
         """Write U^n (with ghosts), the Kahan compensation and the run
         metadata to `path` (.npz); `load` resumes bit for bit."""
         meta = dict(system=self.system, n=self.n, dx=self.dx, dt=self.dt,
-                    precision=self.precision, ghost=self.g, step=step, t=t,
+                    precision=self.precision, ghost=self.g, step=step, t=t, pitch=self.pitch,
                     prm={f: getattr(self.prm, f) for f in self._PRM_FIELDS})
         arrays = {"A": self.A.cpu().numpy()}
         if self.E is not None:
@@ -214,7 +229,8 @@ class PatchState:
         z = np.load(path, allow_pickle=False)
         meta = json.loads(str(z["meta"]))
         st = cls(meta["system"], meta["n"], meta["dx"], meta["dt"], precision=meta["precision"],
-                 prm=capi.params(**meta["prm"]), ghost=meta["ghost"], device=device)
+                 prm=capi.params(**meta["prm"]), ghost=meta["ghost"], device=device,
+                 x_pitch=meta.get("pitch"))
         st.A.copy_(torch.from_numpy(z["A"]))
         if st.E is not None and "E" in z:
             st.E.copy_(torch.from_numpy(z["E"]))

@@ -47,10 +47,10 @@ def oracle_params(prm: capi.sf_params):
                          shift_frozen=prm.shift_frozen, lopsided=prm.lopsided)
 
 
-def run_stages(system, U0, dx, dt, prm, precision=capi.SF_FP64):
+def run_stages(system, U0, dx, dt, prm, precision=capi.SF_FP64, pitch=None):
     """GPU stage outputs (interior, numpy float64) of one full step."""
     n = (U0.shape[3], U0.shape[2], U0.shape[1])
-    st = PatchState(system, n, dx, dt, precision=precision, prm=prm)
+    st = PatchState(system, n, dx, dt, precision=precision, prm=prm, x_pitch=pitch)
     st.upload(U0)
     outs = []
     for s in range(st.nstages):
@@ -355,3 +355,65 @@ def test_checkpoint_resume_is_bitwise(tmp_path, precision):
     assert step == 2 and t == pytest.approx(2 * b.dt)
     c.step(2)
     assert torch.equal(a.A, c.A)
+
+
+# ------------------------------------------------------------------ TMA-staged CCZ4 kernel
+# Float CCZ4 on the padded layout (row pitch 104 floats, ny = 96, nx a
+# multiple of 32) runs the kernel that stages every field's halo box in
+# shared memory with cp.async.bulk.tensor loads.  Same right-hand side, same
+# float rounding bound against the oracle; against the global-load kernel on
+# the dense layout the only differences come from FMA contraction.
+@pytest.mark.parametrize("precision", [capi.SF_FP32_BULK, capi.SF_FP32_BULK_DW])
+@pytest.mark.parametrize("nx,nz", [(32, 7), (96, 5)])
+def test_z4_tma_kernel_matches_oracle(precision, nx, nz):
+    n = (nx, 96, nz)
+    U0, dx = inputs.z4_perturbed(n, seed=4, amp=0.05)
+    prm = capi.params()
+    dt = 0.25 * min(dx)
+    eps32 = float(np.finfo(np.float32).eps)
+    bound = 4 * 64 / 12 * eps32 * dt / min(dx) ** 2 / 1e-2
+    got = run_stages(capi.SF_Z4, U0, dx, dt, prm, precision=precision, pitch=104)
+    dense = run_stages(capi.SF_Z4, U0, dx, dt, prm, precision=precision)
+    want = oracle_stages(oracle.Z4, U0, dx, dt, prm)
+    for s in range(4):
+        e = rel_err(got[s], want[s], floor=1e-2)
+        assert e.max() < bound, (s, e, bound)
+        assert rel_err(got[s], dense[s], floor=1e-2).max() < bound
+
+
+def test_z4_tma_kernel_frozen_shift_gauge_wave():
+    # harmonic slicing and a frozen shift: the last three fields' stencils are
+    # never opened, so the staged sequence is 22 boxes long
+    n = (32, 96, 6)
+    U0, dx = inputs.z4_gauge_wave(n, amp=0.01)
+    prm = capi.params(slicing=1, shift_frozen=1)
+    dt = 0.25 * min(dx)
+    eps32 = float(np.finfo(np.float32).eps)
+    bound = 4 * 64 / 12 * eps32 * dt / min(dx) ** 2 / 1e-2
+    got = run_stages(capi.SF_Z4, U0, dx, dt, prm, precision=capi.SF_FP32_BULK_DW, pitch=104)
+    want = oracle_stages(oracle.Z4, U0, dx, dt, prm)
+    assert rel_err(got[3], want[3], floor=1e-2).max() < bound
+
+
+def test_z4_tma_kernel_full_size_sampled():
+    # the benchmark's launch configuration (96^3, FP32-bulk with double-word
+    # islands, row pitch 104): sampled points of the RHS against the oracle.
+    # Stored float values carry |U - U_flat| <= 0.05 here (flat-space offsets),
+    # so a 1/dx^2 stencil holds ~64 eps32 * 0.05 / (12 dx^2) of rounding.
+    n = (96, 96, 96)
+    U0, dx = inputs.z4_minkowski_noise(n, seed=0, amp=1e-10)
+    pert, _ = inputs.z4_perturbed(n, seed=7, amp=0.05)
+    U0 = U0 + (pert - inputs.z4_minkowski(n))
+    prm = capi.params()
+    st = PatchState(capi.SF_Z4, n, dx, 0.25 * dx[0], precision=capi.SF_FP32_BULK_DW, prm=prm,
+                    x_pitch=104)
+    st.upload(U0)
+    r = st.rhs().cpu().numpy().reshape(25, -1).astype(np.float64)
+    pts = inputs.observers(n, 2000, seed=13)
+    want = oracle.rhs_points(oracle.Z4, oracle.ghosted(U0), dx, pts, oracle_params(prm))
+    eps32 = float(np.finfo(np.float32).eps)
+    dev = np.abs(U0 - inputs.z4_minkowski(n)).max()
+    bound = 4 * 64 / 12 * eps32 * dev / dx[0] ** 2
+    for f in range(25):
+        err = np.abs(r[f, pts] - want[f]).max()
+        assert err < bound, (f, err, bound)
