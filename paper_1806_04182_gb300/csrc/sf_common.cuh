@@ -117,29 +117,50 @@ __device__ __forceinline__ Images ghost_images(const PatchArgs<T>& a, const Stag
   return im;
 }
 
+// Periodic ghost images of the value `out` written at offset o.
 template <typename T>
-__device__ __forceinline__ T write_field(const PatchArgs<T>& a, const StageArgs& s,
-                                         const Images& im, int f, long long c, int i, int j,
-                                         int k, T centre, T r) {
-  if (s.mode == 1) {
-    a.nx[f * a.ninterior + ((long long)k * a.n[1] + j) * a.n[0] + i] = r;
-    return r;
+__device__ __forceinline__ void store_images(const PatchArgs<T>& a, const Images& im, long long o,
+                                             T out) {
+  if (!im.mask) return;
+  // shift index 0: none, 1: +n_d (point near the low end), 2: -n_d
+  const unsigned m = im.mask;
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    if (p && !(m & (p == 1 ? 16u : 32u))) continue;
+    const long long oz = p == 0 ? 0 : (p == 1 ? 1 : -1) * (long long)a.n[2] * a.sz;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (q && !(m & (q == 1 ? 4u : 8u))) continue;
+      const long long oy = q == 0 ? 0 : (q == 1 ? 1 : -1) * (long long)a.n[1] * a.sy;
+#pragma unroll
+      for (int w = 0; w < 3; ++w) {
+        if (w && !(m & (w == 1 ? 1u : 2u))) continue;
+        if (p | q | w) a.nx[o + oz + oy + (w == 0 ? 0 : (w == 1 ? a.n[0] : -a.n[0]))] = out;
+      }
+    }
   }
-  const long long o = f * a.sf + c;
-  const T un = s.un_alias ? centre : a.un[o];
+}
+
+// RK stage combination at offset o from the values it reads (u_stage centre,
+// U^n, accumulator, Kahan term; only those the stage uses are meaningful):
+// writes the accumulator / Kahan term and returns the next stage input.
+template <typename T>
+__device__ __forceinline__ T stage_combine(const PatchArgs<T>& a, const StageArgs& s, long long o,
+                                           T centre, T un_m, T acc, T kh, T r) {
+  const T un = s.un_alias ? centre : un_m;
   T out;
   if (s.rk == SF_RK4) {
     if (s.stage == 0) {
       a.acc[o] = (s.kahan ? T(0) : un) + a.c_acc * r;
       out = un + a.c_next * r;
     } else if (s.stage < 3) {
-      a.acc[o] = a.acc[o] + a.c_acc * r;
+      a.acc[o] = acc + a.c_acc * r;
       out = un + a.c_next * r;
     } else if (!s.kahan) {
-      out = a.acc[o] + a.c_next * r;
+      out = acc + a.c_next * r;
     } else {
-      const T inc = a.acc[o] + a.c_next * r;
-      const T y = inc - a.kh[o];
+      const T inc = acc + a.c_next * r;
+      const T y = inc - kh;
       const T t = un + y;
       a.kh[o] = (t - un) - y;
       out = t;
@@ -149,28 +170,77 @@ __device__ __forceinline__ T write_field(const PatchArgs<T>& a, const StageArgs&
     else if (s.stage == 1) out = T(0.75) * un + T(0.25) * (centre + a.dt * r);
     else out = un * T(1.0 / 3.0) + T(2.0 / 3.0) * (centre + a.dt * r);
   }
+  return out;
+}
+
+template <typename T>
+__device__ __forceinline__ T write_field(const PatchArgs<T>& a, const StageArgs& s,
+                                         const Images& im, int f, long long c, int i, int j,
+                                         int k, T centre, T r) {
+  if (s.mode == 1) {
+    a.nx[f * a.ninterior + ((long long)k * a.n[1] + j) * a.n[0] + i] = r;
+    return r;
+  }
+  const long long o = f * a.sf + c;
+  const bool rk4 = s.rk == SF_RK4;
+  const T un = s.un_alias ? centre : a.un[o];
+  const T acc = (rk4 && s.stage > 0) ? a.acc[o] : T(0);
+  const T kh = (rk4 && s.stage == 3 && s.kahan) ? a.kh[o] : T(0);
+  const T out = stage_combine(a, s, o, centre, un, acc, kh, r);
   a.nx[o] = out;
   if (s.check_finite && !finite_(out)) atomicOr(s.status, ST_NONFINITE);
-  if (im.mask) {
-    // shift index 0: none, 1: +n_d (point near the low end), 2: -n_d
-    const unsigned m = im.mask;
+  store_images(a, im, o, out);
+  return out;
+}
+
+// The stage write of all NF fields of one point whose right-hand sides were
+// parked in memory (r[f * stride]), for kernels that produce the 25 CCZ4
+// right-hand sides before writing any of them.  Fields go in batches of
+// five: every read of a batch (u_stage centre, U^n, accumulator, Kahan term,
+// as the stage needs them) is issued before its writes, so five reads of
+// each array are in flight at once instead of one.  The new values replace
+// the right-hand sides in r, and the periodic images (boundary points only)
+// are written by one rolled pass at the end.
+template <typename T, int NF>
+__device__ __forceinline__ void write_fields(const PatchArgs<T>& a, const StageArgs& s,
+                                             const Images& im, long long c, int i, int j, int k,
+                                             T* r, int stride) {
+  static_assert(NF % 5 == 0, "fields go in batches of five");
+  if (s.mode == 1) {
+    const long long oi = ((long long)k * a.n[1] + j) * a.n[0] + i;
+#pragma unroll 1
+    for (int f = 0; f < NF; ++f) a.nx[f * a.ninterior + oi] = r[f * stride];
+    return;
+  }
+  const bool rk4 = s.rk == SF_RK4;
+  const bool need_centre = s.un_alias || !rk4;
+  const bool need_acc = rk4 && s.stage > 0;
+  const bool need_kh = rk4 && s.stage == 3 && s.kahan;
+#pragma unroll 1
+  for (int f0 = 0; f0 < NF; f0 += 5) {
+    T cen[5], un[5], acc[5], kh[5], rr[5];
 #pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      if (p && !(m & (p == 1 ? 16u : 32u))) continue;
-      const long long oz = p == 0 ? 0 : (p == 1 ? 1 : -1) * (long long)a.n[2] * a.sz;
+    for (int q = 0; q < 5; ++q) {
+      const long long o = (f0 + q) * a.sf + c;
+      rr[q] = r[(f0 + q) * stride];
+      cen[q] = need_centre ? a.us[o] : T(0);
+      un[q] = s.un_alias ? T(0) : a.un[o];
+      acc[q] = need_acc ? a.acc[o] : T(0);
+      kh[q] = need_kh ? a.kh[o] : T(0);
+    }
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        if (q && !(m & (q == 1 ? 4u : 8u))) continue;
-        const long long oy = q == 0 ? 0 : (q == 1 ? 1 : -1) * (long long)a.n[1] * a.sy;
-#pragma unroll
-        for (int w = 0; w < 3; ++w) {
-          if (w && !(m & (w == 1 ? 1u : 2u))) continue;
-          if (p | q | w) a.nx[o + oz + oy + (w == 0 ? 0 : (w == 1 ? a.n[0] : -a.n[0]))] = out;
-        }
-      }
+    for (int q = 0; q < 5; ++q) {
+      const long long o = (f0 + q) * a.sf + c;
+      const T out = stage_combine(a, s, o, cen[q], un[q], acc[q], kh[q], rr[q]);
+      a.nx[o] = out;
+      if (s.check_finite && !finite_(out)) atomicOr(s.status, ST_NONFINITE);
+      r[(f0 + q) * stride] = out;
     }
   }
-  return out;
+  if (im.mask) {
+#pragma unroll 1
+    for (int f = 0; f < NF; ++f) store_images(a, im, f * a.sf + c, r[f * stride]);
+  }
 }
 
 // ------------------------------------------------------------ launch plumbing

@@ -34,9 +34,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2)
   const Images im = ghost_images(a, s, i, j, k);
   const int tid = threadIdx.y * 32 + threadIdx.x;
   z4_cell<T, H, LOP>(a, zc, src, [&](int f, T r, T) { rbuf[f * 128 + tid] = r; });
-#pragma unroll 1
-  for (int f = 0; f < 25; ++f)
-    write_field(a, s, im, f, c, i, j, k, a.us[f * a.sf + c], rbuf[f * 128 + tid]);
+  write_fields<T, 25>(a, s, im, c, i, j, k, rbuf + tid, 128);
 }
 
 template <typename T, typename H>

@@ -247,9 +247,7 @@ __global__ void __launch_bounds__(Cfg<BY, KS>::kThreads, Cfg<BY, KS>::kMinBlocks
   // the end as a rolled loop over the fields (as in the global-load kernel)
   float* rbuf = reinterpret_cast<float*>(smem + C::kRbufOffset);
   z4_cell<float, H, false>(a, zc, src, [&](int f, float r, float) { rbuf[f * C::kThreads + tid] = r; });
-#pragma unroll 1
-  for (int f = 0; f < 25; ++f)
-    write_field(a, s, im, f, c, i, j, k, a.us[f * a.sf + c], rbuf[f * C::kThreads + tid]);
+  write_fields<float, 25>(a, s, im, c, i, j, k, rbuf + tid, C::kThreads);
 }
 
 namespace {
