@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) batch_stage_kerne
                                                           unsigned int* counter, StageArgs s,
                                                           Z4Coef<T> zc) {
   __shared__ int s_item;
+  __shared__ T rbuf[25 * 128];  // parked CCZ4 right-hand sides (see write_fields)
   for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
     __syncthreads();
@@ -63,9 +64,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) batch_stage_kerne
       if (system == SF_Z4) {
         GlobalSrc<T, 0, 0> src{a.us + c, a.sf, a.sy, a.sz};
         const Images im = ghost_images(a, s, i, j, k);
-        z4_cell<T, H, LOP>(a, zc, src, [&](int f, T r, T centre) {
-          write_field(a, s, im, f, c, i, j, k, centre, r);
-        });
+        z4_cell<T, H, LOP>(a, zc, src, [&](int f, T r, T) { rbuf[f * 128 + threadIdx.x] = r; });
+        write_fields<T, 25>(a, s, im, c, i, j, k, rbuf + threadIdx.x, 128);
       } else {
         T v[5], r[5];
         wave_point<T, false>(a, a.us + c, v, r);
