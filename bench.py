@@ -399,6 +399,114 @@ def suite(args, hbm_peak: float) -> list[dict]:
         out += _batch_rows(hbm_peak, npatch=args.npatch, per_patch="batch" in rows)
     if "adjoint" in rows:
         out += _adjoint_rows()
+    if "variants" in rows:
+        out += _variant_rows(hbm_peak)
+    if "amr" in rows:
+        out += _amr_rows(hbm_peak)
+    return out
+
+
+def _variant_rows(hbm_peak: float) -> list[dict]:
+    """Reconstruction and advection variants: CCZ4 with one-sided advection,
+    MHD with WENO5-Z and WENO3."""
+    from paper_1806_04182_gb300 import capi, inputs
+    from paper_1806_04182_gb300.state import PatchState
+    out = []
+    U0, dx = inputs.z4_minkowski_noise((N, N, N), seed=0, amp=1e-10)
+    st = PatchState(capi.SF_Z4, (N, N, N), dx, 0.25 * dx[0], precision=capi.SF_FP32_BULK_DW,
+                    prm=capi.params(lopsided=1))
+    st.upload(U0)
+    steps = 10
+    ms = _events_time(lambda: st.step(1), steps, 3)
+    rate = N ** 3 * 4 * steps / (ms * 1e-3)
+    out.append({"workload": "ccz4_96cubed_rk4_fp32dw_lopsided_advection", "value": rate,
+                "unit": UNIT, "ms_per_step": ms / steps, "bytes_per_cell_update": 475,
+                "hbm_frac": rate * 475 / 1e9 / hbm_peak,
+                "note": "one-sided advection stencils (runtime-stride global-load kernel)"})
+    n = (128, 128, 128)
+    U0, dx = inputs.mhd_blast(n, seed=0)
+    for variant, name in ((1, "weno5z"), (2, "weno3")):
+        prm = capi.params(rk=capi.SF_SSPRK3, weno_variant=variant)
+        st = PatchState(capi.SF_MHD, n, dx, 1e-3, precision=capi.SF_FP64, prm=prm)
+        st.upload(U0)
+        steps = 10
+        ms = _events_time(lambda: st.step_cfl(1, cfl=0.3), steps, 3)
+        rate = 128 ** 3 * 3 * steps / (ms * 1e-3)
+        bpc = 8 / 3 * 8 * 8
+        out.append({"workload": f"mhd_128cubed_{name}_llf_ssprk3_fp64", "value": rate, "unit": UNIT,
+                    "ms_per_step": ms / steps, "bytes_per_cell_update": bpc,
+                    "hbm_frac": rate * bpc / 1e9 / hbm_peak})
+    return out
+
+
+def _amr_rows(hbm_peak: float) -> list[dict]:
+    """Inter-patch steps of the level loop (Sec. III): same-level ghost
+    synchronisation, quintic prolongation, BOR prolongation, and a sub-cycled
+    two-level CCZ4 step."""
+    import torch
+    from paper_1806_04182_gb300 import amr, capi, inputs
+    from paper_1806_04182_gb300.state import PatchState
+    out = []
+    h = torch.cuda.current_stream().cuda_stream
+    # ghost synchronisation of a 96^3 CCZ4 box split into 2 x 2 x 2 patches of 48^3 (float)
+    m = (48, 48, 48)
+    dx = (1 / 96,) * 3
+    grid = {}
+    for a in range(2):
+        for b in range(2):
+            for c in range(2):
+                st = PatchState(capi.SF_Z4, m, dx, 0.25 * dx[0], precision=capi.SF_FP32_BULK_DW,
+                                prm=capi.params(ghosts=capi.SF_GHOSTS_NONE))
+                grid[(a, b, c)] = st
+    boxes = amr.halo_boxes(grid, "A")
+    moved = sum(bx.ext[0] * bx.ext[1] * bx.ext[2] * bx.nf for bx in boxes) * 4
+    ms = _events_time(lambda: capi.sf_copy_boxes(boxes, capi.SF_FP32_BULK_DW, h), 50, 3)
+    gbs = 2 * moved * 50 / (ms * 1e-3) / 1e9
+    out.append({"workload": "halo_sync_8_patches_48cubed_ccz4_fp32", "value": gbs, "unit": "GB/s",
+                "ms_per_call": ms / 50, "bytes_per_call": 2 * moved, "hbm_frac": gbs / hbm_peak,
+                "note": f"{len(boxes)} box copies (26 per patch), read + write counted"})
+    # prolongation of a 96^3 fine box (ratio 2) from a 48^3 coarse CCZ4 patch, and the BOR form
+    cst = PatchState(capi.SF_Z4, m, (2 / 96,) * 3, 0.5 / 96, precision=capi.SF_FP32_BULK_DW)
+    U0, _ = inputs.z4_perturbed(m, seed=1, amp=0.02)
+    cst.upload(U0)
+    ext = (90, 90, 90)
+    fine = torch.zeros((25, ext[2], ext[1], ext[0]), dtype=torch.float32, device="cuda")
+    p = cst.patch(cst.A, cst.A, cst.B)
+    pts = ext[0] * ext[1] * ext[2]
+    states = [cst.A.data_ptr(), cst.B.data_ptr(), cst.C.data_ptr(), cst.D.data_ptr(), cst.E.data_ptr()]
+    for name, fn, narr in (
+            ("prolong", lambda: capi.sf_prolong(p, cst.A.data_ptr(), 25, 2, (3, 3, 3), ext,
+                                                fine.data_ptr(), ext[0], ext[0] * ext[1], pts, h), 1),
+            ("bor_prolong", lambda: capi.sf_bor_prolong(p, capi.SF_RK4, states, 25, 2, 1, 2, (3, 3, 3),
+                                                        ext, fine.data_ptr(), ext[0], ext[0] * ext[1],
+                                                        pts, h), 5)):
+        ms = _events_time(fn, 20, 3)
+        rate = pts * 20 / (ms * 1e-3)
+        alg = pts * 25 * 4 + narr * (ext[0] // 2 + 6) ** 3 * 25 * 4
+        out.append({"workload": f"{name}_ratio2_fine_90cubed_ccz4_fp32", "value": rate,
+                    "unit": "fine points/s", "ms_per_call": ms / 20,
+                    "achieved_gbs": alg * 20 / (ms * 1e-3) / 1e9,
+                    "hbm_frac": alg * 20 / (ms * 1e-3) / 1e9 / hbm_peak,
+                    "note": "6x6x6 Lagrange taps per fine point and field; algorithmic bytes = "
+                            "fine writes + one read of each coarse array region"})
+    # sub-cycled two-level CCZ4 step: periodic 64^3 coarse, 64^3 fine patch (ratio 2) inside
+    nc = (64, 64, 64)
+    Uc, dxc = inputs.z4_minkowski_noise(nc, seed=0, amp=1e-10)
+    coarse = PatchState(capi.SF_Z4, nc, dxc, 0.25 * dxc[0], precision=capi.SF_FP32_BULK_DW)
+    coarse.upload(Uc)
+    nf = (64, 64, 64)
+    fine = PatchState(capi.SF_Z4, nf, tuple(v / 2 for v in dxc), 0.125 * dxc[0],
+                      precision=capi.SF_FP32_BULK_DW, prm=capi.params(ghosts=capi.SF_GHOSTS_NONE))
+    Uf, _ = inputs.z4_minkowski_noise(nf, seed=1, amp=1e-10)
+    fine.upload(Uf)
+    pair = amr.SubcycledPair(coarse, fine, 2, (16, 16, 16))
+    steps = 5
+    ms = _events_time(lambda: pair.step(1), steps, 2)
+    cells = 64 ** 3 * 4 + 64 ** 3 * 4 * 2
+    out.append({"workload": "subcycled_bor_ccz4_fp32dw_coarse64_fine64_ratio2", "value":
+                cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_coarse_step": ms / steps,
+                "note": "one coarse RK4 step + 2 fine RK4 steps with BOR ghost fills before every "
+                        "fine stage (6 prolongation boxes each) and restriction"})
     return out
 
 
@@ -583,7 +691,8 @@ def main():
     ap.add_argument("--suite", action="store_true",
                     help="time every workload row (one JSON line each) instead of the headline")
     ap.add_argument("--rows", default=None,
-                    help="comma-separated subset of wave,mhd,batch,batch_graph,adjoint for --suite")
+                    help="comma-separated subset of wave,mhd,batch,batch_graph,adjoint,variants,amr "
+                         "for --suite")
     ap.add_argument("--npatch", type=int, default=512, help="patches of the batch rows")
     ap.add_argument("--pitch", type=int, default=FLOAT_PITCH,
                     help="row pitch of the float arrays (102 = dense: global-load kernel)")

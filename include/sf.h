@@ -216,7 +216,8 @@ sf_status sf_diagnostics(const sf_params* prm, const sf_patch* patch, const void
  *      dst_off + f*dst_sf + z*dst_sz + y*dst_sy + x  (element offsets; the
  * element type follows `precision`).  The caller guarantees both ranges lie
  * inside its arrays and that destination boxes do not overlap sources or each
- * other.  One launch per 16 boxes; nothing is allocated.
+ * other.  One launch per 64 boxes; nothing is allocated.  Each box holds fewer
+ * than 2^31 values.
  */
 typedef struct {
   const void* src;
@@ -264,8 +265,9 @@ sf_status sf_prolong(const sf_patch* coarse, const void* coarse_array, int32_t n
  *   stage = 0 .. s-1  ->  fine stage input U^(stage+1) of fine step r,
  *   stage = s         ->  U^{n+(r+1)/ratio},
  * with s = 4 (RK4) or 3 (SSP-RK3).  The result is then prolonged in space as
- * sf_prolong does (ratio 1: a copy) and written to fine_out.  Every value is
- * formed in double precision and stored in the coarse element type.
+ * sf_prolong does (ratio 1: a copy) and written to fine_out.  Values are
+ * formed in the arrays' element type (float arrays: float arithmetic, which
+ * holds their accuracy since every weight set sums to one).
  * SF_EINVAL for a NULL or misaligned state, stage or r out of range, or a
  * stencil node outside the ghosted coarse box.
  */

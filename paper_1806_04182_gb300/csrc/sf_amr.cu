@@ -12,32 +12,38 @@
 //                    stage states whose coefficients the host derives.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "sf_internal.cuh"
 
 namespace sf {
 
-constexpr int kBoxesPerLaunch = 16;
+// 64 descriptors (6.6 KB) travel as kernel parameters, so a launch needs no
+// device-side table.
+constexpr int kBoxesPerLaunch = 64;
 
 struct BoxBatch {
   sf_box_copy b[kBoxesPerLaunch];
   int n;
 };
 
+// One grid row (blockIdx.y) per box; threads run over the box's points with
+// 32-bit index arithmetic (the host checks that a box holds < 2^31 values).
 template <typename T>
 __global__ void __launch_bounds__(256) copy_boxes_kernel(BoxBatch bb) {
   const sf_box_copy& b = bb.b[blockIdx.y];
-  const long long vol = (long long)b.ext[0] * b.ext[1] * b.ext[2];
-  const long long total = vol * b.nf;
+  const unsigned ex = (unsigned)b.ext[0], ey = (unsigned)b.ext[1], ez = (unsigned)b.ext[2];
+  const unsigned total = ex * ey * ez * (unsigned)b.nf;
   const T* src = static_cast<const T*>(b.src);
   T* dst = static_cast<T*>(b.dst);
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    long long r = t;
-    const int x = (int)(r % b.ext[0]); r /= b.ext[0];
-    const int y = (int)(r % b.ext[1]); r /= b.ext[1];
-    const int z = (int)(r % b.ext[2]); r /= b.ext[2];
-    const int f = (int)r;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    unsigned r = t;
+    const unsigned x = r % ex;
+    r /= ex;
+    const unsigned y = r % ey;
+    r /= ey;
+    const unsigned z = r % ez;
+    const unsigned f = r / ez;
     const long long s = b.src_off + f * b.src_sf + (long long)z * b.src_step * b.src_sz +
                         (long long)y * b.src_step * b.src_sy + (long long)x * b.src_step;
     const long long d = b.dst_off + f * b.dst_sf + (long long)z * b.dst_sz + (long long)y * b.dst_sy + x;
@@ -47,6 +53,7 @@ __global__ void __launch_bounds__(256) copy_boxes_kernel(BoxBatch bb) {
 
 struct ProlongArgs {
   double w[8][6];      // Lagrange weights l_j(r/R), r = 0..R-1, nodes -2..3
+  float wf[8][6];      // the same, rounded to float (float arrays)
   int R;
   int n[3], g;
   long long sy, sz, sf;          // coarse strides
@@ -58,58 +65,112 @@ struct ProlongArgs {
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 // Value of the coarse data at a node: NS == 0 reads one array; otherwise a
-// fixed linear combination of NS+1 arrays,  S_0 + sum_m c_m (S_m - S_0),
-// formed in double precision (the BOR fine-time values below).
+// fixed linear combination of NS+1 arrays,  S_0 + sum_m c_m (S_m - S_0)
+// (the BOR fine-time values below).
 template <typename T>
 struct Combo {
   const T* s[5];
   double c[4];
 };
 
+// Formed in the arrays' own precision: float arrays hold values to float
+// accuracy, and the combination and interpolation weights sum to one.
 template <typename T, int NS>
-__device__ __forceinline__ double node_value(const Combo<T>& cb, long long o) {
-  double v = double(__ldg(cb.s[0] + o));
+__device__ __forceinline__ T node_value(const Combo<T>& cb, long long o) {
+  T v = __ldg(cb.s[0] + o);
   if (NS > 0) {
-    const double u = v;
+    const T u = v;
 #pragma unroll
-    for (int m = 1; m <= NS; ++m) v += cb.c[m - 1] * (double(__ldg(cb.s[m] + o)) - u);
+    for (int m = 1; m <= NS; ++m) v += T(cb.c[m - 1]) * (__ldg(cb.s[m] + o) - u);
   }
   return v;
 }
 
+template <typename T>
+__device__ __forceinline__ T lagrange_w(const ProlongArgs& p, int r, int q);
+template <>
+__device__ __forceinline__ double lagrange_w<double>(const ProlongArgs& p, int r, int q) {
+  return p.w[r][q];
+}
+template <>
+__device__ __forceinline__ float lagrange_w<float>(const ProlongArgs& p, int r, int q) {
+  return p.wf[r][q];
+}
+
+// Fine tile of PX x PY x PZ points per CTA.  Along each axis the tile's
+// points reach coarse nodes floor(F/R) - 2 .. floor(F/R) + 3, at most
+// (P - 1)/R + 7 of them (P + 6 for R = 1).  The kernel stages those nodes in
+// shared memory (after the BOR combination, once per node), then
+// interpolates separably: along x into tx, along y into ty, along z into the
+// output.  One field per CTA, so thin boxes (ghost shells) still fill the GPU.  18 weighted sums per fine point and field instead of 216, and the
+// 6-point order of summation is the tensor product's (x innermost).
+constexpr int PX = 32, PY = 4, PZ = 4;
+constexpr int CXM = PX + 6, CYM = PY + 6, CZM = PZ + 6;
+template <typename T>
+constexpr int prolong_smem() {
+  return (CZM * CYM * CXM + CZM * CYM * PX + CZM * PY * PX) * (int)sizeof(T);
+}
+
 template <typename T, int NS>
-__global__ void __launch_bounds__(128) prolong_kernel(Combo<T> cb, T* out, ProlongArgs p) {
-  const long long vol = (long long)p.ext[0] * p.ext[1] * p.ext[2];
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < vol;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % p.ext[0]);
-    const int j = (int)((t / p.ext[0]) % p.ext[1]);
-    const int k = (int)(t / ((long long)p.ext[0] * p.ext[1]));
-    const int F[3] = {p.origin[0] + i, p.origin[1] + j, p.origin[2] + k};
-    int base[3], r[3];
+__global__ void __launch_bounds__(256) prolong_kernel(Combo<T> cb, T* out, ProlongArgs p) {
+  extern __shared__ __align__(16) unsigned char psm_raw[];
+  T* cn = reinterpret_cast<T*>(psm_raw);  // [CZM][CYM][CXM]
+  T* tx = cn + CZM * CYM * CXM;           // [CZM][CYM][PX]
+  T* ty = tx + CZM * CYM * PX;            // [CZM][PY][PX]
+  const int R = p.R;
+  // one field per CTA: blockIdx.z = z tile * nf + field
+  const int f = (int)blockIdx.z % p.nf;
+  const int zt = (int)blockIdx.z / p.nf;
+  const int F0[3] = {p.origin[0] + (int)blockIdx.x * PX, p.origin[1] + (int)blockIdx.y * PY,
+                     p.origin[2] + zt * PZ};
+  const int P[3] = {PX, PY, PZ};
+  int nv[3], lo[3], nc[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      base[d] = floordiv(F[d], p.R);
-      r[d] = F[d] - base[d] * p.R;
+  for (int d = 0; d < 3; ++d) {
+    nv[d] = min(P[d], p.origin[d] + p.ext[d] - F0[d]);        // valid fine points in the tile
+    lo[d] = floordiv(F0[d], R) - 2;                            // first coarse node
+    nc[d] = floordiv(F0[d] + nv[d] - 1, R) + 3 - lo[d] + 1;    // coarse nodes spanned
+  }
+  const int tid = threadIdx.x;
+  {
+    const long long fo = f * p.sf;
+    for (int t = tid; t < nc[0] * nc[1] * nc[2]; t += blockDim.x) {
+      const int cx = t % nc[0], cy = (t / nc[0]) % nc[1], cz = t / (nc[0] * nc[1]);
+      const long long o = fo + (long long)(lo[2] + cz + p.g) * p.sz +
+                          (long long)(lo[1] + cy + p.g) * p.sy + (lo[0] + cx + p.g);
+      cn[(cz * CYM + cy) * CXM + cx] = node_value<T, NS>(cb, o);
     }
-    // coarse node (base-2, base-2, base-2) in the ghosted array
-    const long long c0 = (long long)(base[2] - 2 + p.g) * p.sz + (long long)(base[1] - 2 + p.g) * p.sy +
-                         (base[0] - 2 + p.g);
-    for (int f = 0; f < p.nf; ++f) {
-      const long long q = f * p.sf + c0;
-      double acc = 0.0;
-      for (int c = 0; c < 6; ++c) {
-        double ay = 0.0;
-        for (int b = 0; b < 6; ++b) {
-          const long long row = q + c * p.sz + b * p.sy;
-          double ax = 0.0;
+    __syncthreads();
+    for (int t = tid; t < nc[2] * nc[1] * nv[0]; t += blockDim.x) {
+      const int xi = t % nv[0], cy = (t / nv[0]) % nc[1], cz = t / (nv[0] * nc[1]);
+      const int F = F0[0] + xi, b = floordiv(F, R), r = F - b * R;
+      const T* row = cn + (cz * CYM + cy) * CXM + (b - 2 - lo[0]);
+      T v = T(0);
 #pragma unroll
-          for (int a = 0; a < 6; ++a) ax += p.w[r[0]][a] * node_value<T, NS>(cb, row + a);
-          ay += p.w[r[1]][b] * ax;
-        }
-        acc += p.w[r[2]][c] * ay;
-      }
-      out[f * p.osf + (long long)k * p.osz + (long long)j * p.osy + i] = T(acc);
+      for (int q = 0; q < 6; ++q) v += lagrange_w<T>(p, r, q) * row[q];
+      tx[(cz * CYM + cy) * PX + xi] = v;
+    }
+    __syncthreads();
+    for (int t = tid; t < nc[2] * nv[1] * nv[0]; t += blockDim.x) {
+      const int xi = t % nv[0], yi = (t / nv[0]) % nv[1], cz = t / (nv[0] * nv[1]);
+      const int F = F0[1] + yi, b = floordiv(F, R), r = F - b * R;
+      const T* col = tx + (cz * CYM + (b - 2 - lo[1])) * PX + xi;
+      T v = T(0);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) v += lagrange_w<T>(p, r, q) * col[q * PX];
+      ty[(cz * PY + yi) * PX + xi] = v;
+    }
+    __syncthreads();
+    for (int t = tid; t < nv[2] * nv[1] * nv[0]; t += blockDim.x) {
+      const int xi = t % nv[0], yi = (t / nv[0]) % nv[1], zi = t / (nv[0] * nv[1]);
+      const int F = F0[2] + zi, b = floordiv(F, R), r = F - b * R;
+      const T* col = ty + ((b - 2 - lo[2]) * PY + yi) * PX + xi;
+      T v = T(0);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) v += lagrange_w<T>(p, r, q) * col[q * PY * PX];
+      const int i = F0[0] - p.origin[0] + xi, j = F0[1] - p.origin[1] + yi,
+                k = F0[2] - p.origin[2] + zi;
+      out[f * p.osf + (long long)k * p.osz + (long long)j * p.osy + i] = v;
     }
   }
 }
@@ -228,17 +289,20 @@ extern "C" sf_status sf_copy_boxes(const sf_box_copy* boxes, int32_t nbox, int32
       return set_error(SF_EINVAL, "box %d: misaligned array", q);
     if (b.nf < 1 || b.src_step < 1 || b.ext[0] < 0 || b.ext[1] < 0 || b.ext[2] < 0)
       return set_error(SF_EINVAL, "box %d: nf >= 1, src_step >= 1 and ext >= 0 required", q);
+    if ((long long)b.ext[0] * b.ext[1] * b.ext[2] * b.nf >= (1LL << 31))
+      return set_error(SF_EINVAL, "box %d: more than 2^31 values", q);
   }
   cudaStream_t st = (cudaStream_t)stream;
   for (int q0 = 0; q0 < nbox; q0 += kBoxesPerLaunch) {
     BoxBatch bb;
     bb.n = nbox - q0 < kBoxesPerLaunch ? nbox - q0 : kBoxesPerLaunch;
-    long long maxv = 1;
+    long long maxv = 0;
     for (int q = 0; q < bb.n; ++q) {
       bb.b[q] = boxes[q0 + q];
       const long long v = (long long)bb.b[q].ext[0] * bb.b[q].ext[1] * bb.b[q].ext[2] * bb.b[q].nf;
       maxv = v > maxv ? v : maxv;
     }
+    if (maxv == 0) continue;
     int gx = (int)((maxv + 255) / 256);
     if (gx > 1024) gx = 1024;
     if (precision == SF_FP64)
@@ -294,6 +358,7 @@ static sf_status prolong_launch(const sf_patch* coarse, const void* const* array
       for (int m = 0; m < 6; ++m)
         if (m != j) l *= (t - double(m - 2)) / (double(j - 2) - double(m - 2));
       a.w[r][j] = l;
+      a.wf[r][j] = (float)l;
     }
   }
   a.R = ratio;
@@ -310,20 +375,30 @@ static sf_status prolong_launch(const sf_patch* coarse, const void* const* array
   a.osz = out_sz;
   a.osf = out_sf;
   a.nf = nf;
-  const long long vol = (long long)ext[0] * ext[1] * ext[2];
-  int blocks = (int)((vol + 127) / 128);
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  const long long zt = (ext[2] + PZ - 1) / PZ;
+  if (ext[1] > 65535LL * PY || zt * nf > 65535) return set_error(SF_EINVAL, "box too large");
+  const dim3 grid((ext[0] + PX - 1) / PX, (ext[1] + PY - 1) / PY, (unsigned)(zt * nf));
   cudaStream_t st = (cudaStream_t)stream;
   if (p.precision == SF_FP64) {
     Combo<double> cb;
     for (int m = 0; m < 5; ++m) cb.s[m] = m <= NS ? (const double*)arrays[m] : nullptr;
     for (int m = 0; m < 4; ++m) cb.c[m] = (c && m < NS) ? c[m] : 0.0;
-    prolong_kernel<double, NS><<<blocks, 128, 0, st>>>(cb, (double*)fine_out, a);
+    static std::once_flag once;
+    std::call_once(once, [] {
+      cudaFuncSetAttribute(prolong_kernel<double, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           prolong_smem<double>());
+    });
+    prolong_kernel<double, NS><<<grid, 256, prolong_smem<double>(), st>>>(cb, (double*)fine_out, a);
   } else {
     Combo<float> cb;
     for (int m = 0; m < 5; ++m) cb.s[m] = m <= NS ? (const float*)arrays[m] : nullptr;
     for (int m = 0; m < 4; ++m) cb.c[m] = (c && m < NS) ? c[m] : 0.0;
-    prolong_kernel<float, NS><<<blocks, 128, 0, st>>>(cb, (float*)fine_out, a);
+    static std::once_flag once;
+    std::call_once(once, [] {
+      cudaFuncSetAttribute(prolong_kernel<float, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           prolong_smem<float>());
+    });
+    prolong_kernel<float, NS><<<grid, 256, prolong_smem<float>(), st>>>(cb, (float*)fine_out, a);
   }
   return after_launch("prolong_kernel");
 }

@@ -90,6 +90,27 @@ def test_prolongation_matches_oracle(R):
                                   want[:, off[2]::R, off[1]::R, off[0]::R])
 
 
+@pytest.mark.parametrize("R", [2, 3])
+def test_prolongation_float_arrays(R):
+    # float arrays interpolate in float: the weights of each 1D set sum to one
+    # and |l_j| <= 1.6, so the result carries <= ~(1.6^3 + 1) ulps of max |U|
+    n = (10, 9, 8)
+    rng = np.random.default_rng(10 + R)
+    Uc = rng.standard_normal((25, n[2], n[1], n[0]))
+    st = PatchState(capi.SF_Z4, n, (0.1, 0.1, 0.1), 0.01, precision=capi.SF_FP32_BULK)
+    st.upload(Uc)
+    origin, ext = (R * 2 - 1, R * 1 + 1, R * 3), (R * 5 + 2, R * 4, R * 2 + 1)
+    out = torch.zeros((25, ext[2], ext[1], ext[0]), dtype=torch.float32, device="cuda")
+    capi.sf_prolong(st.patch(st.A, st.A, st.B), st.A.data_ptr(), 25, R, origin, ext,
+                    out.data_ptr(), ext[0], ext[0] * ext[1], ext[0] * ext[1] * ext[2])
+    # the oracle sees the stored float values (flat-space offsets included)
+    stored = st.interior().double().cpu().numpy()
+    want = oracle.prolong(oracle.ghosted(stored), R, origin, ext)
+    got = out.double().cpu().numpy()
+    eps32 = float(np.finfo(np.float32).eps)
+    assert np.abs(got - want).max() <= 8 * eps32 * np.abs(stored).max()
+
+
 def test_prolongation_rejects_stencil_outside_coarse_box():
     st = PatchState(capi.SF_WAVE, (6, 6, 6), (0.1,) * 3, 0.01)
     out = torch.zeros(5 * 8, dtype=torch.float64, device="cuda")
