@@ -32,6 +32,13 @@ Functions and what pins them (tests/test_oracle_*.py):
                    Shu-Osher form.
   misfit_gradient  discrete adjoint of the RK4 wave evolution.  Pinned:
                    central finite differences (exact for the quadratic misfit).
+  radiative_rhs    Sec. V radiative boundary condition at ghost points.
+                   Pinned: zero on U = U_inf; closed form on linear data
+                   (every one-sided stencil exact); 4th-order convergence to
+                   the time derivative of an exact outgoing spherical wave.
+  rk4_step_radiative  RK4 with radiative ghost points.  Pinned: reduces to
+                   the plain step's interior on data that the boundary does
+                   not reach within one step; outgoing wave convergence.
   stencil(DLOP)    Sec. II.B.1 one-sided advection stencils.  Pinned:
                    exactness on quartics, one-sidedness, truncation term.
   prolong          Sec. III.A quintic Lagrange prolongation.  Pinned:
@@ -145,6 +152,9 @@ def lib() -> ctypes.CDLL:
                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_double]
         L.or_stencil.restype = ctypes.c_double
+        L.or_radiative_rhs.argtypes = [ctypes.c_int, ip, ctypes.c_int, dp, dp, dp, dp, dp, dp]
+        L.or_rk4_step_radiative.argtypes = [ctypes.c_int, pp, ip, ctypes.c_int, dp, dp, dp, dp,
+                                            ctypes.c_double, dp, dp]
         L.or_bor_fine_stages.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double,
                                          ctypes.c_int, ctypes.c_int, dp]
         L.or_dense_output.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double,
@@ -164,6 +174,11 @@ def _ivec(n):
 
 def _dvec(d):
     return (ctypes.c_double * 3)(*[float(x) for x in d])
+
+
+def _darr(d):
+    d = [float(x) for x in d]
+    return (ctypes.c_double * len(d))(*d)
 
 
 def shape_info(U: np.ndarray, g: int):
@@ -226,6 +241,36 @@ def restrict(Uf: np.ndarray, ratio: int, origin, ext, g: int = 3) -> np.ndarray:
     if rc:
         raise ValueError("oracle restrict: out of the fine box")
     return out
+
+
+def radiative_rhs(U: np.ndarray, dx, x0, uinf, v, g: int = 3) -> np.ndarray:
+    """Sec. V radiative RHS at every ghost point of the ghosted array U (zero
+    at interior points).  x0 = position of interior point (0,0,0)."""
+    nf, n = shape_info(U, g)
+    out = np.zeros_like(np.ascontiguousarray(U, dtype=np.float64))
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    rc = lib().or_radiative_rhs(nf, _ivec(n), g, _dvec(dx), _dvec(x0), _dp(U),
+                                _darr(np.broadcast_to(uinf, nf)), _darr(np.broadcast_to(v, nf)),
+                                _dp(out))
+    if rc:
+        raise ValueError("oracle radiative_rhs: bad arguments")
+    return out
+
+
+def rk4_step_radiative(system: int, U: np.ndarray, dx, x0, uinf, v, dt: float,
+                       p: Params | None = None, g: int = 3, stages: bool = False):
+    """One RK(4,4) step in place with radiative ghost points (Sec. V); returns
+    the ghosted U(2), U(3), U(4), U^{n+1} if asked."""
+    p = p or params()
+    nf, n = shape_info(U, g)
+    st = np.zeros((4,) + U.shape) if stages else None
+    rc = lib().or_rk4_step_radiative(system, ctypes.byref(p), _ivec(n), g, _dvec(dx), _dvec(x0),
+                                     _darr(np.broadcast_to(uinf, nf)),
+                                     _darr(np.broadcast_to(v, nf)), dt, _dp(U),
+                                     _dp(st) if stages else None)
+    if rc:
+        raise ValueError("oracle rk4_step_radiative: bad arguments")
+    return st
 
 
 def bor_fine_stages(rk: int, Un: np.ndarray, k: np.ndarray, dt: float, R: int, r: int) -> np.ndarray:

@@ -734,6 +734,45 @@ void rhs_all(int system, const or_params& p, const Grid& G, const double* dx, co
       }
 }
 
+// ---------------------------------------------------------------- radiative boundaries
+// Sec. V: radiative (outgoing-wave) boundary condition.  A field behaving as
+// U = U_inf + f(r - v t)/r near the boundary obeys
+//   dU/dt = -v x^i/r d_i U - v (U - U_inf)/r,
+// with x the physical position of the point and r = |x|.  It is applied at
+// every ghost point of a non-periodic patch, whose values are then evolved by
+// the RK stages like the interior.  d_i is the centred 4th-order D_i where the
+// ghosted array holds two points on both sides of the point, and a 4th-order
+// one-sided stencil leaning into the array elsewhere:
+//   one point behind:  (-3 U_{-1} - 10 U_0 + 18 U_{+1} - 6 U_{+2} + U_{+3}) / (12 h),
+//   none behind:       (-25 U_0 + 48 U_{+1} - 36 U_{+2} + 16 U_{+3} - 3 U_{+4}) / (12 h),
+// and their mirror images at the upper end.
+static double rad_deriv(const double* u, const Grid& G, int f, int i, int j, int k, int d,
+                        const double* dx) {
+  const int ig = (d == 0 ? i : (d == 1 ? j : k)) + G.g;
+  const long N = G.N[d];
+  auto U = [&](int s) { return U_off<double>(u, G, f, i, j, k, d, s); };
+  const double h12 = 12.0 * dx[d];
+  if (ig >= 2 && ig <= N - 3) return (U(-2) - 8.0 * U(-1) + 8.0 * U(1) - U(2)) / h12;
+  if (ig == 1) return (-3.0 * U(-1) - 10.0 * U(0) + 18.0 * U(1) - 6.0 * U(2) + U(3)) / h12;
+  if (ig == 0) return (-25.0 * U(0) + 48.0 * U(1) - 36.0 * U(2) + 16.0 * U(3) - 3.0 * U(4)) / h12;
+  if (ig == N - 2) return (3.0 * U(1) + 10.0 * U(0) - 18.0 * U(-1) + 6.0 * U(-2) - U(-3)) / h12;
+  return (25.0 * U(0) - 48.0 * U(-1) + 36.0 * U(-2) - 16.0 * U(-3) + 3.0 * U(-4)) / h12;
+}
+
+static double rad_rhs_point(const double* u, const Grid& G, int f, int i, int j, int k,
+                            const double* dx, const double* x0, double uinf, double v) {
+  const double x[3] = {x0[0] + i * dx[0], x0[1] + j * dx[1], x0[2] + k * dx[2]};
+  const double r = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  if (r == 0.0) return 0.0;
+  double xdu = 0.0;
+  for (int d = 0; d < 3; ++d) xdu += x[d] * rad_deriv(u, G, f, i, j, k, d, dx);
+  return -v * xdu / r - v * (u[G.at(f, i, j, k)] - uinf) / r;
+}
+
+static bool is_ghost(const Grid& G, int i, int j, int k) {
+  return !(i >= 0 && i < G.n[0] && j >= 0 && j < G.n[1] && k >= 0 && k < G.n[2]);
+}
+
 void fill_ghosts(int nf, const Grid& G, double* u) {
   // periodic: ghost (i,j,k) takes the value of interior ((i mod n), ...)
   for (int f = 0; f < nf; ++f)
@@ -1100,6 +1139,64 @@ int or_restrict(int nf, const int* nfine, int gf, const double* fu, int ratio, c
             return 1;
           out[(((long)f * ext[2] + k) * ext[1] + j) * ext[0] + i] = fu[G.at(f, I, J, K)];
         }
+  return 0;
+}
+
+// Radiative right-hand side (Sec. V) at every ghost point of the ghosted
+// array u (nf fields); out has u's layout and receives it at ghost points
+// (interior points are left untouched).  x0 = physical position of interior
+// point (0,0,0); uinf, v = per-field value at infinity and speed.
+int or_radiative_rhs(int nf, const int* n, int g, const double* dx, const double* x0,
+                     const double* u, const double* uinf, const double* v, double* out) {
+  if (g < 3 || nf < 1) return 1;
+  Grid G(n, g);
+  for (int d = 0; d < 3; ++d)
+    if (G.N[d] < 7) return 1;
+  for (int f = 0; f < nf; ++f)
+    for (int k = -g; k < n[2] + g; ++k)
+      for (int j = -g; j < n[1] + g; ++j)
+        for (int i = -g; i < n[0] + g; ++i)
+          if (is_ghost(G, i, j, k))
+            out[G.at(f, i, j, k)] = rad_rhs_point(u, G, f, i, j, k, dx, x0, uinf[f], v[f]);
+  return 0;
+}
+
+// One RK(4,4) step (Sec. II.C) of a non-periodic patch whose ghost points
+// evolve under the radiative condition: interior k_j = dt (L + Q_d)(U(j)),
+// ghost k_j = dt (radiative RHS)(U(j)); the stage inputs are formed at every
+// point.  U is ghosted and updated in place; `stages` (optional) receives the
+// ghosted U(2), U(3), U(4), U^{n+1}.
+int or_rk4_step_radiative(int system, const or_params* p, const int* n, int g, const double* dx,
+                          const double* x0, const double* uinf, const double* v, double dt,
+                          double* U, double* stages) {
+  const int nf = nfields(system, *p);
+  if (nf < 0 || g < 3) return 1;
+  Grid G(n, g);
+  for (int d = 0; d < 3; ++d)
+    if (G.N[d] < 7) return 1;
+  const size_t tot = (size_t)nf * G.sf, inn = (size_t)nf * G.ninterior;
+  std::vector<double> S(U, U + tot), kin(inn), K[4];
+  for (int s = 0; s < 4; ++s) K[s].assign(tot, 0.0);
+  const double a[3] = {0.5, 0.5, 1.0};
+  for (int s = 0; s < 4; ++s) {
+    // k_s = dt * RHS(S) at every point
+    rhs_all(system, *p, G, dx, S.data(), kin.data());
+    for (int f = 0; f < nf; ++f)
+      for (int k = -g; k < n[2] + g; ++k)
+        for (int j = -g; j < n[1] + g; ++j)
+          for (int i = -g; i < n[0] + g; ++i) {
+            const long o = G.at(f, i, j, k);
+            K[s][o] = dt * (is_ghost(G, i, j, k)
+                                ? rad_rhs_point(S.data(), G, f, i, j, k, dx, x0, uinf[f], v[f])
+                                : kin[G.out(f, i, j, k)]);
+          }
+    if (s < 3) {
+      for (size_t o = 0; o < tot; ++o) S[o] = U[o] + a[s] * K[s][o];
+      if (stages) std::copy(S.begin(), S.end(), stages + s * tot);
+    }
+  }
+  for (size_t o = 0; o < tot; ++o) U[o] += (K[0][o] + 2.0 * K[1][o] + 2.0 * K[2][o] + K[3][o]) / 6.0;
+  if (stages) std::copy(U, U + tot, stages + 3 * tot);
   return 0;
 }
 

@@ -269,6 +269,71 @@ def z4_perturbed(n, seed: int = 0, amp: float = 0.05):
 
 
 # ------------------------------------------------------------------- batches
+def z4_puncture_box(n, length: float):
+    """Cell-centred grid on the cube [-length/2, length/2)^3: returns
+    (dx, x0) with x0 the position of point (0,0,0), so no point sits on the
+    origin (or on a puncture placed at a cell corner)."""
+    dx = tuple(length / v for v in n)
+    x0 = tuple(-length / 2 + 0.5 * h for h in dx)
+    return dx, x0
+
+
+def z4_puncture(n, length: float = 8.0, holes=None, ghost: int = 0):
+    """Puncture initial data of Sec. V on a cell-centred box (Brill-Lindquist
+    conformal factor, Bowen-York extrinsic curvature):
+      psi = 1 + sum_A m_A / (2 r_A),  chi = psi^-4,  alpha = psi^-2,
+      gt_ij = delta_ij,  Khat = Theta = 0,  Gammahat = beta = B = 0,
+      At_ij = sum_A 3/(2 r_A^2 psi^6) [P_i n_j + P_j n_i - (delta_ij - n_i n_j) P.n]
+            + sum_A 3/(r_A^3 psi^6) [eps_kil S^l n^k n_j + eps_kjl S^l n^k n_i],
+    n = x^(A)/r_A.  `holes` is a list of dicts with keys m, pos, P, S (default:
+    one spinning, boosted hole of bare mass 1 at (0.05, -0.03, 0.02)).
+    With ghost > 0 the data also cover the ghost points (the arrays are then
+    (25, nz+2g, ny+2g, nx+2g)).  Returns (U, dx, x0), x0 = position of
+    interior point (0,0,0)."""
+    if holes is None:
+        holes = [dict(m=1.0, pos=(0.05, -0.03, 0.02), P=(0.1, 0.05, 0.0), S=(0.0, 0.0, 0.2))]
+    dx, x0 = z4_puncture_box(n, length)
+    g = ghost
+    ax = [x0[d] + dx[d] * np.arange(-g, n[d] + g) for d in range(3)]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    xs = (X, Y, Z)
+    psi = np.ones_like(X)
+    for h in holes:
+        r = np.sqrt(sum((xs[d] - h["pos"][d]) ** 2 for d in range(3)))
+        psi += h["m"] / (2 * r)
+    At = np.zeros((3, 3) + X.shape)
+    eps = np.zeros((3, 3, 3))
+    eps[0, 1, 2] = eps[1, 2, 0] = eps[2, 0, 1] = 1.0
+    eps[0, 2, 1] = eps[2, 1, 0] = eps[1, 0, 2] = -1.0
+    for h in holes:
+        rel = [xs[d] - h["pos"][d] for d in range(3)]
+        r = np.sqrt(sum(c * c for c in rel))
+        nv = [c / r for c in rel]
+        P, S = h["P"], h["S"]
+        Pn = sum(P[d] * nv[d] for d in range(3))
+        for i in range(3):
+            for j in range(3):
+                dij = 1.0 if i == j else 0.0
+                lin = P[i] * nv[j] + P[j] * nv[i] - (dij - nv[i] * nv[j]) * Pn
+                spin = 0.0
+                for k in range(3):
+                    for l in range(3):
+                        spin = spin + eps[k, i, l] * S[l] * nv[k] * nv[j] + eps[k, j, l] * S[l] * nv[k] * nv[i]
+                At[i, j] += 1.5 / r ** 2 * lin + 3.0 / r ** 3 * spin
+    At /= psi ** 6
+    U = np.zeros((Z4_NF,) + X.shape)
+    U[0] = psi ** -4
+    U[1] = U[4] = U[6] = 1.0
+    for q, (i, j) in enumerate([(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]):
+        U[8 + q] = At[i, j]
+    U[18] = psi ** -2
+    return U, dx, x0
+
+
+# values at infinity of the CCZ4 fields (flat space) for radiative boundaries
+Z4_UINF = np.array([1.0, 1, 0, 0, 1, 0, 1] + [0.0] * 11 + [1.0] + [0.0] * 6)
+
+
 def amr_patch_table(npatch: int = 512, seed: int = 0, lo: int = 16, hi: int = 64):
     """Seeded patch descriptors for the batched AMR step: sizes (nx, ny, nz)
     each uniform in {lo..hi}, level in {0, 1, 2} with dx = 1/64, 1/128, 1/384
