@@ -403,6 +403,33 @@ def suite(args, hbm_peak: float) -> list[dict]:
         out += _variant_rows(hbm_peak)
     if "amr" in rows:
         out += _amr_rows(hbm_peak)
+    if "puncture" in rows:
+        out += _puncture_rows(hbm_peak)
+    return out
+
+
+def _puncture_rows(hbm_peak: float) -> list[dict]:
+    """Second workload (Sec. V): a spinning, boosted puncture on a 96^3
+    non-periodic box with radiative boundaries (interior stage kernel +
+    radiative ghost-shell kernel per stage)."""
+    import numpy as np
+    from paper_1806_04182_gb300 import capi, inputs
+    from paper_1806_04182_gb300.state import PatchState
+    out = []
+    n = (N, N, N)
+    U, dx, x0 = inputs.z4_puncture(n, length=16.0, ghost=GHOST)
+    speed = np.ones(NF)
+    for prec, name, pitch in ((capi.SF_FP32_BULK_DW, "fp32dw", FLOAT_PITCH), (capi.SF_FP64, "fp64", None)):
+        st = PatchState(capi.SF_Z4, n, dx, 0.25 * dx[0], precision=prec,
+                        prm=capi.params(ghosts=capi.SF_GHOSTS_NONE), x_pitch=pitch)
+        st.upload_ghosted(U)
+        steps = 10 if prec != capi.SF_FP64 else 3
+        ms = _events_time(lambda: st.step_radiative(1, x0, inputs.Z4_UINF, speed), steps, 2)
+        rate = N ** 3 * 4 * steps / (ms * 1e-3)
+        out.append({"workload": f"ccz4_puncture_96cubed_radiative_{name}", "value": rate, "unit": UNIT,
+                    "ms_per_step": ms / steps, "hbm_frac": rate * (475 if prec != capi.SF_FP64 else 800)
+                    / 1e9 / hbm_peak,
+                    "note": "interior cells; 1+log slicing, Gamma-driver, radiative ghost shell"})
     return out
 
 
@@ -691,7 +718,7 @@ def main():
     ap.add_argument("--suite", action="store_true",
                     help="time every workload row (one JSON line each) instead of the headline")
     ap.add_argument("--rows", default=None,
-                    help="comma-separated subset of wave,mhd,batch,batch_graph,adjoint,variants,amr "
+                    help="comma-separated subset of wave,mhd,batch,batch_graph,adjoint,variants,amr,puncture "
                          "for --suite")
     ap.add_argument("--npatch", type=int, default=512, help="patches of the batch rows")
     ap.add_argument("--pitch", type=int, default=FLOAT_PITCH,

@@ -208,6 +208,26 @@ sf_status sf_diagnostics(const sf_params* prm, const sf_patch* patch, const void
                          double* d_out, void* stream);
 
 /*
+ * Radiative (outgoing-wave) boundary condition of Sec. V: one RK stage at
+ * every ghost point of a non-periodic patch, with the right-hand side
+ *   dU/dt = -speed[f] ( x^i/r d_i U + (U - u_inf[f]) / r ),
+ * x = x0 + (i, j, k) dx the physical position of the point (x0 = position of
+ * interior point (0,0,0)), r = |x|, and d_i the centred 4th-order stencil
+ * where the ghosted array holds two points on both sides, else the 4th-order
+ * one-sided stencil leaning into the array.  The stage combination and the
+ * array roles are those of sf_substep, which advances the interior of the
+ * same patch for the same stage (with prm->ghosts = SF_GHOSTS_NONE, so that
+ * it leaves the ghost shell to this call; both only read u_stage).  u_inf
+ * and speed hold one value per field (u_inf in field values: the flat-space
+ * offsets of float CCZ4 storage are applied here).  SF_EINVAL if
+ * prm->ghosts is not SF_GHOSTS_NONE, for non-finite x0 or u_inf, negative
+ * speeds, or any argument sf_substep rejects.
+ */
+sf_status sf_radiative_substep(const sf_params* prm, const sf_patch* patch, const double* x0,
+                               const double* u_inf, const double* speed, int32_t stage,
+                               void* stream);
+
+/*
  * Box copies between patch arrays, for the AMR level loop (Sec. III): same-
  * level ghost synchronisation between neighbouring patches, and, with
  * src_step = R, restriction by injection (Sec. III.A: coarse point i takes

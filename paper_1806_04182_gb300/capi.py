@@ -26,7 +26,7 @@ EXPORTS = ["sf_nfields", "sf_substep", "sf_rhs", "sf_fill_ghosts_periodic", "sf_
            "sf_adjoint_substep", "sf_gather", "sf_scatter_add", "sf_diagnostics",
            "sf_batch_create", "sf_batch_substep", "sf_batch_tune", "sf_batch_capture",
            "sf_batch_launch", "sf_batch_launches_per_step", "sf_batch_destroy",
-           "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong", "sf_bor_prolong",
+           "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong", "sf_bor_prolong", "sf_radiative_substep",
            "sf_get_device_status", "sf_last_error", "sf_launch_count"]
 
 
@@ -138,6 +138,8 @@ def lib() -> ctypes.CDLL:
         L.sf_batch_substep_static.argtypes = [P(sf_params), P(sf_patch), i32, i32, vp]
         L.sf_copy_boxes.argtypes = [P(sf_box_copy), i32, i32, vp]
         L.sf_prolong.argtypes = [P(sf_patch), vp, i32, i32, P(i32), P(i32), vp, i64, i64, i64, vp]
+        L.sf_radiative_substep.argtypes = [P(sf_params), P(sf_patch), P(ctypes.c_double),
+                                           P(ctypes.c_double), P(ctypes.c_double), i32, vp]
         L.sf_bor_prolong.argtypes = [P(sf_patch), i32, P(vp), i32, i32, i32, i32, P(i32), P(i32), vp,
                                      i64, i64, i64, vp]
         L.sf_get_device_status.argtypes = [vp]
@@ -260,6 +262,16 @@ def sf_prolong(coarse: sf_patch, coarse_array: int, nf: int, ratio: int, origin,
     e = (ctypes.c_int32 * 3)(*ext)
     _check(lib().sf_prolong(ctypes.byref(coarse), coarse_array, nf, ratio, o, e, fine_out, out_sy,
                             out_sz, out_sf, stream), "sf_prolong")
+
+
+def sf_radiative_substep(prm: sf_params, patch: sf_patch, x0, u_inf, speed, stage: int,
+                         stream: int = 0) -> None:
+    """RK stage of the radiative boundary condition on the ghost shell (Sec. V)."""
+    d3 = (ctypes.c_double * 3)(*[float(v) for v in x0])
+    ui = (ctypes.c_double * len(u_inf))(*[float(v) for v in u_inf])
+    sp = (ctypes.c_double * len(speed))(*[float(v) for v in speed])
+    _check(lib().sf_radiative_substep(ctypes.byref(prm), ctypes.byref(patch), d3, ui, sp, stage,
+                                      stream), "sf_radiative_substep")
 
 
 def sf_bor_prolong(coarse: sf_patch, rk: int, states, nf: int, ratio: int, r: int, stage: int,

@@ -191,6 +191,31 @@ const char* sf_last_error(void) { return t_err; }
 
 int64_t sf_launch_count(void) { return g_launches.load(); }
 
+sf_status sf_radiative_substep(const sf_params* prm, const sf_patch* patch, const double* x0,
+                               const double* u_inf, const double* speed, int32_t stage,
+                               void* stream) {
+  t_err[0] = 0;
+  if (!prm || !patch || !x0 || !u_inf || !speed) return set_error(SF_EINVAL, "NULL argument");
+  sf_patch p = *patch;
+  const int nf = sf_nfields(p.system);
+  normalise_strides(p, nf);
+  sf_status e = check_patch(prm, p, 1, stage);
+  if (e) return e;
+  if (prm->ghosts != SF_GHOSTS_NONE)
+    return set_error(SF_EINVAL, "radiative boundaries need ghosts = SF_GHOSTS_NONE");
+  for (int d = 0; d < 3; ++d)
+    if (!(x0[d] == x0[d]) || x0[d] > 1e300 || x0[d] < -1e300)
+      return set_error(SF_EINVAL, "x0[%d] not finite", d);
+  for (int f = 0; f < nf; ++f) {
+    if (!(speed[f] >= 0.0) || speed[f] > 1e300) return set_error(SF_EINVAL, "speed[%d] must be >= 0", f);
+    if (!(u_inf[f] == u_inf[f]) || u_inf[f] > 1e300 || u_inf[f] < -1e300)
+      return set_error(SF_EINVAL, "u_inf[%d] not finite", f);
+  }
+  StageArgs s = stage_args(*prm, p, stage, 0);
+  if (!s.status) return set_error(SF_ECUDA, "no CUDA device / status word unavailable");
+  return launch_radiative(*prm, p, s, stage, x0, u_inf, speed, (cudaStream_t)stream);
+}
+
 sf_status sf_substep(const sf_params* prm, const sf_patch* patches, int32_t npatch, int32_t stage,
                      void* stream) {
   t_err[0] = 0;

@@ -20,6 +20,10 @@ sf_status launch_z4(const sf_params& prm, const sf_patch& p, const StageArgs& s,
 bool z4_tma_eligible(const sf_params& prm, const sf_patch& p);
 sf_status launch_z4_tma(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                         void* rhs_out, cudaStream_t st);
+// radiative boundary stage on the ghost shell (sf_radiative.cu)
+sf_status launch_radiative(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
+                           const double* x0, const double* u_inf, const double* speed,
+                           cudaStream_t st);
 sf_status launch_mhd(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                      void* rhs_out, cudaStream_t st);
 

@@ -126,6 +126,30 @@ class PatchState:
         self._rate = None
         self.fill_ghosts(self.A, stream)
 
+    def upload_ghosted(self, ghosted, stream=None) -> None:
+        """Set U^n from a full ghosted array (nf, nz+2g, ny+2g, nx+2g) of field
+        values, ghost points included (non-periodic patches)."""
+        t = torch.as_tensor(np.ascontiguousarray(ghosted) if isinstance(ghosted, np.ndarray)
+                            else ghosted).double().clone()
+        for f in self.offset_fields:
+            t[f] -= 1.0
+        nx = self.n[0] + 2 * self.g
+        self.A[:, :, :, :nx].copy_(t.to(self.dtype))
+        if self.E is not None:
+            self.E.zero_()
+        self._rate = None
+
+    def step_radiative(self, nsteps: int, x0, u_inf, speed, stream=None) -> None:
+        """RK steps of a non-periodic patch: the interior by sf_substep, the
+        ghost shell by the radiative boundary condition (Sec. V).  The patch's
+        params must have ghosts = SF_GHOSTS_NONE."""
+        h = _stream_handle(stream)
+        for _ in range(nsteps):
+            for s in range(self.nstages):
+                p = self.stage_patch(s)
+                capi.sf_substep(self.prm, p, s, h)
+                capi.sf_radiative_substep(self.prm, p, x0, u_inf, speed, s, h)
+
     def fill_ghosts(self, array: torch.Tensor, stream=None) -> None:
         capi.sf_fill_ghosts_periodic(self.patch(array, array, array), array.data_ptr(), self.nf,
                                      _stream_handle(stream))
