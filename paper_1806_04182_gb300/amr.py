@@ -134,8 +134,11 @@ def ghost_shell_boxes(st: PatchState):
 
 
 class SubcycledPair:
-    """A periodic coarse patch and one fine patch, `ratio` times finer in
-    space and time, advanced with sub-cycling (Sec. III.B).
+    """A coarse patch and one fine patch, `ratio` times finer in space and
+    time, advanced with sub-cycling (Sec. III.B).  The coarse patch is
+    periodic, or, with `coarse_radiative` = (x0, u_inf, speed), an outer box
+    whose ghost shell follows the radiative condition of Sec. V (its params
+    must then have ghosts = SF_GHOSTS_NONE).
 
     The fine patch covers coarse interior points at .. at + n_fine/ratio - 1
     and has no periodic images of its own: before each fine RK stage its
@@ -148,13 +151,17 @@ class SubcycledPair:
     are copied aside (RK4: U^n and U^(2); SSP-RK3: U^n).
     """
 
-    def __init__(self, coarse: PatchState, fine: PatchState, ratio: int, at):
+    def __init__(self, coarse: PatchState, fine: PatchState, ratio: int, at,
+                 coarse_radiative=None):
         if coarse.prm.rk != fine.prm.rk:
             raise ValueError("coarse and fine levels must use the same RK scheme")
         if fine.prm.ghosts != capi.SF_GHOSTS_NONE:
             raise ValueError("the fine patch must be created with ghosts=SF_GHOSTS_NONE")
         if any(v % ratio for v in fine.n):
             raise ValueError("fine patch size must be a multiple of the ratio")
+        if coarse_radiative is not None and coarse.prm.ghosts != capi.SF_GHOSTS_NONE:
+            raise ValueError("a radiative coarse patch needs ghosts=SF_GHOSTS_NONE")
+        self.radiative = coarse_radiative
         self.coarse, self.fine, self.R = coarse, fine, int(ratio)
         self.at = tuple(int(v) for v in at)
         self.rk = coarse.prm.rk
@@ -196,7 +203,10 @@ class SubcycledPair:
         for _ in range(nsteps):
             capi.sf_copy_boxes([self._box_S0], c.precision, h)
             for s in range(c.nstages):
-                capi.sf_substep(c.prm, c.stage_patch(s), s, h)
+                cp = c.stage_patch(s)
+                capi.sf_substep(c.prm, cp, s, h)
+                if self.radiative is not None:
+                    capi.sf_radiative_substep(c.prm, cp, *self.radiative, s, h)
                 if s == 0 and self._box_S1 is not None:
                     capi.sf_copy_boxes([self._box_S1], c.precision, h)
             for r in range(R):
@@ -204,7 +214,8 @@ class SubcycledPair:
                     self.fill_fine_ghosts(f.roles(s)[0], r, s, h)
                     capi.sf_substep(f.prm, f.stage_patch(s), s, h)
             capi.sf_copy_boxes([self._restrict], c.precision, h)
-            c.fill_ghosts(c.A, h)
+            if self.radiative is None:
+                c.fill_ghosts(c.A, h)
 
 
 def _stream(stream) -> int:

@@ -36,55 +36,63 @@ __device__ __forceinline__ T rad_d(const T* __restrict__ p, long long s, int ig,
          i12h;
 }
 
-// One thread per ghost point, enumerated as the two z slabs (full x-y
-// planes), the two y slabs (interior z) and the two x slabs (interior y, z).
+// One thread per ghost point and group of five fields (gridDim.y groups);
+// ghost points are enumerated as the two z slabs (full x-y planes), the two y
+// slabs (interior z) and the two x slabs (interior y, z).  32-bit index
+// arithmetic (the host checks the count); the five fields' reads are issued
+// together.
+constexpr int kFieldGroup = 5;
+
 template <typename T>
 __global__ void __launch_bounds__(256) radiative_kernel(PatchArgs<T> a, StageArgs s, RadArgs ra) {
-  const int g = a.g;
-  const long long N0 = a.n[0] + 2 * g, N1 = a.n[1] + 2 * g;
-  const long long zslab = 2LL * g * N1 * N0;
-  const long long yslab = (long long)a.n[2] * 2 * g * N0;
-  const long long xslab = (long long)a.n[2] * a.n[1] * 2 * g;
-  const long long total = zslab + yslab + xslab;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
+  const unsigned g = (unsigned)a.g;
+  const unsigned N0 = a.n[0] + 2 * g, N1 = a.n[1] + 2 * g;
+  const unsigned zslab = 2 * g * N1 * N0;
+  const unsigned yslab = (unsigned)a.n[2] * 2 * g * N0;
+  const unsigned xslab = (unsigned)a.n[2] * a.n[1] * 2 * g;
+  const unsigned total = zslab + yslab + xslab;
+  const int f0 = blockIdx.y * kFieldGroup;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
     int i, j, k;  // interior coordinates; ghost points lie outside [0, n)
     if (t < zslab) {
-      long long q = t;
-      i = (int)(q % N0) - g;
+      unsigned q = t;
+      i = (int)(q % N0) - (int)g;
       q /= N0;
-      j = (int)(q % N1) - g;
+      j = (int)(q % N1) - (int)g;
       const int kk = (int)(q / N1);
-      k = kk < g ? kk - g : a.n[2] + (kk - g);
+      k = kk < (int)g ? kk - (int)g : a.n[2] + (kk - (int)g);
     } else if (t < zslab + yslab) {
-      long long q = t - zslab;
-      i = (int)(q % N0) - g;
+      unsigned q = t - zslab;
+      i = (int)(q % N0) - (int)g;
       q /= N0;
       const int jj = (int)(q % (2 * g));
       k = (int)(q / (2 * g));
-      j = jj < g ? jj - g : a.n[1] + (jj - g);
+      j = jj < (int)g ? jj - (int)g : a.n[1] + (jj - (int)g);
     } else {
-      long long q = t - zslab - yslab;
+      unsigned q = t - zslab - yslab;
       const int ii = (int)(q % (2 * g));
       q /= 2 * g;
-      j = (int)(q % a.n[1]);
-      k = (int)(q / a.n[1]);
-      i = ii < g ? ii - g : a.n[0] + (ii - g);
+      j = (int)(q % (unsigned)a.n[1]);
+      k = (int)(q / (unsigned)a.n[1]);
+      i = ii < (int)g ? ii - (int)g : a.n[0] + (ii - (int)g);
     }
-    const long long c = (long long)(k + g) * a.sz + (long long)(j + g) * a.sy + (i + g);
+    const long long c = (long long)(k + (int)g) * a.sz + (long long)(j + (int)g) * a.sy + (i + (int)g);
     const double x = ra.x0[0] + i * ra.dx[0], y = ra.x0[1] + j * ra.dx[1], z = ra.x0[2] + k * ra.dx[2];
     const double r = sqrt(x * x + y * y + z * z);
     const T ir = r > 0.0 ? T(1.0 / r) : T(0);
     const T ex = T(x) * ir, ey = T(y) * ir, ez = T(z) * ir;
-    const int N[3] = {a.n[0] + 2 * g, a.n[1] + 2 * g, a.n[2] + 2 * g};
+    const int N[3] = {a.n[0] + 2 * (int)g, a.n[1] + 2 * (int)g, a.n[2] + 2 * (int)g};
     const bool rk4 = s.rk == SF_RK4;
-    for (int f = 0; f < ra.nf; ++f) {
+#pragma unroll
+    for (int q = 0; q < kFieldGroup; ++q) {
+      const int f = f0 + q;
+      if (f >= ra.nf) break;
       const long long o = f * a.sf + c;
       const T* p = a.us + o;
       const T U = p[0];
-      const T du = ex * rad_d(p, 1, i + g, N[0], a.i12h[0]) +
-                   ey * rad_d(p, a.sy, j + g, N[1], a.i12h[1]) +
-                   ez * rad_d(p, a.sz, k + g, N[2], a.i12h[2]);
+      const T du = ex * rad_d(p, 1, i + (int)g, N[0], a.i12h[0]) +
+                   ey * rad_d(p, a.sy, j + (int)g, N[1], a.i12h[1]) +
+                   ez * rad_d(p, a.sz, k + (int)g, N[2], a.i12h[2]);
       const T rhs = -T(ra.v[f]) * (du + (U - T(ra.uinf[f])) * ir);
       const T un = s.un_alias ? U : a.un[o];
       const T acc = (rk4 && s.stage > 0) ? a.acc[o] : T(0);
@@ -103,9 +111,11 @@ sf_status launch(const sf_params& prm, const sf_patch& p, const StageArgs& s, in
   const int g = p.ghost;
   const long long N0 = p.n[0] + 2 * g, N1 = p.n[1] + 2 * g, N2 = p.n[2] + 2 * g;
   const long long ghosts = N0 * N1 * N2 - (long long)p.n[0] * p.n[1] * p.n[2];
+  if (ghosts >= (1LL << 31)) return set_error(SF_EINVAL, "ghost shell too large");
   long long blocks = (ghosts + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  radiative_kernel<T><<<(int)blocks, 256, 0, st>>>(a, s, ra);
+  const dim3 grid((unsigned)blocks, (unsigned)((ra.nf + kFieldGroup - 1) / kFieldGroup));
+  radiative_kernel<T><<<grid, 256, 0, st>>>(a, s, ra);
   return after_launch("radiative_kernel");
 }
 

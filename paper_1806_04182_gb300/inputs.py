@@ -11,7 +11,8 @@ draw i of stream `seed` is mix(seed * 2^32 + i + 1) scaled by the golden
 gamma; doubles take the top 53 bits; normals use Box-Muller.
 
 All arrays are numpy float64, interior-only, shape (nf, nz, ny, nx) with x
-fastest; domains are periodic, x_i = i * dx (Sec. II.A).
+fastest; domains are periodic, x_i = i * dx (Sec. II.A), except the puncture
+boxes of Sec. V (cell-centred, non-periodic, optionally with ghost points).
 """
 from __future__ import annotations
 
@@ -278,24 +279,21 @@ def z4_puncture_box(n, length: float):
     return dx, x0
 
 
-def z4_puncture(n, length: float = 8.0, holes=None, ghost: int = 0):
-    """Puncture initial data of Sec. V on a cell-centred box (Brill-Lindquist
-    conformal factor, Bowen-York extrinsic curvature):
+DEFAULT_HOLES = [dict(m=1.0, pos=(0.05, -0.03, 0.02), P=(0.1, 0.05, 0.0), S=(0.0, 0.0, 0.2))]
+
+
+def z4_puncture_at(X, Y, Z, holes=None):
+    """Puncture initial data of Sec. V at the points (X, Y, Z) (arrays of one
+    shape): Brill-Lindquist conformal factor and Bowen-York curvature,
       psi = 1 + sum_A m_A / (2 r_A),  chi = psi^-4,  alpha = psi^-2,
       gt_ij = delta_ij,  Khat = Theta = 0,  Gammahat = beta = B = 0,
       At_ij = sum_A 3/(2 r_A^2 psi^6) [P_i n_j + P_j n_i - (delta_ij - n_i n_j) P.n]
             + sum_A 3/(r_A^3 psi^6) [eps_kil S^l n^k n_j + eps_kjl S^l n^k n_i],
-    n = x^(A)/r_A.  `holes` is a list of dicts with keys m, pos, P, S (default:
-    one spinning, boosted hole of bare mass 1 at (0.05, -0.03, 0.02)).
-    With ghost > 0 the data also cover the ghost points (the arrays are then
-    (25, nz+2g, ny+2g, nx+2g)).  Returns (U, dx, x0), x0 = position of
-    interior point (0,0,0)."""
+    n = (x - x_A)/r_A.  `holes`: list of dicts with keys m, pos, P, S (default
+    DEFAULT_HOLES: one spinning, boosted hole of bare mass 1 near the origin).
+    Returns an array (25,) + X.shape."""
     if holes is None:
-        holes = [dict(m=1.0, pos=(0.05, -0.03, 0.02), P=(0.1, 0.05, 0.0), S=(0.0, 0.0, 0.2))]
-    dx, x0 = z4_puncture_box(n, length)
-    g = ghost
-    ax = [x0[d] + dx[d] * np.arange(-g, n[d] + g) for d in range(3)]
-    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+        holes = DEFAULT_HOLES
     xs = (X, Y, Z)
     psi = np.ones_like(X)
     for h in holes:
@@ -327,7 +325,19 @@ def z4_puncture(n, length: float = 8.0, holes=None, ghost: int = 0):
     for q, (i, j) in enumerate([(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]):
         U[8 + q] = At[i, j]
     U[18] = psi ** -2
-    return U, dx, x0
+    return U
+
+
+def z4_puncture(n, length: float = 8.0, holes=None, ghost: int = 0):
+    """z4_puncture_at on the cell-centred box of z4_puncture_box.  With
+    ghost > 0 the data also cover the ghost points (arrays (25, nz+2g,
+    ny+2g, nx+2g)).  Returns (U, dx, x0), x0 = position of interior point
+    (0,0,0)."""
+    dx, x0 = z4_puncture_box(n, length)
+    g = ghost
+    ax = [x0[d] + dx[d] * np.arange(-g, n[d] + g) for d in range(3)]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    return z4_puncture_at(X, Y, Z, holes), dx, x0
 
 
 # values at infinity of the CCZ4 fields (flat space) for radiative boundaries

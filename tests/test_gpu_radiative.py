@@ -8,7 +8,7 @@ import pytest
 import torch
 
 import oracle
-from paper_1806_04182_gb300 import build, capi, inputs
+from paper_1806_04182_gb300 import amr, build, capi, inputs
 from paper_1806_04182_gb300.state import PatchState
 
 pytestmark = pytest.mark.gpu
@@ -111,3 +111,63 @@ def test_rejects_periodic_ghost_mode():
     with pytest.raises(capi.SfError, match="speed"):
         capi.sf_radiative_substep(st2.prm, st2.stage_patch(0), (0, 0, 0), inputs.Z4_UINF,
                                   -SPEED, 0)
+
+
+def test_fixed_refinement_ratio_one_equals_single_level():
+    # a puncture box with radiative boundaries carrying a fine patch at the
+    # same resolution around the hole (ratio 1): the BOR ghost values are then
+    # the coarse stage values, so the fine patch evolves as the same region of
+    # the single-level run
+    n = (20, 20, 20)
+    U, dx, x0 = inputs.z4_puncture(n, length=6.0, ghost=3)
+    dt = 0.25 * min(dx)
+    prm = capi.params(ghosts=capi.SF_GHOSTS_NONE)
+    whole = PatchState(capi.SF_Z4, n, dx, dt, prm=prm)
+    whole.upload_ghosted(U)
+    whole.step_radiative(3, x0, inputs.Z4_UINF, SPEED)
+    coarse = PatchState(capi.SF_Z4, n, dx, dt, prm=prm)
+    coarse.upload_ghosted(U)
+    at, m = (6, 6, 6), (8, 8, 8)
+    fine = PatchState(capi.SF_Z4, m, dx, dt, prm=prm)
+    g = 3
+    fine.upload_ghosted(np.ascontiguousarray(U[:, at[2]:at[2] + m[2] + 2 * g,
+                                               at[1]:at[1] + m[1] + 2 * g,
+                                               at[0]:at[0] + m[0] + 2 * g]))
+    pair = amr.SubcycledPair(coarse, fine, 1, at, coarse_radiative=(x0, inputs.Z4_UINF, SPEED))
+    pair.step(3)
+    torch.cuda.synchronize()
+    W = whole.fields().cpu().numpy()
+    want = W[:, at[2]:at[2] + m[2], at[1]:at[1] + m[1], at[0]:at[0] + m[0]]
+    got = pair.fine.fields().cpu().numpy()
+    assert rel(got, want, 1e-2).max() < 1e-11
+    assert rel(pair.coarse.fields().cpu().numpy(), W, 1e-2).max() < 1e-11
+
+
+def test_fixed_refinement_puncture_ratio_two_runs():
+    # coarse 32^3 box (radiative boundary) with a ratio-2 fine patch of 32^3
+    # around the hole (fine point 2 i on coarse point i + at): every value
+    # stays finite over 6 coarse steps, and the fine solution, injected back,
+    # agrees with the coarse one where the coarse grid resolves the data
+    nc = (32, 32, 32)
+    U, dx, x0 = inputs.z4_puncture(nc, length=8.0, ghost=3)
+    prm = capi.params(ghosts=capi.SF_GHOSTS_NONE, check_finite=1)
+    coarse = PatchState(capi.SF_Z4, nc, dx, 0.25 * dx[0], prm=prm)
+    coarse.upload_ghosted(U)
+    at, m = (8, 8, 8), (32, 32, 32)
+    dxf = tuple(v / 2 for v in dx)
+    x0f = tuple(x0[d] + at[d] * dx[d] for d in range(3))
+    g = 3
+    ax = [x0f[d] + dxf[d] * np.arange(-g, m[d] + g) for d in range(3)]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    fine = PatchState(capi.SF_Z4, m, dxf, 0.125 * dx[0], prm=prm)
+    fine.upload_ghosted(inputs.z4_puncture_at(X, Y, Z))
+    pair = amr.SubcycledPair(coarse, fine, 2, at, coarse_radiative=(x0, inputs.Z4_UINF, SPEED))
+    pair.step(6)
+    torch.cuda.synchronize()
+    assert capi.sf_get_device_status() == capi.SF_OK
+    F = pair.fine.fields().cpu().numpy()
+    C = pair.coarse.fields().cpu().numpy()
+    assert np.all(np.isfinite(F)) and np.all(np.isfinite(C))
+    # injection: coarse points under the fine patch hold the fine values
+    np.testing.assert_array_equal(C[:, at[2]:at[2] + 16, at[1]:at[1] + 16, at[0]:at[0] + 16],
+                                  F[:, ::2, ::2, ::2])
