@@ -94,7 +94,7 @@ class Params(ctypes.Structure):
         ("shift_frozen", ctypes.c_int32),
         ("mhd_glm", ctypes.c_int32),
         ("lopsided", ctypes.c_int32),
-        ("pad_", ctypes.c_int32),
+        ("flux_split", ctypes.c_int32),
     ]
 
 
@@ -103,7 +103,7 @@ def params(**kw) -> Params:
     kappa_z = kappa_c = 1, eta = 2, g = 3/4, 1+log slicing (Sec. V with M = 1)."""
     d = dict(sigma=0.1, gamma_eos=5.0 / 3.0, weno_eps=0.0, weno_q=2.0, kappa_z=1.0,
              kappa_c=1.0, eta=2.0, g_shift=0.75, ch=0.0, kappa_psi=0.0, weno_variant=0,
-             slicing=0, shift_frozen=0, mhd_glm=0, lopsided=0, pad_=0)
+             slicing=0, shift_frozen=0, mhd_glm=0, lopsided=0, flux_split=0)
     d.update(kw)
     return Params(**d)
 

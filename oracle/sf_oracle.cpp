@@ -47,7 +47,7 @@ typedef struct {
   int32_t shift_frozen;  // 1: d/dt beta = d/dt B = 0
   int32_t mhd_glm;       // 1: 9th MHD field psi
   int32_t lopsided;      // 1: CCZ4 advection beta^k d_k with the one-sided stencils (Sec. II.B.1)
-  int32_t pad_;
+  int32_t flux_split;    // 1: MHD reconstruction of the split fluxes (Lax-Friedrichs splitting)
 } or_params;
 }
 
@@ -362,13 +362,41 @@ T weno3_right(const T* w, double eps) {
   return (a0 * c0 + a1 * c1) / (a0 + a1);
 }
 
-// LLF flux at the interface x_{i+1/2} along d (Eq. LLF), from the WENO left
-// state (stencil centred at i) and right state (stencil centred at i+1).
+// Flux at the interface x_{i+1/2} along d.
+//  flux_split = 0 (the paper's tests): WENO left state (stencil centred at i)
+//    and right state (centred at i+1) of the evolved fields, then the LLF
+//    formula (Eq. LLF).
+//  flux_split = 1: reconstruction of the fluxes (Sec. II.B.2 lists it as the
+//    alternative to reconstructing the fields), in Lax-Friedrichs splitting
+//    form: S = the largest signal speed |v_d| + c_f over the six cells
+//    i-2..i+3 of the stencil, F^(+-)_c = (F(U_c) +- S U_c)/2 at each cell,
+//    F_{i+1/2} = F^+ reconstructed from the left + F^- from the right.
 template <class T>
 void mhd_interface_flux(const or_params& p, const double* u, const Grid& G, const double* dx,
                         int nf, int i, int j, int k, int d, T* Fout) {
   double eps = p.weno_eps > 0 ? p.weno_eps
                               : (p.weno_variant == 2 ? dx[d] * dx[d] : dx[d] * dx[d] * dx[d] * dx[d]);
+  if (p.flux_split) {
+    T Uc[6][9], Fc[6][9];
+    T S = T(0.0);
+    for (int c = 0; c < 6; ++c) {
+      for (int f = 0; f < nf; ++f) Uc[c][f] = U_off<T>(u, G, f, i, j, k, d, c - 2);
+      mhd_flux<T>(p, Uc[c], d, nf, Fc[c]);
+      S = max_(S, mhd_speed<T>(p, Uc[c], d, nf));
+    }
+    for (int f = 0; f < nf; ++f) {
+      T wp[5], wm[5];
+      for (int c = 0; c < 5; ++c) {
+        wp[c] = T(0.5) * (Fc[c][f] + S * Uc[c][f]);          // cells i-2..i+2
+        wm[c] = T(0.5) * (Fc[c + 1][f] - S * Uc[c + 1][f]);  // cells i-1..i+3
+      }
+      if (p.weno_variant == 2)
+        Fout[f] = weno3_left<T>(wp, eps) + weno3_right<T>(wm, eps);
+      else
+        Fout[f] = weno5_left<T>(p, wp, eps) + weno5_right<T>(p, wm, eps);
+    }
+    return;
+  }
   T UL[9], UR[9];
   for (int f = 0; f < nf; ++f) {
     T wl[5], wr[5];
