@@ -139,7 +139,13 @@ typedef struct {
   int32_t lopsided;     /* SF_Z4: 1 = advection terms beta^k d_k with the 4th-order
                            one-sided stencils of Sec. II.B.1, chosen by the sign
                            of beta^k; 0 = centred D_k */
-  int32_t reserved;     /* set to 0 */
+  int32_t flux_split;   /* SF_MHD: 0 = WENO reconstruction of the evolved fields at
+                           each interface, then the LLF formula (Eq. LLF; the paper's
+                           tests); 1 = reconstruction of the fluxes (Sec. II.B.2) in
+                           Lax-Friedrichs splitting form: S = largest signal speed
+                           over the interface's six-cell stencil, F+- = (F(U) +- S U)/2
+                           at each cell, F+ reconstructed from the left plus F- from
+                           the right */
 } sf_params;
 
 /* Number of evolved fields of a system (5, 8 or 25); -1 if unknown. */

@@ -53,7 +53,7 @@ class sf_params(ctypes.Structure):
         ("eta", ctypes.c_double),
         ("g_shift", ctypes.c_double),
         ("lopsided", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("flux_split", ctypes.c_int32),
     ]
 
 
@@ -99,7 +99,7 @@ def params(**kw) -> sf_params:
     d = dict(rk=SF_RK4, ghosts=SF_GHOSTS_PERIODIC, sigma_ko=0.1, gamma_eos=5.0 / 3.0,
              weno_eps=0.0, weno_q=2.0, weno_variant=0, slicing=0, shift_frozen=0,
              check_finite=0, kappa_z=1.0, kappa_c=1.0, eta=2.0, g_shift=0.75, lopsided=0,
-             reserved=0)
+             flux_split=0)
     d.update(kw)
     return sf_params(**d)
 

@@ -93,6 +93,8 @@ sf_status check_patch(const sf_params* prm, const sf_patch& p, int need_stage_ar
   if (!(prm->sigma_ko >= 0)) return set_error(SF_EINVAL, "sigma_ko must be >= 0");
   if (prm->weno_variant < 0 || prm->weno_variant > 2)
     return set_error(SF_EINVAL, "weno_variant %d not in {0, 1, 2}", prm->weno_variant);
+  if (prm->flux_split != 0 && prm->flux_split != 1)
+    return set_error(SF_EINVAL, "flux_split %d not in {0, 1}", prm->flux_split);
   if (p.cfl_rate && p.system != SF_MHD)
     return set_error(SF_EINVAL, "cfl_rate is an SF_MHD output");
   if (p.cfl_rate && !aligned(p.cfl_rate, 8)) return set_error(SF_EINVAL, "cfl_rate misaligned");

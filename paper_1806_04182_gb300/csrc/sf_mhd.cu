@@ -3,9 +3,10 @@
 // in conservative form L(U)_i = -sum_d (F_{i+1/2} - F_{i-1/2}) / dx_d (Eq. 5).
 // Interface fluxes: WENO reconstruction of the evolved fields from the left
 // and right (WENO5 with JS or Z weights, App. B; WENO3, App. A), physical
-// fluxes of both states and the
-// local Lax-Friedrichs formula (Eq. LLF) with the largest fast magnetosonic
-// signal speed of the two states.  Fused with the RK stage update.
+// fluxes of both states and the local Lax-Friedrichs formula (Eq. LLF) with
+// the largest fast magnetosonic signal speed of the two states; or, with
+// flux_split, the same reconstructions applied to the Lax-Friedrichs split
+// fluxes.  Fused with the RK stage update.
 #include "sf_internal.cuh"
 
 namespace sf {
@@ -16,6 +17,7 @@ struct MhdCoef {
   T eps[3];   // WENO epsilon per direction
   T q;        // WENO-Z exponent
   int variant;
+  int split;  // 1: reconstruction of the Lax-Friedrichs split fluxes
   T idx[3];   // 1/dx_d
 };
 
@@ -153,6 +155,46 @@ __device__ __forceinline__ void face_flux(const T* __restrict__ p, long long F, 
   for (int f = 0; f < 8; ++f) Fout[f] = T(0.5) * (FL[f] + FR[f] - S * (UR[f] - UL[f]));
 }
 
+// Flux through the same face from the reconstruction of the split fluxes
+// (Sec. II.B.2, Lax-Friedrichs splitting): S = the largest signal speed over
+// the six cells p-2..p+3, F+- = (F(U) +- S U)/2 at each cell, F+ reconstructed
+// from the left (cells p-2..p+2) plus F- from the right (cells p-1..p+3).
+template <typename T>
+__device__ __forceinline__ void face_flux_split(const T* __restrict__ p, long long F, long long s,
+                                                int d, const MhdCoef<T>& mc, T* Fout) {
+  T Uc[6][8], Fc[6][8];
+  T S = T(0);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+#pragma unroll
+    for (int f = 0; f < 8; ++f) Uc[c][f] = __ldg(p + f * F + (c - 2) * s);
+    const T sp = flux_speed(Uc[c], d, mc, Fc[c]);
+    S = sp > S ? sp : S;
+  }
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    T wp[6], wm[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      wp[c] = T(0.5) * (Fc[c][f] + S * Uc[c][f]);
+      wm[c] = T(0.5) * (Fc[c][f] - S * Uc[c][f]);
+    }
+    if (mc.variant == 2)
+      Fout[f] = weno3_left(wp, mc.eps[d]) + weno3_right(wm + 1, mc.eps[d]);
+    else
+      Fout[f] = weno_left(wp, mc.eps[d], mc) + weno_right(wm + 1, mc.eps[d], mc);
+  }
+}
+
+template <typename T, bool SPLIT>
+__device__ __forceinline__ void interface_flux(const T* __restrict__ p, long long F, long long s,
+                                               int d, const MhdCoef<T>& mc, T* Fout) {
+  if (SPLIT)
+    face_flux_split(p, F, s, d, mc, Fout);
+  else
+    face_flux(p, F, s, d, mc, Fout);
+}
+
 // Stage kernel.  Each interface flux is evaluated once: a block of 32 x 8
 // threads owns 31 x 7 output cells of a plane; thread (tx, ty) evaluates the
 // x-face at i - 1/2 and the y-face at j - 1/2 of its column, so the +1/2
@@ -163,7 +205,7 @@ __device__ __forceinline__ void face_flux(const T* __restrict__ p, long long F, 
 // lie inside the 3-point ghost zone.
 constexpr int MX = 32, MY = 8, MZ = 16;
 
-template <typename T>
+template <typename T, bool SPLIT>
 __global__ void __launch_bounds__(MX * MY) mhd_stage_kernel(PatchArgs<T> a, StageArgs s,
                                                            MhdCoef<T> mc) {
   __shared__ T fy[MY][MX][8];
@@ -182,24 +224,24 @@ __global__ void __launch_bounds__(MX * MY) mhd_stage_kernel(PatchArgs<T> a, Stag
     return a.us + (long long)(kk + g) * a.sz + (long long)(jj + g) * a.sy + (ii + g);
   };
   T Fzm[8];
-  if (out) face_flux(at(i, j, k0 - 1), a.sf, a.sz, 2, mc, Fzm);
+  if (out) interface_flux<T, SPLIT>(at(i, j, k0 - 1), a.sf, a.sz, 2, mc, Fzm);
   for (int k = k0; k < k1; ++k) {
     T Fx[8], Fy[8], Fz[8];
     if (xface) {
-      face_flux(at(i - 1, j, k), a.sf, 1, 0, mc, Fx);
+      interface_flux<T, SPLIT>(at(i - 1, j, k), a.sf, 1, 0, mc, Fx);
     } else {
 #pragma unroll
       for (int f = 0; f < 8; ++f) Fx[f] = T(0);
     }
     if (yface) {
-      face_flux(at(i, j - 1, k), a.sf, a.sy, 1, mc, Fy);
+      interface_flux<T, SPLIT>(at(i, j - 1, k), a.sf, a.sy, 1, mc, Fy);
     } else {
 #pragma unroll
       for (int f = 0; f < 8; ++f) Fy[f] = T(0);
     }
 #pragma unroll
     for (int f = 0; f < 8; ++f) fy[ty][tx][f] = Fy[f];
-    if (out) face_flux(at(i, j, k), a.sf, a.sz, 2, mc, Fz);
+    if (out) interface_flux<T, SPLIT>(at(i, j, k), a.sf, a.sz, 2, mc, Fz);
     T Fxp[8];
 #pragma unroll
     for (int f = 0; f < 8; ++f) Fxp[f] = __shfl_down_sync(0xffffffffu, Fx[f], 1);
@@ -285,6 +327,7 @@ static MhdCoef<T> coef(const sf_params& prm, const sf_patch& p) {
   }
   mc.q = T(prm.weno_q);
   mc.variant = prm.weno_variant;
+  mc.split = prm.flux_split;
   return mc;
 }
 
@@ -300,7 +343,10 @@ static sf_status launch(const sf_params& prm, const sf_patch& p, const StageArgs
   }
   dim3 block(MX, MY, 1);
   dim3 grid((p.n[0] + MX - 2) / (MX - 1), (p.n[1] + MY - 2) / (MY - 1), (p.n[2] + MZ - 1) / MZ);
-  mhd_stage_kernel<T><<<grid, block, 0, st>>>(a, s, coef<T>(prm, p));
+  if (prm.flux_split)
+    mhd_stage_kernel<T, true><<<grid, block, 0, st>>>(a, s, coef<T>(prm, p));
+  else
+    mhd_stage_kernel<T, false><<<grid, block, 0, st>>>(a, s, coef<T>(prm, p));
   return after_launch("mhd_stage_kernel");
 }
 

@@ -44,7 +44,8 @@ def oracle_params(prm: capi.sf_params):
     return oracle.params(sigma=prm.sigma_ko, gamma_eos=prm.gamma_eos, weno_eps=prm.weno_eps,
                          weno_q=prm.weno_q, kappa_z=prm.kappa_z, kappa_c=prm.kappa_c, eta=prm.eta,
                          g_shift=prm.g_shift, weno_variant=prm.weno_variant, slicing=prm.slicing,
-                         shift_frozen=prm.shift_frozen, lopsided=prm.lopsided)
+                         shift_frozen=prm.shift_frozen, lopsided=prm.lopsided,
+                         flux_split=prm.flux_split)
 
 
 def run_stages(system, U0, dx, dt, prm, precision=capi.SF_FP64, pitch=None):
@@ -201,11 +202,12 @@ def test_z4_fp32_bulk_step():
 
 
 # ------------------------------------------------------------------ MHD
+@pytest.mark.parametrize("split", [0, 1])
 @pytest.mark.parametrize("variant", [0, 1, 2])
-def test_mhd_fp64_stages(variant):
+def test_mhd_fp64_stages(variant, split):
     n = (35, 10, 7)
     U0, dx = inputs.mhd_blast(n, seed=4, radius=0.3)
-    prm = capi.params(rk=capi.SF_SSPRK3, weno_variant=variant)
+    prm = capi.params(rk=capi.SF_SSPRK3, weno_variant=variant, flux_split=split)
     rate = oracle.mhd_max_rate(oracle.ghosted(U0), dx)
     dt = 0.3 / rate
     got = run_stages(capi.SF_MHD, U0, dx, dt, prm)
