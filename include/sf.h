@@ -303,6 +303,24 @@ sf_status sf_bor_prolong(const sf_patch* coarse, int32_t rk, const void* const* 
                          int64_t out_sf, void* stream);
 
 /*
+ * sf_bor_prolong for several output boxes at once (for example the six slabs
+ * of a fine patch's ghost shell): one launch per 16 boxes.  Each box names its
+ * fine points (origin, ext, as in sf_bor_prolong) and its output (pointer and
+ * element strides).  Every box is validated before anything is launched;
+ * boxes with a zero extent write nothing and may have a NULL output.
+ */
+typedef struct {
+  int32_t origin[3];
+  int32_t ext[3];
+  void* out;
+  int64_t out_sy, out_sz, out_sf;
+} sf_prolong_box;
+
+sf_status sf_bor_prolong_boxes(const sf_patch* coarse, int32_t rk, const void* const* states,
+                               int32_t nf, int32_t ratio, int32_t r, int32_t stage,
+                               const sf_prolong_box* boxes, int32_t nbox, void* stream);
+
+/*
  * Batched AMR-patch dispatch: one persistent launch per stage over a table of
  * patches of mixed systems (SF_WAVE and SF_Z4) and sizes, each with its own
  * dx and dt.  CTAs take (patch, tile) work items from a device queue.

@@ -191,11 +191,13 @@ class SubcycledPair:
         es = array.element_size()
         states = self._states()
         cpatch = c.patch(c.A, c.A, c.B)
+        boxes = []
         for lo, ext in self._shell:
             origin = tuple(R * a + l for a, l in zip(self.at, lo))
             ptr = array.data_ptr() + _off(f, *lo) * es
-            capi.sf_bor_prolong(cpatch, self.rk, states, f.nf, R, r, stage, origin, ext, ptr, sy, sz,
-                                sf, h)
+            boxes.append(capi.prolong_box(origin, ext, ptr, sy, sz, sf))
+        # the six slabs of the shell in one launch
+        capi.sf_bor_prolong_boxes(cpatch, self.rk, states, f.nf, R, r, stage, boxes, h)
 
     def step(self, nsteps: int = 1, stream=None) -> None:
         c, f, R = self.coarse, self.fine, self.R

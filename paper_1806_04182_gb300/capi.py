@@ -26,7 +26,7 @@ EXPORTS = ["sf_nfields", "sf_substep", "sf_rhs", "sf_fill_ghosts_periodic", "sf_
            "sf_adjoint_substep", "sf_gather", "sf_scatter_add", "sf_diagnostics",
            "sf_batch_create", "sf_batch_substep", "sf_batch_tune", "sf_batch_capture",
            "sf_batch_launch", "sf_batch_launches_per_step", "sf_batch_destroy",
-           "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong", "sf_bor_prolong", "sf_radiative_substep",
+           "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong", "sf_bor_prolong", "sf_bor_prolong_boxes", "sf_radiative_substep",
            "sf_get_device_status", "sf_last_error", "sf_launch_count"]
 
 
@@ -54,6 +54,17 @@ class sf_params(ctypes.Structure):
         ("g_shift", ctypes.c_double),
         ("lopsided", ctypes.c_int32),
         ("flux_split", ctypes.c_int32),
+    ]
+
+
+class sf_prolong_box(ctypes.Structure):
+    _fields_ = [
+        ("origin", ctypes.c_int32 * 3),
+        ("ext", ctypes.c_int32 * 3),
+        ("out", ctypes.c_void_p),
+        ("out_sy", ctypes.c_int64),
+        ("out_sz", ctypes.c_int64),
+        ("out_sf", ctypes.c_int64),
     ]
 
 
@@ -138,6 +149,8 @@ def lib() -> ctypes.CDLL:
         L.sf_batch_substep_static.argtypes = [P(sf_params), P(sf_patch), i32, i32, vp]
         L.sf_copy_boxes.argtypes = [P(sf_box_copy), i32, i32, vp]
         L.sf_prolong.argtypes = [P(sf_patch), vp, i32, i32, P(i32), P(i32), vp, i64, i64, i64, vp]
+        L.sf_bor_prolong_boxes.argtypes = [P(sf_patch), i32, P(vp), i32, i32, i32, i32,
+                                           P(sf_prolong_box), i32, vp]
         L.sf_radiative_substep.argtypes = [P(sf_params), P(sf_patch), P(ctypes.c_double),
                                            P(ctypes.c_double), P(ctypes.c_double), i32, vp]
         L.sf_bor_prolong.argtypes = [P(sf_patch), i32, P(vp), i32, i32, i32, i32, P(i32), P(i32), vp,
@@ -286,6 +299,24 @@ def sf_bor_prolong(coarse: sf_patch, rk: int, states, nf: int, ratio: int, r: in
     e = (ctypes.c_int32 * 3)(*ext)
     _check(lib().sf_bor_prolong(ctypes.byref(coarse), rk, arr, nf, ratio, r, stage, o, e, fine_out,
                                 out_sy, out_sz, out_sf, stream), "sf_bor_prolong")
+
+
+def prolong_box(origin, ext, out: int, out_sy: int, out_sz: int, out_sf: int) -> sf_prolong_box:
+    b = sf_prolong_box()
+    b.origin[:] = origin
+    b.ext[:] = ext
+    b.out = out
+    b.out_sy, b.out_sz, b.out_sf = out_sy, out_sz, out_sf
+    return b
+
+
+def sf_bor_prolong_boxes(coarse: sf_patch, rk: int, states, nf: int, ratio: int, r: int,
+                         stage: int, boxes, stream: int = 0) -> None:
+    """sf_bor_prolong over several output boxes (sf_prolong_box) in one launch."""
+    arr = (ctypes.c_void_p * len(states))(*states)
+    bx = (sf_prolong_box * max(1, len(boxes)))(*boxes)
+    _check(lib().sf_bor_prolong_boxes(ctypes.byref(coarse), rk, arr, nf, ratio, r, stage, bx,
+                                      len(boxes), stream), "sf_bor_prolong_boxes")
 
 
 def sf_get_device_status(stream: int = 0) -> int:

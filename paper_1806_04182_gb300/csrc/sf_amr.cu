@@ -51,15 +51,25 @@ __global__ void __launch_bounds__(256) copy_boxes_kernel(BoxBatch bb) {
   }
 }
 
+// One output box of a prolongation launch: fine points origin..origin+ext-1
+// written to out with element strides (osy, osz, osf); t[3] = tiles per axis.
+struct PBox {
+  int origin[3], ext[3], t[3];
+  void* out;
+  long long osy, osz, osf;
+};
+constexpr int kMaxPBoxes = 16;
+
 struct ProlongArgs {
   double w[8][6];      // Lagrange weights l_j(r/R), r = 0..R-1, nodes -2..3
   float wf[8][6];      // the same, rounded to float (float arrays)
   int R;
   int n[3], g;
   long long sy, sz, sf;          // coarse strides
-  int origin[3], ext[3];
-  long long osy, osz, osf;       // output strides
   int nf;
+  int nbox;
+  int tiles_end[kMaxPBoxes];     // cumulative CTA counts (tiles x fields) per box
+  PBox box[kMaxPBoxes];
 };
 
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
@@ -112,22 +122,30 @@ constexpr int prolong_smem() {
 }
 
 template <typename T, int NS>
-__global__ void __launch_bounds__(256) prolong_kernel(Combo<T> cb, T* out, ProlongArgs p) {
+__global__ void __launch_bounds__(256) prolong_kernel(Combo<T> cb, ProlongArgs p) {
   extern __shared__ __align__(16) unsigned char psm_raw[];
   T* cn = reinterpret_cast<T*>(psm_raw);  // [CZM][CYM][CXM]
   T* tx = cn + CZM * CYM * CXM;           // [CZM][CYM][PX]
   T* ty = tx + CZM * CYM * PX;            // [CZM][PY][PX]
   const int R = p.R;
-  // one field per CTA: blockIdx.z = z tile * nf + field
-  const int f = (int)blockIdx.z % p.nf;
-  const int zt = (int)blockIdx.z / p.nf;
-  const int F0[3] = {p.origin[0] + (int)blockIdx.x * PX, p.origin[1] + (int)blockIdx.y * PY,
-                     p.origin[2] + zt * PZ};
+  // the CTA's box, tile and field (one field per CTA, field slowest)
+  int bi = 0;
+  while (bi + 1 < p.nbox && (int)blockIdx.x >= p.tiles_end[bi]) ++bi;
+  const PBox& B = p.box[bi];
+  int local = (int)blockIdx.x - (bi ? p.tiles_end[bi - 1] : 0);
+  const int xt = local % B.t[0];
+  local /= B.t[0];
+  const int yt = local % B.t[1];
+  local /= B.t[1];
+  const int zt = local % B.t[2];
+  const int f = local / B.t[2];
+  T* out = static_cast<T*>(B.out);
+  const int F0[3] = {B.origin[0] + xt * PX, B.origin[1] + yt * PY, B.origin[2] + zt * PZ};
   const int P[3] = {PX, PY, PZ};
   int nv[3], lo[3], nc[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    nv[d] = min(P[d], p.origin[d] + p.ext[d] - F0[d]);        // valid fine points in the tile
+    nv[d] = min(P[d], B.origin[d] + B.ext[d] - F0[d]);        // valid fine points in the tile
     lo[d] = floordiv(F0[d], R) - 2;                            // first coarse node
     nc[d] = floordiv(F0[d] + nv[d] - 1, R) + 3 - lo[d] + 1;    // coarse nodes spanned
   }
@@ -168,9 +186,9 @@ __global__ void __launch_bounds__(256) prolong_kernel(Combo<T> cb, T* out, Prolo
       T v = T(0);
 #pragma unroll
       for (int q = 0; q < 6; ++q) v += lagrange_w<T>(p, r, q) * col[q * PY * PX];
-      const int i = F0[0] - p.origin[0] + xi, j = F0[1] - p.origin[1] + yi,
-                k = F0[2] - p.origin[2] + zi;
-      out[f * p.osf + (long long)k * p.osz + (long long)j * p.osy + i] = v;
+      const int i = F0[0] - B.origin[0] + xi, j = F0[1] - B.origin[1] + yi,
+                k = F0[2] - B.origin[2] + zi;
+      out[f * B.osf + (long long)k * B.osz + (long long)j * B.osy + i] = v;
     }
   }
 }
@@ -315,14 +333,15 @@ extern "C" sf_status sf_copy_boxes(const sf_box_copy* boxes, int32_t nbox, int32
   return SF_OK;
 }
 
-// Shared set-up of sf_prolong and sf_bor_prolong: validation of the box
-// against the ghosted coarse layout, the Lagrange weight table, the launch.
+// Shared set-up of sf_prolong, sf_bor_prolong and sf_bor_prolong_boxes:
+// validation of every box against the ghosted coarse layout, the Lagrange
+// weight table, and one launch per kMaxPBoxes boxes.
 template <int NS>
 static sf_status prolong_launch(const sf_patch* coarse, const void* const* arrays, const double* c,
-                                int32_t nf, int32_t ratio, const int32_t* origin, const int32_t* ext,
-                                void* fine_out, int64_t out_sy, int64_t out_sz, int64_t out_sf,
-                                void* stream) {
-  if (!coarse || !arrays || !origin || !ext || !fine_out) return set_error(SF_EINVAL, "NULL argument");
+                                int32_t nf, int32_t ratio, const sf_prolong_box* boxes,
+                                int32_t nbox, void* stream) {
+  if (!coarse || !arrays || (nbox > 0 && !boxes) || nbox < 0)
+    return set_error(SF_EINVAL, "NULL argument or nbox < 0");
   if (ratio < 1 || ratio > 8) return set_error(SF_EINVAL, "ratio %d not in [1, 8]", ratio);
   if (nf < 1) return set_error(SF_EINVAL, "nf < 1");
   sf_patch p = *coarse;
@@ -337,19 +356,6 @@ static sf_status prolong_launch(const sf_patch* coarse, const void* const* array
   p.u_stage = const_cast<void*>(arrays[0]);
   sf_status e = check_patch(&dummy, p, 0, 0);
   if (e) return e;
-  if (reinterpret_cast<uintptr_t>(fine_out) % es) return set_error(SF_EINVAL, "fine_out misaligned");
-  for (int d = 0; d < 3; ++d) {
-    if (ext[d] < 0) return set_error(SF_EINVAL, "ext[%d] < 0", d);
-    if (ext[d] == 0) return SF_OK;
-    // coarse nodes floor(F/R)-2 .. floor(F/R)+3 must lie in the ghosted coarse box
-    const int lo = origin[d], hi = origin[d] + ext[d] - 1;
-    const int blo = lo >= 0 ? lo / ratio : -((-lo + ratio - 1) / ratio);
-    const int bhi = hi >= 0 ? hi / ratio : -((-hi + ratio - 1) / ratio);
-    if (blo - 2 < -p.ghost || bhi + 3 > p.n[d] + p.ghost - 1)
-      return set_error(SF_EINVAL, "prolongation stencil leaves the coarse box along %d", d);
-  }
-  if (out_sy < ext[0] || out_sz < out_sy * ext[1] || out_sf < out_sz * ext[2])
-    return set_error(SF_EINVAL, "output strides too small for the box");
   ProlongArgs a;
   for (int r = 0; r < ratio; ++r) {
     const double t = double(r) / double(ratio);
@@ -362,71 +368,138 @@ static sf_status prolong_launch(const sf_patch* coarse, const void* const* array
     }
   }
   a.R = ratio;
-  for (int d = 0; d < 3; ++d) {
-    a.n[d] = p.n[d];
-    a.origin[d] = origin[d];
-    a.ext[d] = ext[d];
-  }
+  for (int d = 0; d < 3; ++d) a.n[d] = p.n[d];
   a.g = p.ghost;
   a.sy = p.sy;
   a.sz = p.sz;
   a.sf = p.sf;
-  a.osy = out_sy;
-  a.osz = out_sz;
-  a.osf = out_sf;
   a.nf = nf;
-  const long long zt = (ext[2] + PZ - 1) / PZ;
-  if (ext[1] > 65535LL * PY || zt * nf > 65535) return set_error(SF_EINVAL, "box too large");
-  const dim3 grid((ext[0] + PX - 1) / PX, (ext[1] + PY - 1) / PY, (unsigned)(zt * nf));
   cudaStream_t st = (cudaStream_t)stream;
-  if (p.precision == SF_FP64) {
-    Combo<double> cb;
-    for (int m = 0; m < 5; ++m) cb.s[m] = m <= NS ? (const double*)arrays[m] : nullptr;
-    for (int m = 0; m < 4; ++m) cb.c[m] = (c && m < NS) ? c[m] : 0.0;
-    static std::once_flag once;
-    std::call_once(once, [] {
-      cudaFuncSetAttribute(prolong_kernel<double, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           prolong_smem<double>());
-    });
-    prolong_kernel<double, NS><<<grid, 256, prolong_smem<double>(), st>>>(cb, (double*)fine_out, a);
-  } else {
-    Combo<float> cb;
-    for (int m = 0; m < 5; ++m) cb.s[m] = m <= NS ? (const float*)arrays[m] : nullptr;
-    for (int m = 0; m < 4; ++m) cb.c[m] = (c && m < NS) ? c[m] : 0.0;
-    static std::once_flag once;
-    std::call_once(once, [] {
-      cudaFuncSetAttribute(prolong_kernel<float, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           prolong_smem<float>());
-    });
-    prolong_kernel<float, NS><<<grid, 256, prolong_smem<float>(), st>>>(cb, (float*)fine_out, a);
+  // validate every box before any launch
+  for (int q = 0; q < nbox; ++q) {
+    const sf_prolong_box& bx = boxes[q];
+    if (bx.ext[0] < 0 || bx.ext[1] < 0 || bx.ext[2] < 0)
+      return set_error(SF_EINVAL, "box %d: negative extent", q);
+    if (bx.ext[0] == 0 || bx.ext[1] == 0 || bx.ext[2] == 0) continue;  // writes nothing
+    if (!bx.out) return set_error(SF_EINVAL, "box %d: out is NULL", q);
+    if (reinterpret_cast<uintptr_t>(bx.out) % es) return set_error(SF_EINVAL, "box %d: out misaligned", q);
+    for (int d = 0; d < 3; ++d) {
+      if (bx.ext[d] < 0) return set_error(SF_EINVAL, "box %d: ext[%d] < 0", q, d);
+      if (bx.ext[d] == 0) continue;
+      // coarse nodes floor(F/R)-2 .. floor(F/R)+3 must lie in the ghosted coarse box
+      const int lo = bx.origin[d], hi = bx.origin[d] + bx.ext[d] - 1;
+      const int blo = lo >= 0 ? lo / ratio : -((-lo + ratio - 1) / ratio);
+      const int bhi = hi >= 0 ? hi / ratio : -((-hi + ratio - 1) / ratio);
+      if (blo - 2 < -p.ghost || bhi + 3 > p.n[d] + p.ghost - 1)
+        return set_error(SF_EINVAL, "box %d: prolongation stencil leaves the coarse box along %d", q, d);
+    }
+    if (bx.out_sy < bx.ext[0] || bx.out_sz < bx.out_sy * bx.ext[1] ||
+        bx.out_sf < bx.out_sz * bx.ext[2])
+      return set_error(SF_EINVAL, "box %d: output strides too small for the box", q);
   }
-  return after_launch("prolong_kernel");
+  for (int q0 = 0; q0 < nbox; q0 += kMaxPBoxes) {
+    long long total = 0;
+    a.nbox = 0;
+    for (int q = q0; q < nbox && q < q0 + kMaxPBoxes; ++q) {
+      const sf_prolong_box& bx = boxes[q];
+      if (bx.ext[0] == 0 || bx.ext[1] == 0 || bx.ext[2] == 0) continue;
+      PBox& B = a.box[a.nbox];
+      for (int d = 0; d < 3; ++d) {
+        B.origin[d] = bx.origin[d];
+        B.ext[d] = bx.ext[d];
+      }
+      B.t[0] = (bx.ext[0] + PX - 1) / PX;
+      B.t[1] = (bx.ext[1] + PY - 1) / PY;
+      B.t[2] = (bx.ext[2] + PZ - 1) / PZ;
+      B.out = bx.out;
+      B.osy = bx.out_sy;
+      B.osz = bx.out_sz;
+      B.osf = bx.out_sf;
+      total += (long long)B.t[0] * B.t[1] * B.t[2] * nf;
+      if (total >= (1LL << 31)) return set_error(SF_EINVAL, "boxes too large");
+      a.tiles_end[a.nbox] = (int)total;
+      ++a.nbox;
+    }
+    if (a.nbox == 0) continue;
+    if (p.precision == SF_FP64) {
+      Combo<double> cb;
+      for (int m = 0; m < 5; ++m) cb.s[m] = m <= NS ? (const double*)arrays[m] : nullptr;
+      for (int m = 0; m < 4; ++m) cb.c[m] = (c && m < NS) ? c[m] : 0.0;
+      static std::once_flag once;
+      std::call_once(once, [] {
+        cudaFuncSetAttribute(prolong_kernel<double, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             prolong_smem<double>());
+      });
+      prolong_kernel<double, NS><<<(unsigned)total, 256, prolong_smem<double>(), st>>>(cb, a);
+    } else {
+      Combo<float> cb;
+      for (int m = 0; m < 5; ++m) cb.s[m] = m <= NS ? (const float*)arrays[m] : nullptr;
+      for (int m = 0; m < 4; ++m) cb.c[m] = (c && m < NS) ? c[m] : 0.0;
+      static std::once_flag once;
+      std::call_once(once, [] {
+        cudaFuncSetAttribute(prolong_kernel<float, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             prolong_smem<float>());
+      });
+      prolong_kernel<float, NS><<<(unsigned)total, 256, prolong_smem<float>(), st>>>(cb, a);
+    }
+    e = after_launch("prolong_kernel");
+    if (e) return e;
+  }
+  return SF_OK;
+}
+
+static sf_prolong_box one_box(const int32_t* origin, const int32_t* ext, void* out, int64_t sy,
+                              int64_t sz, int64_t sf) {
+  sf_prolong_box b;
+  for (int d = 0; d < 3; ++d) {
+    b.origin[d] = origin[d];
+    b.ext[d] = ext[d];
+  }
+  b.out = out;
+  b.out_sy = sy;
+  b.out_sz = sz;
+  b.out_sf = sf;
+  return b;
 }
 
 extern "C" sf_status sf_prolong(const sf_patch* coarse, const void* coarse_array, int32_t nf,
                                 int32_t ratio, const int32_t* origin, const int32_t* ext,
                                 void* fine_out, int64_t out_sy, int64_t out_sz, int64_t out_sf,
                                 void* stream) {
+  if (!origin || !ext) return set_error(SF_EINVAL, "NULL argument");
   const void* arrays[1] = {coarse_array};
-  return prolong_launch<0>(coarse, arrays, nullptr, nf, ratio, origin, ext, fine_out, out_sy, out_sz,
-                           out_sf, stream);
+  const sf_prolong_box b = one_box(origin, ext, fine_out, out_sy, out_sz, out_sf);
+  return prolong_launch<0>(coarse, arrays, nullptr, nf, ratio, &b, 1, stream);
 }
 
-extern "C" sf_status sf_bor_prolong(const sf_patch* coarse, int32_t rk, const void* const* states,
-                                    int32_t nf, int32_t ratio, int32_t r, int32_t stage,
-                                    const int32_t* origin, const int32_t* ext, void* fine_out,
-                                    int64_t out_sy, int64_t out_sz, int64_t out_sf, void* stream) {
+static sf_status bor_args(int32_t rk, const void* const* states, int32_t ratio, int32_t r,
+                          int32_t stage, double c[4]) {
   if (rk != SF_RK4 && rk != SF_SSPRK3) return set_error(SF_EINVAL, "unknown rk %d", rk);
   if (!states) return set_error(SF_EINVAL, "states NULL");
   if (ratio < 1 || ratio > 8) return set_error(SF_EINVAL, "ratio %d not in [1, 8]", ratio);
   if (r < 0 || r >= ratio) return set_error(SF_EINVAL, "fine step r = %d not in [0, %d)", r, ratio);
   const int s = rk == SF_RK4 ? 4 : 3;
   if (stage < 0 || stage > s) return set_error(SF_EINVAL, "stage %d not in [0, %d]", stage, s);
-  double c[4];
   bor_coefficients(rk, ratio, r, stage, c);
-  if (rk == SF_RK4)
-    return prolong_launch<4>(coarse, states, c, nf, ratio, origin, ext, fine_out, out_sy, out_sz,
-                             out_sf, stream);
-  return prolong_launch<3>(coarse, states, c, nf, ratio, origin, ext, fine_out, out_sy, out_sz,
-                           out_sf, stream);
+  return SF_OK;
+}
+
+extern "C" sf_status sf_bor_prolong_boxes(const sf_patch* coarse, int32_t rk,
+                                          const void* const* states, int32_t nf, int32_t ratio,
+                                          int32_t r, int32_t stage, const sf_prolong_box* boxes,
+                                          int32_t nbox, void* stream) {
+  double c[4];
+  sf_status e = bor_args(rk, states, ratio, r, stage, c);
+  if (e) return e;
+  if (rk == SF_RK4) return prolong_launch<4>(coarse, states, c, nf, ratio, boxes, nbox, stream);
+  return prolong_launch<3>(coarse, states, c, nf, ratio, boxes, nbox, stream);
+}
+
+extern "C" sf_status sf_bor_prolong(const sf_patch* coarse, int32_t rk, const void* const* states,
+                                    int32_t nf, int32_t ratio, int32_t r, int32_t stage,
+                                    const int32_t* origin, const int32_t* ext, void* fine_out,
+                                    int64_t out_sy, int64_t out_sz, int64_t out_sf, void* stream) {
+  if (!origin || !ext) return set_error(SF_EINVAL, "NULL argument");
+  const sf_prolong_box b = one_box(origin, ext, fine_out, out_sy, out_sz, out_sf);
+  return sf_bor_prolong_boxes(coarse, rk, states, nf, ratio, r, stage, &b, 1, stream);
 }

@@ -164,3 +164,31 @@ def test_subcycled_plane_wave_converges_at_fourth_order():
         errs.append(max(e_f, e_c))
     order = math.log2(errs[0] / errs[1])
     assert 3.5 < order < 4.8, (errs, order)
+
+
+def test_bor_prolong_boxes_equals_single_box_calls():
+    # several boxes in one launch give the same values as one call per box
+    n = (10, 9, 8)
+    R = 2
+    U0, dx = inputs.wave_plane(n, seed=5)
+    st = PatchState(capi.SF_WAVE, n, dx, 0.01)
+    st.upload(U0)
+    arrs = [st.A, st.B, st.C, st.D, st.A]
+    for a_ in (st.B, st.C, st.D):
+        a_.copy_(st.A * 1.01)
+    ptrs = [a_.data_ptr() for a_ in arrs]
+    specs = [((R * 2 - 1, R + 1, R * 3), (7, 5, 3)), ((0, 0, 0), (12, 2, 4)), ((3, 5, 2), (1, 1, 1)),
+             ((1, 2, 3), (0, 4, 4))]
+    outs_a = [torch.zeros((5,) + tuple(reversed(e)), dtype=torch.float64, device="cuda") for _, e in specs]
+    outs_b = [torch.zeros_like(o) for o in outs_a]
+    p = st.patch(st.A, st.A, st.B)
+    boxes = []
+    for (o, e), oa in zip(specs, outs_a):
+        boxes.append(capi.prolong_box(o, e, oa.data_ptr(), e[0], e[0] * e[1], e[0] * e[1] * e[2]))
+    capi.sf_bor_prolong_boxes(p, capi.SF_RK4, ptrs, 5, R, 1, 2, boxes)
+    for (o, e), ob in zip(specs, outs_b):
+        capi.sf_bor_prolong(p, capi.SF_RK4, ptrs, 5, R, 1, 2, o, e, ob.data_ptr(), e[0], e[0] * e[1],
+                            e[0] * e[1] * e[2])
+    torch.cuda.synchronize()
+    for oa, ob in zip(outs_a, outs_b):
+        assert torch.equal(oa, ob)
