@@ -33,6 +33,15 @@ N = 96
 GHOST = 3
 NF = 25
 WORKLOAD = "ccz4_96cubed_rk4_periodic"
+# Algorithmic operations of one CCZ4 cell-update (right-hand side of the
+# plain formulation, counted by instantiating the oracle's per-cell function
+# on a counting scalar: 3680 add + 3970 mul + 164 div + 1 log; the RK
+# combination adds two or three per field and is left out), and the ALU
+# peaks they are set against: FP32 from the unit counts and the maximum SM
+# clock, FP64 as measured with an FMA probe on this GPU.
+FLOPS_PER_CELL_UPDATE = 3680 + 3970 + 164 + 1
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.20
 # Row pitch of the float arrays: 104 floats (416 bytes) puts every row, plane
 # and field on a 16-byte boundary, which the TMA-staged CCZ4 kernel needs;
 # FP64 keeps the dense pitch (its kernel reads stencils from global memory).
@@ -338,6 +347,14 @@ def gpu_arm(args):
                                 else "z4_stage_kernel<float,dw> (global-load stencils)"),
                      "bytes_per_cell_update": r32["bytes_per_cell_update"],
                      "per_stage_ms": r32["per_stage_ms"], "per_stage_gbs": r32["per_stage_gbs"]},
+        "alu_roofline": {
+            "bound": "alu", "flops_per_cell_update": FLOPS_PER_CELL_UPDATE,
+            "achieved": r32["value"] * FLOPS_PER_CELL_UPDATE / 1e12, "unit": "TFLOP/s",
+            "peak": FP32_PEAK_TFLOPS, "frac": r32["value"] * FLOPS_PER_CELL_UPDATE / 1e12 / FP32_PEAK_TFLOPS,
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
+            "fp64_frac": r64["value"] * FLOPS_PER_CELL_UPDATE / 1e12 / FP64_PEAK_TFLOPS,
+            "fp64_peak": FP64_PEAK_TFLOPS,
+            "fp64_peak_source": "measured FMA probe, 1/58 of the FP32 rate"},
         "fp32_bulk_fp64_islands": {
             "value": r32n["value"], "ms_per_step": r32n["ms_per_step"],
             "achieved_gbs": r32n["achieved_gbs"], "hbm_frac": r32n["achieved_gbs"] / hbm_peak,

@@ -32,6 +32,9 @@ Functions and what pins them (tests/test_oracle_*.py):
                    Shu-Osher form.
   misfit_gradient  discrete adjoint of the RK4 wave evolution.  Pinned:
                    central finite differences (exact for the quadratic misfit).
+  weno             one reconstruction of five values (App. A, App. B).
+                   Pinned: each candidate and the linear weights reproduce the
+                   coefficient tables the paper prints (tests/golden).
   radiative_rhs    Sec. V radiative boundary condition at ghost points.
                    Pinned: zero on U = U_inf; closed form on linear data
                    (every one-sided stencil exact); 4th-order convergence to
@@ -152,6 +155,8 @@ def lib() -> ctypes.CDLL:
                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_double]
         L.or_stencil.restype = ctypes.c_double
+        L.or_weno.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double]
+        L.or_weno.restype = ctypes.c_double
         L.or_radiative_rhs.argtypes = [ctypes.c_int, ip, ctypes.c_int, dp, dp, dp, dp, dp, dp]
         L.or_rk4_step_radiative.argtypes = [ctypes.c_int, pp, ip, ctypes.c_int, dp, dp, dp, dp,
                                             ctypes.c_double, dp, dp]
@@ -241,6 +246,13 @@ def restrict(Uf: np.ndarray, ratio: int, origin, ext, g: int = 3) -> np.ndarray:
     if rc:
         raise ValueError("oracle restrict: out of the fine box")
     return out
+
+
+def weno(variant: int, side: int, w, eps: float, q: float = 2.0) -> float:
+    """One reconstruction of w = U_{i-2..i+2}: side 0 -> U^L_{i+1/2}, 1 -> U^R_{i-1/2}."""
+    a = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    assert a.shape == (5,)
+    return lib().or_weno(variant, side, _dp(a), eps, q)
 
 
 def radiative_rhs(U: np.ndarray, dx, x0, uinf, v, g: int = 3) -> np.ndarray:

@@ -1170,6 +1170,18 @@ int or_restrict(int nf, const int* nfine, int gf, const double* fu, int ratio, c
   return 0;
 }
 
+// One WENO reconstruction (Sec. II.B.2, App. A, App. B) of the five values
+// w[0..4] = U_{i-2..i+2}: side 0 gives U^L_{i+1/2}, side 1 gives U^R_{i-1/2};
+// variant as in or_params (0 JS, 1 Z, 2 WENO3 on w[1..3]).
+double or_weno(int variant, int side, const double* w, double eps, double q) {
+  or_params p;
+  std::memset(&p, 0, sizeof(p));
+  p.weno_variant = variant;
+  p.weno_q = q;
+  if (variant == 2) return side == 0 ? weno3_left<double>(w, eps) : weno3_right<double>(w, eps);
+  return side == 0 ? weno5_left<double>(p, w, eps) : weno5_right<double>(p, w, eps);
+}
+
 // Radiative right-hand side (Sec. V) at every ghost point of the ghosted
 // array u (nf fields); out has u's layout and receives it at ghost points
 // (interior points are left untouched).  x0 = physical position of interior

@@ -194,3 +194,12 @@ def test_lopsided_advection_converges_to_centred():
         b = oracle.rhs(oracle.Z4, G, dx, oracle.params(lopsided=1))
         errs.append(np.abs(a - b).max())
     assert errs[0] > 0 and errs[0] / errs[1] > 13.0, errs
+
+
+def test_bench_flop_constant_is_the_oracle_count():
+    # bench.py reports the ALU roofline with the per-cell operation count of
+    # the CCZ4 right-hand side; it must be the count of the counting scalar
+    import bench
+    U, dx = inputs.z4_perturbed((6, 6, 6), seed=1, amp=0.05)
+    c = oracle.count_ops(oracle.Z4, oracle.ghosted(U), dx)
+    assert c["add"] + c["mul"] + c["div"] + c["log"] == bench.FLOPS_PER_CELL_UPDATE, c
