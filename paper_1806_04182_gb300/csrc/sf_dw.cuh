@@ -68,11 +68,45 @@ __device__ __forceinline__ dw dw_mul(dw x, dw y) {  // DWTimesDW3
   return dw_fast_two_sum(c.hi, cl3);
 }
 
-// 1/x by one Newton step from the float reciprocal: r = r0 + r0 (1 - x r0)
+// 1/x by one Newton step from the float reciprocal r0: with the residual
+// e = 1 - x r0 (|e| ~ 2^-24, formed by an FMA, which is exact for it, minus
+// x.lo r0), 1/x = r0 + r0 e + O(e^2); the two terms are normalised by
+// FastTwoSum (|r0| > |r0 e|).
 __device__ __forceinline__ dw dw_recip(dw x) {
   const float r0 = __frcp_rn(x.hi);
-  const dw e = dw_add(dw{1.0f, 0.0f}, dw_neg(dw_mulf(x, r0)));
-  return dw_add(dw{r0, 0.0f}, dw_mulf(e, r0));
+  const float e = __fmaf_rn(-x.lo, r0, __fmaf_rn(-x.hi, r0, 1.0f));
+  return dw_fast_two_sum(r0, __fmul_rn(r0, e));
+}
+
+// Dot product sum_q a_q x_q of double-word a_q and float x_q, in the manner
+// of Ogita, Rump & Oishi, "Accurate sum and dot product", SIAM J. Sci.
+// Comput. 26 (2005) (Dot2): each product's high part is exact by TwoProd,
+// the high parts are added by a cascade of TwoSums, and every rounding error
+// (and the low parts a_q.lo x_q) is summed in float; the result is as
+// accurate as a dot product evaluated in twice the float precision.
+template <int N>
+__device__ __forceinline__ dw dw_dot(const dw* a, const float* x) {
+  float s = __fmul_rn(a[0].hi, x[0]);
+  float err = __fmaf_rn(a[0].lo, x[0], __fmaf_rn(a[0].hi, x[0], -s));
+#pragma unroll
+  for (int q = 1; q < N; ++q) {
+    const float p = __fmul_rn(a[q].hi, x[q]);
+    const float pe = __fmaf_rn(a[q].lo, x[q], __fmaf_rn(a[q].hi, x[q], -p));
+    const dw t = dw_two_sum(s, p);
+    s = t.hi;
+    err = __fadd_rn(err, __fadd_rn(t.lo, pe));
+  }
+  return dw_two_sum(s, err);
+}
+
+// x - a y rounded to float, for float x, y and double-word a: the product's
+// high part is exact (TwoProd), its subtraction from x exact (TwoSum), and
+// the remaining small terms are added once.
+__device__ __forceinline__ float dw_sub_prod_f(float x, dw a, float y) {
+  const float p = __fmul_rn(a.hi, y);
+  const float pe = __fmaf_rn(a.lo, y, __fmaf_rn(a.hi, y, -p));
+  const dw t = dw_two_sum(x, -p);
+  return __fadd_rn(t.hi, __fadd_rn(t.lo, -pe));
 }
 
 // ------------------------------------------------------------ island ops
@@ -83,6 +117,8 @@ template <> struct Isl<double> {
   using H = double;
   static __device__ __forceinline__ H from(float a) { return double(a); }
   static __device__ __forceinline__ H from(double a) { return a; }
+  static __device__ __forceinline__ H sum2(float a, float b) { return double(a) + double(b); }
+  static __device__ __forceinline__ H sum2(double a, double b) { return a + b; }
   static __device__ __forceinline__ H prod(float a, float b) { return double(a) * double(b); }
   static __device__ __forceinline__ H prod(double a, double b) { return a * b; }
   static __device__ __forceinline__ H add(H a, H b) { return a + b; }
@@ -92,14 +128,25 @@ template <> struct Isl<double> {
   static __device__ __forceinline__ H mulf(H a, double b) { return a * b; }
   static __device__ __forceinline__ H recip(H a) { return 1.0 / a; }
   static __device__ __forceinline__ H third(H a) { return a * (1.0 / 3.0); }
+  // a_0 x_0 + a_3 x_3 + a_5 x_5 + 2 (a_1 x_1 + a_2 x_2 + a_4 x_4): the trace
+  // of a symmetric X stored as xx, xy, xz, yy, yz, zz against symmetric a
+  template <typename T> static __device__ __forceinline__ H trace_sym(const H* a, const T* x) {
+    return (a[0] * double(x[0]) + a[3] * double(x[3]) + a[5] * double(x[5])) +
+           2.0 * (a[1] * double(x[1]) + a[2] * double(x[2]) + a[4] * double(x[4]));
+  }
+  // x - a y in the bulk type
+  template <typename T> static __device__ __forceinline__ T sub_prod(T x, H a, T y) {
+    return T(double(x) - a * double(y));
+  }
   template <typename T> static __device__ __forceinline__ T to(H a) { return T(a); }
-  // ln of a value close to 1, returned in the bulk type
-  template <typename T> static __device__ __forceinline__ T log(H a) { return T(::log(a)); }
+  // ln of a value close to 1, returned in the bulk type (r: 1/a, unused here)
+  template <typename T> static __device__ __forceinline__ T log(H a, H) { return T(::log(a)); }
 };
 
 template <> struct Isl<dw> {
   using H = dw;
   static __device__ __forceinline__ H from(float a) { return {a, 0.0f}; }
+  static __device__ __forceinline__ H sum2(float a, float b) { return dw_two_sum(a, b); }
   static __device__ __forceinline__ H prod(float a, float b) { return dw_two_prod(a, b); }
   static __device__ __forceinline__ H add(H a, H b) { return dw_add(a, b); }
   static __device__ __forceinline__ H sub(H a, H b) { return dw_add(a, dw_neg(b)); }
@@ -110,10 +157,19 @@ template <> struct Isl<dw> {
     // multiply by 1/3 represented as a double-word constant
     return dw_mul(a, dw{0.333333343267f, -9.93410746e-09f});
   }
+  template <typename T> static __device__ __forceinline__ H trace_sym(const H* a, const T* x) {
+    const dw aa[6] = {a[0], a[3], a[5], a[1], a[2], a[4]};
+    const float xx[6] = {x[0], x[3], x[5], 2.0f * x[1], 2.0f * x[2], 2.0f * x[4]};
+    return dw_dot<6>(aa, xx);
+  }
+  template <typename T> static __device__ __forceinline__ T sub_prod(T x, H a, T y) {
+    return dw_sub_prod_f(x, a, y);
+  }
   template <typename T> static __device__ __forceinline__ T to(H a) { return T(a.hi + a.lo); }
-  // ln(hi + lo) = ln(hi) + ln(1 + lo/hi) ~ logf(hi) + lo/hi (|lo/hi| < 2^-24)
-  template <typename T> static __device__ __forceinline__ T log(H a) {
-    return T(::logf(a.hi) + a.lo / a.hi);
+  // ln(hi + lo) = ln(hi) + ln(1 + lo/hi) ~ logf(hi) + lo/hi (|lo/hi| < 2^-24);
+  // r is 1/a, so lo/hi = lo r.hi to far better than the term's own size
+  template <typename T> static __device__ __forceinline__ T log(H a, H r) {
+    return T(::logf(a.hi) + a.lo * r.hi);
   }
 };
 

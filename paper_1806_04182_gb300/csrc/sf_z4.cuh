@@ -147,40 +147,34 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
   const T kz = zc.kappa_z, kc = zc.kappa_c;
 
   // ---- islands: determinant, inverse and ln det of the conformal metric,
-  // from the exact stored value + offset (not its rounding to the bulk type)
-  H gH[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    const T sq = c0(1 + q);
-    gH[q] = (q == 0 || q == 3 || q == 5) ? I::add(I::from(sq), I::from(off)) : I::from(sq);
-  }
-  const H c00 = I::sub(I::mul(gH[3], gH[5]), I::mul(gH[4], gH[4]));
-  const H c01 = I::sub(I::mul(gH[2], gH[4]), I::mul(gH[1], gH[5]));
-  const H c02 = I::sub(I::mul(gH[1], gH[4]), I::mul(gH[2], gH[3]));
-  const H c11 = I::sub(I::mul(gH[0], gH[5]), I::mul(gH[2], gH[2]));
-  const H c12 = I::sub(I::mul(gH[1], gH[2]), I::mul(gH[0], gH[4]));
-  const H c22 = I::sub(I::mul(gH[0], gH[3]), I::mul(gH[1], gH[1]));
-  const H det = I::add(I::add(I::mul(c00, gH[0]), I::mul(c01, gH[1])), I::mul(c02, gH[2]));
+  // from the exact stored value + offset (not its rounding to the bulk type).
+  // The diagonal entries 1 + h are exact sums in the island type; products
+  // of two stored values are exact there too, so each cofactor costs one
+  // island product (or product by a stored value) and one subtraction.
+  const T sg1 = c0(2), sg2 = c0(3), sg4 = c0(5);  // xy, xz, yz
+  const H g0 = I::sum2(c0(1), off), g3 = I::sum2(c0(4), off), g5 = I::sum2(c0(6), off);
+  const H c00 = I::sub(I::mul(g3, g5), I::prod(sg4, sg4));
+  const H c01 = I::sub(I::prod(sg2, sg4), I::mulf(g5, sg1));
+  const H c02 = I::sub(I::prod(sg1, sg4), I::mulf(g3, sg2));
+  const H c11 = I::sub(I::mul(g0, g5), I::prod(sg2, sg2));
+  const H c12 = I::sub(I::prod(sg1, sg2), I::mulf(g0, sg4));
+  const H c22 = I::sub(I::mul(g0, g3), I::prod(sg1, sg1));
+  const H det = I::add(I::add(I::mul(c00, g0), I::mulf(c01, sg1)), I::mulf(c02, sg2));
   const H idet = I::recip(det);
   const H igH[6] = {I::mul(c00, idet), I::mul(c01, idet), I::mul(c02, idet),
                     I::mul(c11, idet), I::mul(c12, idet), I::mul(c22, idet)};
-  const T lndet = I::template log<T>(det);
+  const T lndet = I::template log<T>(det, idet);
   T ig[6];
 #pragma unroll
   for (int q = 0; q < 6; ++q) ig[q] = I::template to<T>(igH[q]);
   const T w[6] = {ig[0], T(2) * ig[1], T(2) * ig[2], ig[3], T(2) * ig[4], ig[5]};
   // island trace gt^{ij} X_ij (off-diagonal entries counted twice)
-  auto trace_isl = [&](const T* X) {
-    const H d = I::add(I::add(I::mulf(igH[0], X[0]), I::mulf(igH[3], X[3])), I::mulf(igH[5], X[5]));
-    const H o = I::add(I::add(I::mulf(igH[1], X[1]), I::mulf(igH[2], X[2])), I::mulf(igH[4], X[4]));
-    return I::add(d, I::add(o, o));
-  };
-  // island trace removal X_q - gt_q tr / 3, rounded to the bulk type
-  auto tf_isl = [&](T Xq, T gq, const H& tr) {
-    return I::template to<T>(I::sub(I::from(Xq), I::third(I::mulf(tr, gq))));
-  };
+  auto trace_isl = [&](const T* X) { return I::trace_sym(igH, X); };
+  // island trace removal X_q - gt_q tr / 3, rounded to the bulk type (tr3 = tr / 3)
+  auto tf_isl = [&](T Xq, T gq, const H& tr3) { return I::template sub_prod<T>(Xq, tr3, gq); };
   const H trAH = trace_isl(At);
   const T trA = I::template to<T>(trAH);
+  const H trA3 = I::third(trAH);
 
   // ---- shift: first derivatives, gt^{mn} d_m d_n beta^c and d_b d_k beta^k
   T dbe[3][3], koBe[3], advBe[3];
@@ -233,7 +227,7 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
         T s = T(0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) s += gt[S(p, c)] * dbe[c][b] + gt[S(c, b)] * dbe[c][p];
-        const T AtTF = tf_isl(At[q], gt[q], trAH);
+        const T AtTF = tf_isl(At[q], gt[q], trA3);
         out(1 + q,
             adv(x) + s - T(2.0 / 3.0) * gt[q] * divbe - T(2) * al * AtTF -
                 kc * T(1.0 / 3.0) * al * gt[q] * lndet + x.ko,
@@ -419,7 +413,7 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
 
   // ---- d/dt A~_ab (trace removal of M in the island type)
   {
-    const H trM = trace_isl(M);
+    const H trM3 = I::third(trace_isl(M));
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll
@@ -432,7 +426,7 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
           s += At[S(p, c)] * dbe[c][b] + At[S(c, b)] * dbe[c][p];
           AAd += At[S(p, c)] * Aud[c][b];
         }
-        const T MTF = tf_isl(M[q], gt[q], trM);
+        const T MTF = tf_isl(M[q], gt[q], trM3);
         out(8 + q,
             adv(x) + s - T(2.0 / 3.0) * At[q] * divbe - kc * T(1.0 / 3.0) * al * gt[q] * trA +
                 chi * MTF + al * (Kh * At[q] - T(2) * AAd) + x.ko,
