@@ -349,7 +349,7 @@ sf_status sf_batch_destroy(sf_batch* b);
  * batched persistent kernel over `patches` (same buffer roles as sf_batch:
  * u_n = state, u_stage and u_next = scratch, acc, kahan), with the kernel's
  * scratch (queue counter, per-patch stage table, work list) kept in a
- * file-scope device array of 145,408 bytes that every GPU loading the
+ * file-scope device array of 170,496 bytes that every GPU loading the
  * library holds until the process exits.  The call allocates nothing; it
  * copies the stage table from a static host buffer and clears the queue
  * counter on `stream` before the launch.

@@ -407,10 +407,11 @@ constexpr size_t kOffSys = kOffArgs + kArgsBytes;
 constexpr size_t kOffShape = kOffSys + align256(kStaticMaxPatches * sizeof(int));
 constexpr size_t kOffItems = kOffShape + align256(kStaticMaxPatches * sizeof(int2));
 constexpr size_t kStaticBytes = kOffItems + align256(kStaticMaxItems * sizeof(Item));
+static_assert(kStaticBytes == 170496, "the scratch size is stated in sf.h: update it there");
 
 }  // namespace
 
-// Scratch of sf_batch_substep_static: 145,408 bytes (about 142 KB).  Every GPU that loads
+// Scratch of sf_batch_substep_static: 170,496 bytes (about 167 KB).  Every GPU that loads
 // the library holds one copy until the process exits.  Host code must not
 // use this name as a device address; it asks the runtime for the address.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];

@@ -36,6 +36,17 @@ struct PatchArgs {
   T i12h2[3];   // 1 / (12 dx_d^2)
   T i144hh[3];  // 1 / (144 dx_a dx_b) for (xy, xz, yz)
   T ko[3];      // sigma / (64 dx_d)
+  // The same stencil weights folded into per-direction coefficients, for
+  // kernels that evaluate two directions at once (sf_pair.cuh): entry k of
+  // direction d is cst[k][d]; pairs (x, y) are 8-byte aligned.
+  //   0: 1/(12 dx)    1: 8/(12 dx)                          (D_d)
+  //   2: s   3: 15 s   4: -6 s   5: -20 s,  s = sigma/(64 dx)  (KO)
+  //   6: 16 e   7: -e   8: -30 e,  e = 1/(12 dx^2)            (D_dd)
+  // and mixed: cmx[k] = (w, 8 w, 64 w)[k] with w = 1/(144 dx_a dx_b) for
+  // (xy, xz) as a pair and yz alone.
+  struct alignas(8) Dir3 { T v[4]; };
+  Dir3 cst[9];
+  Dir3 cmx[3];
   T c_next;     // u_next = un + c_next * r   (or ssp weights)
   T c_acc;      // acc += c_acc * r
   T dt;
@@ -269,6 +280,24 @@ PatchArgs<T> make_args(const sf_params& prm, const sf_patch& p, int stage, int n
     a.i12h[d] = T(1.0 / (12.0 * p.dx[d]));
     a.i12h2[d] = T(1.0 / (12.0 * p.dx[d] * p.dx[d]));
     a.ko[d] = T(prm.sigma_ko / (64.0 * p.dx[d]));
+  }
+  for (int d = 0; d < 3; ++d) {
+    const double h = p.dx[d], sk = prm.sigma_ko / (64.0 * h), e = 1.0 / (12.0 * h * h);
+    const double w[9] = {1.0 / (12.0 * h), 8.0 / (12.0 * h), sk, 15.0 * sk, -6.0 * sk, -20.0 * sk,
+                         16.0 * e, -e, -30.0 * e};
+    for (int k = 0; k < 9; ++k) a.cst[k].v[d] = T(w[k]);
+  }
+  for (int k = 0; k < 9; ++k) a.cst[k].v[3] = T(0);
+  {
+    const double wxy = 1.0 / (144.0 * p.dx[0] * p.dx[1]), wxz = 1.0 / (144.0 * p.dx[0] * p.dx[2]),
+                 wyz = 1.0 / (144.0 * p.dx[1] * p.dx[2]);
+    const double f[3] = {1.0, 8.0, 64.0};
+    for (int k = 0; k < 3; ++k) {
+      a.cmx[k].v[0] = T(f[k] * wxy);
+      a.cmx[k].v[1] = T(f[k] * wxz);
+      a.cmx[k].v[2] = T(f[k] * wyz);
+      a.cmx[k].v[3] = T(0);
+    }
   }
   a.i144hh[0] = T(1.0 / (144.0 * p.dx[0] * p.dx[1]));
   a.i144hh[1] = T(1.0 / (144.0 * p.dx[0] * p.dx[2]));

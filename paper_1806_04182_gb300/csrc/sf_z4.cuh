@@ -23,6 +23,7 @@
 #pragma once
 #include "sf_common.cuh"
 #include "sf_dw.cuh"
+#include "sf_pair.cuh"
 
 namespace sf {
 
@@ -87,6 +88,12 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
   auto U = [&](int f) { return src.p(f); };
   auto c0 = [&](int f) { return src.centre(f); };
   T be[3], Gh[3];  // loaded with the other centre values below
+  // Float storage with centred advection evaluates the x and y directions of
+  // a field's cross (and the xy and xz mixed derivatives) as pairs, with the
+  // stencil weights folded into per-direction coefficients (PatchArgs::cst):
+  // the same stencils, one instruction for two lanes.
+  constexpr bool PAIR = sizeof(T) == 4 && !LOP;
+  auto cxy = [&](int k) { return p2<T>(a.cst[k].v[0], a.cst[k].v[1]); };
   // 19-point cross of field f: first derivatives, KO, optional D_ii
   auto cross = [&](int f, bool second) {
     src.begin(f);
@@ -95,6 +102,34 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
     x.c = src.ld(p);
     x.ko = T(0);
     x.adv = T(0);
+    if constexpr (PAIR) {
+      const P2<T> m1 = p2(src.ld(p - 1), src.ld(p - sy)), q1 = p2(src.ld(p + 1), src.ld(p + sy));
+      const P2<T> m2 = p2(src.ld(p - 2), src.ld(p - 2 * sy)),
+                  q2 = p2(src.ld(p + 2), src.ld(p + 2 * sy));
+      const P2<T> m3 = p2(src.ld(p - 3), src.ld(p - 3 * sy)),
+                  q3 = p2(src.ld(p + 3), src.ld(p + 3 * sy));
+      const T zm1 = src.ld(p - sz), zq1 = src.ld(p + sz), zm2 = src.ld(p - 2 * sz),
+              zq2 = src.ld(p + 2 * sz), zm3 = src.ld(p - 3 * sz), zq3 = src.ld(p + 3 * sz);
+      const P2<T> cc = p2(x.c, x.c);
+      const P2<T> d = pfma(psub(q1, m1), cxy(1), pmul(psub(m2, q2), cxy(0)));
+      const P2<T> s1 = padd(m1, q1), s2 = padd(m2, q2), s3 = padd(m3, q3);
+      const P2<T> ko = pfma(s1, cxy(3), pfma(s2, cxy(4), pfma(cc, cxy(5), pmul(s3, cxy(2)))));
+      const T z1 = zm1 + zq1, z2 = zm2 + zq2, z3 = zm3 + zq3;
+      x.d[0] = d.x;
+      x.d[1] = d.y;
+      x.d[2] = (zq1 - zm1) * a.cst[1].v[2] + (zm2 - zq2) * a.cst[0].v[2];
+      x.ko = (ko.x + ko.y) + (z1 * a.cst[3].v[2] + (z2 * a.cst[4].v[2] +
+                                                    (x.c * a.cst[5].v[2] + z3 * a.cst[2].v[2])));
+      if (second) {
+        const P2<T> dd = pfma(s1, cxy(6), pfma(s2, cxy(7), pmul(cc, cxy(8))));
+        x.dd[0] = dd.x;
+        x.dd[1] = dd.y;
+        x.dd[2] = z1 * a.cst[6].v[2] + (z2 * a.cst[7].v[2] + x.c * a.cst[8].v[2]);
+      } else {
+        x.dd[0] = x.dd[1] = x.dd[2] = T(0);
+      }
+      return x;
+    }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const long long s = st[d];
@@ -129,6 +164,37 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
       return (src.ld(q - 2 * sa) - src.ld(q + 2 * sa)) + T(8) * (src.ld(q + sa) - src.ld(q - sa));
     };
     return ((row(-2 * sb) - row(2 * sb)) + T(8) * (row(sb) - row(-sb))) * a.i144hh[pi];
+  };
+  // the three mixed derivatives (xy, xz, yz) of field f.  The paired form
+  // splits each 16-point tensor-product stencil by weight: with row
+  // differences r1(o) = U(o - 2) - U(o + 2) and r8(o) = U(o + 1) - U(o - 1)
+  // along x at the offsets o = +-1, +-2 across, D_xb = w (r1(-2) - r1(2)) +
+  // 8 w (r8(-2) - r8(2) + r1(1) - r1(-1)) + 64 w (r8(1) - r8(-1)).
+  auto mix3 = [&](int f, T* out) {
+    if constexpr (PAIR) {
+      const T* p = U(f);
+      auto r1 = [&](int o) {
+        return psub(p2(src.ld(p + o * sy - 2), src.ld(p + o * sz - 2)),
+                    p2(src.ld(p + o * sy + 2), src.ld(p + o * sz + 2)));
+      };
+      auto r8 = [&](int o) {
+        return psub(p2(src.ld(p + o * sy + 1), src.ld(p + o * sz + 1)),
+                    p2(src.ld(p + o * sy - 1), src.ld(p + o * sz - 1)));
+      };
+      const P2<T> x1 = psub(r1(-2), r1(2));
+      const P2<T> x8 = padd(psub(r8(-2), r8(2)), psub(r1(1), r1(-1)));
+      const P2<T> x64 = psub(r8(1), r8(-1));
+      const P2<T> w1 = p2<T>(a.cmx[0].v[0], a.cmx[0].v[1]), w8 = p2<T>(a.cmx[1].v[0], a.cmx[1].v[1]),
+                  w64 = p2<T>(a.cmx[2].v[0], a.cmx[2].v[1]);
+      const P2<T> r = pfma(x64, w64, pfma(x8, w8, pmul(x1, w1)));
+      out[0] = r.x;
+      out[1] = r.y;
+      out[2] = MIX(f, 1, 2);
+    } else {
+      out[0] = MIX(f, 0, 1);
+      out[1] = MIX(f, 0, 2);
+      out[2] = MIX(f, 1, 2);
+    }
   };
 
   // float storage holds chi, gt_xx, gt_yy, gt_zz and alpha minus their flat
@@ -190,11 +256,13 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
       s2[c] += w[S(d, d)] * x.dd[d];
     }
     ddiv[c] += x.dd[c];
+    T mx[3];
+    mix3(19 + c, mx);
 #pragma unroll
     for (int m = 0; m < 3; ++m)
 #pragma unroll
       for (int n = m + 1; n < 3; ++n) {
-        const T y = MIX(19 + c, m, n);
+        const T y = mx[m + n - 1];
         s2[c] += w[S(m, n)] * y;
         if (n == c) ddiv[m] += y;
         if (m == c) ddiv[n] += y;
@@ -219,10 +287,9 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
           dgt[q][d] = x.d[d];
           s1 += w[S(d, d)] * x.dd[d];
         }
-#pragma unroll
-        for (int m = 0; m < 3; ++m)
-#pragma unroll
-          for (int n = m + 1; n < 3; ++n) s1 += w[S(m, n)] * MIX(1 + q, m, n);
+        T mx[3];
+        mix3(1 + q, mx);
+        s1 += w[1] * mx[0] + w[2] * mx[1] + w[4] * mx[2];
         t1[q] = s1;
         T s = T(0);
 #pragma unroll
@@ -263,9 +330,13 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
     const Cross<T> x = cross(0, true);
 #pragma unroll
     for (int d = 0; d < 3; ++d) { dchi[d] = x.d[d]; ddchi[S(d, d)] = x.dd[d]; }
-    ddchi[1] = MIX(0, 0, 1);
-    ddchi[2] = MIX(0, 0, 2);
-    ddchi[4] = MIX(0, 1, 2);
+    {
+      T mx[3];
+      mix3(0, mx);
+      ddchi[1] = mx[0];
+      ddchi[2] = mx[1];
+      ddchi[4] = mx[2];
+    }
     out(0, adv(x) + T(2.0 / 3.0) * chi * (al * Kt - divbe) + x.ko, x.c);
   }
   const T ialpha = T(1) / al;
@@ -273,9 +344,13 @@ __device__ __forceinline__ void z4_cell(const PatchArgs<T>& a, const Z4Coef<T>& 
     const Cross<T> x = cross(18, true);
 #pragma unroll
     for (int d = 0; d < 3; ++d) { dal[d] = x.d[d]; ddal[S(d, d)] = x.dd[d]; }
-    ddal[1] = MIX(18, 0, 1);
-    ddal[2] = MIX(18, 0, 2);
-    ddal[4] = MIX(18, 1, 2);
+    {
+      T mx[3];
+      mix3(18, mx);
+      ddal[1] = mx[0];
+      ddal[2] = mx[1];
+      ddal[4] = mx[2];
+    }
     const T fsl = zc.slicing == 0 ? T(2) * ialpha : T(1);
     out(18, adv(x) - al * al * fsl * Kh + x.ko, x.c);
   }
