@@ -130,7 +130,8 @@ class ClockSampler:
 # profiles/; it is reported only while the kernel sources still hash to the
 # value recorded there (null once the kernel has changed).
 PROFILE = os.path.join(ROOT, "profiles", "z4_tma_fp32dw_96cubed.md")
-KERNEL_SOURCES = ["sf_common.cuh", "sf_dw.cuh", "sf_pair.cuh", "sf_z4.cuh", "sf_z4.cu", "sf_z4_tma.cu"]
+KERNEL_SOURCES = ["sf_common.cuh", "sf_dw.cuh", "sf_mbar.cuh", "sf_pair.cuh", "sf_z4.cuh", "sf_z4.cu",
+                  "sf_z4_tma.cu"]
 
 
 def kernel_source_hash() -> str:

@@ -365,6 +365,18 @@ sf_status sf_batch_substep_static(const sf_params* prm, const sf_patch* patches,
                                   int32_t stage, void* stream);
 
 /*
+ * Self-test of failure detection (the paper has no counterpart).  Launches
+ * one warp that waits, through the bounded mbarrier wait of the TMA-staged
+ * stage kernels, on a barrier that nothing ever completes; after
+ * `limit_cycles` SM clock cycles (1 .. 2e9, about a second at most) the wait
+ * gives up and the kernel sets the time-out bit of the status word, which the
+ * next sf_get_device_status() returns as SF_ETIMEOUT.  Nothing faults, traps
+ * or hangs; the context stays usable.  Asynchronous on `stream`; a limit out
+ * of range returns SF_EINVAL and enqueues nothing.
+ */
+sf_status sf_selftest_wait_timeout(int64_t limit_cycles, void* stream);
+
+/*
  * Synchronises `stream`, returns and clears the device status word:
  * SF_OK, SF_ENONFINITE or SF_ETIMEOUT.
  */

@@ -27,7 +27,7 @@ EXPORTS = ["sf_nfields", "sf_substep", "sf_rhs", "sf_fill_ghosts_periodic", "sf_
            "sf_batch_create", "sf_batch_substep", "sf_batch_tune", "sf_batch_capture",
            "sf_batch_launch", "sf_batch_launches_per_step", "sf_batch_destroy",
            "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong", "sf_bor_prolong", "sf_bor_prolong_boxes", "sf_radiative_substep",
-           "sf_get_device_status", "sf_last_error", "sf_launch_count"]
+           "sf_selftest_wait_timeout", "sf_get_device_status", "sf_last_error", "sf_launch_count"]
 
 
 class SfError(RuntimeError):
@@ -156,6 +156,7 @@ def lib() -> ctypes.CDLL:
         L.sf_bor_prolong.argtypes = [P(sf_patch), i32, P(vp), i32, i32, i32, i32, P(i32), P(i32), vp,
                                      i64, i64, i64, vp]
         L.sf_get_device_status.argtypes = [vp]
+        L.sf_selftest_wait_timeout.argtypes = [i64, vp]
         L.sf_last_error.argtypes = []
         L.sf_last_error.restype = ctypes.c_char_p
         L.sf_launch_count.argtypes = []
@@ -164,7 +165,8 @@ def lib() -> ctypes.CDLL:
                      "sf_adjoint_substep", "sf_gather", "sf_scatter_add", "sf_diagnostics",
                      "sf_batch_create", "sf_batch_substep", "sf_batch_tune", "sf_batch_capture",
                      "sf_batch_launch", "sf_batch_destroy", "sf_get_device_status",
-                     "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong"):
+                     "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong",
+                     "sf_selftest_wait_timeout"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -317,6 +319,12 @@ def sf_bor_prolong_boxes(coarse: sf_patch, rk: int, states, nf: int, ratio: int,
     bx = (sf_prolong_box * max(1, len(boxes)))(*boxes)
     _check(lib().sf_bor_prolong_boxes(ctypes.byref(coarse), rk, arr, nf, ratio, r, stage, bx,
                                       len(boxes), stream), "sf_bor_prolong_boxes")
+
+
+def sf_selftest_wait_timeout(limit_cycles: int, stream: int = 0) -> None:
+    """Launches a bounded wait that must give up (see sf.h); the next
+    sf_get_device_status() then returns SF_ETIMEOUT."""
+    _check(lib().sf_selftest_wait_timeout(limit_cycles, stream), "sf_selftest_wait_timeout")
 
 
 def sf_get_device_status(stream: int = 0) -> int:

@@ -7,6 +7,7 @@
 #include <cstring>
 
 #include "sf_internal.cuh"
+#include "sf_mbar.cuh"
 
 namespace sf {
 
@@ -177,6 +178,30 @@ static sf_status dispatch(const sf_params& prm, const sf_patch& p, const StageAr
 }  // namespace sf
 
 using namespace sf;
+
+namespace sf {
+namespace {
+
+// Longest self-test wait accepted: about a second at GB300 clocks, the limit
+// the stage kernels themselves use.
+constexpr long long kMaxSelftestCycles = 2000000000LL;
+
+// One warp waits on an mbarrier that nothing ever arrives on, through the
+// same bounded wait the TMA-staged kernels use; the wait gives up after
+// `limit` cycles and the kernel records ST_TIMEOUT.
+__global__ void wait_selftest_kernel(long long limit, unsigned int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(&bar, 0, limit);
+  if (!ok && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+}
+
+}  // namespace
+}  // namespace sf
 
 extern "C" {
 
@@ -350,6 +375,16 @@ sf_status sf_scatter_add(const sf_patch* patch, void* array, int32_t field, cons
         (float*)array, field * p.sf, p.n[0], p.n[1], p.ghost, p.sy, p.sz,
         (long long)p.n[0] * p.n[1] * p.n[2], obs, nobs, (const float*)vals);
   return after_launch("scatter_add_kernel");
+}
+
+sf_status sf_selftest_wait_timeout(int64_t limit_cycles, void* stream) {
+  t_err[0] = 0;
+  if (limit_cycles < 1 || limit_cycles > kMaxSelftestCycles)
+    return set_error(SF_EINVAL, "limit_cycles must be in [1, %lld]", kMaxSelftestCycles);
+  unsigned int* st = status_ptr();
+  if (!st) return set_error(SF_ECUDA, "no CUDA device / status word unavailable");
+  wait_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>((long long)limit_cycles, st);
+  return after_launch("wait_selftest_kernel");
 }
 
 sf_status sf_get_device_status(void* stream) {

@@ -26,6 +26,7 @@
 #include <mutex>
 
 #include "sf_internal.cuh"
+#include "sf_mbar.cuh"
 #include "sf_z4.cuh"
 
 namespace sf {
@@ -64,43 +65,6 @@ constexpr int kBY = 12, kKS = 8;
 // the last three are not used.
 __constant__ signed char kFieldSeq[25] = {19, 20, 21, 1, 2,  3,  4,  5,  6,  0,  18, 14, 15,
                                           16, 7,  17, 8, 9, 10, 11, 12, 13, 22, 23, 24};
-
-__device__ __forceinline__ uint32_t saddr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(saddr(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for the phase with the given parity; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
-  if (mbar_try(b, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try(b, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
-  return true;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect(uint64_t* b, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes)
-               : "memory");
-}
 
 __device__ __forceinline__ void tma_load_4d(float* dst, const CUtensorMap* map, int x, int y, int z,
                                             int f, uint64_t* bar) {
@@ -146,7 +110,7 @@ struct TmaSrc {
   // (use j - kSlots) has been released by every warp
   __device__ __forceinline__ void issue(int j) {
     const int sl = j % kSlots;
-    if (j >= kSlots && !dead && !mbar_wait(&empty[sl], ((j / kSlots) - 1) & 1)) fail();
+    if (j >= kSlots && !dead && !mbar_wait(&empty[sl], ((j / kSlots) - 1) & 1, kWaitCycles)) fail();
     if (dead) return;
     mbar_expect(&full[sl], kBoxBytes);
     tma_load_4d(tiles + sl * kSlotFloats, map, gx, gy, gz, kFieldSeq[j], &full[sl]);
@@ -166,14 +130,14 @@ struct TmaSrc {
       if (lane0) mbar_arrive(&empty[(i - 1) % kSlots]);
     }
     cur = i % kSlots;
-    if (!dead && !mbar_wait(&full[cur], (i / kSlots) & 1)) fail();
+    if (!dead && !mbar_wait(&full[cur], (i / kSlots) & 1, kWaitCycles)) fail();
   }
 
   // the leader's warp consumed every load it issued unless a wait gave up;
   // then it waits (bounded) for the loads still in flight before exiting
   __device__ __forceinline__ void finish() {
     if (leader && dead)
-      for (int j = use; j < issued; ++j) mbar_wait(&full[j % kSlots], (j / kSlots) & 1);
+      for (int j = use; j < issued; ++j) mbar_wait(&full[j % kSlots], (j / kSlots) & 1, kWaitCycles);
   }
 };
 

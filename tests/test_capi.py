@@ -117,3 +117,12 @@ def test_adjoint_only_for_wave(L):
 def test_mixed_systems_rejected_by_substep(L):
     with pytest.raises(capi.SfError, match="sf_batch"):
         capi.sf_substep(capi.params(), [fake_patch(), fake_patch(system=capi.SF_Z4)], 0)
+
+
+def test_selftest_wait_limit_checked(L):
+    # rejected on the host before any device work
+    for bad in (0, -5, 2_000_000_001):
+        with pytest.raises(capi.SfError) as e:
+            capi.sf_selftest_wait_timeout(bad)
+        assert e.value.status == capi.SF_EINVAL
+        assert "limit_cycles" in str(e.value)
