@@ -586,7 +586,10 @@ def _batch_rows(hbm_peak: float, npatch: int = 512, per_patch: bool = True) -> l
     # batched AMR step: npatch patches, one persistent launch per stage in a CUDA graph
     table = inputs.amr_patch_table(npatch, seed=0)
 
-    def states(precision):
+    def states(precision, tma_pitch=False):
+        # tma_pitch: float CCZ4 rows padded to a multiple of 4 floats, which
+        # sends those patches to the TMA-staged kernel inside the batch; the
+        # other run keeps every CCZ4 row off that multiple (persistent only)
         sts = []
         for q, t in enumerate(table):
             h = t["dx"]
@@ -595,26 +598,39 @@ def _batch_rows(hbm_peak: float, npatch: int = 512, per_patch: bool = True) -> l
                 U0, _ = inputs.wave_plane(t["n"], seed=q, length=t["n"][0] * h)
             else:
                 U0, _ = inputs.z4_minkowski_noise(t["n"], seed=q)
-            sts.append(PatchState(system, t["n"], (h, h, h), t["dt"], precision=precision))
+            pitch = None
+            if system == capi.SF_Z4:
+                # a multiple of 4 floats for the TMA-staged kernel; otherwise a
+                # pitch that is not, so every CCZ4 patch takes the persistent kernel
+                row = t["n"][0] + 6
+                pitch = (row + 3) // 4 * 4 if tma_pitch else (row + 1 if row % 4 == 0 else row)
+            sts.append(PatchState(system, t["n"], (h, h, h), t["dt"], precision=precision,
+                                  x_pitch=pitch))
             sts[-1].upload(U0)
         return sts
 
     cells = sum(t["n"][0] * t["n"][1] * t["n"][2] for t in table)
     bytes_step = sum(t["n"][0] * t["n"][1] * t["n"][2] * (19 * (25 if t["system"] == "z4" else 5) * 4)
                      for t in table)
-    sts = states(capi.SF_FP32_BULK_DW)
-    stream = torch.cuda.Stream()
-    b = capi.sf_batch_create(capi.params(), [s_.patch(s_.B, s_.A, s_.C) for s_ in sts])
-    with torch.cuda.stream(stream):
-        capi.sf_batch_tune(b, stream.cuda_stream)
-        capi.sf_batch_capture(b, stream.cuda_stream)
-        ms = _events_time(lambda: capi.sf_batch_launch(b, stream.cuda_stream), 10, 3)
-    capi.sf_batch_destroy(b)
-    batch_rate = cells * 4 * 10 / (ms * 1e-3)
-    out.append({"workload": f"amr_batch_{npatch}_patches_fp32_bulk_dw_graph", "value": batch_rate,
-                "unit": UNIT, "ms_per_step": ms / 10, "cells": cells,
-                "hbm_frac": bytes_step * 10 / (ms * 1e-3) / 1e9 / hbm_peak})
-    del sts
+    batch_rate = None
+    for tma in (True, False):
+        sts = states(capi.SF_FP32_BULK_DW, tma_pitch=tma)
+        stream = torch.cuda.Stream()
+        b = capi.sf_batch_create(capi.params(), [s_.patch(s_.B, s_.A, s_.C) for s_ in sts])
+        launches = capi.sf_batch_launches_per_step(b)
+        with torch.cuda.stream(stream):
+            capi.sf_batch_tune(b, stream.cuda_stream)
+            capi.sf_batch_capture(b, stream.cuda_stream)
+            ms = _events_time(lambda: capi.sf_batch_launch(b, stream.cuda_stream), 10, 3)
+        capi.sf_batch_destroy(b)
+        rate = cells * 4 * 10 / (ms * 1e-3)
+        batch_rate = rate if batch_rate is None else batch_rate
+        name = ("tma_ccz4_tiles_plus_persistent" if tma else "persistent_only")
+        out.append({"workload": f"amr_batch_{npatch}_patches_fp32_bulk_dw_graph_{name}",
+                    "value": rate, "unit": UNIT, "ms_per_step": ms / 10, "cells": cells,
+                    "launches_per_step": launches,
+                    "hbm_frac": bytes_step * 10 / (ms * 1e-3) / 1e9 / hbm_peak})
+        del sts
     if not per_patch:
         return out
     sts = states(capi.SF_FP64)

@@ -5,6 +5,10 @@
 // (patch, tile) work items from a device counter until the list is empty;
 // CCZ4 tiles are queued first so the heavy items start early.  No CTA ever
 // waits on another, so the queue has no spin-waits.
+// Float CCZ4 patches whose layout suits TMA (pitches and arrays on 16-byte
+// boundaries, centred advection) go instead to the TMA-staged kernel, one
+// launch per stage over all their 32 x 12 x 1 tiles, ahead of the persistent
+// launch that takes the remaining patches; both are captured in the graph.
 //
 // Buffer roles per patch (sf_patch fields as passed to sf_batch_create):
 //   u_n = A: the state U^n, updated in place by the last stage
@@ -95,6 +99,10 @@ struct sf_batch {
   Item* d_items = nullptr;
   int nitems = 0;
   unsigned int* d_counter = nullptr;
+  std::vector<char> tma;  // patch q goes to the TMA-staged CCZ4 kernel
+  void* d_maps = nullptr; // tensor maps, 3 per patch (u_n, u_stage, u_next roles)
+  TmaTile* d_tiles = nullptr;
+  int ntiles = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -141,6 +149,7 @@ sf_status build_items(sf_batch* b, int only_class) {
       const sf_patch& p = b->patches[q];
       const bool z4 = p.system == SF_Z4;
       if ((pass == 0) != z4) continue;
+      if (!b->tma.empty() && b->tma[q]) continue;
       const int cls = class_of(p);
       const Shape sh = kShapes[b->shape_of_class[cls]];
       shapes[q] = make_int2(sh.tx, sh.tz);
@@ -165,6 +174,43 @@ sf_status build_items(sf_batch* b, int only_class) {
   return SF_OK;
 }
 
+// Tensor maps and the tile list of the patches served by the TMA-staged
+// CCZ4 kernel (float precision, eligible layouts).
+sf_status build_tma(sf_batch* b) {
+  b->tma.assign(b->npatch, 0);
+  if (b->precision == SF_FP64) return SF_OK;
+  std::vector<unsigned char> maps;
+  std::vector<TmaTile> tiles;
+  for (int q = 0; q < b->npatch; ++q) {
+    const sf_patch& p = b->patches[q];
+    if (!z4_tma_batch_eligible(b->prm, p)) continue;
+    b->tma[q] = 1;
+  }
+  maps.assign((size_t)3 * b->npatch * kTmaMapBytes, 0);
+  for (int q = 0; q < b->npatch; ++q) {
+    if (!b->tma[q]) continue;
+    const sf_patch& p = b->patches[q];
+    const void* arr[3] = {p.u_n, p.u_stage, p.u_next};
+    for (int r = 0; r < 3; ++r) {
+      sf_status e = encode_z4_tma_map(maps.data() + ((size_t)3 * q + r) * kTmaMapBytes, p, arr[r]);
+      if (e) return e;
+    }
+    for (int z = 0; z < p.n[2]; ++z)
+      for (int y = 0; y < p.n[1]; y += kTmaTileY)
+        for (int x = 0; x < p.n[0]; x += kTmaTileX) tiles.push_back(TmaTile{q, x, y, z});
+  }
+  b->ntiles = (int)tiles.size();
+  if (tiles.empty()) return SF_OK;
+  if (cudaMalloc(&b->d_maps, maps.size()) != cudaSuccess ||
+      cudaMalloc(&b->d_tiles, tiles.size() * sizeof(TmaTile)) != cudaSuccess)
+    return set_error(SF_ECUDA, "batch: cudaMalloc of tensor maps failed");
+  if (cudaMemcpy(b->d_maps, maps.data(), maps.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(TmaTile), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return set_error(SF_ECUDA, "batch: upload of tensor maps failed");
+  return SF_OK;
+}
+
 StageArgs batch_stage_args(const sf_batch* b, int stage, unsigned int* status) {
   StageArgs s;
   s.mode = 0;
@@ -180,6 +226,16 @@ StageArgs batch_stage_args(const sf_batch* b, int stage, unsigned int* status) {
 
 template <typename T, typename H>
 sf_status launch_stage(sf_batch* b, int stage, cudaStream_t st, unsigned int* status) {
+  if (b->ntiles > 0) {
+    // stage roles of the stage input: A (u_n), B (u_stage), C (u_next), B
+    const int role[4] = {0, 1, 2, 1};
+    const PatchArgs<float>* fargs =
+        static_cast<const PatchArgs<float>*>(b->d_args) + (size_t)stage * b->npatch;
+    sf_status e = launch_z4_tma_batch(b->prm, b->precision, b->d_maps, role[stage], fargs,
+                                      b->d_tiles, b->ntiles, batch_stage_args(b, stage, status), st);
+    if (e) return e;
+    if (b->nitems == 0) return SF_OK;
+  }
   if (cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), st) != cudaSuccess)
     return set_error(SF_ECUDA, "batch: counter reset failed");
   Z4Coef<T> zc;
@@ -265,7 +321,7 @@ sf_status sf_batch_create(const sf_params* prm, const sf_patch* patches, int32_t
   }
   cudaMemcpy(b->d_sys, sys.data(), npatch * sizeof(int), cudaMemcpyHostToDevice);
   sf_status e = b->precision == SF_FP64 ? upload_args<double>(b) : upload_args<float>(b);
-  (void)0;
+  if (!e) e = build_tma(b);
   if (!e) e = build_items(b, -1);
   if (e) {
     sf_batch_destroy(b);
@@ -294,9 +350,12 @@ sf_status sf_batch_tune(sf_batch* b, void* stream) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   sf_status err = SF_OK;
+  // the TMA-staged patches have a fixed tile: time the persistent kernel alone
+  const int ntiles = b->ntiles;
+  b->ntiles = 0;
   for (int cls = 0; cls < kClasses && !err; ++cls) {
     bool any = false;
-    for (const auto& p : b->patches) any |= class_of(p) == cls;
+    for (int q = 0; q < b->npatch; ++q) any |= class_of(b->patches[q]) == cls && !b->tma[q];
     if (!any) continue;
     float best = 1e30f;
     int best_shape = 0;
@@ -320,6 +379,7 @@ sf_status sf_batch_tune(sf_batch* b, void* stream) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  b->ntiles = ntiles;
   if (!err) err = build_items(b, -1);
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
@@ -367,7 +427,11 @@ sf_status sf_batch_launch(sf_batch* b, void* stream) {
   return after_launch("batch graph");
 }
 
-int32_t sf_batch_launches_per_step(const sf_batch* b) { return b ? 4 : 0; }
+int32_t sf_batch_launches_per_step(const sf_batch* b) {
+  if (!b) return 0;
+  const int per_stage = (b->ntiles > 0 ? 1 : 0) + (b->ntiles == 0 || b->nitems > 0 ? 1 : 0);
+  return 4 * per_stage;
+}
 
 sf_status sf_batch_destroy(sf_batch* b) {
   if (!b) return SF_OK;
@@ -378,6 +442,8 @@ sf_status sf_batch_destroy(sf_batch* b) {
   if (b->d_shape) cudaFree(b->d_shape);
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_counter) cudaFree(b->d_counter);
+  if (b->d_maps) cudaFree(b->d_maps);
+  if (b->d_tiles) cudaFree(b->d_tiles);
   delete b;
   return SF_OK;
 }

@@ -59,6 +59,7 @@ struct Cfg {
 // other (the ring couples them), so they share the instruction cache, and
 // the kernel is bound by instruction fetch.
 constexpr int kBY = 12, kKS = 8;
+static_assert(kTmaTileX == 32 && kTmaTileY == kBY, "batch tiles are the kernel's tiles");
 
 // Order in which z4_cell opens the fields' stencils (cross, then the mixed
 // derivatives of the same field).  Without the Gamma-driver (shift frozen)
@@ -214,6 +215,76 @@ __global__ void __launch_bounds__(Cfg<BY, KS>::kThreads, Cfg<BY, KS>::kMinBlocks
   write_fields<float, 25>(a, s, im, c, i, j, k, rbuf + tid, C::kThreads);
 }
 
+// The same staged stage over the 32 x 12 x 1 tiles of many patches (the
+// CCZ4 patches of a batch): one CTA per tile, the tile's patch from `tiles`,
+// its arguments copied from `args` into shared memory (uniform reads), its
+// stage input's tensor map from `maps` (three per patch, for the u_n,
+// u_stage and u_next buffer roles; `role` picks this stage's input).  Runtime
+// strides; a tile may overhang the patch in x and y: the TMA box reads zeros
+// beyond the array, the overhanging threads still take part in the ring
+// (they compute on clamped centre values) and write nothing.
+template <typename H>
+__global__ void __launch_bounds__(Cfg<kBY, kKS>::kThreads, 1)
+    z4_tma_batch_kernel(const CUtensorMap* __restrict__ maps, int role,
+                        const PatchArgs<float>* __restrict__ args, const TmaTile* __restrict__ tl,
+                        StageArgs s, Z4Coef<float> zc) {
+  using C = Cfg<kBY, kKS>;
+  constexpr int kSlots = kKS;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ PatchArgs<float> pa;
+  float* tiles = reinterpret_cast<float*>(smem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kSlots * C::kSlotFloats * 4);
+  uint64_t* empty = full + kSlots;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const TmaTile w = tl[blockIdx.x];
+  {
+    static_assert(sizeof(PatchArgs<float>) % 4 == 0, "word copy");
+    const int* from = reinterpret_cast<const int*>(args + w.patch);
+    int* to = reinterpret_cast<int*>(&pa);
+    for (int q = tid; q < (int)(sizeof(PatchArgs<float>) / 4); q += C::kThreads) to[q] = from[q];
+  }
+  if (tid == 0) {
+    for (int q = 0; q < kSlots; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], kBY);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  const PatchArgs<float>& a = pa;
+  const int i = w.x0 + threadIdx.x, j = w.y0 + threadIdx.y, k = w.z0;
+  const bool valid = i < a.n[0] && j < a.n[1];
+  const int ic = min(i, a.n[0] - 1), jc = min(j, a.n[1] - 1);
+  const long long c = (long long)(k + 3) * a.sz + (long long)(jc + 3) * a.sy + (ic + 3);
+  TmaSrc<kBY, kKS> src;
+  src.u = a.us + c;
+  src.F = a.sf;
+  src.tiles = tiles;
+  src.full = full;
+  src.empty = empty;
+  src.map = maps + 3 * w.patch + role;
+  src.status = s.status;
+  src.local = (3 * C::TY + threadIdx.y + 3) * TX + threadIdx.x + 3;
+  src.use = 0;
+  src.cur = 0;
+  src.nuses = zc.shift_frozen ? 22 : 25;
+  src.issued = 0;
+  src.gx = w.x0;  // interior x0 - 3, in ghosted coordinates
+  src.gy = w.y0;
+  src.gz = k;
+  src.leader = tid == 0;
+  src.lane0 = threadIdx.x == 0;
+  src.dead = false;
+  src.prologue();
+  float* rbuf = reinterpret_cast<float*>(smem + C::kRbufOffset);
+  z4_cell<float, H, false>(a, zc, src, [&](int f, float r, float) { rbuf[f * C::kThreads + tid] = r; });
+  if (valid) {
+    const Images im = ghost_images(a, s, i, j, k);
+    write_fields<float, 25>(a, s, im, c, i, j, k, rbuf + tid, C::kThreads);
+  }
+}
+
 namespace {
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -272,6 +343,66 @@ bool z4_tma_eligible(const sf_params& prm, const sf_patch& p) {
   if (p.n[0] % 32 || p.n[1] % kBY || p.n[0] + 6 > kSY || p.n[1] + 6 > 102) return false;
   if (reinterpret_cast<uintptr_t>(p.u_stage) % 16) return false;
   return true;
+}
+
+// Batch form: float storage, centred advection, 3 ghosts, row / plane /
+// field pitches that are multiples of 4 floats (16 bytes, as TMA requires)
+// and 16-byte aligned arrays; any interior size (tiles may overhang).
+bool z4_tma_batch_eligible(const sf_params& prm, const sf_patch& p) {
+  if (p.system != SF_Z4 || p.precision == SF_FP64 || prm.lopsided) return false;
+  if (p.ghost != 3 || p.sy % 4 || p.sz % 4 || p.sf % 4) return false;
+  for (const void* q : {(const void*)p.u_n, (const void*)p.u_stage, (const void*)p.u_next})
+    if (reinterpret_cast<uintptr_t>(q) % 16) return false;
+  return true;
+}
+
+// Tensor map of the ghosted float array `base` with p's extents and strides,
+// boxes of the staged kernel (40 x 18 x 7 x 1).
+sf_status encode_z4_tma_map(void* out, const sf_patch& p, const void* base) {
+  static_assert(sizeof(CUtensorMap) == kTmaMapBytes, "tensor map size");
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return set_error(SF_ECUDA, "cuTensorMapEncodeTiled not available");
+  using C = Cfg<kBY, kKS>;
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  const cuuint64_t dims[4] = {(cuuint64_t)(p.n[0] + 6), (cuuint64_t)(p.n[1] + 6),
+                              (cuuint64_t)(p.n[2] + 6), 25};
+  const cuuint64_t strides[3] = {(cuuint64_t)p.sy * 4, (cuuint64_t)p.sz * 4, (cuuint64_t)p.sf * 4};
+  const cuuint32_t box[4] = {TX, (cuuint32_t)C::TY, TZ, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(SF_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  memcpy(out, &map, sizeof(map));
+  return SF_OK;
+}
+
+namespace {
+template <typename H>
+sf_status launch_tma_batch(const sf_params& prm, const void* d_maps, int role,
+                           const PatchArgs<float>* d_args, const TmaTile* d_tiles, int ntiles,
+                           const StageArgs& s, cudaStream_t st) {
+  using C = Cfg<kBY, kKS>;
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(z4_tma_batch_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         C::kSmemBytes);
+  });
+  const Z4Coef<float> zc = z4_coef<float>(prm);
+  z4_tma_batch_kernel<H><<<ntiles, dim3(32, kBY, 1), C::kSmemBytes, st>>>(
+      static_cast<const CUtensorMap*>(d_maps), role, d_args, d_tiles, s, zc);
+  return after_launch("z4_tma_batch_kernel");
+}
+}  // namespace
+
+sf_status launch_z4_tma_batch(const sf_params& prm, int precision, const void* d_maps, int role,
+                              const PatchArgs<float>* d_args, const TmaTile* d_tiles, int ntiles,
+                              const StageArgs& s, cudaStream_t st) {
+  if (ntiles <= 0) return SF_OK;
+  if (precision == SF_FP32_BULK_DW)
+    return launch_tma_batch<dw>(prm, d_maps, role, d_args, d_tiles, ntiles, s, st);
+  return launch_tma_batch<double>(prm, d_maps, role, d_args, d_tiles, ntiles, s, st);
 }
 
 sf_status launch_z4_tma(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,

@@ -20,7 +20,9 @@ def lib():
     return capi.lib()
 
 
-def make_states(table, precision, seed=0):
+def make_states(table, precision, seed=0, tma_pitch=False):
+    """tma_pitch: CCZ4 rows padded to a multiple of 4 floats, so that a float
+    batch sends those patches to the TMA-staged kernel."""
     states = []
     for q, t in enumerate(table):
         n = t["n"]
@@ -31,7 +33,10 @@ def make_states(table, precision, seed=0):
             U0 = U0 * 1e-2
         else:
             U0, _ = inputs.z4_perturbed(n, seed=seed + q, amp=0.03)
-        st = PatchState(system, n, (h, h, h), t["dt"], precision=precision)
+        pitch = None
+        if tma_pitch and system == capi.SF_Z4:
+            pitch = (n[0] + 6 + 3) // 4 * 4
+        st = PatchState(system, n, (h, h, h), t["dt"], precision=precision, x_pitch=pitch)
         st.upload(U0)
         st.U0 = U0
         states.append(st)
@@ -120,7 +125,11 @@ def test_batch_graph_tune_and_capture():
             for _ in range(3):
                 capi.sf_batch_launch(b, stream.cuda_stream)
         stream.synchronize()
-        assert capi.sf_batch_launches_per_step(b) == 4
+        # float CCZ4 patches whose dense rows happen to be a multiple of 4 floats
+        # go to the TMA-staged kernel: then two launches per stage
+        tma = [st.system == capi.SF_Z4 and st.pitch % 4 == 0 for st in states]
+        per_stage = (1 if any(tma) else 0) + (0 if all(tma) else 1)
+        assert capi.sf_batch_launches_per_step(b) == 4 * per_stage
         for st, r in zip(states, ref):
             a, w = st.interior(), r.interior()
             scale = w.abs().amax(dim=(1, 2, 3)).clamp_min(1e-2)
@@ -139,3 +148,68 @@ def test_batch_rejects_mixed_precision_and_mhd():
     m = PatchState(capi.SF_MHD, (8, 8, 8), (0.1,) * 3, 0.01, prm=capi.params())
     with pytest.raises(capi.SfError):
         capi.sf_batch_create(capi.params(), [m.patch(m.B, m.A, m.C)])
+
+
+# ------------------------------------------------------------------ TMA-staged CCZ4 tiles
+@pytest.mark.parametrize("precision", [capi.SF_FP32_BULK_DW, capi.SF_FP32_BULK])
+def test_batch_tma_tiles_equal_per_patch_launches(precision):
+    # CCZ4 rows padded to 16 bytes: the batch sends those patches to the
+    # TMA-staged kernel (32 x 12 x 1 tiles overhanging every patch here,
+    # sizes 6..21), the wave patches to the persistent kernel; per-patch
+    # launches run the global-load kernel on the same layouts.
+    table = small_table(10, seed=11)
+    ref_states = make_states(table, precision, tma_pitch=True)
+    for st in ref_states:
+        st.step(2)
+    states = make_states(table, precision, tma_pitch=True)
+    b = capi.sf_batch_create(capi.params(), batch_patches(states))
+    try:
+        assert capi.sf_batch_launches_per_step(b) == 8  # TMA tiles + persistent, 4 stages
+        for _ in range(2):
+            for s in range(4):
+                capi.sf_batch_substep(b, s, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert capi.sf_get_device_status() == capi.SF_OK
+        for st, ref in zip(states, ref_states):
+            a, r = st.interior(), ref.interior()
+            scale = r.abs().amax(dim=(1, 2, 3)).clamp_min(1e-2)
+            err = ((a - r).abs().amax(dim=(1, 2, 3)) / scale).max().item()
+            assert err < fp_bound(precision, st), err
+    finally:
+        capi.sf_batch_destroy(b)
+
+
+def test_batch_tma_tiles_match_oracle_through_graph():
+    # CCZ4 patches only (one launch per stage), sizes across the tile edges,
+    # one RK4 step through the captured graph against the FP64 oracle; the
+    # smooth periodic data of z4_perturbed with its own dx per patch, and the
+    # float bound of the single-patch TMA test
+    eps32 = float(np.finfo(np.float32).eps)
+    states = []
+    for q, n in enumerate(((32, 12, 4), (33, 13, 5), (7, 25, 3), (45, 11, 6))):
+        U0, dx = inputs.z4_perturbed(n, seed=20 + q, amp=0.05)
+        st = PatchState(capi.SF_Z4, n, dx, 0.25 * min(dx), precision=capi.SF_FP32_BULK_DW,
+                        x_pitch=(n[0] + 6 + 3) // 4 * 4)
+        st.upload(U0)
+        st.U0 = U0
+        states.append(st)
+    b = capi.sf_batch_create(capi.params(), batch_patches(states))
+    stream = torch.cuda.Stream()
+    try:
+        assert capi.sf_batch_launches_per_step(b) == 4
+        with torch.cuda.stream(stream):
+            capi.sf_batch_tune(b, stream.cuda_stream)  # nothing to tune: no persistent items
+            capi.sf_batch_capture(b, stream.cuda_stream)
+            capi.sf_batch_launch(b, stream.cuda_stream)
+        stream.synchronize()
+    finally:
+        capi.sf_batch_destroy(b)
+    for st in states:
+        G = oracle.ghosted(st.U0.copy())
+        oracle.rk4_step(oracle.Z4, G, st.dx, st.dt, oracle.params())
+        want = oracle.interior(G)
+        got = st.fields().cpu().numpy()  # flat-space offsets added back
+        bound = 4 * 64 / 12 * eps32 * st.dt / min(st.dx) ** 2 / 1e-2
+        for f in range(want.shape[0]):
+            e = np.abs(got[f] - want[f]).max() / max(np.abs(want[f]).max(), 1e-2)
+            assert e < bound, (st.n, f, e, bound)

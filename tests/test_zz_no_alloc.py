@@ -28,7 +28,12 @@ def states_for(table, precision):
             U0 = 1e-2 * U0
         else:
             U0, _ = inputs.z4_perturbed(n, seed=q, amp=0.03)
-        st = PatchState(system, n, (h, h, h), t["dt"], precision=precision)
+        # rows kept off a multiple of 4 floats: sf_batch would send float CCZ4
+        # patches with 16-byte rows to its TMA-staged kernel, and this test
+        # compares the two entry points on the one persistent kernel they share
+        row = n[0] + 6
+        st = PatchState(system, n, (h, h, h), t["dt"], precision=precision,
+                        x_pitch=row + 1 if row % 4 == 0 else row)
         st.upload(U0)
         out.append(st)
     return out
