@@ -537,11 +537,14 @@ def _amr_rows(hbm_peak: float) -> list[dict]:
     # sub-cycled two-level CCZ4 step: periodic 64^3 coarse, 64^3 fine patch (ratio 2) inside
     nc = (64, 64, 64)
     Uc, dxc = inputs.z4_minkowski_noise(nc, seed=0, amp=1e-10)
-    coarse = PatchState(capi.SF_Z4, nc, dxc, 0.25 * dxc[0], precision=capi.SF_FP32_BULK_DW)
+    # rows of 72 floats (16 bytes): both levels step with the TMA-staged kernel
+    coarse = PatchState(capi.SF_Z4, nc, dxc, 0.25 * dxc[0], precision=capi.SF_FP32_BULK_DW,
+                        x_pitch=72)
     coarse.upload(Uc)
     nf = (64, 64, 64)
     fine = PatchState(capi.SF_Z4, nf, tuple(v / 2 for v in dxc), 0.125 * dxc[0],
-                      precision=capi.SF_FP32_BULK_DW, prm=capi.params(ghosts=capi.SF_GHOSTS_NONE))
+                      precision=capi.SF_FP32_BULK_DW, prm=capi.params(ghosts=capi.SF_GHOSTS_NONE),
+                      x_pitch=72)
     Uf, _ = inputs.z4_minkowski_noise(nf, seed=1, amp=1e-10)
     fine.upload(Uf)
     pair = amr.SubcycledPair(coarse, fine, 2, (16, 16, 16))

@@ -17,7 +17,8 @@ sf_status launch_wave(const sf_params& prm, const sf_patch& p, const StageArgs& 
 sf_status launch_z4(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                     void* rhs_out, cudaStream_t st);
 // TMA-staged CCZ4 kernel (sf_z4_tma.cu) and the layouts it serves
-bool z4_tma_eligible(const sf_params& prm, const sf_patch& p);
+bool z4_tma_eligible(const sf_params& prm, const sf_patch& p);      // padded 96^3, compile-time strides
+bool z4_tma_any_eligible(const sf_params& prm, const sf_patch& p);  // any size, 16-byte pitches
 sf_status launch_z4_tma(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                         void* rhs_out, cudaStream_t st);
 // TMA-staged CCZ4 kernel over the tiles of many patches (sf_z4_tma.cu), for

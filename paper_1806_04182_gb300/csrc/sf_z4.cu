@@ -1,6 +1,7 @@
 // Standalone CCZ4 stage kernel (one launch per patch); the per-point
-// right-hand side lives in sf_z4.cuh.  Float storage on the padded 96^3
-// layout goes to the TMA-staged kernel (sf_z4_tma.cu).  Layouts with the
+// right-hand side lives in sf_z4.cuh.  Float storage with centred advection
+// and row / plane / field pitches on 16-byte boundaries goes to the
+// TMA-staged kernels (sf_z4_tma.cu).  Layouts with the
 // strides of a dense 96^3 patch with 3 ghosts get a kernel with compile-time
 // strides; every other layout, and one-sided advection, uses runtime strides.
 #include "sf_internal.cuh"
@@ -55,7 +56,7 @@ static sf_status launch(const sf_params& prm, const sf_patch& p, const StageArgs
 
 sf_status launch_z4(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                     void* rhs_out, cudaStream_t st) {
-  if (z4_tma_eligible(prm, p)) return launch_z4_tma(prm, p, s, stage, rhs_out, st);
+  if (z4_tma_any_eligible(prm, p)) return launch_z4_tma(prm, p, s, stage, rhs_out, st);
   if (p.precision == SF_FP64) return launch<double, double>(prm, p, s, stage, rhs_out, st);
   if (p.precision == SF_FP32_BULK_DW) return launch<float, dw>(prm, p, s, stage, rhs_out, st);
   return launch<float, double>(prm, p, s, stage, rhs_out, st);

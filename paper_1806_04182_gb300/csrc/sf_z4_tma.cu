@@ -215,63 +215,48 @@ __global__ void __launch_bounds__(Cfg<BY, KS>::kThreads, Cfg<BY, KS>::kMinBlocks
   write_fields<float, 25>(a, s, im, c, i, j, k, rbuf + tid, C::kThreads);
 }
 
-// The same staged stage over the 32 x 12 x 1 tiles of many patches (the
-// CCZ4 patches of a batch): one CTA per tile, the tile's patch from `tiles`,
-// its arguments copied from `args` into shared memory (uniform reads), its
-// stage input's tensor map from `maps` (three per patch, for the u_n,
-// u_stage and u_next buffer roles; `role` picks this stage's input).  Runtime
-// strides; a tile may overhang the patch in x and y: the TMA box reads zeros
-// beyond the array, the overhanging threads still take part in the ring
-// (they compute on clamped centre values) and write nothing.
+// One 32 x 12 x 1 tile at interior (x0, y0, z0) of a patch with runtime
+// strides (row, plane and field pitches multiples of 4 floats).  The tile may
+// overhang the patch in x and y: the TMA box reads zeros beyond the array,
+// the overhanging threads still take part in the ring (they compute on
+// clamped centre values) and write nothing.  `a` may live in shared memory.
 template <typename H>
-__global__ void __launch_bounds__(Cfg<kBY, kKS>::kThreads, 1)
-    z4_tma_batch_kernel(const CUtensorMap* __restrict__ maps, int role,
-                        const PatchArgs<float>* __restrict__ args, const TmaTile* __restrict__ tl,
-                        StageArgs s, Z4Coef<float> zc) {
+__device__ __forceinline__ void tma_tile_runtime(const CUtensorMap* map, const PatchArgs<float>& a,
+                                                 const StageArgs& s, const Z4Coef<float>& zc,
+                                                 int x0, int y0, int k, unsigned char* smem) {
   using C = Cfg<kBY, kKS>;
   constexpr int kSlots = kKS;
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ PatchArgs<float> pa;
   float* tiles = reinterpret_cast<float*>(smem);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kSlots * C::kSlotFloats * 4);
   uint64_t* empty = full + kSlots;
   const int tid = threadIdx.y * 32 + threadIdx.x;
-  const TmaTile w = tl[blockIdx.x];
-  {
-    static_assert(sizeof(PatchArgs<float>) % 4 == 0, "word copy");
-    const int* from = reinterpret_cast<const int*>(args + w.patch);
-    int* to = reinterpret_cast<int*>(&pa);
-    for (int q = tid; q < (int)(sizeof(PatchArgs<float>) / 4); q += C::kThreads) to[q] = from[q];
-  }
-  if (tid == 0) {
-    for (int q = 0; q < kSlots; ++q) {
-      mbar_init(&full[q], 1);
-      mbar_init(&empty[q], kBY);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  __syncthreads();
-  const PatchArgs<float>& a = pa;
-  const int i = w.x0 + threadIdx.x, j = w.y0 + threadIdx.y, k = w.z0;
+  const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
   const bool valid = i < a.n[0] && j < a.n[1];
   const int ic = min(i, a.n[0] - 1), jc = min(j, a.n[1] - 1);
   const long long c = (long long)(k + 3) * a.sz + (long long)(jc + 3) * a.sy + (ic + 3);
+  if (threadIdx.x == 0 && s.mode == 0 && x0 + 32 <= a.n[0] && j < a.n[1]) {
+    // rows start on 16 bytes, so ghosted x = x0 does too: 144 B cover the
+    // warp's 32 points (byte offsets 12 .. 139) inside the row
+    const long long c0 = c - 3;
+    if (!s.un_alias) prefetch_rows(a.un + c0, a.sf);
+    if (s.rk == SF_RK4 && s.stage > 0) prefetch_rows(a.acc + c0, a.sf);
+    if (s.kahan && s.stage == 3) prefetch_rows(a.kh + c0, a.sf);
+  }
   TmaSrc<kBY, kKS> src;
   src.u = a.us + c;
   src.F = a.sf;
   src.tiles = tiles;
   src.full = full;
   src.empty = empty;
-  src.map = maps + 3 * w.patch + role;
+  src.map = map;
   src.status = s.status;
   src.local = (3 * C::TY + threadIdx.y + 3) * TX + threadIdx.x + 3;
   src.use = 0;
   src.cur = 0;
   src.nuses = zc.shift_frozen ? 22 : 25;
   src.issued = 0;
-  src.gx = w.x0;  // interior x0 - 3, in ghosted coordinates
-  src.gy = w.y0;
+  src.gx = x0;  // interior x0 - 3, in ghosted coordinates
+  src.gy = y0;
   src.gz = k;
   src.leader = tid == 0;
   src.lane0 = threadIdx.x == 0;
@@ -283,6 +268,58 @@ __global__ void __launch_bounds__(Cfg<kBY, kKS>::kThreads, 1)
     const Images im = ghost_images(a, s, i, j, k);
     write_fields<float, 25>(a, s, im, c, i, j, k, rbuf + tid, C::kThreads);
   }
+}
+
+__device__ __forceinline__ void init_ring(unsigned char* smem) {
+  using C = Cfg<kBY, kKS>;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kKS * C::kSlotFloats * 4);
+  uint64_t* empty = full + kKS;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    for (int q = 0; q < kKS; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], kBY);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+}
+
+// Any patch size and any 16-byte pitches (one patch, map and arguments as
+// kernel parameters): grid (ceil(nx / 32), ceil(ny / 12), nz).
+template <typename H>
+__global__ void __launch_bounds__(Cfg<kBY, kKS>::kThreads, 1)
+    z4_tma_any_kernel(const __grid_constant__ CUtensorMap map, PatchArgs<float> a, StageArgs s,
+                      Z4Coef<float> zc) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  init_ring(smem);
+  __syncthreads();
+  tma_tile_runtime<H>(&map, a, s, zc, blockIdx.x * 32, blockIdx.y * kBY, blockIdx.z, smem);
+}
+
+// The same over the tiles of many patches (the CCZ4 patches of a batch): one
+// CTA per tile, the tile's patch from `tl`, its arguments copied from `args`
+// into shared memory (uniform reads), its stage input's tensor map from
+// `maps` (three per patch, for the u_n, u_stage and u_next buffer roles;
+// `role` picks this stage's input).
+template <typename H>
+__global__ void __launch_bounds__(Cfg<kBY, kKS>::kThreads, 1)
+    z4_tma_batch_kernel(const CUtensorMap* __restrict__ maps, int role,
+                        const PatchArgs<float>* __restrict__ args, const TmaTile* __restrict__ tl,
+                        StageArgs s, Z4Coef<float> zc) {
+  using C = Cfg<kBY, kKS>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ PatchArgs<float> pa;
+  const TmaTile w = tl[blockIdx.x];
+  {
+    static_assert(sizeof(PatchArgs<float>) % 4 == 0, "word copy");
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int* from = reinterpret_cast<const int*>(args + w.patch);
+    int* to = reinterpret_cast<int*>(&pa);
+    for (int q = tid; q < (int)(sizeof(PatchArgs<float>) / 4); q += C::kThreads) to[q] = from[q];
+  }
+  init_ring(smem);
+  __syncthreads();
+  tma_tile_runtime<H>(maps + 3 * w.patch + role, pa, s, zc, w.x0, w.y0, w.z0, smem);
 }
 
 namespace {
@@ -405,10 +442,45 @@ sf_status launch_z4_tma_batch(const sf_params& prm, int precision, const void* d
   return launch_tma_batch<double>(prm, d_maps, role, d_args, d_tiles, ntiles, s, st);
 }
 
+namespace {
+template <typename H>
+sf_status launch_tma_any(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
+                         void* rhs_out, cudaStream_t st) {
+  using C = Cfg<kBY, kKS>;
+  alignas(64) unsigned char map[kTmaMapBytes];
+  sf_status e = encode_z4_tma_map(map, p, p.u_stage);
+  if (e) return e;
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(z4_tma_any_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         C::kSmemBytes);
+  });
+  PatchArgs<float> a = make_args<float>(prm, p, stage, 25, rhs_out);
+  const Z4Coef<float> zc = z4_coef<float>(prm);
+  dim3 grid((p.n[0] + 31) / 32, (p.n[1] + kBY - 1) / kBY, p.n[2]);
+  z4_tma_any_kernel<H><<<grid, dim3(32, kBY, 1), C::kSmemBytes, st>>>(
+      *reinterpret_cast<const CUtensorMap*>(map), a, s, zc);
+  return after_launch("z4_tma_any_kernel");
+}
+}  // namespace
+
+// Float storage with centred advection and 16-byte pitches and arrays, any
+// interior size: the compile-time-stride kernel for the padded 96^3 layout,
+// the runtime-stride kernel (tiles may overhang) for every other.
+bool z4_tma_any_eligible(const sf_params& prm, const sf_patch& p) {
+  if (p.precision == SF_FP64 || prm.lopsided) return false;
+  if (p.ghost != 3 || p.sy % 4 || p.sz % 4 || p.sf % 4) return false;
+  return reinterpret_cast<uintptr_t>(p.u_stage) % 16 == 0;
+}
+
 sf_status launch_z4_tma(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                         void* rhs_out, cudaStream_t st) {
-  if (p.precision == SF_FP32_BULK_DW) return launch_tma<dw, kBY, kKS>(prm, p, s, stage, rhs_out, st);
-  return launch_tma<double, kBY, kKS>(prm, p, s, stage, rhs_out, st);
+  if (z4_tma_eligible(prm, p)) {
+    if (p.precision == SF_FP32_BULK_DW) return launch_tma<dw, kBY, kKS>(prm, p, s, stage, rhs_out, st);
+    return launch_tma<double, kBY, kKS>(prm, p, s, stage, rhs_out, st);
+  }
+  if (p.precision == SF_FP32_BULK_DW) return launch_tma_any<dw>(prm, p, s, stage, rhs_out, st);
+  return launch_tma_any<double>(prm, p, s, stage, rhs_out, st);
 }
 
 }  // namespace sf

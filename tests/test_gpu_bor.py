@@ -98,17 +98,23 @@ def test_bor_prolong_rejects_bad_arguments():
                             out.data_ptr(), 2, 4, 8)
 
 
-def _pair(system, precision, nc, nf_coarse, at, R, data, dt_factor, steps):
+def _pitch(n, pitch4):
+    """Row pitch: 16-byte rows (the TMA-staged float CCZ4 kernel) or dense."""
+    return (n[0] + 6 + 3) // 4 * 4 if pitch4 else None
+
+
+def _pair(system, precision, nc, nf_coarse, at, R, data, dt_factor, steps, pitch4=False):
     """Run a SubcycledPair; returns (pair, coarse dx, coarse dt)."""
     U0c, dxc = data(nc)
     dtc = dt_factor * min(dxc)
     prm = capi.params()
-    coarse = PatchState(system, nc, dxc, dtc, precision=precision, prm=prm)
+    coarse = PatchState(system, nc, dxc, dtc, precision=precision, prm=prm,
+                        x_pitch=_pitch(nc, pitch4))
     coarse.upload(U0c)
     nfine = tuple(R * v for v in nf_coarse)
     dxf = tuple(v / R for v in dxc)
     fine = PatchState(system, nfine, dxf, dtc / R, precision=precision,
-                      prm=capi.params(ghosts=capi.SF_GHOSTS_NONE))
+                      prm=capi.params(ghosts=capi.SF_GHOSTS_NONE), x_pitch=_pitch(nfine, pitch4))
     Uf_all, _ = data(tuple(R * v for v in nc))
     sub = Uf_all[:, R * at[2]:R * at[2] + nfine[2], R * at[1]:R * at[1] + nfine[1],
                  R * at[0]:R * at[0] + nfine[0]]
@@ -141,6 +147,28 @@ def test_ratio_one_equals_uniform_run(system, data):
         assert err <= 1e-11 * scale, (f, err, scale)
     # the coarse level, fine values injected back, equals the uniform run too
     np.testing.assert_allclose(pair.coarse.fields().cpu().numpy(), W, rtol=0, atol=1e-11 * np.abs(W).max())
+
+
+def test_ratio_one_equals_uniform_run_float_tma():
+    # FP32-bulk CCZ4 on 16-byte rows (the TMA-staged kernel on both levels and
+    # for the uniform run), ratio 1: the fine patch follows the uniform run to
+    # float rounding of the 1/dx^2 stencils, accumulated over 3 steps
+    data = lambda n: inputs.z4_perturbed(n, seed=3, amp=0.04)
+    nc, at, m = (16, 14, 12), (4, 3, 3), (8, 7, 6)
+    steps = 3
+    pair = _pair(capi.SF_Z4, capi.SF_FP32_BULK_DW, nc, m, at, 1, data, 0.2, steps, pitch4=True)
+    U0, dx = data(nc)
+    whole = PatchState(capi.SF_Z4, nc, dx, 0.2 * min(dx), precision=capi.SF_FP32_BULK_DW,
+                       x_pitch=_pitch(nc, True))
+    whole.upload(U0)
+    whole.step(steps)
+    torch.cuda.synchronize()
+    W = whole.fields().cpu().numpy()
+    want = W[:, at[2]:at[2] + m[2], at[1]:at[1] + m[1], at[0]:at[0] + m[0]]
+    got = pair.fine.fields().cpu().numpy()
+    eps32 = float(np.finfo(np.float32).eps)
+    bound = 2 * steps * 4 * 64 / 12 * eps32 * 0.2 * min(dx) / min(dx) ** 2
+    assert np.abs(got - want).max() <= bound, (np.abs(got - want).max(), bound)
 
 
 def test_subcycled_plane_wave_converges_at_fourth_order():

@@ -383,6 +383,28 @@ def test_z4_tma_kernel_matches_oracle(precision, nx, nz):
         assert rel_err(got[s], dense[s], floor=1e-2).max() < bound
 
 
+# Any patch size with 16-byte row pitch: the runtime-stride TMA kernel, whose
+# 32 x 12 tiles overhang the patch in x and y.  Against the oracle with the
+# float bound, and against the global-load kernel on a pitch that is not a
+# multiple of 4 floats.
+@pytest.mark.parametrize("precision", [capi.SF_FP32_BULK, capi.SF_FP32_BULK_DW])
+@pytest.mark.parametrize("n", [(37, 13, 5), (20, 30, 4), (64, 12, 3)])
+def test_z4_tma_any_size_matches_oracle(precision, n):
+    U0, dx = inputs.z4_perturbed(n, seed=6, amp=0.05)
+    prm = capi.params()
+    dt = 0.25 * min(dx)
+    eps32 = float(np.finfo(np.float32).eps)
+    bound = 4 * 64 / 12 * eps32 * dt / min(dx) ** 2 / 1e-2
+    row = n[0] + 6
+    got = run_stages(capi.SF_Z4, U0, dx, dt, prm, precision=precision, pitch=(row + 3) // 4 * 4)
+    dense = run_stages(capi.SF_Z4, U0, dx, dt, prm, precision=precision,
+                       pitch=row + 1 if row % 4 == 0 else row)
+    want = oracle_stages(oracle.Z4, U0, dx, dt, prm)
+    for s in range(4):
+        assert rel_err(got[s], want[s], floor=1e-2).max() < bound, s
+        assert rel_err(got[s], dense[s], floor=1e-2).max() < bound, s
+
+
 def test_z4_tma_kernel_frozen_shift_gauge_wave():
     # harmonic slicing and a frozen shift: the last three fields' stencils are
     # never opened, so the staged sequence is 22 boxes long
