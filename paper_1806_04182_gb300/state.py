@@ -260,3 +260,80 @@ class PatchState:
             st.E.copy_(torch.from_numpy(z["E"]))
         return st, meta["step"], meta["t"]
 
+
+class HostPipeline:
+    """RK steps of patch states that live in host memory.
+
+    Each ``step(host_in, host_out)`` copies a ghosted U^n (the layout and
+    storage convention of ``PatchState.A``, in pinned host memory) to the
+    device, runs one RK step there and copies U^{n+1} back into ``host_out``.
+    Two device ``PatchState``s alternate between steps, and the host-to-device
+    and device-to-host copies run on streams of their own, so the upload of
+    step k+1 and the download of step k-1 overlap the stages of step k; the
+    stages of successive steps stay in order on one compute stream.  A step's
+    host buffers must stay untouched until ``synchronize()`` (or a later
+    step's copies) has finished with them; ``host_out`` holds U^{n+1} after
+    ``synchronize()``.  The float Kahan compensation restarts from zero with
+    every uploaded state.
+    """
+
+    def __init__(self, *args, **kw):
+        """Arguments as for ``PatchState`` (one patch description)."""
+        self.states = (PatchState(*args, **kw), PatchState(*args, **kw))
+        cur = torch.cuda.current_stream()
+        self.compute = torch.cuda.Stream()
+        self.up = torch.cuda.Stream()
+        self.down = torch.cuda.Stream()
+        for st_ in (self.compute, self.up, self.down):
+            st_.wait_stream(cur)  # the buffers' zero fill
+        self._uploaded = [torch.cuda.Event(), torch.cuda.Event()]
+        self._computed = [torch.cuda.Event(), torch.cuda.Event()]
+        self._downloaded = [torch.cuda.Event(), torch.cuda.Event()]
+        self._used = [False, False]
+        self._k = 0
+
+    @property
+    def shape(self):
+        return self.states[0].shape
+
+    @property
+    def dtype(self):
+        return self.states[0].dtype
+
+    def step(self, host_in: torch.Tensor, host_out: torch.Tensor) -> None:
+        q = self._k % 2
+        st = self.states[q]
+        if self._used[q]:
+            # buffer q was last read by the download of step k-2, which itself
+            # followed that step's stages
+            self.up.wait_event(self._downloaded[q])
+        with torch.cuda.stream(self.up):
+            st.A.copy_(host_in, non_blocking=True)
+            if st.E is not None:
+                st.E.zero_()
+        self._uploaded[q].record(self.up)
+        self.compute.wait_event(self._uploaded[q])
+        st.step(1, stream=self.compute)
+        self._computed[q].record(self.compute)
+        self.down.wait_event(self._computed[q])
+        with torch.cuda.stream(self.down):
+            host_out.copy_(st.A, non_blocking=True)
+        self._downloaded[q].record(self.down)
+        self._used[q] = True
+        self._k += 1
+
+    def join(self, stream: torch.cuda.Stream | None = None) -> None:
+        """Make `stream` (default: the current one) wait for all queued work."""
+        stream = stream if stream is not None else torch.cuda.current_stream()
+        for st_ in (self.up, self.compute, self.down):
+            stream.wait_stream(st_)
+
+    def start(self, stream: torch.cuda.Stream | None = None) -> None:
+        """Order the pipeline's streams after the work queued on `stream`."""
+        stream = stream if stream is not None else torch.cuda.current_stream()
+        for st_ in (self.up, self.compute, self.down):
+            st_.wait_stream(stream)
+
+    def synchronize(self) -> None:
+        for st_ in (self.up, self.compute, self.down):
+            st_.synchronize()
