@@ -145,15 +145,22 @@ def kernel_source_hash() -> str:
 
 def profiled_traffic():
     """(bytes per launch, source hash) from the profile summary, or (None, None)."""
+    v = profiled_values()
+    return v.get("traffic_bytes_per_launch"), v.get("kernel_source_sha256_16")
+
+
+def profiled_values() -> dict:
+    """The `key: value` lines at the end of the profile summary."""
+    out = {}
     if not os.path.exists(PROFILE):
-        return None, None
-    traffic = src = None
+        return out
     for line in open(PROFILE):
-        if line.startswith("traffic_bytes_per_launch:"):
-            traffic = float(line.split(":")[1])
+        for key in ("traffic_bytes_per_launch", "warp_instructions_per_launch"):
+            if line.startswith(key + ":"):
+                out[key] = float(line.split(":")[1])
         if line.startswith("kernel_source_sha256_16:"):
-            src = line.split(":")[1].strip()
-    return traffic, src
+            out["kernel_source_sha256_16"] = line.split(":")[1].strip()
+    return out
 
 
 # ---------------------------------------------------------------- ranks
@@ -355,6 +362,7 @@ def gpu_arm(args):
             "fp64_frac": r64["value"] * FLOPS_PER_CELL_UPDATE / 1e12 / FP64_PEAK_TFLOPS,
             "fp64_peak": FP64_PEAK_TFLOPS,
             "fp64_peak_source": "measured FMA probe, 1/58 of the FP32 rate"},
+        "issue_roofline": issue_roofline(r32, clocks),
         "fp32_bulk_fp64_islands": {
             "value": r32n["value"], "ms_per_step": r32n["ms_per_step"],
             "achieved_gbs": r32n["achieved_gbs"], "hbm_frac": r32n["achieved_gbs"] / hbm_peak,
@@ -374,6 +382,25 @@ def gpu_arm(args):
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
     return line
+
+
+def issue_roofline(r32, clocks) -> dict | None:
+    """The bound the float CCZ4 kernel actually meets: instruction issue.
+    achieved = warp instructions per launch (ncu count of the same kernel
+    source, from the profile summary) / mean CUDA-event stage time; peak = one
+    warp instruction per cycle on each of the 4 schedulers of the 152 SMs at
+    the median SM clock sampled during the timed region."""
+    v = profiled_values()
+    inst = v.get("warp_instructions_per_launch")
+    if inst is None or v.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    mhz = clocks.get("sm_mhz") or 2070.0
+    t = statistics.fmean(r32["per_stage_ms"]) * 1e-3
+    peak = 152 * 4 * mhz * 1e6
+    return {"bound": "issue", "warp_instructions_per_launch": inst, "achieved": inst / t,
+            "peak": peak, "unit": "warp instructions/s", "frac": inst / t / peak,
+            "peak_source": f"152 SMs x 4 schedulers x 1 instruction/cycle x {mhz:.0f} MHz "
+                           "(median sampled SM clock)"}
 
 
 # ---------------------------------------------------------------- other rows
