@@ -22,12 +22,18 @@ Functions and what pins them (tests/test_oracle_*.py):
                    circularly polarised Alfven wave (Sec. IV.B.1).
   rhs(Z4)          Sec. V.  Pinned: Minkowski gives zero, gauge-wave exact
                    solution (4th-order truncation), flat metric in curvilinear
-                   coordinates (Ricci and Christoffels), lapse Laplacian.
-                   The Z^i / Theta coupling terms vanish on every exact
-                   solution available: parity unpinned for those terms.
+                   coordinates (Ricci and Christoffels), lapse Laplacian;
+                   every algebraic term (Theta, Z, K, A~ products, damping,
+                   gauge) on homogeneous states against the damped covariant
+                   Z4 equations in 3+1 form.  The terms that couple Z or Theta
+                   to gradients (Z^i d_i alpha, Z^k d_k chi in R^chi_ij,
+                   Theta d_i alpha / alpha in d/dt Gammahat) vanish on every
+                   exact solution used: parity unpinned for those terms.
   rk4_step         Sec. II.C Table RK44.  Pinned: amplification polynomial
                    of a single Fourier mode.
-  ssprk3_step      App. C/D (garbles read as stated in the design doc).  Pinned:
+  ssprk3_step      App. C/D, read as U(3) = U + k1/4 + k2/4 and
+                   U^{n+1} = U + (k1 + k2 + 4 k3)/6 (the printed k2/4 + k3/4
+                   and (k1 + 2 k2 + 4 k3)/6 are inconsistent).  Pinned:
                    third-order amplification polynomial; equal to the
                    Shu-Osher form.
   misfit_gradient  discrete adjoint of the RK4 wave evolution.  Pinned:

@@ -22,7 +22,7 @@
 // (i,j,k), 0 <= i < nx, sits at x offset i+g.  RHS outputs are interior-only
 // arrays nf x nz x ny x nx.
 //
-// Parity status per function is stated in oracle/__init__.py and the design doc.
+// Parity status per function is stated in oracle/__init__.py.
 
 #include <cmath>
 #include <cstdint>

@@ -9,7 +9,7 @@ otherwise), floored at 1e-12 (noise data) or 1e-3 (gauge wave).  Bounds: the
 noise data live at 1e-10 with float storage of their deviations (relative
 precision 6e-8); 100 steps x 4 stages of rounding that grows through the
 1/dx^2 stencils keep the relative error of every field below 1e-3.  The table
-is printed (pytest -s) and recorded in DESIGN.md.
+is printed (pytest -s).
 """
 import numpy as np
 import pytest

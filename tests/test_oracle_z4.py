@@ -13,7 +13,9 @@
 * The same flat metric with a non-trivial lapse: d/dt Khat = -Laplacian(alpha)
   and d/dt A~_ij = -chi [nabla_i nabla_j alpha]^TF, computed here with SymPy
   from the physical metric (Laplace-Beltrami, physical Christoffels).
-* Z^i / Theta coupling terms vanish on all of these; they stay unpinned.
+* Z^i / Theta coupling terms vanish on all of these; their algebraic parts are
+  pinned on homogeneous states in test_oracle_z4_homogeneous.py, the parts that
+  multiply gradients stay unpinned.
 """
 import math
 
