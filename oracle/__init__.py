@@ -24,11 +24,11 @@ Functions and what pins them (tests/test_oracle_*.py):
                    solution (4th-order truncation), flat metric in curvilinear
                    coordinates (Ricci and Christoffels), lapse Laplacian;
                    every algebraic term (Theta, Z, K, A~ products, damping,
-                   gauge) on homogeneous states against the damped covariant
-                   Z4 equations in 3+1 form.  The terms that couple Z or Theta
-                   to gradients (Z^i d_i alpha, Z^k d_k chi in R^chi_ij,
-                   Theta d_i alpha / alpha in d/dt Gammahat) vanish on every
-                   exact solution used: parity unpinned for those terms.
+                   gauge) on homogeneous states, and the whole right-hand
+                   side (gradient couplings of Z and Theta, conformal Ricci,
+                   shift terms) on polynomial states where the stencils are
+                   exact, both against the damped covariant Z4 equations in
+                   3+1 form mapped to the CCZ4 variables.
   rk4_step         Sec. II.C Table RK44.  Pinned: amplification polynomial
                    of a single Fourier mode.
   ssprk3_step      App. C/D, read as U(3) = U + k1/4 + k2/4 and

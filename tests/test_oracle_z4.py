@@ -13,9 +13,10 @@
 * The same flat metric with a non-trivial lapse: d/dt Khat = -Laplacian(alpha)
   and d/dt A~_ij = -chi [nabla_i nabla_j alpha]^TF, computed here with SymPy
   from the physical metric (Laplace-Beltrami, physical Christoffels).
-* Z^i / Theta coupling terms vanish on all of these; their algebraic parts are
-  pinned on homogeneous states in test_oracle_z4_homogeneous.py, the parts that
-  multiply gradients stay unpinned.
+* Z^i / Theta coupling terms vanish on all of these; they are pinned on
+  homogeneous states (test_oracle_z4_homogeneous.py) and on polynomial states
+  with gradients and shift (test_oracle_z4_polynomial.py) against the damped
+  covariant Z4 equations.
 """
 import math
 
