@@ -135,11 +135,16 @@ KERNEL_SOURCES = ["sf_common.cuh", "sf_dw.cuh", "sf_mbar.cuh", "sf_pair.cuh", "s
 
 
 def kernel_source_hash() -> str:
+    """Hash of the headline kernel's sources with // comments, trailing blanks
+    and empty lines removed, so that comment edits keep the profiled counters."""
     import hashlib
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1806_04182_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1806_04182_gb300", "csrc", name)) as f:
+            for line in f:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

@@ -1,6 +1,15 @@
-// CCZ4 stage kernel with TMA-staged stencils (float storage, centred
+// CCZ4 stage kernels with TMA-staged stencils (float storage, centred
 // advection).  The per-point right-hand side is the same z4_cell as the
-// global-load kernel; only its stencil source differs.
+// global-load kernel; only its stencil source differs.  Three kernels share
+// the staging scheme below:
+//   z4_tma_kernel        the padded 96^3 layout, compile-time global strides
+//                        (the benchmark's configuration);
+//   z4_tma_any_kernel    any patch size with row, plane and field pitches on
+//                        16-byte boundaries, runtime strides, tiles that may
+//                        overhang the patch;
+//   z4_tma_batch_kernel  the tiles of many such patches in one launch (the
+//                        CCZ4 patches of sf_batch), arguments and tensor maps
+//                        read from device memory.
 //
 // Each CTA computes a 32 x 12 x 1 tile of points, one warp per row.  The
 // CCZ4 right-hand side consumes the 25 fields' stencils one field at a time in
