@@ -286,6 +286,12 @@ class HostPipeline:
         self.down = torch.cuda.Stream()
         for st_ in (self.compute, self.up, self.down):
             st_.wait_stream(cur)  # the buffers' zero fill
+            # the caching allocator must not hand these buffers out again while
+            # work queued on the pipeline's streams still uses them
+            for state in self.states:
+                for t in (state.A, state.B, state.C, state.D, state.E):
+                    if t is not None:
+                        t.record_stream(st_)
         self._uploaded = [torch.cuda.Event(), torch.cuda.Event()]
         self._computed = [torch.cuda.Event(), torch.cuda.Event()]
         self._downloaded = [torch.cuda.Event(), torch.cuda.Event()]
