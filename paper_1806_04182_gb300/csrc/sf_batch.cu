@@ -7,8 +7,9 @@
 // waits on another, so the queue has no spin-waits.
 // Float CCZ4 patches whose layout suits TMA (pitches and arrays on 16-byte
 // boundaries, centred advection) go instead to the TMA-staged kernel, one
-// launch per stage over all their 32 x 12 x 1 tiles, ahead of the persistent
-// launch that takes the remaining patches; both are captured in the graph.
+// launch per stage and tile width over all their 32 x 12 x 1 or 16 x 24 x 1
+// tiles, ahead of the persistent launch that takes the remaining patches;
+// all are captured in the graph.
 //
 // Buffer roles per patch (sf_patch fields as passed to sf_batch_create):
 //   u_n = A: the state U^n, updated in place by the last stage
@@ -101,8 +102,9 @@ struct sf_batch {
   unsigned int* d_counter = nullptr;
   std::vector<char> tma;  // patch q goes to the TMA-staged CCZ4 kernel
   void* d_maps = nullptr; // tensor maps, 3 per patch (u_n, u_stage, u_next roles)
-  TmaTile* d_tiles = nullptr;
-  int ntiles = 0;
+  TmaTile* d_tiles = nullptr;   // 32 x 12 tiles, then 16 x 24 tiles
+  int ntiles = 0;               // all TMA tiles
+  int ntiles16 = 0;             // of which the last ntiles16 are 16 x 24
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -174,38 +176,44 @@ sf_status build_items(sf_batch* b, int only_class) {
   return SF_OK;
 }
 
-// Tensor maps and the tile list of the patches served by the TMA-staged
-// CCZ4 kernel (float precision, eligible layouts).
+// Tensor maps and the tile lists of the patches served by the TMA-staged
+// CCZ4 kernel (float precision, eligible layouts).  Each patch takes the
+// tile width (32 x 12 or 16 x 24 points, the same cost per tile) that covers
+// it with fewer tiles, i.e. with fewer idle lanes where tiles overhang it.
 sf_status build_tma(sf_batch* b) {
   b->tma.assign(b->npatch, 0);
+  b->ntiles = b->ntiles16 = 0;
   if (b->precision == SF_FP64) return SF_OK;
-  std::vector<unsigned char> maps;
-  std::vector<TmaTile> tiles;
+  std::vector<unsigned char> maps((size_t)3 * b->npatch * kTmaMapBytes, 0);
+  std::vector<TmaTile> tiles[2];  // [0]: 32 x 12, [1]: 16 x 24
   for (int q = 0; q < b->npatch; ++q) {
     const sf_patch& p = b->patches[q];
     if (!z4_tma_batch_eligible(b->prm, p)) continue;
     b->tma[q] = 1;
-  }
-  maps.assign((size_t)3 * b->npatch * kTmaMapBytes, 0);
-  for (int q = 0; q < b->npatch; ++q) {
-    if (!b->tma[q]) continue;
-    const sf_patch& p = b->patches[q];
+    auto count = [&](int tx, int ty) {
+      return (long long)((p.n[0] + tx - 1) / tx) * ((p.n[1] + ty - 1) / ty);
+    };
+    const int w = count(kTmaTileX16, kTmaTileY16) < count(kTmaTileX, kTmaTileY) ? 1 : 0;
+    const int tx = w ? kTmaTileX16 : kTmaTileX, ty = w ? kTmaTileY16 : kTmaTileY;
     const void* arr[3] = {p.u_n, p.u_stage, p.u_next};
     for (int r = 0; r < 3; ++r) {
-      sf_status e = encode_z4_tma_map(maps.data() + ((size_t)3 * q + r) * kTmaMapBytes, p, arr[r]);
+      sf_status e = encode_z4_tma_map(maps.data() + ((size_t)3 * q + r) * kTmaMapBytes, p, arr[r], tx);
       if (e) return e;
     }
     for (int z = 0; z < p.n[2]; ++z)
-      for (int y = 0; y < p.n[1]; y += kTmaTileY)
-        for (int x = 0; x < p.n[0]; x += kTmaTileX) tiles.push_back(TmaTile{q, x, y, z});
+      for (int y = 0; y < p.n[1]; y += ty)
+        for (int x = 0; x < p.n[0]; x += tx) tiles[w].push_back(TmaTile{q, x, y, z});
   }
-  b->ntiles = (int)tiles.size();
-  if (tiles.empty()) return SF_OK;
+  b->ntiles16 = (int)tiles[1].size();
+  tiles[0].insert(tiles[0].end(), tiles[1].begin(), tiles[1].end());
+  std::vector<TmaTile>& all = tiles[0];
+  b->ntiles = (int)all.size();
+  if (all.empty()) return SF_OK;
   if (cudaMalloc(&b->d_maps, maps.size()) != cudaSuccess ||
-      cudaMalloc(&b->d_tiles, tiles.size() * sizeof(TmaTile)) != cudaSuccess)
+      cudaMalloc(&b->d_tiles, all.size() * sizeof(TmaTile)) != cudaSuccess)
     return set_error(SF_ECUDA, "batch: cudaMalloc of tensor maps failed");
   if (cudaMemcpy(b->d_maps, maps.data(), maps.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(TmaTile), cudaMemcpyHostToDevice) !=
+      cudaMemcpy(b->d_tiles, all.data(), all.size() * sizeof(TmaTile), cudaMemcpyHostToDevice) !=
           cudaSuccess)
     return set_error(SF_ECUDA, "batch: upload of tensor maps failed");
   return SF_OK;
@@ -231,8 +239,13 @@ sf_status launch_stage(sf_batch* b, int stage, cudaStream_t st, unsigned int* st
     const int role[4] = {0, 1, 2, 1};
     const PatchArgs<float>* fargs =
         static_cast<const PatchArgs<float>*>(b->d_args) + (size_t)stage * b->npatch;
+    const StageArgs sa = batch_stage_args(b, stage, status);
+    const int n32 = b->ntiles - b->ntiles16;
     sf_status e = launch_z4_tma_batch(b->prm, b->precision, b->d_maps, role[stage], fargs,
-                                      b->d_tiles, b->ntiles, batch_stage_args(b, stage, status), st);
+                                      b->d_tiles, n32, kTmaTileX, sa, st);
+    if (!e)
+      e = launch_z4_tma_batch(b->prm, b->precision, b->d_maps, role[stage], fargs, b->d_tiles + n32,
+                              b->ntiles16, kTmaTileX16, sa, st);
     if (e) return e;
     if (b->nitems == 0) return SF_OK;
   }
@@ -351,8 +364,8 @@ sf_status sf_batch_tune(sf_batch* b, void* stream) {
   cudaEventCreate(&e1);
   sf_status err = SF_OK;
   // the TMA-staged patches have a fixed tile: time the persistent kernel alone
-  const int ntiles = b->ntiles;
-  b->ntiles = 0;
+  const int ntiles = b->ntiles, ntiles16 = b->ntiles16;
+  b->ntiles = b->ntiles16 = 0;
   for (int cls = 0; cls < kClasses && !err; ++cls) {
     bool any = false;
     for (int q = 0; q < b->npatch; ++q) any |= class_of(b->patches[q]) == cls && !b->tma[q];
@@ -380,6 +393,7 @@ sf_status sf_batch_tune(sf_batch* b, void* stream) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->ntiles = ntiles;
+  b->ntiles16 = ntiles16;
   if (!err) err = build_items(b, -1);
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
@@ -429,7 +443,9 @@ sf_status sf_batch_launch(sf_batch* b, void* stream) {
 
 int32_t sf_batch_launches_per_step(const sf_batch* b) {
   if (!b) return 0;
-  const int per_stage = (b->ntiles > 0 ? 1 : 0) + (b->ntiles == 0 || b->nitems > 0 ? 1 : 0);
+  const int n32 = b->ntiles - b->ntiles16;
+  const int per_stage = (n32 > 0 ? 1 : 0) + (b->ntiles16 > 0 ? 1 : 0) +
+                        (b->ntiles == 0 || b->nitems > 0 ? 1 : 0);
   return 4 * per_stage;
 }
 

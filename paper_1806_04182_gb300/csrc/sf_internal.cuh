@@ -22,18 +22,20 @@ bool z4_tma_any_eligible(const sf_params& prm, const sf_patch& p);  // any size,
 sf_status launch_z4_tma(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                         void* rhs_out, cudaStream_t st);
 // TMA-staged CCZ4 kernel over the tiles of many patches (sf_z4_tma.cu), for
-// sf_batch: 32 x 12 x 1 tiles, tensor maps in device memory (3 per patch:
-// u_n, u_stage, u_next roles), the stage's u_stage role picked by `role`.
+// sf_batch: 32 x 12 x 1 or 16 x 24 x 1 tiles (a patch's maps are encoded for
+// its tile width), tensor maps in device memory (3 per patch: u_n, u_stage,
+// u_next roles), the stage's u_stage role picked by `role`.
 struct TmaTile {
   int patch, x0, y0, z0;
 };
-constexpr int kTmaTileX = 32, kTmaTileY = 12;
+constexpr int kTmaTileX = 32, kTmaTileY = 12;      // the wide tile
+constexpr int kTmaTileX16 = 16, kTmaTileY16 = 24;  // the narrow tile
 constexpr size_t kTmaMapBytes = 128;  // sizeof(CUtensorMap)
 bool z4_tma_batch_eligible(const sf_params& prm, const sf_patch& p);
-sf_status encode_z4_tma_map(void* map, const sf_patch& p, const void* base);
+sf_status encode_z4_tma_map(void* map, const sf_patch& p, const void* base, int xp);
 sf_status launch_z4_tma_batch(const sf_params& prm, int precision, const void* d_maps, int role,
                               const PatchArgs<float>* d_args, const TmaTile* d_tiles, int ntiles,
-                              const StageArgs& s, cudaStream_t st);
+                              int xp, const StageArgs& s, cudaStream_t st);
 // radiative boundary stage on the ghost shell (sf_radiative.cu)
 sf_status launch_radiative(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                            const double* x0, const double* u_inf, const double* speed,

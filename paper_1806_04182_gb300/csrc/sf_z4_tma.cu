@@ -41,21 +41,24 @@
 namespace sf {
 namespace {
 
-// A CTA computes a 32 x BY x 1 tile of points (one warp per row); the staged
-// box of a field is TX x (BY + 6) x TZ floats, each slot rounded up to 128 B.
-// Shared memory: KS slots, 2 KS mbarriers, and the 25 right-hand sides of
-// every thread (parked until the RK combination at the end).
+// A CTA computes an XP x BY x 1 tile of points (32 / XP rows per warp: one
+// row of 32 points, or two rows of 16); the staged box of a field is
+// XB x (BY + 6) x TZ floats with XB = XP + 6 rounded up to 16 bytes, each slot
+// rounded up to 128 B.  Shared memory: KS slots, 2 KS mbarriers, and the 25
+// right-hand sides of every thread (parked until the RK combination at the
+// end).
 constexpr int TX = 40, TZ = 7;
 constexpr int kSY = 104, kSZ = 104 * 102;         // global strides of the padded 96^3 layout
 constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at GB300 clocks
 
-template <int BY, int KS>
+template <int BY, int KS, int XP = 32>
 struct Cfg {
+  static constexpr int XB = ((XP + 6 + 3) / 4) * 4;  // 40 for XP = 32, 24 for XP = 16
   static constexpr int TY = BY + 6;
-  static constexpr int kBoxBytes = TX * TY * TZ * 4;
+  static constexpr int kBoxBytes = XB * TY * TZ * 4;
   static constexpr int kSlotFloats = ((kBoxBytes + 127) / 128) * 32;
   static constexpr int kSlots = KS;
-  static constexpr int kThreads = 32 * BY;
+  static constexpr int kThreads = XP * BY;
   static constexpr int kRbufOffset = KS * kSlotFloats * 4 + 2 * KS * 8;
   static constexpr int kSmemBytes = kRbufOffset + 25 * kThreads * 4;
   static constexpr int kMinBlocks = BY <= 4 ? 3 : 1;  // 168 registers a thread
@@ -69,6 +72,13 @@ struct Cfg {
 // the kernel is bound by instruction fetch.
 constexpr int kBY = 12, kKS = 8;
 static_assert(kTmaTileX == 32 && kTmaTileY == kBY, "batch tiles are the kernel's tiles");
+static_assert(Cfg<kBY, kKS>::XB == TX, "the 32-wide box");
+// The second tile of the batch kernel: 16 x 24 points, same 12 warps, same
+// slot size (24 x 30 x 7 floats), for patches that a 32-wide tile overhangs.
+constexpr int kBY16 = 24;
+static_assert(Cfg<kBY16, kKS, 16>::kThreads == Cfg<kBY, kKS>::kThreads, "12 warps either way");
+static_assert(Cfg<kBY16, kKS, 16>::kSlotFloats == Cfg<kBY, kKS>::kSlotFloats, "same slots");
+static_assert(kTmaTileX16 == 16 && kTmaTileY16 == kBY16, "batch narrow tiles are the kernel's tiles");
 
 // Order in which z4_cell opens the fields' stencils (cross, then the mixed
 // derivatives of the same field).  Without the Gamma-driver (shift frozen)
@@ -86,9 +96,10 @@ __device__ __forceinline__ void tma_load_4d(float* dst, const CUtensorMap* map, 
 }
 
 // Stencil source for z4_cell reading the staged boxes.
-template <int BY, int KS>
+template <int BY, int KS, int XP = 32>
 struct TmaSrc {
-  using C = Cfg<BY, KS>;
+  using C = Cfg<BY, KS, XP>;
+  static constexpr int XB = C::XB;
   static constexpr int TY = C::TY;
   static constexpr int kSlots = KS;
   static constexpr int kSlotFloats = C::kSlotFloats;
@@ -105,8 +116,8 @@ struct TmaSrc {
   int gx, gy, gz;     // ghosted coordinates of the box origin
   bool leader, lane0, dead;
 
-  __device__ __forceinline__ static constexpr long long sy() { return TX; }
-  __device__ __forceinline__ static constexpr long long sz() { return TX * TY; }
+  __device__ __forceinline__ static constexpr long long sy() { return XB; }
+  __device__ __forceinline__ static constexpr long long sz() { return XB * TY; }
   __device__ __forceinline__ const float* p(int) const { return tiles + cur * kSlotFloats + local; }
   __device__ __forceinline__ float ld(const float* q) const { return *q; }
   __device__ __forceinline__ float centre(int f) const { return __ldg(u + f * F); }
@@ -157,10 +168,13 @@ struct TmaSrc {
 // combination of this stage reads (U^n, the accumulator, the Kahan term):
 // those reads come late in the point's computation, one field at a time, and
 // would otherwise each wait for DRAM.
+template <int kBytes = 144>
 __device__ __forceinline__ void prefetch_rows(const float* base, long long F) {
+  static_assert(kBytes % 16 == 0, "bulk prefetch size");
 #pragma unroll 1
   for (int f = 0; f < 25; ++f)
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], 144;" ::"l"(base + f * F) : "memory");
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + f * F), "n"(kBytes)
+                 : "memory");
 }
 
 template <typename H, int BY, int KS>
@@ -224,34 +238,42 @@ __global__ void __launch_bounds__(Cfg<BY, KS>::kThreads, Cfg<BY, KS>::kMinBlocks
   write_fields<float, 25>(a, s, im, c, i, j, k, rbuf + tid, C::kThreads);
 }
 
-// One 32 x 12 x 1 tile at interior (x0, y0, z0) of a patch with runtime
-// strides (row, plane and field pitches multiples of 4 floats).  The tile may
-// overhang the patch in x and y: the TMA box reads zeros beyond the array,
-// the overhanging threads still take part in the ring (they compute on
+// One XP x BY x 1 tile at interior (x0, y0, z0) of a patch with runtime
+// strides (row, plane and field pitches multiples of 4 floats): 32 x 12 (one
+// row per warp) or 16 x 24 (two rows per warp, lanes 0-15 and 16-31).  The
+// tile may overhang the patch in x and y: the TMA box reads zeros beyond the
+// array, the overhanging threads still take part in the ring (they compute on
 // clamped centre values) and write nothing.  `a` may live in shared memory.
-template <typename H>
+template <typename H, int XP>
 __device__ __forceinline__ void tma_tile_runtime(const CUtensorMap* map, const PatchArgs<float>& a,
                                                  const StageArgs& s, const Z4Coef<float>& zc,
                                                  int x0, int y0, int k, unsigned char* smem) {
-  using C = Cfg<kBY, kKS>;
+  constexpr int BY = XP == 32 ? kBY : kBY16;
+  using C = Cfg<BY, kKS, XP>;
   constexpr int kSlots = kKS;
   float* tiles = reinterpret_cast<float*>(smem);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kSlots * C::kSlotFloats * 4);
   uint64_t* empty = full + kSlots;
   const int tid = threadIdx.y * 32 + threadIdx.x;
-  const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
+  // 16-wide tiles: the half-warps take rows two apart (warp w: rows
+  // 4 (w / 2) + w % 2 and that + 2), so that their shared-memory rows, 24
+  // floats each, start 48 floats = 16 banks apart and never share a bank
+  const int lx = threadIdx.x % XP;
+  const int ly = XP == 32 ? (int)threadIdx.y
+                          : 4 * (threadIdx.y / 2) + threadIdx.y % 2 + 2 * (threadIdx.x / 16);
+  const int i = x0 + lx, j = y0 + ly;
   const bool valid = i < a.n[0] && j < a.n[1];
   const int ic = min(i, a.n[0] - 1), jc = min(j, a.n[1] - 1);
   const long long c = (long long)(k + 3) * a.sz + (long long)(jc + 3) * a.sy + (ic + 3);
-  if (threadIdx.x == 0 && s.mode == 0 && x0 + 32 <= a.n[0] && j < a.n[1]) {
-    // rows start on 16 bytes, so ghosted x = x0 does too: 144 B cover the
-    // warp's 32 points (byte offsets 12 .. 139) inside the row
+  if (lx == 0 && s.mode == 0 && x0 + XP <= a.n[0] && j < a.n[1]) {
+    // rows start on 16 bytes, so ghosted x = x0 does too: the row segment's
+    // XP points sit at byte offsets 12 .. 4 XP + 11, inside 4 XP + 16 bytes
     const long long c0 = c - 3;
-    if (!s.un_alias) prefetch_rows(a.un + c0, a.sf);
-    if (s.rk == SF_RK4 && s.stage > 0) prefetch_rows(a.acc + c0, a.sf);
-    if (s.kahan && s.stage == 3) prefetch_rows(a.kh + c0, a.sf);
+    if (!s.un_alias) prefetch_rows<4 * XP + 16>(a.un + c0, a.sf);
+    if (s.rk == SF_RK4 && s.stage > 0) prefetch_rows<4 * XP + 16>(a.acc + c0, a.sf);
+    if (s.kahan && s.stage == 3) prefetch_rows<4 * XP + 16>(a.kh + c0, a.sf);
   }
-  TmaSrc<kBY, kKS> src;
+  TmaSrc<BY, kKS, XP> src;
   src.u = a.us + c;
   src.F = a.sf;
   src.tiles = tiles;
@@ -259,7 +281,7 @@ __device__ __forceinline__ void tma_tile_runtime(const CUtensorMap* map, const P
   src.empty = empty;
   src.map = map;
   src.status = s.status;
-  src.local = (3 * C::TY + threadIdx.y + 3) * TX + threadIdx.x + 3;
+  src.local = (3 * C::TY + ly + 3) * C::XB + lx + 3;
   src.use = 0;
   src.cur = 0;
   src.nuses = zc.shift_frozen ? 22 : 25;
@@ -286,7 +308,7 @@ __device__ __forceinline__ void init_ring(unsigned char* smem) {
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     for (int q = 0; q < kKS; ++q) {
       mbar_init(&full[q], 1);
-      mbar_init(&empty[q], kBY);
+      mbar_init(&empty[q], kBY);  // one arrival per warp: 12 warps for either tile
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -302,15 +324,15 @@ __global__ void __launch_bounds__(Cfg<kBY, kKS>::kThreads, 1)
   extern __shared__ __align__(128) unsigned char smem[];
   init_ring(smem);
   __syncthreads();
-  tma_tile_runtime<H>(&map, a, s, zc, blockIdx.x * 32, blockIdx.y * kBY, blockIdx.z, smem);
+  tma_tile_runtime<H, 32>(&map, a, s, zc, blockIdx.x * 32, blockIdx.y * kBY, blockIdx.z, smem);
 }
 
 // The same over the tiles of many patches (the CCZ4 patches of a batch): one
 // CTA per tile, the tile's patch from `tl`, its arguments copied from `args`
 // into shared memory (uniform reads), its stage input's tensor map from
 // `maps` (three per patch, for the u_n, u_stage and u_next buffer roles;
-// `role` picks this stage's input).
-template <typename H>
+// `role` picks this stage's input; the maps' boxes match the tile width XP).
+template <typename H, int XP>
 __global__ void __launch_bounds__(Cfg<kBY, kKS>::kThreads, 1)
     z4_tma_batch_kernel(const CUtensorMap* __restrict__ maps, int role,
                         const PatchArgs<float>* __restrict__ args, const TmaTile* __restrict__ tl,
@@ -328,7 +350,7 @@ __global__ void __launch_bounds__(Cfg<kBY, kKS>::kThreads, 1)
   }
   init_ring(smem);
   __syncthreads();
-  tma_tile_runtime<H>(maps + 3 * w.patch + role, pa, s, zc, w.x0, w.y0, w.z0, smem);
+  tma_tile_runtime<H, XP>(maps + 3 * w.patch + role, pa, s, zc, w.x0, w.y0, w.z0, smem);
 }
 
 namespace {
@@ -403,18 +425,22 @@ bool z4_tma_batch_eligible(const sf_params& prm, const sf_patch& p) {
 }
 
 // Tensor map of the ghosted float array `base` with p's extents and strides,
-// boxes of the staged kernel (40 x 18 x 7 x 1).
-sf_status encode_z4_tma_map(void* out, const sf_patch& p, const void* base) {
+// boxes of the staged kernel for tiles xp wide: 40 x 18 x 7 x 1 (xp = 32) or
+// 24 x 30 x 7 x 1 (xp = 16).
+sf_status encode_z4_tma_map(void* out, const sf_patch& p, const void* base, int xp) {
   static_assert(sizeof(CUtensorMap) == kTmaMapBytes, "tensor map size");
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return set_error(SF_ECUDA, "cuTensorMapEncodeTiled not available");
-  using C = Cfg<kBY, kKS>;
+  if (xp != 32 && xp != 16) return set_error(SF_EINVAL, "tile width %d is not 32 or 16", xp);
+  using C32 = Cfg<kBY, kKS>;
+  using C16 = Cfg<kBY16, kKS, 16>;
   CUtensorMap map;
   memset(&map, 0, sizeof(map));
   const cuuint64_t dims[4] = {(cuuint64_t)(p.n[0] + 6), (cuuint64_t)(p.n[1] + 6),
                               (cuuint64_t)(p.n[2] + 6), 25};
   const cuuint64_t strides[3] = {(cuuint64_t)p.sy * 4, (cuuint64_t)p.sz * 4, (cuuint64_t)p.sf * 4};
-  const cuuint32_t box[4] = {TX, (cuuint32_t)C::TY, TZ, 1};
+  const cuuint32_t box[4] = {(cuuint32_t)(xp == 32 ? C32::XB : C16::XB),
+                             (cuuint32_t)(xp == 32 ? C32::TY : C16::TY), TZ, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides,
                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -425,18 +451,18 @@ sf_status encode_z4_tma_map(void* out, const sf_patch& p, const void* base) {
 }
 
 namespace {
-template <typename H>
+template <typename H, int XP>
 sf_status launch_tma_batch(const sf_params& prm, const void* d_maps, int role,
                            const PatchArgs<float>* d_args, const TmaTile* d_tiles, int ntiles,
                            const StageArgs& s, cudaStream_t st) {
-  using C = Cfg<kBY, kKS>;
+  using C = Cfg<XP == 32 ? kBY : kBY16, kKS, XP>;
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
-    cudaFuncSetAttribute(z4_tma_batch_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(z4_tma_batch_kernel<H, XP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          C::kSmemBytes);
   });
   const Z4Coef<float> zc = z4_coef<float>(prm);
-  z4_tma_batch_kernel<H><<<ntiles, dim3(32, kBY, 1), C::kSmemBytes, st>>>(
+  z4_tma_batch_kernel<H, XP><<<ntiles, dim3(32, kBY, 1), C::kSmemBytes, st>>>(
       static_cast<const CUtensorMap*>(d_maps), role, d_args, d_tiles, s, zc);
   return after_launch("z4_tma_batch_kernel");
 }
@@ -444,11 +470,14 @@ sf_status launch_tma_batch(const sf_params& prm, const void* d_maps, int role,
 
 sf_status launch_z4_tma_batch(const sf_params& prm, int precision, const void* d_maps, int role,
                               const PatchArgs<float>* d_args, const TmaTile* d_tiles, int ntiles,
-                              const StageArgs& s, cudaStream_t st) {
+                              int xp, const StageArgs& s, cudaStream_t st) {
   if (ntiles <= 0) return SF_OK;
-  if (precision == SF_FP32_BULK_DW)
-    return launch_tma_batch<dw>(prm, d_maps, role, d_args, d_tiles, ntiles, s, st);
-  return launch_tma_batch<double>(prm, d_maps, role, d_args, d_tiles, ntiles, s, st);
+  const bool d = precision == SF_FP32_BULK_DW;
+  if (xp == 16)
+    return d ? launch_tma_batch<dw, 16>(prm, d_maps, role, d_args, d_tiles, ntiles, s, st)
+             : launch_tma_batch<double, 16>(prm, d_maps, role, d_args, d_tiles, ntiles, s, st);
+  return d ? launch_tma_batch<dw, 32>(prm, d_maps, role, d_args, d_tiles, ntiles, s, st)
+           : launch_tma_batch<double, 32>(prm, d_maps, role, d_args, d_tiles, ntiles, s, st);
 }
 
 namespace {
@@ -457,7 +486,7 @@ sf_status launch_tma_any(const sf_params& prm, const sf_patch& p, const StageArg
                          void* rhs_out, cudaStream_t st) {
   using C = Cfg<kBY, kKS>;
   alignas(64) unsigned char map[kTmaMapBytes];
-  sf_status e = encode_z4_tma_map(map, p, p.u_stage);
+  sf_status e = encode_z4_tma_map(map, p, p.u_stage, 32);
   if (e) return e;
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {

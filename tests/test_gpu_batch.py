@@ -48,6 +48,22 @@ def batch_patches(states):
     return [st.patch(st.B, st.A, st.C) for st in states]
 
 
+def expected_launches_per_step(states):
+    """Launches per RK4 step of a batch: one per stage for each TMA tile width
+    in use (float CCZ4 patches with 16-byte rows; a patch takes the 16 x 24
+    tile when that covers it with fewer tiles than 32 x 12) and one for the
+    persistent kernel unless every patch is on TMA."""
+    def tiles(n, tx, ty):
+        return -(-n[0] // tx) * -(-n[1] // ty)
+    widths, rest = set(), False
+    for st in states:
+        if st.system == capi.SF_Z4 and st.precision != capi.SF_FP64 and st.pitch % 4 == 0:
+            widths.add(16 if tiles(st.n, 16, 24) < tiles(st.n, 32, 12) else 32)
+        else:
+            rest = True
+    return 4 * (len(widths) + (1 if rest or not widths else 0))
+
+
 def fp_bound(precision, st, steps=2):
     """FP64: summation-order rounding.  FP32: the two kernels are compiled
     separately (FMA contraction may differ), so they differ by the float
@@ -126,10 +142,8 @@ def test_batch_graph_tune_and_capture():
                 capi.sf_batch_launch(b, stream.cuda_stream)
         stream.synchronize()
         # float CCZ4 patches whose dense rows happen to be a multiple of 4 floats
-        # go to the TMA-staged kernel: then two launches per stage
-        tma = [st.system == capi.SF_Z4 and st.pitch % 4 == 0 for st in states]
-        per_stage = (1 if any(tma) else 0) + (0 if all(tma) else 1)
-        assert capi.sf_batch_launches_per_step(b) == 4 * per_stage
+        # go to the TMA-staged kernel
+        assert capi.sf_batch_launches_per_step(b) == expected_launches_per_step(states)
         for st, r in zip(states, ref):
             a, w = st.interior(), r.interior()
             scale = w.abs().amax(dim=(1, 2, 3)).clamp_min(1e-2)
@@ -164,7 +178,8 @@ def test_batch_tma_tiles_equal_per_patch_launches(precision):
     states = make_states(table, precision, tma_pitch=True)
     b = capi.sf_batch_create(capi.params(), batch_patches(states))
     try:
-        assert capi.sf_batch_launches_per_step(b) == 8  # TMA tiles + persistent, 4 stages
+        assert capi.sf_batch_launches_per_step(b) == expected_launches_per_step(states)
+        assert capi.sf_batch_launches_per_step(b) >= 8  # TMA tiles + persistent, 4 stages
         for _ in range(2):
             for s in range(4):
                 capi.sf_batch_substep(b, s, torch.cuda.current_stream().cuda_stream)
@@ -196,7 +211,9 @@ def test_batch_tma_tiles_match_oracle_through_graph():
     b = capi.sf_batch_create(capi.params(), batch_patches(states))
     stream = torch.cuda.Stream()
     try:
-        assert capi.sf_batch_launches_per_step(b) == 4
+        # (33, 13, 5) and (7, 25, 3) take the 16 x 24 tile, the others 32 x 12: two
+        # launches per stage
+        assert capi.sf_batch_launches_per_step(b) == expected_launches_per_step(states) == 8
         with torch.cuda.stream(stream):
             capi.sf_batch_tune(b, stream.cuda_stream)  # nothing to tune: no persistent items
             capi.sf_batch_capture(b, stream.cuda_stream)

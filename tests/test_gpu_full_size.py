@@ -90,7 +90,7 @@ def test_batch_512_patches_first_stage_sampled():
     b = capi.sf_batch_create(capi.params(), [s_.patch(s_.B, s_.A, s_.C) for s_ in sts])
     stream = torch.cuda.Stream()
     try:
-        assert capi.sf_batch_launches_per_step(b) == 8
+        assert capi.sf_batch_launches_per_step(b) == 12  # both TMA tile widths + persistent
         with torch.cuda.stream(stream):
             capi.sf_batch_tune(b, stream.cuda_stream)   # stage 1 on scratch only
             capi.sf_batch_substep(b, 0, stream.cuda_stream)
