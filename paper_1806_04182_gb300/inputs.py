@@ -164,6 +164,28 @@ def mhd_blast(n, seed: int = 0, gamma: float = 5.0 / 3.0, vrms: float = 0.1,
     return mhd_primitive_to_conserved(rho, [g[0], g[1], g[2]], p, B, gamma), dx
 
 
+def mhd_brio_wu(n, gamma: float = 2.0):
+    """Brio & Wu magnetic shock tube (Sec. IV.B.2) on a periodic domain
+    [0, 2) along x, doubled so that it needs no outflow boundary: the left
+    state (rho, p, B_y) = (1, 1, 1) for x <= 0.5 and x > 1.5, the right state
+    (0.125, 0.1, -1) in between, B_x = 0.75, B_z = v = 0, Gamma = 2.  The jump
+    at x = 0.5 is the paper's tube; the waves of the two jumps stay apart
+    until t = 0.2 (fastest speed below 2).  Uniform in y and z; dx = 2 / nx
+    in every direction.  Returns (U, dx)."""
+    nx, ny, nz = n
+    h = 2.0 / nx
+    dx = (h, h, h)
+    x = np.arange(nx) * h
+    left = (x <= 0.5) | (x > 1.5)
+    shape = (nz, ny, nx)
+    rho = np.broadcast_to(np.where(left, 1.0, 0.125), shape)
+    p = np.broadcast_to(np.where(left, 1.0, 0.1), shape)
+    by = np.broadcast_to(np.where(left, 1.0, -1.0), shape)
+    zero = np.zeros(shape)
+    B = [0.75 * np.ones(shape), by.copy(), zero.copy()]
+    return mhd_primitive_to_conserved(rho.copy(), [zero.copy()] * 3, p.copy(), B, gamma), dx
+
+
 def mhd_alfven(n, t: float = 0.0, m=(1, 1), gamma: float = 5.0 / 3.0):
     """Circularly polarised Alfven wave (Sec. IV.B.1) on the unit box, z-invariant.
 

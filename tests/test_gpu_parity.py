@@ -217,6 +217,29 @@ def test_mhd_fp64_stages(variant, split):
         assert e.max() < TOL64, (s, e)
 
 
+# The Brio & Wu shock tube (Sec. IV.B.2; Gamma = 2, dt = 0.2 dx): stage
+# outputs on discontinuous data, where the WENO weights are far from the
+# linear ones, from the initial jumps and from the developed waves after 30
+# oracle steps, for every reconstruction.
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("developed", [False, True])
+def test_mhd_brio_wu_stages(variant, developed):
+    n = (256, 3, 3)
+    U0, dx = inputs.mhd_brio_wu(n)
+    prm = capi.params(rk=capi.SF_SSPRK3, weno_variant=variant, gamma_eos=2.0)
+    dt = 0.2 * dx[0]
+    if developed:
+        G = oracle.ghosted(U0.copy())
+        for _ in range(30):
+            oracle.ssprk3_step(oracle.MHD, G, dx, dt, oracle_params(prm))
+        U0 = np.ascontiguousarray(oracle.interior(G))
+    got = run_stages(capi.SF_MHD, U0, dx, dt, prm)
+    want = oracle_stages(oracle.MHD, U0, dx, dt, prm)
+    for s in range(3):
+        e = rel_err(got[s], want[s], floor=1e-3)
+        assert e.max() < TOL64, (s, e)
+
+
 def test_mhd_max_rate_and_rhs():
     n = (20, 9, 8)
     U0, dx = inputs.mhd_blast(n, seed=5, radius=0.3)
