@@ -321,13 +321,21 @@ sf_status sf_bor_prolong_boxes(const sf_patch* coarse, int32_t rk, const void* c
                                const sf_prolong_box* boxes, int32_t nbox, void* stream);
 
 /*
- * Batched AMR-patch dispatch: one persistent launch per stage over a table of
- * patches of mixed systems (SF_WAVE and SF_Z4) and sizes, each with its own
- * dx and dt.  CTAs take (patch, tile) work items from a device queue.
- * sf_batch_create copies the patch table to the device (allocates; not in
- * the hot path).  sf_batch_tune times the tile shapes of each (system, size
- * class) on `stream` and keeps the fastest.  sf_batch_capture records the
- * RK stages of one full step into a CUDA graph; sf_batch_launch replays it.
+ * Batched AMR-patch dispatch (the level loop of Sec. III over many patches):
+ * one persistent launch per stage over a table of patches of mixed systems
+ * (SF_WAVE and SF_Z4) and sizes, each with its own dx and dt.  CTAs take
+ * (patch, tile) work items from a device queue.  Float CCZ4 patches with
+ * centred advection whose row, plane and field pitches are multiples of 4
+ * floats and whose arrays are 16-byte aligned go instead to the TMA-staged
+ * stage kernel: one launch per stage for each tile width in use (32 x 12 or
+ * 16 x 24 points; each patch takes the width that covers it with fewer
+ * tiles), ahead of the persistent launch for the other patches.
+ * sf_batch_create copies the patch table (and the TMA patches' tensor maps
+ * and tile lists) to the device (allocates; not in the hot path).
+ * sf_batch_tune times the tile shapes of the persistent kernel for each
+ * (system, size class) on `stream` and keeps the fastest.  sf_batch_capture
+ * records the RK stages of one full step into a CUDA graph; sf_batch_launch
+ * replays it.
  */
 typedef struct sf_batch sf_batch;
 sf_status sf_batch_create(const sf_params* prm, const sf_patch* patches, int32_t npatch,
@@ -336,7 +344,8 @@ sf_status sf_batch_substep(sf_batch* b, int32_t stage, void* stream);
 sf_status sf_batch_tune(sf_batch* b, void* stream);
 sf_status sf_batch_capture(sf_batch* b, void* stream);
 sf_status sf_batch_launch(sf_batch* b, void* stream);
-/* Number of persistent-kernel launches made by one sf_batch_launch. */
+/* Number of kernel launches (TMA tile launches and persistent launches) made
+ * by one sf_batch_launch, i.e. one RK4 step. */
 int32_t sf_batch_launches_per_step(const sf_batch* b);
 sf_status sf_batch_destroy(sf_batch* b);
 
