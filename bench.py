@@ -366,7 +366,10 @@ def gpu_arm(args):
             "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
             "fp64_frac": r64["value"] * FLOPS_PER_CELL_UPDATE / 1e12 / FP64_PEAK_TFLOPS,
             "fp64_peak": FP64_PEAK_TFLOPS,
-            "fp64_peak_source": "measured FMA probe, 1/58 of the FP32 rate"},
+            "fp64_peak_source": "measured FMA probe, 1/58 of the FP32 rate",
+            "note": "flops counted on the oracle's plain formulation (unfused, symmetric sums "
+                    "expanded); the kernels evaluate a factored form with fewer operations, so "
+                    "the FP64 fraction can exceed 1 (ncu: FP64 pipe 86% busy)"},
         "issue_roofline": issue_roofline(r32, clocks),
         "fp32_bulk_fp64_islands": {
             "value": r32n["value"], "ms_per_step": r32n["ms_per_step"],
