@@ -585,12 +585,16 @@ def _amr_rows(hbm_peak: float) -> list[dict]:
     fine.upload(Uf)
     pair = amr.SubcycledPair(coarse, fine, 2, (16, 16, 16))
     steps = 5
-    ms = _events_time(lambda: pair.step(1), steps, 2)
+    ms_launch = _events_time(lambda: pair.step(1), steps, 2)
+    pair.capture(1)
+    ms = _events_time(pair.replay, steps, 2)
     cells = 64 ** 3 * 4 + 64 ** 3 * 4 * 2
     out.append({"workload": "subcycled_bor_ccz4_fp32dw_coarse64_fine64_ratio2", "value":
                 cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_coarse_step": ms / steps,
+                "ms_per_coarse_step_python_driver": ms_launch / steps,
                 "note": "one coarse RK4 step + 2 fine RK4 steps with BOR ghost fills before every "
-                        "fine stage (6 prolongation boxes each) and restriction"})
+                        "fine stage (6 prolongation boxes each) and restriction, replayed as one "
+                        "CUDA graph (amr.SubcycledPair.capture)"})
     return out
 
 

@@ -219,6 +219,25 @@ class SubcycledPair:
             if self.radiative is None:
                 c.fill_ghosts(c.A, h)
 
+    def capture(self, nsteps: int = 1) -> None:
+        """Record `nsteps` coarse steps (every launch of step(), the coarse and
+        fine stages, the BOR ghost fills, the stage-state copies and the
+        restriction) into a CUDA graph; replay() then advances the pair by
+        those steps with one graph launch, free of the per-launch host work of
+        the Python driver.  Call step() at least once first, so that the
+        library's one-time set-up (kernel attributes, device addresses) has
+        run outside the capture.  The graph holds the current buffers and dt."""
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.step(nsteps)
+        self._graph = g
+
+    def replay(self) -> None:
+        """Advance by the steps recorded with capture()."""
+        if getattr(self, "_graph", None) is None:
+            raise RuntimeError("capture() first")
+        self._graph.replay()
+
 
 def _stream(stream) -> int:
     if stream is None:

@@ -171,6 +171,22 @@ def test_ratio_one_equals_uniform_run_float_tma():
     assert np.abs(got - want).max() <= bound, (np.abs(got - want).max(), bound)
 
 
+def test_subcycled_graph_replay_equals_steps():
+    # the captured coarse step (stages, BOR ghost fills, copies, restriction
+    # in one CUDA graph) advances the pair exactly as step() does
+    data = lambda n: inputs.z4_perturbed(n, seed=5, amp=0.04)
+    nc, at, m, R = (24, 20, 16), (6, 5, 4), (8, 6, 4), 2
+    pairs = [_pair(capi.SF_Z4, capi.SF_FP32_BULK_DW, nc, m, at, R, data, 0.2, 1, pitch4=True)
+             for _ in range(2)]
+    pairs[0].step(2)
+    pairs[1].capture(1)
+    pairs[1].replay()
+    pairs[1].replay()
+    torch.cuda.synchronize()
+    for a, b in zip((pairs[0].coarse, pairs[0].fine), (pairs[1].coarse, pairs[1].fine)):
+        assert torch.equal(a.A, b.A)
+
+
 def test_subcycled_plane_wave_converges_at_fourth_order():
     R = 2
     errs = []
