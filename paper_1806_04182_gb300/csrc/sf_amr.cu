@@ -10,6 +10,7 @@
 //                    Berger-Oliger without order reduction (Sec. III.B,
 //                    App. C-D), a fixed linear combination of the coarse
 //                    stage states whose coefficients the host derives.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -52,9 +53,10 @@ __global__ void __launch_bounds__(256) copy_boxes_kernel(BoxBatch bb) {
 }
 
 // One output box of a prolongation launch: fine points origin..origin+ext-1
-// written to out with element strides (osy, osz, osf); t[3] = tiles per axis.
+// written to out with element strides (osy, osz, osf); p[3] = the box's tile
+// of fine points, t[3] = tiles per axis.
 struct PBox {
-  int origin[3], ext[3], t[3];
+  int origin[3], ext[3], p[3], t[3];
   void* out;
   long long osy, osz, osf;
 };
@@ -107,31 +109,56 @@ __device__ __forceinline__ float lagrange_w<float>(const ProlongArgs& p, int r, 
   return p.wf[r][q];
 }
 
-// Fine tile of PX x PY x PZ points per CTA.  Along each axis the tile's
-// points reach coarse nodes floor(F/R) - 2 .. floor(F/R) + 3, at most
-// (P - 1)/R + 7 of them (P + 6 for R = 1).  The kernel stages those nodes in
-// shared memory (after the BOR combination, once per node), then
-// interpolates separably: along x into tx, along y into ty, along z into the
-// output.  One field per CTA, so thin boxes (ghost shells) still fill the GPU.  18 weighted sums per fine point and field instead of 216, and the
-// 6-point order of summation is the tensor product's (x innermost).
-constexpr int PX = 32, PY = 4, PZ = 4;
-constexpr int CXM = PX + 6, CYM = PY + 6, CZM = PZ + 6;
+// Fine tile of PX x PY x PZ points per CTA, chosen per box: 32 x 4 x 4 for
+// a thick box; for a box at most 4 points thin along one axis (the slabs of a
+// ghost shell) a tile 4 points deep along that axis and wider along the
+// others, 4 x 16 x 16, 32 x 4 x 16 or 32 x 16 x 4, so that the coarse nodes
+// a tile stages serve more fine points.  Along each axis the tile's points
+// reach coarse nodes floor(F/R) - 2 .. floor(F/R) + 3, at most (P - 1)/R + 7
+// of them (P + 6 for R = 1).  The kernel stages those nodes in shared memory
+// (after the BOR combination, once per node), then interpolates separably:
+// along x into tx, along y into ty, along z into the output.  One field per
+// CTA, so thin boxes still fill the GPU.  18 weighted sums per fine point and
+// field instead of 216, and the 6-point order of summation is the tensor
+// product's (x innermost).
+struct TileShape {
+  int px, py, pz;
+};
+constexpr int prolong_elems(TileShape t) {
+  return (t.pz + 6) * (t.py + 6) * (t.px + 6) + (t.pz + 6) * (t.py + 6) * t.px +
+         (t.pz + 6) * t.py * t.px;
+}
+constexpr TileShape kThick = {32, 4, 4}, kThinX = {4, 16, 16}, kThinY = {32, 4, 16},
+                    kThinZ = {32, 16, 4};
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+constexpr int kProlongMaxElems = cmax(cmax(prolong_elems(kThick), prolong_elems(kThinX)),
+                                      cmax(prolong_elems(kThinY), prolong_elems(kThinZ)));
 template <typename T>
-constexpr int prolong_smem() {
-  return (CZM * CYM * CXM + CZM * CYM * PX + CZM * PY * PX) * (int)sizeof(T);
+constexpr int prolong_smem_max() {
+  return kProlongMaxElems * (int)sizeof(T);
+}
+static_assert(prolong_smem_max<double>() <= 227 * 1024, "prolongation tile fits shared memory");
+
+static TileShape tile_for(const int* ext) {
+  if (ext[0] <= 4) return kThinX;
+  if (ext[1] <= 4) return kThinY;
+  if (ext[2] <= 4) return kThinZ;
+  return kThick;
 }
 
 template <typename T, int NS>
 __global__ void __launch_bounds__(256) prolong_kernel(Combo<T> cb, ProlongArgs p) {
   extern __shared__ __align__(16) unsigned char psm_raw[];
-  T* cn = reinterpret_cast<T*>(psm_raw);  // [CZM][CYM][CXM]
-  T* tx = cn + CZM * CYM * CXM;           // [CZM][CYM][PX]
-  T* ty = tx + CZM * CYM * PX;            // [CZM][PY][PX]
   const int R = p.R;
   // the CTA's box, tile and field (one field per CTA, field slowest)
   int bi = 0;
   while (bi + 1 < p.nbox && (int)blockIdx.x >= p.tiles_end[bi]) ++bi;
   const PBox& B = p.box[bi];
+  const int PX = B.p[0], PY = B.p[1], PZ = B.p[2];
+  const int CXM = PX + 6, CYM = PY + 6, CZM = PZ + 6;
+  T* cn = reinterpret_cast<T*>(psm_raw);  // [CZM][CYM][CXM]
+  T* tx = cn + CZM * CYM * CXM;           // [CZM][CYM][PX]
+  T* ty = tx + CZM * CYM * PX;            // [CZM][PY][PX]
   int local = (int)blockIdx.x - (bi ? p.tiles_end[bi - 1] : 0);
   const int xt = local % B.t[0];
   local /= B.t[0];
@@ -399,6 +426,7 @@ static sf_status prolong_launch(const sf_patch* coarse, const void* const* array
   }
   for (int q0 = 0; q0 < nbox; q0 += kMaxPBoxes) {
     long long total = 0;
+    int smem_elems = 0;
     a.nbox = 0;
     for (int q = q0; q < nbox && q < q0 + kMaxPBoxes; ++q) {
       const sf_prolong_box& bx = boxes[q];
@@ -408,9 +436,14 @@ static sf_status prolong_launch(const sf_patch* coarse, const void* const* array
         B.origin[d] = bx.origin[d];
         B.ext[d] = bx.ext[d];
       }
-      B.t[0] = (bx.ext[0] + PX - 1) / PX;
-      B.t[1] = (bx.ext[1] + PY - 1) / PY;
-      B.t[2] = (bx.ext[2] + PZ - 1) / PZ;
+      const TileShape ts = tile_for(bx.ext);
+      B.p[0] = ts.px;
+      B.p[1] = ts.py;
+      B.p[2] = ts.pz;
+      B.t[0] = (bx.ext[0] + ts.px - 1) / ts.px;
+      B.t[1] = (bx.ext[1] + ts.py - 1) / ts.py;
+      B.t[2] = (bx.ext[2] + ts.pz - 1) / ts.pz;
+      smem_elems = std::max(smem_elems, prolong_elems(ts));
       B.out = bx.out;
       B.osy = bx.out_sy;
       B.osz = bx.out_sz;
@@ -428,9 +461,9 @@ static sf_status prolong_launch(const sf_patch* coarse, const void* const* array
       static std::once_flag once;
       std::call_once(once, [] {
         cudaFuncSetAttribute(prolong_kernel<double, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             prolong_smem<double>());
+                             prolong_smem_max<double>());
       });
-      prolong_kernel<double, NS><<<(unsigned)total, 256, prolong_smem<double>(), st>>>(cb, a);
+      prolong_kernel<double, NS><<<(unsigned)total, 256, smem_elems * sizeof(double), st>>>(cb, a);
     } else {
       Combo<float> cb;
       for (int m = 0; m < 5; ++m) cb.s[m] = m <= NS ? (const float*)arrays[m] : nullptr;
@@ -438,9 +471,9 @@ static sf_status prolong_launch(const sf_patch* coarse, const void* const* array
       static std::once_flag once;
       std::call_once(once, [] {
         cudaFuncSetAttribute(prolong_kernel<float, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             prolong_smem<float>());
+                             prolong_smem_max<float>());
       });
-      prolong_kernel<float, NS><<<(unsigned)total, 256, prolong_smem<float>(), st>>>(cb, a);
+      prolong_kernel<float, NS><<<(unsigned)total, 256, smem_elems * sizeof(float), st>>>(cb, a);
     }
     e = after_launch("prolong_kernel");
     if (e) return e;
