@@ -242,7 +242,7 @@ sf_status sf_radiative_substep(const sf_params* prm, const sf_patch* patch, cons
  *      dst_off + f*dst_sf + z*dst_sz + y*dst_sy + x  (element offsets; the
  * element type follows `precision`).  The caller guarantees both ranges lie
  * inside its arrays and that destination boxes do not overlap sources or each
- * other.  One launch per 64 boxes; nothing is allocated.  Each box holds fewer
+ * other.  One launch per 256 boxes; nothing is allocated.  Each box holds fewer
  * than 2^31 values.
  */
 typedef struct {

@@ -19,25 +19,38 @@
 
 namespace sf {
 
-// 64 descriptors (6.6 KB) travel as kernel parameters, so a launch needs no
-// device-side table.
-constexpr int kBoxesPerLaunch = 64;
+// 256 descriptors and their block offsets (27.7 KB) travel as kernel
+// parameters, so a launch needs no device-side table: the 26 halo boxes of
+// each of 8 patches, or the six slabs of many ghost shells, go in one launch.
+constexpr int kBoxesPerLaunch = 256;
 
 struct BoxBatch {
   sf_box_copy b[kBoxesPerLaunch];
+  int end[kBoxesPerLaunch];  // cumulative blocks per box
   int n;
 };
 
-// One grid row (blockIdx.y) per box; threads run over the box's points with
-// 32-bit index arithmetic (the host checks that a box holds < 2^31 values).
+// Each box gets blocks in proportion to its size (a corner box one, a face
+// box hundreds); block b of the launch belongs to the first box whose end
+// exceeds b.  Threads run over the box's points with 32-bit index arithmetic
+// (the host checks that a box holds < 2^31 values).
 template <typename T>
 __global__ void __launch_bounds__(256) copy_boxes_kernel(BoxBatch bb) {
-  const sf_box_copy& b = bb.b[blockIdx.y];
+  int lo = 0, hi = bb.n - 1;  // first box with end > blockIdx.x
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    if (bb.end[mid] > (int)blockIdx.x) hi = mid;
+    else lo = mid + 1;
+  }
+  const sf_box_copy& b = bb.b[lo];
+  const unsigned first = lo ? (unsigned)bb.end[lo - 1] : 0u;
+  const unsigned nblk = (unsigned)bb.end[lo] - first;
   const unsigned ex = (unsigned)b.ext[0], ey = (unsigned)b.ext[1], ez = (unsigned)b.ext[2];
   const unsigned total = ex * ey * ez * (unsigned)b.nf;
   const T* src = static_cast<const T*>(b.src);
   T* dst = static_cast<T*>(b.dst);
-  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+  for (unsigned t = (blockIdx.x - first) * blockDim.x + threadIdx.x; t < total;
+       t += nblk * blockDim.x) {
     unsigned r = t;
     const unsigned x = r % ex;
     r /= ex;
@@ -339,21 +352,25 @@ extern "C" sf_status sf_copy_boxes(const sf_box_copy* boxes, int32_t nbox, int32
   }
   cudaStream_t st = (cudaStream_t)stream;
   for (int q0 = 0; q0 < nbox; q0 += kBoxesPerLaunch) {
+    static_assert(sizeof(BoxBatch) < 32000, "kernel parameter limit");
     BoxBatch bb;
-    bb.n = nbox - q0 < kBoxesPerLaunch ? nbox - q0 : kBoxesPerLaunch;
-    long long maxv = 0;
-    for (int q = 0; q < bb.n; ++q) {
-      bb.b[q] = boxes[q0 + q];
-      const long long v = (long long)bb.b[q].ext[0] * bb.b[q].ext[1] * bb.b[q].ext[2] * bb.b[q].nf;
-      maxv = v > maxv ? v : maxv;
+    bb.n = 0;
+    int blocks = 0;
+    for (int q = q0; q < nbox && q < q0 + kBoxesPerLaunch; ++q) {
+      const long long v = (long long)boxes[q].ext[0] * boxes[q].ext[1] * boxes[q].ext[2] * boxes[q].nf;
+      if (v == 0) continue;  // writes nothing
+      long long nb = (v + 255) / 256;
+      if (nb > 1024) nb = 1024;  // the threads stride over larger boxes
+      bb.b[bb.n] = boxes[q];
+      blocks += (int)nb;
+      bb.end[bb.n] = blocks;
+      ++bb.n;
     }
-    if (maxv == 0) continue;
-    int gx = (int)((maxv + 255) / 256);
-    if (gx > 1024) gx = 1024;
+    if (bb.n == 0) continue;
     if (precision == SF_FP64)
-      copy_boxes_kernel<double><<<dim3(gx, bb.n), 256, 0, st>>>(bb);
+      copy_boxes_kernel<double><<<blocks, 256, 0, st>>>(bb);
     else
-      copy_boxes_kernel<float><<<dim3(gx, bb.n), 256, 0, st>>>(bb);
+      copy_boxes_kernel<float><<<blocks, 256, 0, st>>>(bb);
     sf_status e = after_launch("copy_boxes_kernel");
     if (e) return e;
   }
