@@ -174,6 +174,12 @@ class SubcycledPair:
         cext = tuple(v // ratio for v in fine.n)
         self._restrict = restrict_box(fine, coarse, ratio, self.at, cext, fine_at=self.at)
         self._shell = ghost_shell_boxes(fine)
+        # the periodic images of the coarse patch change with the restriction
+        # only if it writes inside the g layers next to a face (the images'
+        # sources); otherwise the last coarse stage's fused ghost writes stand
+        g = coarse.g
+        self._refresh_images = any(a < g or a + e > n - g
+                                   for a, e, n in zip(self.at, cext, coarse.n))
 
     def _states(self):
         c = self.coarse
@@ -216,7 +222,7 @@ class SubcycledPair:
                     self.fill_fine_ghosts(f.roles(s)[0], r, s, h)
                     capi.sf_substep(f.prm, f.stage_patch(s), s, h)
             capi.sf_copy_boxes([self._restrict], c.precision, h)
-            if self.radiative is None:
+            if self.radiative is None and self._refresh_images:
                 c.fill_ghosts(c.A, h)
 
     def capture(self, nsteps: int = 1) -> None:

@@ -103,23 +103,51 @@ sf_status check_patch(const sf_params* prm, const sf_patch& p, int need_stage_ar
 }
 
 // ---------------------------------------------------------------- ghosts
+// Periodic images into the ghost shell only, enumerated as six slabs (z
+// slabs over the whole ghosted x-y plane, then y slabs over the interior z
+// range, then x slabs over the interior y-z range): blockIdx.y is the field,
+// the threads stride over the field's shell points with 32-bit indices (the
+// host checks the count).  Every ghost reads an interior point, so the order
+// of the writes does not matter.
 template <typename T>
-__global__ void ghost_fill_kernel(T* u, int nf, int nx, int ny, int nz, int g, long long sy,
-                                  long long sz, long long sf) {
-  const long long NX = nx + 2 * g, NY = ny + 2 * g, NZ = nz + 2 * g;
-  const long long total = NX * NY * NZ * nf;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    long long r = t;
-    const int x = (int)(r % NX); r /= NX;
-    const int y = (int)(r % NY); r /= NY;
-    const int z = (int)(r % NZ); r /= NZ;
-    const int f = (int)r;
-    const int i = x - g, j = y - g, k = z - g;
-    if (i >= 0 && i < nx && j >= 0 && j < ny && k >= 0 && k < nz) continue;
-    const int ii = ((i % nx) + nx) % nx, jj = ((j % ny) + ny) % ny, kk = ((k % nz) + nz) % nz;
-    u[f * sf + (long long)z * sz + (long long)y * sy + x] =
-        u[f * sf + (long long)(kk + g) * sz + (long long)(jj + g) * sy + (ii + g)];
+__global__ void __launch_bounds__(256) ghost_fill_kernel(T* u, int nx, int ny, int nz, int g,
+                                                         long long sy, long long sz, long long sf) {
+  const unsigned X = nx + 2 * g, Y = ny + 2 * g, G2 = 2 * g;
+  const unsigned s1 = G2 * X * Y, s2 = G2 * X * nz, total = s1 + s2 + G2 * ny * nz;
+  T* uf = u + blockIdx.y * sf;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    int x, y, z;  // ghosted coordinates of the ghost point
+    if (t < s1) {
+      x = t % X;
+      y = (t / X) % Y;
+      const int q = t / (X * Y);
+      z = q < g ? q : nz + q;
+    } else if (t < s1 + s2) {
+      const unsigned r = t - s1;
+      x = r % X;
+      const int q = (r / X) % G2;
+      y = q < g ? q : ny + q;
+      z = g + (int)(r / (X * G2));
+    } else {
+      const unsigned r = t - s1 - s2;
+      const int q = r % G2;
+      x = q < g ? q : nx + q;
+      y = g + (int)((r / G2) % ny);
+      z = g + (int)(r / (G2 * ny));
+    }
+    // interior source: the periodic image of (x, y, z) - g (more than one
+    // wrap only when the patch is thinner than its ghost zone)
+    int i = x - g, j = y - g, k = z - g;
+    while (i < 0) i += nx;
+    while (i >= nx) i -= nx;
+    while (j < 0) j += ny;
+    while (j >= ny) j -= ny;
+    while (k < 0) k += nz;
+    while (k >= nz) k -= nz;
+    i += g;
+    j += g;
+    k += g;
+    uf[(long long)z * sz + (long long)y * sy + x] = uf[(long long)k * sz + (long long)j * sy + i];
   }
 }
 
@@ -314,16 +342,19 @@ sf_status sf_fill_ghosts_periodic(const sf_patch* patch, void* array, int32_t nf
   p.u_stage = array;
   sf_status e = check_patch(&dummy, p, 0, 0);
   if (e) return e;
-  const long long total = (long long)(p.n[0] + 2 * p.ghost) * (p.n[1] + 2 * p.ghost) *
-                          (p.n[2] + 2 * p.ghost) * nf;
-  int blocks = (int)((total + 255) / 256);
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  const long long g = p.ghost, X = p.n[0] + 2 * g, Y = p.n[1] + 2 * g;
+  const long long shell = 2 * g * (X * Y + X * p.n[2] + (long long)p.n[1] * p.n[2]);
+  if (shell >= (1LL << 31)) return set_error(SF_EINVAL, "ghost shell of %lld points too large", shell);
+  if (nf > 65535) return set_error(SF_EINVAL, "nf = %d > 65535", nf);
+  long long gx = (shell + 255) / 256;
+  if (gx > 1024) gx = 1024;
+  const dim3 grid((unsigned)gx, (unsigned)nf);
   if (p.precision == SF_FP64)
-    ghost_fill_kernel<double><<<blocks, 256, 0, (cudaStream_t)stream>>>(
-        (double*)array, nf, p.n[0], p.n[1], p.n[2], p.ghost, p.sy, p.sz, p.sf);
+    ghost_fill_kernel<double><<<grid, 256, 0, (cudaStream_t)stream>>>(
+        (double*)array, p.n[0], p.n[1], p.n[2], p.ghost, p.sy, p.sz, p.sf);
   else
-    ghost_fill_kernel<float><<<blocks, 256, 0, (cudaStream_t)stream>>>(
-        (float*)array, nf, p.n[0], p.n[1], p.n[2], p.ghost, p.sy, p.sz, p.sf);
+    ghost_fill_kernel<float><<<grid, 256, 0, (cudaStream_t)stream>>>(
+        (float*)array, p.n[0], p.n[1], p.n[2], p.ghost, p.sy, p.sz, p.sf);
   return after_launch("ghost_fill_kernel");
 }
 

@@ -95,6 +95,19 @@ def test_wave_rhs_and_ghost_fill():
     assert rel_err(r, want).max() < TOL64
 
 
+@pytest.mark.parametrize("n", [(1, 2, 5), (2, 1, 1), (33, 4, 3)])
+@pytest.mark.parametrize("precision", [capi.SF_FP64, capi.SF_FP32_BULK])
+def test_periodic_ghost_fill_thin_patches(n, precision):
+    # patches thinner than the ghost zone wrap more than once; the fill is a
+    # copy, so it is bit-exact against the oracle's in either precision
+    U0 = inputs.wave_noise(n, seed=7, amp=1.0)
+    st = PatchState(capi.SF_WAVE, n, (0.1, 0.1, 0.1), 0.01, precision=precision)
+    st.upload(U0)
+    want = oracle.ghosted(U0.astype(np.float32).astype(np.float64) if precision else U0.copy())
+    got = st.A.cpu().numpy()[..., :n[0] + 6].astype(np.float64)
+    np.testing.assert_array_equal(got, want)
+
+
 def test_wave_adjoint_step():
     n = (19, 11, 9)
     dx = (1 / 19, 1 / 11, 1 / 9)
