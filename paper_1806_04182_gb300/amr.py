@@ -147,8 +147,9 @@ class SubcycledPair:
     the fine interior is injected into the coarse points it covers.
 
     The coarse stage states that BOR needs are the stage inputs the coarse
-    substeps leave behind; only those that a later coarse stage overwrites
-    are copied aside (RK4: U^n and U^(2); SSP-RK3: U^n).
+    substeps leave behind.  U^n, which the last coarse stage overwrites, is
+    copied aside; under RK4 the third coarse stage writes U^(4) into an array
+    of its own (instead of over U^(2), as a lone patch does), so U^(2) stays.
     """
 
     def __init__(self, coarse: PatchState, fine: PatchState, ratio: int, at,
@@ -170,7 +171,6 @@ class SubcycledPair:
         self.S0 = torch.zeros(coarse.shape, **kw)
         self.S1 = torch.zeros(coarse.shape, **kw) if self.rk == capi.SF_RK4 else None
         self._box_S0 = whole_array_box(coarse, coarse.A, self.S0)
-        self._box_S1 = whole_array_box(coarse, coarse.B, self.S1) if self.S1 is not None else None
         cext = tuple(v // ratio for v in fine.n)
         self._restrict = restrict_box(fine, coarse, ratio, self.at, cext, fine_at=self.at)
         self._shell = ghost_shell_boxes(fine)
@@ -184,9 +184,16 @@ class SubcycledPair:
     def _states(self):
         c = self.coarse
         if self.rk == capi.SF_RK4:
-            return [self.S0.data_ptr(), self.S1.data_ptr(), c.C.data_ptr(), c.B.data_ptr(),
+            return [self.S0.data_ptr(), c.B.data_ptr(), c.C.data_ptr(), self.S1.data_ptr(),
                     c.A.data_ptr()]
         return [self.S0.data_ptr(), c.B.data_ptr(), c.C.data_ptr(), c.A.data_ptr()]
+
+    def _coarse_stage_patch(self, s: int) -> capi.sf_patch:
+        """The coarse patch's stage s; under RK4 U^(4) goes to S1."""
+        c = self.coarse
+        if self.rk == capi.SF_RK4 and s >= 2:
+            return c.patch(self.S1, c.A, c.A) if s == 3 else c.patch(c.C, c.A, self.S1)
+        return c.stage_patch(s)
 
     def fill_fine_ghosts(self, array, r: int, stage: int, stream=None) -> None:
         """BOR value of fine step r, fine stage `stage`, into the ghost shell
@@ -211,12 +218,10 @@ class SubcycledPair:
         for _ in range(nsteps):
             capi.sf_copy_boxes([self._box_S0], c.precision, h)
             for s in range(c.nstages):
-                cp = c.stage_patch(s)
+                cp = self._coarse_stage_patch(s)
                 capi.sf_substep(c.prm, cp, s, h)
                 if self.radiative is not None:
                     capi.sf_radiative_substep(c.prm, cp, *self.radiative, s, h)
-                if s == 0 and self._box_S1 is not None:
-                    capi.sf_copy_boxes([self._box_S1], c.precision, h)
             for r in range(R):
                 for s in range(f.nstages):
                     self.fill_fine_ghosts(f.roles(s)[0], r, s, h)
