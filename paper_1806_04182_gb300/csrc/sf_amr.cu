@@ -66,10 +66,11 @@ __global__ void __launch_bounds__(256) copy_boxes_kernel(BoxBatch bb) {
 }
 
 // One output box of a prolongation launch: fine points origin..origin+ext-1
-// written to out with element strides (osy, osz, osf); p[3] = the box's tile
-// of fine points, t[3] = tiles per axis.
+// written to out with element strides (osy, osz, osf); kind = the box's tile
+// shape (kTileShapes), p[3] = that tile of fine points, t[3] = tiles per axis.
 struct PBox {
   int origin[3], ext[3], p[3], t[3];
+  int kind;
   void* out;
   long long osy, osz, osf;
 };
@@ -122,8 +123,8 @@ __device__ __forceinline__ float lagrange_w<float>(const ProlongArgs& p, int r, 
   return p.wf[r][q];
 }
 
-// Fine tile of PX x PY x PZ points per CTA, chosen per box: 32 x 4 x 4 for
-// a thick box; for a box at most 4 points thin along one axis (the slabs of a
+// Fine tile of PX x PY x PZ points per CTA, chosen per box: 32 x 8 x 4 for a
+// thick box; for a box at most 4 points thin along one axis (the slabs of a
 // ghost shell) a tile 4 points deep along that axis and wider along the
 // others, 4 x 16 x 16, 32 x 4 x 16 or 32 x 16 x 4, so that the coarse nodes
 // a tile stages serve more fine points.  Along each axis the tile's points
@@ -134,45 +135,56 @@ __device__ __forceinline__ float lagrange_w<float>(const ProlongArgs& p, int r, 
 // CTA, so thin boxes still fill the GPU.  18 weighted sums per fine point and
 // field instead of 216, and the 6-point order of summation is the tensor
 // product's (x innermost).
+//
+// The tile shapes are compile-time constants of the tile body, so every
+// index into the staged arrays splits by constant divisors; the fine offsets'
+// coarse node and weight row along each axis come from small tables the CTA
+// builds once (the only divisions by R).
 struct TileShape {
   int px, py, pz;
 };
+constexpr TileShape kTileShapes[4] = {{32, 8, 4}, {4, 16, 16}, {32, 4, 16}, {32, 16, 4}};
+constexpr int kThick = 0, kThinX = 1, kThinY = 2, kThinZ = 3;
+constexpr int kProlongThreads = 256;
+constexpr int kProlongTableBytes = 8 * 6 * 8 + 3 * 32 * 4;  // weights [R][6], node/row tables [3][32]
 constexpr int prolong_elems(TileShape t) {
   return (t.pz + 6) * (t.py + 6) * (t.px + 6) + (t.pz + 6) * (t.py + 6) * t.px +
          (t.pz + 6) * t.py * t.px;
 }
-constexpr TileShape kThick = {32, 4, 4}, kThinX = {4, 16, 16}, kThinY = {32, 4, 16},
-                    kThinZ = {32, 16, 4};
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
-constexpr int kProlongMaxElems = cmax(cmax(prolong_elems(kThick), prolong_elems(kThinX)),
-                                      cmax(prolong_elems(kThinY), prolong_elems(kThinZ)));
+constexpr int kProlongMaxElems =
+    cmax(cmax(prolong_elems(kTileShapes[0]), prolong_elems(kTileShapes[1])),
+         cmax(prolong_elems(kTileShapes[2]), prolong_elems(kTileShapes[3])));
+template <typename T>
+constexpr int prolong_smem_bytes(int elems) {
+  return elems * (int)sizeof(T) + kProlongTableBytes;
+}
 template <typename T>
 constexpr int prolong_smem_max() {
-  return kProlongMaxElems * (int)sizeof(T);
+  return prolong_smem_bytes<T>(kProlongMaxElems);
 }
 static_assert(prolong_smem_max<double>() <= 227 * 1024, "prolongation tile fits shared memory");
 
-static TileShape tile_for(const int* ext) {
+static int tile_for(const int* ext) {
   if (ext[0] <= 4) return kThinX;
   if (ext[1] <= 4) return kThinY;
   if (ext[2] <= 4) return kThinZ;
   return kThick;
 }
 
-template <typename T, int NS>
-__global__ void __launch_bounds__(256) prolong_kernel(Combo<T> cb, ProlongArgs p) {
-  extern __shared__ __align__(16) unsigned char psm_raw[];
-  const int R = p.R;
-  // the CTA's box, tile and field (one field per CTA, field slowest)
-  int bi = 0;
-  while (bi + 1 < p.nbox && (int)blockIdx.x >= p.tiles_end[bi]) ++bi;
-  const PBox& B = p.box[bi];
-  const int PX = B.p[0], PY = B.p[1], PZ = B.p[2];
-  const int CXM = PX + 6, CYM = PY + 6, CZM = PZ + 6;
-  T* cn = reinterpret_cast<T*>(psm_raw);  // [CZM][CYM][CXM]
+template <typename T, int NS, int PX, int PY, int PZ>
+__device__ __forceinline__ void prolong_tile(const Combo<T>& cb, const ProlongArgs& p, const PBox& B,
+                                             int local, unsigned char* raw) {
+  constexpr int CXM = PX + 6, CYM = PY + 6, CZM = PZ + 6;
+  constexpr int NT = kProlongThreads;
+  static_assert(NT % PX == 0 && PX <= 32 && PY <= 32 && PZ <= 32, "tile shape");
+  constexpr int ROWS = NT / PX;           // rows of a pass per sweep of the CTA
+  T* cn = reinterpret_cast<T*>(raw);      // [CZM][CYM][CXM] staged nodes
   T* tx = cn + CZM * CYM * CXM;           // [CZM][CYM][PX]
   T* ty = tx + CZM * CYM * PX;            // [CZM][PY][PX]
-  int local = (int)blockIdx.x - (bi ? p.tiles_end[bi - 1] : 0);
+  T* wt = ty + CZM * PY * PX;             // [R][6] Lagrange weights
+  int* tab = reinterpret_cast<int*>(wt + 48);  // [3][32]: 8 x first node + weight row
+  const int R = p.R;
   const int xt = local % B.t[0];
   local /= B.t[0];
   const int yt = local % B.t[1];
@@ -190,46 +202,107 @@ __global__ void __launch_bounds__(256) prolong_kernel(Combo<T> cb, ProlongArgs p
     nc[d] = floordiv(F0[d] + nv[d] - 1, R) + 3 - lo[d] + 1;    // coarse nodes spanned
   }
   const int tid = threadIdx.x;
+  if (tid < 48) {
+    wt[tid] = tid < 6 * R ? lagrange_w<T>(p, tid / 6, tid % 6) : T(0);
+  } else if (tid >= 64 && tid < 64 + 96) {
+    const int d = (tid - 64) >> 5, i = tid & 31;
+    const int F = (d == 0 ? F0[0] : d == 1 ? F0[1] : F0[2]) + i;
+    const int b = floordiv(F, R);
+    tab[tid - 64] = (b - 2 - (d == 0 ? lo[0] : d == 1 ? lo[1] : lo[2])) * 8 + (F - b * R);
+  }
+  // coarse nodes (the BOR combination formed once per node)
   {
-    const long long fo = f * p.sf;
-    for (int t = tid; t < nc[0] * nc[1] * nc[2]; t += blockDim.x) {
-      const int cx = t % nc[0], cy = (t / nc[0]) % nc[1], cz = t / (nc[0] * nc[1]);
-      const long long o = fo + (long long)(lo[2] + cz + p.g) * p.sz +
-                          (long long)(lo[1] + cy + p.g) * p.sy + (lo[0] + cx + p.g);
-      cn[(cz * CYM + cy) * CXM + cx] = node_value<T, NS>(cb, o);
+    const long long o0 = f * p.sf + (long long)(lo[2] + p.g) * p.sz + (long long)(lo[1] + p.g) * p.sy +
+                         (lo[0] + p.g);
+    const int end = nc[2] * CYM * CXM;
+#pragma unroll 4
+    for (int t = tid; t < end; t += NT) {
+      const int cx = t % CXM, cy = (t / CXM) % CYM, cz = t / (CXM * CYM);
+      if (cx < nc[0] && cy < nc[1])
+        cn[t] = node_value<T, NS>(cb, o0 + (long long)cz * p.sz + (long long)cy * p.sy + cx);
     }
-    __syncthreads();
-    for (int t = tid; t < nc[2] * nc[1] * nv[0]; t += blockDim.x) {
-      const int xi = t % nv[0], cy = (t / nv[0]) % nc[1], cz = t / (nv[0] * nc[1]);
-      const int F = F0[0] + xi, b = floordiv(F, R), r = F - b * R;
-      const T* row = cn + (cz * CYM + cy) * CXM + (b - 2 - lo[0]);
+  }
+  __syncthreads();
+  const int xi = tid % PX;  // the same x offset in every sweep (NT is a multiple of PX)
+  {
+    const int e = tab[xi];
+    const T* w = wt + (e & 7) * 6;
+    T wx[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) wx[q] = w[q];
+    const int s0 = e >> 3;
+    const int end = nc[2] * CYM;
+    if (xi < nv[0])
+      for (int row = tid / PX; row < end; row += ROWS) {
+        if (row % CYM >= nc[1]) continue;
+        const T* c = cn + row * CXM + s0;
+        T v = T(0);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v += wx[q] * c[q];
+        tx[row * PX + xi] = v;
+      }
+  }
+  __syncthreads();
+  {
+    const int end = nc[2] * PY;
+    if (xi < nv[0])
+      for (int row = tid / PX; row < end; row += ROWS) {
+        const int yi = row % PY, cz = row / PY;
+        if (yi >= nv[1]) continue;
+        const int e = tab[32 + yi];
+        const T* c = tx + (cz * CYM + (e >> 3)) * PX + xi;
+        const T* w = wt + (e & 7) * 6;
+        T v = T(0);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v += w[q] * c[q * PX];
+        ty[row * PX + xi] = v;
+      }
+  }
+  __syncthreads();
+  if (xi < nv[0]) {
+    T* o = out + f * B.osf + (long long)(F0[2] - B.origin[2]) * B.osz +
+           (long long)(F0[1] - B.origin[1]) * B.osy + (F0[0] - B.origin[0]) + xi;
+    static_assert(PX * PY * PZ % NT == 0, "whole sweeps");
+#pragma unroll
+    for (int k = 0; k < PX * PY * PZ / NT; ++k) {
+      const int t = tid + k * NT;
+      const int yi = (t / PX) % PY, zi = t / (PX * PY);
+      if (yi >= nv[1] || zi >= nv[2]) continue;
+      const int e = tab[64 + zi];
+      const T* c = ty + ((e >> 3) * PY + yi) * PX + xi;
+      const T* w = wt + (e & 7) * 6;
       T v = T(0);
 #pragma unroll
-      for (int q = 0; q < 6; ++q) v += lagrange_w<T>(p, r, q) * row[q];
-      tx[(cz * CYM + cy) * PX + xi] = v;
+      for (int q = 0; q < 6; ++q) v += w[q] * c[q * PY * PX];
+      o[(long long)zi * B.osz + (long long)yi * B.osy] = v;
     }
-    __syncthreads();
-    for (int t = tid; t < nc[2] * nv[1] * nv[0]; t += blockDim.x) {
-      const int xi = t % nv[0], yi = (t / nv[0]) % nv[1], cz = t / (nv[0] * nv[1]);
-      const int F = F0[1] + yi, b = floordiv(F, R), r = F - b * R;
-      const T* col = tx + (cz * CYM + (b - 2 - lo[1])) * PX + xi;
-      T v = T(0);
-#pragma unroll
-      for (int q = 0; q < 6; ++q) v += lagrange_w<T>(p, r, q) * col[q * PX];
-      ty[(cz * PY + yi) * PX + xi] = v;
-    }
-    __syncthreads();
-    for (int t = tid; t < nv[2] * nv[1] * nv[0]; t += blockDim.x) {
-      const int xi = t % nv[0], yi = (t / nv[0]) % nv[1], zi = t / (nv[0] * nv[1]);
-      const int F = F0[2] + zi, b = floordiv(F, R), r = F - b * R;
-      const T* col = ty + ((b - 2 - lo[2]) * PY + yi) * PX + xi;
-      T v = T(0);
-#pragma unroll
-      for (int q = 0; q < 6; ++q) v += lagrange_w<T>(p, r, q) * col[q * PY * PX];
-      const int i = F0[0] - B.origin[0] + xi, j = F0[1] - B.origin[1] + yi,
-                k = F0[2] - B.origin[2] + zi;
-      out[f * B.osf + (long long)k * B.osz + (long long)j * B.osy + i] = v;
-    }
+  }
+}
+
+template <typename T, int NS>
+__global__ void __launch_bounds__(kProlongThreads) prolong_kernel(Combo<T> cb, ProlongArgs p) {
+  extern __shared__ __align__(16) unsigned char psm_raw[];
+  // the CTA's box, tile and field (one field per CTA, field slowest)
+  int bi = 0;
+  while (bi + 1 < p.nbox && (int)blockIdx.x >= p.tiles_end[bi]) ++bi;
+  const PBox& B = p.box[bi];
+  const int local = (int)blockIdx.x - (bi ? p.tiles_end[bi - 1] : 0);
+  switch (B.kind) {
+    case kThinX:
+      prolong_tile<T, NS, kTileShapes[kThinX].px, kTileShapes[kThinX].py, kTileShapes[kThinX].pz>(
+          cb, p, B, local, psm_raw);
+      break;
+    case kThinY:
+      prolong_tile<T, NS, kTileShapes[kThinY].px, kTileShapes[kThinY].py, kTileShapes[kThinY].pz>(
+          cb, p, B, local, psm_raw);
+      break;
+    case kThinZ:
+      prolong_tile<T, NS, kTileShapes[kThinZ].px, kTileShapes[kThinZ].py, kTileShapes[kThinZ].pz>(
+          cb, p, B, local, psm_raw);
+      break;
+    default:
+      prolong_tile<T, NS, kTileShapes[kThick].px, kTileShapes[kThick].py, kTileShapes[kThick].pz>(
+          cb, p, B, local, psm_raw);
   }
 }
 
@@ -453,7 +526,8 @@ static sf_status prolong_launch(const sf_patch* coarse, const void* const* array
         B.origin[d] = bx.origin[d];
         B.ext[d] = bx.ext[d];
       }
-      const TileShape ts = tile_for(bx.ext);
+      B.kind = tile_for(bx.ext);
+      const TileShape ts = kTileShapes[B.kind];
       B.p[0] = ts.px;
       B.p[1] = ts.py;
       B.p[2] = ts.pz;
@@ -480,7 +554,8 @@ static sf_status prolong_launch(const sf_patch* coarse, const void* const* array
         cudaFuncSetAttribute(prolong_kernel<double, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              prolong_smem_max<double>());
       });
-      prolong_kernel<double, NS><<<(unsigned)total, 256, smem_elems * sizeof(double), st>>>(cb, a);
+      prolong_kernel<double, NS><<<(unsigned)total, kProlongThreads, prolong_smem_bytes<double>(smem_elems),
+                                    st>>>(cb, a);
     } else {
       Combo<float> cb;
       for (int m = 0; m < 5; ++m) cb.s[m] = m <= NS ? (const float*)arrays[m] : nullptr;
@@ -490,7 +565,8 @@ static sf_status prolong_launch(const sf_patch* coarse, const void* const* array
         cudaFuncSetAttribute(prolong_kernel<float, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              prolong_smem_max<float>());
       });
-      prolong_kernel<float, NS><<<(unsigned)total, 256, smem_elems * sizeof(float), st>>>(cb, a);
+      prolong_kernel<float, NS><<<(unsigned)total, kProlongThreads, prolong_smem_bytes<float>(smem_elems),
+                                   st>>>(cb, a);
     }
     e = after_launch("prolong_kernel");
     if (e) return e;
