@@ -546,6 +546,36 @@ def _amr_rows(hbm_peak: float) -> list[dict]:
     out.append({"workload": "halo_sync_8_patches_48cubed_ccz4_fp32", "value": gbs, "unit": "GB/s",
                 "ms_per_call": ms / 50, "bytes_per_call": 2 * moved, "hbm_frac": gbs / hbm_peak,
                 "note": f"{len(boxes)} box copies (26 per patch), read + write counted"})
+    # the same 96^3 CCZ4 box as a level of 2 x 2 x 2 patches stepped as ONE batch: every
+    # stage's TMA tile launch ends with the halo copies of the buffer it wrote, and one RK4
+    # step of the level (stages + synchronisation) is one captured graph
+    Ub, dxb = inputs.z4_minkowski_noise((96, 96, 96), seed=0, amp=1e-10)
+    level = {}
+    for a in range(2):
+        for b_ in range(2):
+            for c in range(2):
+                st = PatchState(capi.SF_Z4, m, dxb, 0.25 * dxb[0], precision=capi.SF_FP32_BULK_DW,
+                                prm=capi.params(ghosts=capi.SF_GHOSTS_NONE), x_pitch=56)
+                st.upload(np.ascontiguousarray(Ub[:, c * 48:(c + 1) * 48, b_ * 48:(b_ + 1) * 48,
+                                                  a * 48:(a + 1) * 48]))
+                level[(a, b_, c)] = st
+    gs = torch.cuda.Stream()
+    gs.wait_stream(torch.cuda.current_stream())
+    lb = amr.level_batch(level)
+    try:
+        with torch.cuda.stream(gs):
+            capi.sf_copy_boxes(amr.halo_boxes(level, "A"), capi.SF_FP32_BULK_DW, gs.cuda_stream)
+            capi.sf_batch_capture(lb, gs.cuda_stream)
+            nlevel = 20
+            ms = _events_time(lambda: capi.sf_batch_launch(lb, gs.cuda_stream), nlevel, 3)
+        out.append({"workload": "level_8_patches_48cubed_ccz4_fp32dw_batch_halo_graph",
+                    "value": 96 ** 3 * 4 * nlevel / (ms * 1e-3), "unit": UNIT,
+                    "ms_per_step": ms / nlevel, "launches_per_step": capi.sf_batch_launches_per_step(lb),
+                    "note": "96^3 CCZ4 box as 2x2x2 patches of 48^3 (rows of 56 floats): per stage one "
+                            "TMA tile launch over all patches + one launch of the 208 halo box copies, "
+                            "one graph per RK4 step (amr.level_batch)"})
+    finally:
+        capi.sf_batch_destroy(lb)
     # prolongation of a 96^3 fine box (ratio 2) from a 48^3 coarse CCZ4 patch, and the BOR form
     cst = PatchState(capi.SF_Z4, m, (2 / 96,) * 3, 0.5 / 96, precision=capi.SF_FP32_BULK_DW)
     U0, _ = inputs.z4_perturbed(m, seed=1, amp=0.02)

@@ -330,6 +330,9 @@ sf_status sf_bor_prolong_boxes(const sf_patch* coarse, int32_t rk, const void* c
  * stage kernel: one launch per stage for each tile width in use (32 x 12 or
  * 16 x 24 points; each patch takes the width that covers it with fewer
  * tiles), ahead of the persistent launch for the other patches.
+ * prm->ghosts applies to every patch: SF_GHOSTS_PERIODIC, each patch
+ * periodic on its own (the stages write its periodic ghost shell), or
+ * SF_GHOSTS_NONE, ghosts left to sf_batch_set_halo or the caller.
  * sf_batch_create copies the patch table (and the TMA patches' tensor maps
  * and tile lists) to the device (allocates; not in the hot path).
  * sf_batch_tune times the tile shapes of the persistent kernel for each
@@ -344,8 +347,22 @@ sf_status sf_batch_substep(sf_batch* b, int32_t stage, void* stream);
 sf_status sf_batch_tune(sf_batch* b, void* stream);
 sf_status sf_batch_capture(sf_batch* b, void* stream);
 sf_status sf_batch_launch(sf_batch* b, void* stream);
-/* Number of kernel launches (TMA tile launches and persistent launches) made
- * by one sf_batch_launch, i.e. one RK4 step. */
+/*
+ * Patches that tile a level (Sec. III: the patches of one level exchange
+ * ghost zones, "level synchronisation"), created with ghosts =
+ * SF_GHOSTS_NONE: sf_batch_set_halo gives, for buffer role `role` (0: the
+ * u_n arrays, 1: u_stage, 2: u_next, as passed to sf_batch_create), the box
+ * copies that fill every patch's ghost shell from its neighbours' interiors
+ * (sf_box_copy semantics).  Each stage then ends with the copies of the role
+ * it wrote (stage 0: u_stage, 1: u_next, 2: u_stage, 3: u_n), launched by
+ * sf_batch_substep on its stream and recorded by sf_batch_capture.  The list
+ * is copied (nbox = 0 clears it); the caller keeps the arrays alive.  Setting
+ * a list drops a captured graph (capture again).  Errors: SF_EINVAL for a
+ * NULL batch, a role outside 0..2, or a box sf_copy_boxes would reject.
+ */
+sf_status sf_batch_set_halo(sf_batch* b, int32_t role, const sf_box_copy* boxes, int32_t nbox);
+/* Number of kernel launches (TMA tile launches, persistent launches and halo
+ * box-copy launches) made by one sf_batch_launch, i.e. one RK4 step. */
 int32_t sf_batch_launches_per_step(const sf_batch* b);
 sf_status sf_batch_destroy(sf_batch* b);
 

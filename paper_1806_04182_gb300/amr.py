@@ -4,6 +4,10 @@
   patches exchanges its ghost shells with ``sf_copy_boxes``; for each patch
   and each of its 26 neighbours, the neighbour's interior slab next to the
   shared face, edge or corner is copied into this patch's ghost zone.
+* A level stepped as one batch (``level_batch``): the patches of the grid
+  go into one ``sf_batch`` whose every stage ends with the ghost-shell
+  copies of the buffer it wrote, so a whole step of the level (stage
+  kernels and synchronisation) is one captured CUDA graph.
 * Restriction by injection (``restrict_box``).
 * Sub-cycling in time (``SubcycledPair``): a periodic coarse patch and one
   fine patch R times finer in space and time; the fine ghost zone at every
@@ -77,6 +81,26 @@ def halo_boxes(grid: dict, which: str = "A") -> list:
             bx.reserved = 0
             boxes.append(bx)
     return boxes
+
+
+def level_batch(grid: dict) -> int:
+    """One sf_batch over the patches of `grid` (as for halo_boxes; created
+    with ghosts=SF_GHOSTS_NONE and one common precision and RK scheme) with
+    the halo copies of each buffer role registered: u_n = A, u_stage = B,
+    u_next = C.  Fill the A ghosts once (sf_copy_boxes of halo_boxes(grid,
+    "A")) before the first step.  The caller destroys the batch."""
+    sts = list(grid.values())
+    prm = sts[0].prm
+    if prm.ghosts != capi.SF_GHOSTS_NONE:
+        raise ValueError("level patches need ghosts=SF_GHOSTS_NONE (their ghosts come from neighbours)")
+    b = capi.sf_batch_create(prm, [st.patch(st.B, st.A, st.C) for st in sts])
+    try:
+        for role, name in enumerate("ABC"):
+            capi.sf_batch_set_halo(b, role, halo_boxes(grid, name))
+    except Exception:
+        capi.sf_batch_destroy(b)
+        raise
+    return b
 
 
 def restrict_box(fine: PatchState, coarse: PatchState, ratio: int, coarse_origin, ext,

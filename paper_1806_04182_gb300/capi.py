@@ -26,7 +26,7 @@ EXPORTS = ["sf_nfields", "sf_substep", "sf_rhs", "sf_fill_ghosts_periodic", "sf_
            "sf_adjoint_substep", "sf_gather", "sf_scatter_add", "sf_diagnostics",
            "sf_batch_create", "sf_batch_substep", "sf_batch_tune", "sf_batch_capture",
            "sf_batch_launch", "sf_batch_launches_per_step", "sf_batch_destroy",
-           "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong", "sf_bor_prolong", "sf_bor_prolong_boxes", "sf_radiative_substep",
+           "sf_batch_set_halo", "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong", "sf_bor_prolong", "sf_bor_prolong_boxes", "sf_radiative_substep",
            "sf_selftest_wait_timeout", "sf_get_device_status", "sf_last_error", "sf_launch_count"]
 
 
@@ -148,6 +148,7 @@ def lib() -> ctypes.CDLL:
         L.sf_batch_destroy.argtypes = [vp]
         L.sf_batch_substep_static.argtypes = [P(sf_params), P(sf_patch), i32, i32, vp]
         L.sf_copy_boxes.argtypes = [P(sf_box_copy), i32, i32, vp]
+        L.sf_batch_set_halo.argtypes = [vp, i32, P(sf_box_copy), i32]
         L.sf_prolong.argtypes = [P(sf_patch), vp, i32, i32, P(i32), P(i32), vp, i64, i64, i64, vp]
         L.sf_bor_prolong_boxes.argtypes = [P(sf_patch), i32, P(vp), i32, i32, i32, i32,
                                            P(sf_prolong_box), i32, vp]
@@ -166,7 +167,7 @@ def lib() -> ctypes.CDLL:
                      "sf_batch_create", "sf_batch_substep", "sf_batch_tune", "sf_batch_capture",
                      "sf_batch_launch", "sf_batch_destroy", "sf_get_device_status",
                      "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong",
-                     "sf_selftest_wait_timeout"):
+                     "sf_batch_set_halo", "sf_selftest_wait_timeout"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -249,6 +250,13 @@ def sf_batch_capture(batch: int, stream: int) -> None:
 
 def sf_batch_launch(batch: int, stream: int = 0) -> None:
     _check(lib().sf_batch_launch(batch, stream), "sf_batch_launch")
+
+
+def sf_batch_set_halo(batch: int, role: int, boxes) -> None:
+    """Ghost-shell box copies run after every stage that writes buffer role
+    `role` (0: u_n, 1: u_stage, 2: u_next)."""
+    arr = (sf_box_copy * max(1, len(boxes)))(*boxes)
+    _check(lib().sf_batch_set_halo(batch, role, arr, len(boxes)), "sf_batch_set_halo")
 
 
 def sf_batch_launches_per_step(batch: int) -> int:

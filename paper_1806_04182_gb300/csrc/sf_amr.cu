@@ -403,12 +403,8 @@ static void bor_coefficients(int rk, int R, int r, int stage, double c[4]) {
   }
 }
 
-}  // namespace sf
-
-using namespace sf;
-
-extern "C" sf_status sf_copy_boxes(const sf_box_copy* boxes, int32_t nbox, int32_t precision,
-                                   void* stream) {
+// Host checks of a box-copy list (everything sf_copy_boxes rejects).
+sf_status check_box_copies(const sf_box_copy* boxes, int nbox, int precision) {
   if (nbox < 0 || (nbox > 0 && !boxes)) return set_error(SF_EINVAL, "boxes NULL or nbox < 0");
   if (precision < SF_FP64 || precision > SF_FP32_BULK_DW)
     return set_error(SF_EINVAL, "unknown precision %d", precision);
@@ -423,6 +419,30 @@ extern "C" sf_status sf_copy_boxes(const sf_box_copy* boxes, int32_t nbox, int32
     if ((long long)b.ext[0] * b.ext[1] * b.ext[2] * b.nf >= (1LL << 31))
       return set_error(SF_EINVAL, "box %d: more than 2^31 values", q);
   }
+  return SF_OK;
+}
+
+// Kernel launches sf_copy_boxes makes for a list: one per group of
+// kBoxesPerLaunch boxes that holds a non-empty box.
+int box_copy_launches(const sf_box_copy* boxes, int nbox) {
+  int n = 0;
+  for (int q0 = 0; q0 < nbox; q0 += kBoxesPerLaunch) {
+    bool any = false;
+    for (int q = q0; q < nbox && q < q0 + kBoxesPerLaunch; ++q)
+      any = any || (long long)boxes[q].ext[0] * boxes[q].ext[1] * boxes[q].ext[2] * boxes[q].nf > 0;
+    n += any ? 1 : 0;
+  }
+  return n;
+}
+
+}  // namespace sf
+
+using namespace sf;
+
+extern "C" sf_status sf_copy_boxes(const sf_box_copy* boxes, int32_t nbox, int32_t precision,
+                                   void* stream) {
+  sf_status e0 = check_box_copies(boxes, nbox, precision);
+  if (e0) return e0;
   cudaStream_t st = (cudaStream_t)stream;
   for (int q0 = 0; q0 < nbox; q0 += kBoxesPerLaunch) {
     static_assert(sizeof(BoxBatch) < 32000, "kernel parameter limit");

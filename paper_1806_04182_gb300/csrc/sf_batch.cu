@@ -16,6 +16,10 @@
 //   u_stage = B, u_next = C: stage scratch
 //   acc = D: RK4 accumulator, kahan = E (FP32_BULK)
 // stage 0: A -> B, stage 1: B -> C, stage 2: C -> B, stage 3: B -> A.
+// Patches that tile a level (ghosts = SF_GHOSTS_NONE) get their ghost shells
+// from their neighbours: sf_batch_set_halo gives, per buffer role, the box
+// copies that fill them, and each stage ends with one sf_copy_boxes launch
+// for the role it wrote (inside the captured graph too).
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -105,9 +109,15 @@ struct sf_batch {
   TmaTile* d_tiles = nullptr;   // 32 x 12 tiles, then 16 x 24 tiles
   int ntiles = 0;               // all TMA tiles
   int ntiles16 = 0;             // of which the last ntiles16 are 16 x 24
+  std::vector<sf_box_copy> halo[3];  // ghost-shell copies per buffer role (u_n, u_stage, u_next)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
+
+namespace {
+// buffer role each stage writes: B, C, B, A
+constexpr int kOutRole[4] = {1, 2, 1, 0};
+}  // namespace
 
 namespace {
 
@@ -226,7 +236,7 @@ StageArgs batch_stage_args(const sf_batch* b, int stage, unsigned int* status) {
   s.stage = stage;
   s.kahan = b->precision != SF_FP64 ? 1 : 0;
   s.un_alias = stage == 0 ? 1 : 0;
-  s.ghosts = 1;
+  s.ghosts = b->prm.ghosts == SF_GHOSTS_PERIODIC ? 1 : 0;
   s.check_finite = b->prm.check_finite;
   s.status = status;
   return s;
@@ -279,10 +289,11 @@ sf_status sf_batch_create(const sf_params* prm, const sf_patch* patches, int32_t
                           sf_batch** out) {
   if (!prm || !patches || !out || npatch < 1) return set_error(SF_EINVAL, "NULL argument or npatch < 1");
   if (prm->rk != SF_RK4) return set_error(SF_ENOTSUP, "sf_batch runs RK4");
+  if (prm->ghosts != SF_GHOSTS_NONE && prm->ghosts != SF_GHOSTS_PERIODIC)
+    return set_error(SF_EINVAL, "ghosts %d not SF_GHOSTS_NONE or SF_GHOSTS_PERIODIC", prm->ghosts);
   *out = nullptr;
   sf_batch* b = new sf_batch();
   b->prm = *prm;
-  b->prm.ghosts = SF_GHOSTS_PERIODIC;
   b->npatch = npatch;
   b->precision = patches[0].precision;
   b->patches.assign(patches, patches + npatch);
@@ -349,11 +360,32 @@ sf_status sf_batch_substep(sf_batch* b, int32_t stage, void* stream) {
   if (stage < 0 || stage > 3) return set_error(SF_EINVAL, "stage %d out of range [0,4)", stage);
   unsigned int* status = status_ptr();
   if (!status) return set_error(SF_ECUDA, "no status word");
+  sf_status e;
   if (b->precision == SF_FP64)
-    return launch_stage<double, double>(b, stage, (cudaStream_t)stream, status);
-  if (b->precision == SF_FP32_BULK_DW)
-    return launch_stage<float, dw>(b, stage, (cudaStream_t)stream, status);
-  return launch_stage<float, double>(b, stage, (cudaStream_t)stream, status);
+    e = launch_stage<double, double>(b, stage, (cudaStream_t)stream, status);
+  else if (b->precision == SF_FP32_BULK_DW)
+    e = launch_stage<float, dw>(b, stage, (cudaStream_t)stream, status);
+  else
+    e = launch_stage<float, double>(b, stage, (cudaStream_t)stream, status);
+  if (e) return e;
+  const std::vector<sf_box_copy>& h = b->halo[kOutRole[stage]];
+  if (h.empty()) return SF_OK;
+  return sf_copy_boxes(h.data(), (int32_t)h.size(), b->precision, stream);
+}
+
+sf_status sf_batch_set_halo(sf_batch* b, int32_t role, const sf_box_copy* boxes, int32_t nbox) {
+  if (!b) return set_error(SF_EINVAL, "batch is NULL");
+  if (role < 0 || role > 2) return set_error(SF_EINVAL, "role %d not in {0, 1, 2}", role);
+  sf_status e = check_box_copies(boxes, nbox, b->precision);
+  if (e) return e;
+  b->halo[role].assign(boxes, boxes + nbox);
+  if (b->exec) {  // a captured step no longer matches: capture again
+    cudaGraphExecDestroy(b->exec);
+    cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+  }
+  return SF_OK;
 }
 
 sf_status sf_batch_tune(sf_batch* b, void* stream) {
@@ -446,7 +478,12 @@ int32_t sf_batch_launches_per_step(const sf_batch* b) {
   const int n32 = b->ntiles - b->ntiles16;
   const int per_stage = (n32 > 0 ? 1 : 0) + (b->ntiles16 > 0 ? 1 : 0) +
                         (b->ntiles == 0 || b->nitems > 0 ? 1 : 0);
-  return 4 * per_stage;
+  int halo = 0;
+  for (int s = 0; s < 4; ++s) {
+    const std::vector<sf_box_copy>& h = b->halo[kOutRole[s]];
+    halo += box_copy_launches(h.data(), (int)h.size());
+  }
+  return 4 * per_stage + halo;
 }
 
 sf_status sf_batch_destroy(sf_batch* b) {

@@ -36,6 +36,10 @@ sf_status encode_z4_tma_map(void* map, const sf_patch& p, const void* base, int 
 sf_status launch_z4_tma_batch(const sf_params& prm, int precision, const void* d_maps, int role,
                               const PatchArgs<float>* d_args, const TmaTile* d_tiles, int ntiles,
                               int xp, const StageArgs& s, cudaStream_t st);
+// box copies (sf_amr.cu): the host checks of sf_copy_boxes, and the number of
+// launches it makes for a list
+sf_status check_box_copies(const sf_box_copy* boxes, int nbox, int precision);
+int box_copy_launches(const sf_box_copy* boxes, int nbox);
 // radiative boundary stage on the ghost shell (sf_radiative.cu)
 sf_status launch_radiative(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                            const double* x0, const double* u_inf, const double* speed,

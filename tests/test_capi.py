@@ -126,3 +126,11 @@ def test_selftest_wait_limit_checked(L):
             capi.sf_selftest_wait_timeout(bad)
         assert e.value.status == capi.SF_EINVAL
         assert "limit_cycles" in str(e.value)
+
+
+def test_batch_set_halo_rejects_null_batch(L):
+    # rejected on the host: no batch, so nothing reaches the device
+    with pytest.raises(capi.SfError) as e:
+        capi.sf_batch_set_halo(None, 0, [])
+    assert e.value.status == capi.SF_EINVAL
+    assert "batch is NULL" in str(e.value)

@@ -4,6 +4,9 @@
   that exchange ghost shells with sf_copy_boxes between stages must give,
   bit for bit, the state of the undecomposed periodic run (the substep is a
   pure function of its ghosted input, and both runs use the same kernels).
+* The same level as one sf_batch with the halo copies registered per buffer
+  role (amr.level_batch), stepped through its captured graph: equal to the
+  undecomposed run to rounding (the batch runs its own kernel instances).
 * Prolongation (sf_prolong) against the oracle's Lagrange interpolation;
   restriction (sf_copy_boxes with src_step = R) against the oracle's
   injection, bit for bit.
@@ -68,6 +71,78 @@ def test_decomposed_run_equals_undecomposed(system, precision, data):
     for (a, b, c), st in grid.items():
         part = W[:, c * m[2]:(c + 1) * m[2], b * m[1]:(b + 1) * m[1], a * m[0]:(a + 1) * m[0]]
         np.testing.assert_array_equal(st.interior().cpu().numpy(), part)
+
+
+@pytest.mark.parametrize("system,precision,data", CASES[:3])
+def test_level_batch_with_halo_equals_undecomposed(system, precision, data):
+    # float CCZ4 on 16-byte rows: the parts go to the batch's TMA-staged
+    # tiles, the whole patch to the TMA-staged kernel of sf_substep
+    N, parts, steps = (32, 24, 20), (2, 2, 1), 2
+    m = tuple(N[a] // parts[a] for a in range(3))
+    pitch = (lambda n: (n[0] + 6 + 3) // 4 * 4) if precision != capi.SF_FP64 else (lambda n: None)
+    U0, dx = data(N)
+    dt = 0.2 * min(dx)
+    whole = PatchState(system, N, dx, dt, precision=precision, x_pitch=pitch(N))
+    whole.upload(U0)
+    whole.step(steps)
+    grid = {}
+    for a in range(parts[0]):
+        for b in range(parts[1]):
+            st = PatchState(system, m, dx, dt, precision=precision,
+                            prm=capi.params(ghosts=capi.SF_GHOSTS_NONE), x_pitch=pitch(m))
+            st.upload(np.ascontiguousarray(U0[:, :, b * m[1]:(b + 1) * m[1], a * m[0]:(a + 1) * m[0]]))
+            grid[(a, b, 0)] = st
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    batch = amr.level_batch(grid)
+    try:
+        plain = amr.level_batch(grid)  # the same patches without halo lists
+        for role in range(3):
+            capi.sf_batch_set_halo(plain, role, [])
+        # one copy launch per stage (4 patches x 26 boxes < 256)
+        assert capi.sf_batch_launches_per_step(batch) == capi.sf_batch_launches_per_step(plain) + 4
+        capi.sf_batch_destroy(plain)
+        with torch.cuda.stream(stream):
+            capi.sf_copy_boxes(amr.halo_boxes(grid, "A"), precision, stream.cuda_stream)
+            capi.sf_batch_capture(batch, stream.cuda_stream)
+            for _ in range(steps):
+                capi.sf_batch_launch(batch, stream.cuda_stream)
+        stream.synchronize()
+        assert capi.sf_get_device_status() == capi.SF_OK
+    finally:
+        capi.sf_batch_destroy(batch)
+    W = whole.interior().cpu().numpy()
+    h = min(dx)
+    eps32 = float(np.finfo(np.float32).eps)
+    for (a, b, _), st in grid.items():
+        want = W[:, :, b * m[1]:(b + 1) * m[1], a * m[0]:(a + 1) * m[0]]
+        got = st.interior().cpu().numpy()
+        for f in range(W.shape[0]):
+            scale = max(np.abs(want[f]).max(), 1e-2)
+            err = np.abs(got[f] - want[f]).max() / scale
+            # FP64: summation order; float: the float rounding of the 1/dx^2
+            # stencils over dt per stage, 4 stages per step, against the floor
+            bound = 1e-13 if precision == capi.SF_FP64 else \
+                2 * steps * 4 * 64 / 12 * eps32 * dt / h ** 2 / 1e-2
+            assert err < bound, (a, b, f, err, bound)
+
+
+def test_level_batch_rejects_bad_halo_lists():
+    st = PatchState(capi.SF_WAVE, (8, 8, 8), (0.1,) * 3, 0.01, prm=capi.params(ghosts=capi.SF_GHOSTS_NONE))
+    grid = {(0, 0, 0): st}
+    b = amr.level_batch(grid)
+    try:
+        with pytest.raises(capi.SfError, match="role"):
+            capi.sf_batch_set_halo(b, 3, [])
+        bad = amr.halo_boxes(grid, "A")[:1]
+        bad[0].nf = 0
+        with pytest.raises(capi.SfError, match="nf"):
+            capi.sf_batch_set_halo(b, 0, bad)
+    finally:
+        capi.sf_batch_destroy(b)
+    periodic = PatchState(capi.SF_WAVE, (8, 8, 8), (0.1,) * 3, 0.01)
+    with pytest.raises(ValueError, match="GHOSTS_NONE"):
+        amr.level_batch({(0, 0, 0): periodic})
 
 
 @pytest.mark.parametrize("R", [2, 3, 4])
