@@ -33,7 +33,11 @@ struct BoxBatch {
 // Each box gets blocks in proportion to its size (a corner box one, a face
 // box hundreds); block b of the launch belongs to the first box whose end
 // exceeds b.  Threads run over the box's points with 32-bit index arithmetic
-// (the host checks that a box holds < 2^31 values).
+// (the host checks that a box holds < 2^31 values), kCopyIlp points per pass
+// with their loads issued together: a copy is one load and one store, so a
+// thread with a single point would spend its life waiting on one load.
+constexpr int kCopyIlp = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(256) copy_boxes_kernel(BoxBatch bb) {
   int lo = 0, hi = bb.n - 1;  // first box with end > blockIdx.x
@@ -49,19 +53,30 @@ __global__ void __launch_bounds__(256) copy_boxes_kernel(BoxBatch bb) {
   const unsigned total = ex * ey * ez * (unsigned)b.nf;
   const T* src = static_cast<const T*>(b.src);
   T* dst = static_cast<T*>(b.dst);
-  for (unsigned t = (blockIdx.x - first) * blockDim.x + threadIdx.x; t < total;
-       t += nblk * blockDim.x) {
-    unsigned r = t;
-    const unsigned x = r % ex;
-    r /= ex;
-    const unsigned y = r % ey;
-    r /= ey;
-    const unsigned z = r % ez;
-    const unsigned f = r / ez;
-    const long long s = b.src_off + f * b.src_sf + (long long)z * b.src_step * b.src_sz +
-                        (long long)y * b.src_step * b.src_sy + (long long)x * b.src_step;
-    const long long d = b.dst_off + f * b.dst_sf + (long long)z * b.dst_sz + (long long)y * b.dst_sy + x;
-    dst[d] = src[s];
+  const unsigned stride = nblk * blockDim.x;  // <= 1024 x 256
+  for (unsigned t0 = (blockIdx.x - first) * blockDim.x + threadIdx.x; t0 < total;
+       t0 += kCopyIlp * stride) {
+    T v[kCopyIlp];
+    long long d[kCopyIlp];
+#pragma unroll
+    for (int u = 0; u < kCopyIlp; ++u) {
+      const unsigned t = t0 + u * stride;
+      if (t >= total) break;
+      unsigned r = t;
+      const unsigned x = r % ex;
+      r /= ex;
+      const unsigned y = r % ey;
+      r /= ey;
+      const unsigned z = r % ez;
+      const unsigned f = r / ez;
+      const long long si = b.src_off + f * b.src_sf + (long long)z * b.src_step * b.src_sz +
+                           (long long)y * b.src_step * b.src_sy + (long long)x * b.src_step;
+      d[u] = b.dst_off + f * b.dst_sf + (long long)z * b.dst_sz + (long long)y * b.dst_sy + x;
+      v[u] = __ldg(src + si);
+    }
+#pragma unroll
+    for (int u = 0; u < kCopyIlp; ++u)
+      if (t0 + u * stride < total) dst[d[u]] = v[u];
   }
 }
 
@@ -452,7 +467,7 @@ extern "C" sf_status sf_copy_boxes(const sf_box_copy* boxes, int32_t nbox, int32
     for (int q = q0; q < nbox && q < q0 + kBoxesPerLaunch; ++q) {
       const long long v = (long long)boxes[q].ext[0] * boxes[q].ext[1] * boxes[q].ext[2] * boxes[q].nf;
       if (v == 0) continue;  // writes nothing
-      long long nb = (v + 255) / 256;
+      long long nb = (v + 256 * kCopyIlp - 1) / (256 * kCopyIlp);
       if (nb > 1024) nb = 1024;  // the threads stride over larger boxes
       bb.b[bb.n] = boxes[q];
       blocks += (int)nb;
