@@ -77,10 +77,14 @@ __global__ void __launch_bounds__(256) radiative_kernel(PatchArgs<T> a, StageArg
       i = ii < (int)g ? ii - (int)g : a.n[0] + (ii - (int)g);
     }
     const long long c = (long long)(k + (int)g) * a.sz + (long long)(j + (int)g) * a.sy + (i + (int)g);
+    // the point's position, then its radius and direction cosines in the
+    // arrays' precision (float arrays: float sqrt and divide, since the FP64
+    // pipe runs at 1/58 of the FP32 rate and every field group repeats this)
     const double x = ra.x0[0] + i * ra.dx[0], y = ra.x0[1] + j * ra.dx[1], z = ra.x0[2] + k * ra.dx[2];
-    const double r = sqrt(x * x + y * y + z * z);
-    const T ir = r > 0.0 ? T(1.0 / r) : T(0);
-    const T ex = T(x) * ir, ey = T(y) * ir, ez = T(z) * ir;
+    const T xt = T(x), yt = T(y), zt = T(z);
+    const T r = sqrt(xt * xt + yt * yt + zt * zt);
+    const T ir = r > T(0) ? T(1) / r : T(0);
+    const T ex = xt * ir, ey = yt * ir, ez = zt * ir;
     const int N[3] = {a.n[0] + 2 * (int)g, a.n[1] + 2 * (int)g, a.n[2] + 2 * (int)g};
     const bool rk4 = s.rk == SF_RK4;
 #pragma unroll
