@@ -154,7 +154,9 @@ __device__ __forceinline__ float lagrange_w<float>(const ProlongArgs& p, int r, 
 // The tile shapes are compile-time constants of the tile body, so every
 // index into the staged arrays splits by constant divisors; the fine offsets'
 // coarse node and weight row along each axis come from small tables the CTA
-// builds once (the only divisions by R).
+// builds once (the only divisions by R).  The staged extents are sized for
+// R = 1 (P + 6 nodes) or for any R >= 2 ((P - 1)/2 + 7 nodes, about half),
+// a second instance of the body.
 struct TileShape {
   int px, py, pz;
 };
@@ -162,14 +164,16 @@ constexpr TileShape kTileShapes[4] = {{32, 8, 4}, {4, 16, 16}, {32, 4, 16}, {32,
 constexpr int kThick = 0, kThinX = 1, kThinY = 2, kThinZ = 3;
 constexpr int kProlongThreads = 256;
 constexpr int kProlongTableBytes = 8 * 6 * 8 + 3 * 32 * 4;  // weights [R][6], node/row tables [3][32]
-constexpr int prolong_elems(TileShape t) {
-  return (t.pz + 6) * (t.py + 6) * (t.px + 6) + (t.pz + 6) * (t.py + 6) * t.px +
-         (t.pz + 6) * t.py * t.px;
+// coarse nodes a tile of P fine points reaches along an axis, for R >= rmin
+constexpr int node_span(int p, int rmin) { return (p - 1) / rmin + 7; }
+constexpr int prolong_elems(TileShape t, int rmin) {
+  return node_span(t.pz, rmin) * node_span(t.py, rmin) * node_span(t.px, rmin) +
+         node_span(t.pz, rmin) * node_span(t.py, rmin) * t.px + node_span(t.pz, rmin) * t.py * t.px;
 }
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 constexpr int kProlongMaxElems =
-    cmax(cmax(prolong_elems(kTileShapes[0]), prolong_elems(kTileShapes[1])),
-         cmax(prolong_elems(kTileShapes[2]), prolong_elems(kTileShapes[3])));
+    cmax(cmax(prolong_elems(kTileShapes[0], 1), prolong_elems(kTileShapes[1], 1)),
+         cmax(prolong_elems(kTileShapes[2], 1), prolong_elems(kTileShapes[3], 1)));
 template <typename T>
 constexpr int prolong_smem_bytes(int elems) {
   return elems * (int)sizeof(T) + kProlongTableBytes;
@@ -187,10 +191,10 @@ static int tile_for(const int* ext) {
   return kThick;
 }
 
-template <typename T, int NS, int PX, int PY, int PZ>
+template <typename T, int NS, int RMIN, int PX, int PY, int PZ>
 __device__ __forceinline__ void prolong_tile(const Combo<T>& cb, const ProlongArgs& p, const PBox& B,
                                              int local, unsigned char* raw) {
-  constexpr int CXM = PX + 6, CYM = PY + 6, CZM = PZ + 6;
+  constexpr int CXM = node_span(PX, RMIN), CYM = node_span(PY, RMIN), CZM = node_span(PZ, RMIN);
   constexpr int NT = kProlongThreads;
   static_assert(NT % PX == 0 && PX <= 32 && PY <= 32 && PZ <= 32, "tile shape");
   constexpr int ROWS = NT / PX;           // rows of a pass per sweep of the CTA
@@ -294,6 +298,28 @@ __device__ __forceinline__ void prolong_tile(const Combo<T>& cb, const ProlongAr
   }
 }
 
+template <typename T, int NS, int RMIN>
+__device__ __forceinline__ void prolong_kind(const Combo<T>& cb, const ProlongArgs& p, const PBox& B,
+                                             int local, unsigned char* raw) {
+  switch (B.kind) {
+    case kThinX:
+      prolong_tile<T, NS, RMIN, kTileShapes[kThinX].px, kTileShapes[kThinX].py,
+                   kTileShapes[kThinX].pz>(cb, p, B, local, raw);
+      break;
+    case kThinY:
+      prolong_tile<T, NS, RMIN, kTileShapes[kThinY].px, kTileShapes[kThinY].py,
+                   kTileShapes[kThinY].pz>(cb, p, B, local, raw);
+      break;
+    case kThinZ:
+      prolong_tile<T, NS, RMIN, kTileShapes[kThinZ].px, kTileShapes[kThinZ].py,
+                   kTileShapes[kThinZ].pz>(cb, p, B, local, raw);
+      break;
+    default:
+      prolong_tile<T, NS, RMIN, kTileShapes[kThick].px, kTileShapes[kThick].py,
+                   kTileShapes[kThick].pz>(cb, p, B, local, raw);
+  }
+}
+
 template <typename T, int NS>
 __global__ void __launch_bounds__(kProlongThreads) prolong_kernel(Combo<T> cb, ProlongArgs p) {
   extern __shared__ __align__(16) unsigned char psm_raw[];
@@ -302,23 +328,10 @@ __global__ void __launch_bounds__(kProlongThreads) prolong_kernel(Combo<T> cb, P
   while (bi + 1 < p.nbox && (int)blockIdx.x >= p.tiles_end[bi]) ++bi;
   const PBox& B = p.box[bi];
   const int local = (int)blockIdx.x - (bi ? p.tiles_end[bi - 1] : 0);
-  switch (B.kind) {
-    case kThinX:
-      prolong_tile<T, NS, kTileShapes[kThinX].px, kTileShapes[kThinX].py, kTileShapes[kThinX].pz>(
-          cb, p, B, local, psm_raw);
-      break;
-    case kThinY:
-      prolong_tile<T, NS, kTileShapes[kThinY].px, kTileShapes[kThinY].py, kTileShapes[kThinY].pz>(
-          cb, p, B, local, psm_raw);
-      break;
-    case kThinZ:
-      prolong_tile<T, NS, kTileShapes[kThinZ].px, kTileShapes[kThinZ].py, kTileShapes[kThinZ].pz>(
-          cb, p, B, local, psm_raw);
-      break;
-    default:
-      prolong_tile<T, NS, kTileShapes[kThick].px, kTileShapes[kThick].py, kTileShapes[kThick].pz>(
-          cb, p, B, local, psm_raw);
-  }
+  if (p.R == 1)
+    prolong_kind<T, NS, 1>(cb, p, B, local, psm_raw);
+  else
+    prolong_kind<T, NS, 2>(cb, p, B, local, psm_raw);
 }
 
 // App. C dense-output polynomials b_j(theta) of one coarse step and their
@@ -569,7 +582,7 @@ static sf_status prolong_launch(const sf_patch* coarse, const void* const* array
       B.t[0] = (bx.ext[0] + ts.px - 1) / ts.px;
       B.t[1] = (bx.ext[1] + ts.py - 1) / ts.py;
       B.t[2] = (bx.ext[2] + ts.pz - 1) / ts.pz;
-      smem_elems = std::max(smem_elems, prolong_elems(ts));
+      smem_elems = std::max(smem_elems, prolong_elems(ts, ratio >= 2 ? 2 : 1));
       B.out = bx.out;
       B.osy = bx.out_sy;
       B.osz = bx.out_sz;
