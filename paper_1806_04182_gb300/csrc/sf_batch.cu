@@ -378,7 +378,10 @@ sf_status sf_batch_set_halo(sf_batch* b, int32_t role, const sf_box_copy* boxes,
   if (role < 0 || role > 2) return set_error(SF_EINVAL, "role %d not in {0, 1, 2}", role);
   sf_status e = check_box_copies(boxes, nbox, b->precision);
   if (e) return e;
-  b->halo[role].assign(boxes, boxes + nbox);
+  if (nbox > 0)
+    b->halo[role].assign(boxes, boxes + nbox);
+  else
+    b->halo[role].clear();
   if (b->exec) {  // a captured step no longer matches: capture again
     cudaGraphExecDestroy(b->exec);
     cudaGraphDestroy(b->graph);
