@@ -52,15 +52,26 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 
 
 def bytes_per_cell_update(precision: str) -> float:
-    """Algorithmic HBM bytes per interior cell and RK substep (every array
-    pass of one RK4 step, divided by its four substeps).
-    FP64: stage 0 reads U^n and writes acc, U(2) (3 passes); stages 1-2 read
-    U(i), U^n, acc and write acc, U(i+1) (5 each); stage 3 reads U(4), acc and
-    writes U^{n+1} (3): 16 passes.  FP32-bulk adds the Kahan array and U^n in
-    stage 3 (read U(4), acc, U^n, c; write U^{n+1}, c: 6): 19 passes."""
+    """Algorithmic HBM bytes per interior cell and RK substep, as the kernels
+    move them (every array pass of one RK4 step, divided by its four
+    substeps).  FP64: stage 0 reads U^n and writes acc, U(2) (3 passes);
+    stages 1-2 read U(i), U^n, acc and write acc, U(i+1) (5 each); stage 3
+    reads U(4), acc and writes U^{n+1} (3): 16 passes.  FP32-bulk adds the
+    Kahan array (read and written once per step) and one read of U^n in
+    stage 3, since its accumulator holds the increment alone and the
+    compensated sum adds it to U^n there: 19 passes."""
     if precision == "fp64":
         return 16 / 4 * NF * 8
     return 19 / 4 * NF * 4
+
+
+def contract_bytes_per_cell_update(precision: str) -> float:
+    """The measurement contract's algorithmic bytes: FP64 4 nf s = 800 B;
+    FP32-bulk (16 + 2) / 4 nf s = 450 B (the 16 RK4 passes plus the Kahan
+    array's read and write; it does not count the U^n read of stage 3)."""
+    if precision == "fp64":
+        return 4 * NF * 8
+    return (16 + 2) / 4 * NF * 4
 
 
 STAGE_PASSES = {"fp64": [3, 5, 5, 3], "fp32": [3, 5, 5, 6], "fp32dw": [3, 5, 5, 6]}
@@ -126,10 +137,11 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- traffic
-# DRAM traffic of the headline kernel comes from one ncu capture summarised in
-# profiles/; it is reported only while the kernel sources still hash to the
-# value recorded there (null once the kernel has changed).
-PROFILE = os.path.join(ROOT, "profiles", "z4_tma_fp32dw_96cubed.md")
+# DRAM traffic and the instruction count of the headline kernel come from one
+# ncu capture, recorded in a JSON file beside its summary under profiles/;
+# they are reported only while the kernel sources still hash to the value
+# recorded there (null once the kernel has changed).
+PROFILE = os.path.join(ROOT, "profiles", "z4_tma_fp32dw_96cubed.json")
 KERNEL_SOURCES = ["sf_common.cuh", "sf_dw.cuh", "sf_mbar.cuh", "sf_pair.cuh", "sf_z4.cuh", "sf_z4.cu",
                   "sf_z4_tma.cu"]
 
@@ -149,23 +161,17 @@ def kernel_source_hash() -> str:
 
 
 def profiled_traffic():
-    """(bytes per launch, source hash) from the profile summary, or (None, None)."""
+    """(bytes per launch, source hash) from the profile record, or (None, None)."""
     v = profiled_values()
     return v.get("traffic_bytes_per_launch"), v.get("kernel_source_sha256_16")
 
 
 def profiled_values() -> dict:
-    """The `key: value` lines at the end of the profile summary."""
-    out = {}
+    """The ncu figures of the headline kernel (profiles/*.json), or {}."""
     if not os.path.exists(PROFILE):
-        return out
-    for line in open(PROFILE):
-        for key in ("traffic_bytes_per_launch", "warp_instructions_per_launch"):
-            if line.startswith(key + ":"):
-                out[key] = float(line.split(":")[1])
-        if line.startswith("kernel_source_sha256_16:"):
-            out["kernel_source_sha256_16"] = line.split(":")[1].strip()
-    return out
+        return {}
+    with open(PROFILE) as f:
+        return json.load(f)
 
 
 # ---------------------------------------------------------------- ranks
@@ -303,11 +309,14 @@ def gpu_arm(args):
         avg_launch_ms = float(per.mean())
         bpc = bytes_per_cell_update(precision)
         achieved = cells * bpc / (avg_launch_ms * 1e-3) / 1e9
+        bpc_c = contract_bytes_per_cell_update(precision)
+        achieved_c = cells * bpc_c / (avg_launch_ms * 1e-3) / 1e9
         per_stage_ms = per.mean(axis=0).tolist()
         stage_gbs = [cells * p * NF * (8 if precision == "fp64" else 4) / (ms * 1e-3) / 1e9
                      for p, ms in zip(STAGE_PASSES[precision], per_stage_ms)]
         res[precision] = dict(value=value, ms_per_step=total_ms / args.steps, launches=launches,
-                              avg_launch_ms=avg_launch_ms, achieved_gbs=achieved,
+                              avg_launch_ms=avg_launch_ms, achieved_gbs=achieved_c,
+                              achieved_gbs_kernel_passes=achieved, contract_bytes=bpc_c,
                               per_stage_ms=per_stage_ms, per_stage_gbs=stage_gbs,
                               bytes_per_cell_update=bpc, state=st)
     if args.only is not None:
@@ -349,15 +358,29 @@ def gpu_arm(args):
                                 "arithmetic on the FP32 pipe",
                    "slicing": "1+log", "shift": "Gamma-driver", "sigma_ko": 0.1,
                    "dt_over_dx": 0.25, "l2": "inputs larger than L2 (5 arrays x 106 MB fp32)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "forms": {
+                       "fp32_bulk_dw": {"value": r32["value"], "precision":
+                                        "float storage and stencils; det, inverse, ln det and trace "
+                                        "removals in double-word floats (relative error a few 2^-48 "
+                                        "per operation), Kahan RK accumulation (the headline)"},
+                       "fp32_bulk_fp64_islands": {"value": r32n["value"], "precision":
+                                                  "float storage and stencils; det, inverse, ln det "
+                                                  "and trace removals in native FP64, Kahan RK "
+                                                  "accumulation"},
+                       "fp64": {"value": r64["value"], "precision": "FP64 throughout (the paper's precision)"}}},
         "roofline": {"bound": "hbm", "achieved": r32["achieved_gbs"], "peak": hbm_peak,
                      "unit": "GB/s", "frac": r32["achieved_gbs"] / hbm_peak,
                      "traffic": traffic if traffic_src == kernel_source_hash() else None,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read+write, mean of the 4 stages)",
                      "peak_source": peak_src,
+                     "cells_per_launch": cells, "avg_launch_ms": r32["avg_launch_ms"],
+                     "bytes_per_cell_update_kernel_passes": r32["bytes_per_cell_update"],
+                     "achieved_kernel_passes": r32["achieved_gbs_kernel_passes"],
+                     "frac_kernel_passes": r32["achieved_gbs_kernel_passes"] / hbm_peak,
                      "kernel": ("z4_tma_kernel<dw,12,8> (TMA-staged stencils)" if args.pitch == FLOAT_PITCH
                                 else "z4_stage_kernel<float,dw> (global-load stencils)"),
-                     "bytes_per_cell_update": r32["bytes_per_cell_update"],
+                     "bytes_per_cell_update": r32["contract_bytes"],
                      "per_stage_ms": r32["per_stage_ms"], "per_stage_gbs": r32["per_stage_gbs"]},
         "alu_roofline": {
             "bound": "alu", "flops_per_cell_update": FLOPS_PER_CELL_UPDATE,
@@ -377,7 +400,7 @@ def gpu_arm(args):
             "per_stage_ms": r32n["per_stage_ms"]},
         "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"],
                  "achieved_gbs": r64["achieved_gbs"], "hbm_frac": r64["achieved_gbs"] / hbm_peak,
-                 "bytes_per_cell_update": r64["bytes_per_cell_update"],
+                 "bytes_per_cell_update": r64["contract_bytes"],
                  "per_stage_ms": r64["per_stage_ms"]},
         "speedup_fp32_bulk_over_fp64": r32["value"] / r64["value"],
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
@@ -754,18 +777,41 @@ def _adjoint_rows() -> list[dict]:
 
 
 # ---------------------------------------------------------------- oracle arm
-def cpu_baseline(seconds: float = 15.0, nz: int = 4) -> dict:
-    """The FP64 oracle as it stands (OpenMP over z) on a bounded sample of the
-    same workload: a 96 x 96 x nz periodic slab with the same spacing, data
-    distribution and parameters, RK4 steps until `seconds` have passed."""
+# The oracle's sample: a 96 x 96 x 16 periodic slab of the 96^3 workload (same
+# spacing, data distribution and parameters).  Its right-hand-side sweep is
+# parallel over the slab's 16 x 96 = 1536 (z, y) rows, so every host core has
+# work; the CCZ4 cell cost does not depend on the slab's depth.
+ORACLE_NZ = 16
+
+
+def host_cpu() -> str:
+    """CPU model of this host (lscpu's model name, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
+def _oracle_slab(nz: int):
     import oracle
     from paper_1806_04182_gb300 import inputs
     oracle.build()
     U0, _ = inputs.z4_minkowski_noise((N, N, nz), seed=0, amp=1e-10)
     dx = (1.0 / N,) * 3
-    G = oracle.ghosted(U0)
-    p = oracle.params()
-    dt = 0.25 * dx[0]
+    return oracle, oracle.ghosted(U0), dx, oracle.params(), 0.25 * dx[0]
+
+
+def _oracle_rate(threads: int, seconds: float, nz: int) -> tuple[float, int, float, int]:
+    """Cell-updates/s of RK4 steps of the slab on `threads` threads, stepping
+    until `seconds` have passed (at least one step).  Returns (rate, steps,
+    seconds, threads in effect)."""
+    oracle, G, dx, p, dt = _oracle_slab(nz)
+    used = oracle.set_threads(threads)
     t0 = time.perf_counter()
     steps = 0
     while True:
@@ -774,43 +820,50 @@ def cpu_baseline(seconds: float = 15.0, nz: int = 4) -> dict:
         el = time.perf_counter() - t0
         if el > seconds or steps >= 1000:
             break
-    cells = N * N * nz
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": cells * 4 * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} RK4 steps of a 96x96x{nz} periodic slab (same dx, data, params), "
-                      f"{el:.1f} s"}
+    return N * N * nz * 4 * steps / el, steps, el, used
+
+
+def cpu_baseline(seconds: float = 15.0, nz: int = ORACLE_NZ) -> dict:
+    """The FP64 oracle as it stands on a bounded sample of the same workload,
+    on every host core and on one core."""
+    cores = os.cpu_count() or 1
+    rate, steps, el, used = _oracle_rate(cores, seconds, nz)
+    rate1, steps1, el1, _ = _oracle_rate(1, seconds / 2, nz)
+    import oracle
+    oracle.set_threads(cores)
+    return {"value": rate, "unit": UNIT, "cores": min(used, N * nz), "kind": "oracle",
+            "sample": f"{steps} RK4 steps of a 96x96x{nz} periodic slab of the 96^3 workload "
+                      f"(same dx, data, params), {el:.1f} s, OpenMP over its {N * nz} (z, y) rows",
+            "cpu": host_cpu(), "nproc": cores,
+            "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                              "sample": f"{steps1} RK4 steps of the same slab, {el1:.1f} s"},
+            "parallel_speedup": rate / rate1}
 
 
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
-    import oracle
-    from paper_1806_04182_gb300 import inputs
-    oracle.build()
-    nz = 2
-    U0, _ = inputs.z4_minkowski_noise((N, N, nz), seed=0, amp=1e-10)
-    dx = (1.0 / N,) * 3
-    G = oracle.ghosted(U0)
-    p = oracle.params()
-    dt = 0.25 * dx[0]
+    nz = ORACLE_NZ
+    oracle, G, dx, p, dt = _oracle_slab(nz)
+    cores = os.cpu_count() or 1
+    used = oracle.set_threads(cores)
     for _ in range(args.warmup):
         oracle.rk4_step(oracle.Z4, G, dx, dt, p)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         oracle.rk4_step(oracle.Z4, G, dx, dt, p)
     el = time.perf_counter() - t0
-    cells = N * N * nz
-    value = cells * 4 * args.steps / el
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    sample = f"each step: one RK4 step of a 96x96x{nz} periodic slab of the 96^3 workload"
+    value = N * N * nz * 4 * args.steps / el
+    sample = (f"each step: one RK4 step of a 96x96x{nz} periodic slab of the 96^3 workload, "
+              f"OpenMP over its {N * nz} (z, y) rows")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic: Minkowski + seeded uniform noise 1e-10",
             "config": {"workload": WORKLOAD, "n": N, "sample_nz": nz},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(used, N * nz), "kind": "oracle",
+                             "sample": sample, "cpu": host_cpu(), "nproc": cores},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

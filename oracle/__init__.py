@@ -6,7 +6,7 @@ CPU-baseline leg of ``bench.py`` may import it; the product package never
 does, and it shares no code with the CUDA library.
 
 The arithmetic lives in ``sf_oracle.cpp`` (plain C++17, FP64, one cell at a
-time, OpenMP only over the outer z loop of the right-hand-side sweep).  This
+time, OpenMP only over the (z, y) rows of the right-hand-side sweep).  This
 module compiles it with g++ on first use and wraps it with ctypes.
 
 Functions and what pins them (tests/test_oracle_*.py):
@@ -36,6 +36,13 @@ Functions and what pins them (tests/test_oracle_*.py):
                    and (k1 + 2 k2 + 4 k3)/6 are inconsistent).  Pinned:
                    third-order amplification polynomial; equal to the
                    Shu-Osher form.
+  z4_monitors      root mean squares of Theta, |Z| (Z^i = chi/2 (Gammahat^i -
+                   Gamma~^i)), ln det gt~ and gt~^{ij} A~_ij (Sec. V).  Pinned:
+                   closed forms on a rotated homogeneous metric with det != 1
+                   and on a diagonal metric varying along x (closed-form
+                   Gamma~^i), every monitor non-zero.
+  rhs_points       rhs at listed interior points.  Pinned: equal bit for bit
+                   to the columns of rhs, any order, ragged grid.
   misfit_gradient  discrete adjoint of the RK4 wave evolution.  Pinned:
                    central finite differences (exact for the quadratic misfit).
   weno             one reconstruction of five values (App. A, App. B).
@@ -147,6 +154,8 @@ def lib() -> ctypes.CDLL:
         L.or_wave_energy.argtypes = [ip, ctypes.c_int, dp, dp]
         L.or_wave_energy.restype = ctypes.c_double
         L.or_z4_monitors.argtypes = [ip, ctypes.c_int, dp, dp, dp]
+        L.or_set_threads.argtypes = [ctypes.c_int]
+        L.or_max_threads.restype = ctypes.c_int
         L.or_wave_misfit_gradient.argtypes = [pp, ip, dp, ctypes.c_double, ctypes.c_int, dp, dp,
                                               ctypes.c_int, ctypes.POINTER(ctypes.c_int64), dp,
                                               dp, dp]
@@ -353,6 +362,16 @@ def mhd_max_rate(U: np.ndarray, dx, p: Params | None = None, g: int = 3) -> floa
 def wave_energy(U: np.ndarray, dx, g: int = 3) -> float:
     nf, n = shape_info(U, g)
     return lib().or_wave_energy(_ivec(n), g, _dvec(dx), _dp(U))
+
+
+def set_threads(n: int) -> int:
+    """Use n threads in the parallel sweeps; returns the count now in effect."""
+    lib().or_set_threads(int(n))
+    return lib().or_max_threads()
+
+
+def max_threads() -> int:
+    return lib().or_max_threads()
 
 
 def z4_monitors(U: np.ndarray, dx, g: int = 3) -> np.ndarray:

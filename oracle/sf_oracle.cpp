@@ -29,6 +29,9 @@
 #include <cstring>
 #include <vector>
 #include <algorithm>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 extern "C" {
 typedef struct {
@@ -752,7 +755,9 @@ void cell_rhs(int system, const or_params& p, const double* u, const Grid& G, co
 void rhs_all(int system, const or_params& p, const Grid& G, const double* dx, const double* u,
              double* out) {
   int nf = nfields(system, p);
-#pragma omp parallel for schedule(static)
+  // rows (k, j) are independent: parallel over both, so that a thin slab
+  // still gives every host core work
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < G.n[2]; ++k)
     for (int j = 0; j < G.n[1]; ++j)
       for (int i = 0; i < G.n[0]; ++i) {
@@ -838,6 +843,23 @@ void copy_interior_out(int nf, const Grid& G, const double* X, double* out) {
 extern "C" {
 
 int or_nfields(int system, const or_params* p) { return nfields(system, *p); }
+
+// Threads of the parallel sweeps (OpenMP); 1 when built without OpenMP.
+void or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+int or_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 void or_fill_ghosts_periodic(int nf, const int* n, int g, double* u) {
   Grid G(n, g);

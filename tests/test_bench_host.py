@@ -1,6 +1,6 @@
 """Host arithmetic of bench.py, checked on the CPU: the algorithmic bytes per
 cell-update agree with the per-stage array passes they are built from, the
-profile summary the roofline reads parses, and the issue roofline is withheld
+profile record the roofline reads parses, and the issue roofline is withheld
 when the kernel source no longer matches the profiled one."""
 import re
 
@@ -13,6 +13,9 @@ def test_bytes_per_cell_update_equals_the_stage_passes():
         assert bench.bytes_per_cell_update(precision) == passes / 4 * bench.NF * es
     assert bench.bytes_per_cell_update("fp32dw") == 475.0
     assert bench.bytes_per_cell_update("fp64") == 800.0
+    # the contract's figures: 16 RK4 passes (+ the Kahan read and write)
+    assert bench.contract_bytes_per_cell_update("fp64") == 800.0
+    assert bench.contract_bytes_per_cell_update("fp32dw") == 450.0
 
 
 def test_profile_summary_parses():
