@@ -376,9 +376,14 @@ sf_status sf_batch_destroy(sf_batch* b);
  * u_n = state, u_stage and u_next = scratch, acc, kahan), with the kernel's
  * scratch (queue counter, per-patch stage table, work list) kept in a
  * file-scope device array of 170,496 bytes that every GPU loading the
- * library holds until the process exits.  The call allocates nothing; it
- * copies the stage table from a static host buffer and clears the queue
- * counter on `stream` before the launch.
+ * library holds until the process exits.  The call allocates nothing: on
+ * `stream`, ahead of the persistent launch, small kernels whose parameters
+ * carry this call's stage table write it into that array, expand the work
+ * list and reset the queue counter (the call keeps no host buffer and reads
+ * no host memory after it returns).
+ * prm->ghosts: SF_GHOSTS_PERIODIC writes the periodic ghost shell of every
+ * output (as sf_substep does), SF_GHOSTS_NONE leaves ghost shells to the
+ * caller (patches that tile a level); any other value returns SF_EINVAL.
  * Limits: at most 64 patches and 8192 work items of 32x4x4 points per call;
  * larger requests return SF_EINVAL and enqueue nothing.
  * The first call on a device looks up the scratch address and the grid size

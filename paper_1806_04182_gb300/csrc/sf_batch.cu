@@ -520,6 +520,8 @@ namespace {
 constexpr int kStaticMaxPatches = 64;
 constexpr int kStaticMaxItems = 8192;
 constexpr Shape kStaticShape = {32, 4, 4};
+constexpr int kStaticTX = 32, kStaticTY = 4, kStaticTZ = 4;  // kStaticShape, for device code
+static_assert(kStaticShape.tx == kStaticTX && kStaticShape.ty == kStaticTY && kStaticShape.tz == kStaticTZ, "tile");
 constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 constexpr size_t kArgsBytes = align256(kStaticMaxPatches * (sizeof(PatchArgs<double>) > sizeof(PatchArgs<float>)
                                                                ? sizeof(PatchArgs<double>)
@@ -540,14 +542,55 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
 namespace {
 
-std::mutex g_static_mu;                            // guards the host staging copy
-alignas(256) unsigned char g_static_host[kStaticBytes];  // host image of the scratch
-unsigned char* g_static_dev[64] = {nullptr};       // device address per device
+// The stage table reaches the scratch array through kernel parameters: each
+// upload launch carries up to kChunkBytes of it by value, so every call's
+// table is its own (nothing is read from host memory after the call returns)
+// and no host buffer is shared between calls.
+constexpr unsigned kChunkBytes = 28 * 1024;
+struct StaticChunk {
+  unsigned off, nbytes;  // destination offset in the scratch, bytes (multiples of 4)
+  unsigned data[kChunkBytes / 4];
+};
+static_assert(sizeof(StaticChunk) <= 32764, "kernel parameter limit");
+
+__global__ void static_upload_kernel(const __grid_constant__ StaticChunk c, unsigned char* base) {
+  unsigned* dst = reinterpret_cast<unsigned*>(base + c.off);
+  for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < c.nbytes / 4; w += gridDim.x * blockDim.x)
+    dst[w] = c.data[w];
+}
+
+// Work list of one call, expanded on the device: queue position t belongs to
+// the q-th patch in queue order (CCZ4 patches first) when first[q] <= t <
+// first[q + 1]; within a patch the 32x4x4 tiles run x fastest, then y, z.
+struct StaticPlan {
+  int np, nitems;
+  int patch[kStaticMaxPatches];
+  int first[kStaticMaxPatches + 1];
+  int tiles_x[kStaticMaxPatches], tiles_y[kStaticMaxPatches];
+};
+
+__global__ void static_items_kernel(const __grid_constant__ StaticPlan plan, Item* items,
+                                    unsigned int* counter) {
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t0 == 0) *counter = 0u;  // the queue starts at zero on every call
+  for (int t = t0; t < plan.nitems; t += gridDim.x * blockDim.x) {
+    int q = 0;
+    while (q + 1 < plan.np && plan.first[q + 1] <= t) ++q;
+    const int l = t - plan.first[q];
+    const int tx = l % plan.tiles_x[q], r = l / plan.tiles_x[q];
+    const int ty = r % plan.tiles_y[q], tz = r / plan.tiles_y[q];
+    items[t] = Item{plan.patch[q], tx * kStaticTX, ty * kStaticTY, tz * kStaticTZ};
+  }
+}
+
+std::mutex g_static_mu;                       // guards the per-device set-up
+unsigned char* g_static_dev[64] = {nullptr};  // scratch address per device
 int g_static_grid[64][3] = {{0}};
 
 // Per-device set-up, done once with that device current: the device address
 // of the scratch array and the persistent grid sizes.
 sf_status static_setup(int dev) {
+  std::lock_guard<std::mutex> lock(g_static_mu);
   if (g_static_dev[dev]) return SF_OK;
   void* p = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
@@ -564,23 +607,49 @@ sf_status static_setup(int dev) {
   return SF_OK;
 }
 
+// Copy `n` bytes (a multiple of 4) of `src` to scratch offset `off`, one
+// launch per chunk.
+sf_status static_upload(unsigned char* d, size_t off, const void* src, size_t n, cudaStream_t st) {
+  StaticChunk c;
+  for (size_t done = 0; done < n; done += kChunkBytes) {
+    const size_t len = std::min<size_t>(kChunkBytes, n - done);
+    c.off = (unsigned)(off + done);
+    c.nbytes = (unsigned)len;
+    memcpy(c.data, static_cast<const unsigned char*>(src) + done, len);
+    static_upload_kernel<<<(unsigned)((len / 4 + 255) / 256), 256, 0, st>>>(c, d);
+    sf_status e = after_launch("static_upload_kernel");
+    if (e) return e;
+  }
+  return SF_OK;
+}
+
 template <typename T, typename H>
 sf_status static_stage(const sf_params& prm, const sf_patch* pin, int np, int stage, int dev,
                        cudaStream_t st) {
   unsigned char* d = g_static_dev[dev];
-  PatchArgs<T>* hargs = reinterpret_cast<PatchArgs<T>*>(g_static_host + kOffArgs);
-  int* hsys = reinterpret_cast<int*>(g_static_host + kOffSys);
-  int2* hshape = reinterpret_cast<int2*>(g_static_host + kOffShape);
-  Item* hitems = reinterpret_cast<Item*>(g_static_host + kOffItems);
-  int nitems = 0;
+  PatchArgs<T> args[kStaticMaxPatches];
+  // sys at [0, 256), shapes at [256, 768): the layout of [kOffSys, kOffItems)
+  static_assert(kOffShape - kOffSys == kStaticMaxPatches * sizeof(int), "sys block");
+  struct {
+    int sys[kStaticMaxPatches];
+    int2 shape[kStaticMaxPatches];
+  } small;
+  StaticPlan plan;
+  plan.np = np;
+  int nq = 0, nitems = 0;
   for (int pass = 0; pass < 2; ++pass)  // CCZ4 items first, as in sf_batch_substep
     for (int q = 0; q < np; ++q) {
       const sf_patch& p = pin[q];
       if ((pass == 0) != (p.system == SF_Z4)) continue;
-      for (int z = 0; z < p.n[2]; z += kStaticShape.tz)
-        for (int y = 0; y < p.n[1]; y += kStaticShape.ty)
-          for (int x = 0; x < p.n[0]; x += kStaticShape.tx) hitems[nitems++] = Item{q, x, y, z};
+      plan.patch[nq] = q;
+      plan.first[nq] = nitems;
+      plan.tiles_x[nq] = (p.n[0] + kStaticShape.tx - 1) / kStaticShape.tx;
+      plan.tiles_y[nq] = (p.n[1] + kStaticShape.ty - 1) / kStaticShape.ty;
+      nitems += plan.tiles_x[nq] * plan.tiles_y[nq] * ((p.n[2] + kStaticShape.tz - 1) / kStaticShape.tz);
+      ++nq;
     }
+  plan.first[nq] = nitems;
+  plan.nitems = nitems;
   for (int q = 0; q < np; ++q) {
     sf_patch p = pin[q];
     void* A = p.u_n;
@@ -588,23 +657,19 @@ sf_status static_stage(const sf_params& prm, const sf_patch* pin, int np, int st
     void* nx[4] = {p.u_stage, p.u_next, p.u_stage, A};
     p.u_stage = us[stage];
     p.u_next = nx[stage];
-    hargs[q] = make_args<T>(prm, p, stage, sf_nfields(p.system), nullptr);
-    hsys[q] = p.system;
-    hshape[q] = make_int2(kStaticShape.tx, kStaticShape.tz);
+    args[q] = make_args<T>(prm, p, stage, sf_nfields(p.system), nullptr);
+    small.sys[q] = p.system;
+    small.shape[q] = make_int2(kStaticShape.tx, kStaticShape.tz);
   }
-  // pageable source: the copies have left g_static_host when they return
-  if (cudaMemcpyAsync(d + kOffArgs, g_static_host + kOffArgs, np * sizeof(PatchArgs<T>),
-                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(d + kOffSys, g_static_host + kOffSys, np * sizeof(int),
-                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(d + kOffShape, g_static_host + kOffShape, np * sizeof(int2),
-                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(d + kOffItems, g_static_host + kOffItems, nitems * sizeof(Item),
-                      cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return set_error(SF_ECUDA, "upload of the stage table failed");
-  // the queue counter must start at zero on every call
-  if (cudaMemsetAsync(d, 0, sizeof(unsigned int), st) != cudaSuccess)
-    return set_error(SF_ECUDA, "queue counter reset failed");
+  sf_status e = static_upload(d, kOffArgs, args, np * sizeof(PatchArgs<T>), st);
+  if (!e) e = static_upload(d, kOffSys, small.sys, np * sizeof(int), st);
+  if (!e) e = static_upload(d, kOffShape, small.shape, np * sizeof(int2), st);
+  if (e) return e;
+  unsigned int* tcounter = reinterpret_cast<unsigned int*>(d);
+  Item* titems = reinterpret_cast<Item*>(d + kOffItems);
+  static_items_kernel<<<(nitems + 255) / 256, 256, 0, st>>>(plan, titems, tcounter);
+  e = after_launch("static_items_kernel");
+  if (e) return e;
   sf_batch tmp;  // only carries the fields batch_stage_args reads
   tmp.prm = prm;
   tmp.precision = pin[0].precision;
@@ -621,8 +686,6 @@ sf_status static_stage(const sf_params& prm, const sf_patch* pin, int np, int st
   const PatchArgs<T>* targs = reinterpret_cast<const PatchArgs<T>*>(d + kOffArgs);
   const int* tsys = reinterpret_cast<const int*>(d + kOffSys);
   const int2* tshape = reinterpret_cast<const int2*>(d + kOffShape);
-  const Item* titems = reinterpret_cast<const Item*>(d + kOffItems);
-  unsigned int* tcounter = reinterpret_cast<unsigned int*>(d);
   if (prm.lopsided)
     batch_stage_kernel<T, H, true><<<grid, 128, 0, st>>>(targs, tsys, tshape, titems, nitems,
                                                          tcounter, sa, zc);
@@ -642,8 +705,9 @@ extern "C" sf_status sf_batch_substep_static(const sf_params* prm, const sf_patc
                      kStaticMaxPatches);
   if (stage < 0 || stage > 3) return set_error(SF_EINVAL, "stage %d out of range [0,4)", stage);
   if (prm->rk != SF_RK4) return set_error(SF_ENOTSUP, "sf_batch_substep_static runs RK4");
-  sf_params q = *prm;
-  q.ghosts = SF_GHOSTS_PERIODIC;
+  if (prm->ghosts != SF_GHOSTS_NONE && prm->ghosts != SF_GHOSTS_PERIODIC)
+    return set_error(SF_EINVAL, "ghosts %d not SF_GHOSTS_NONE or SF_GHOSTS_PERIODIC", prm->ghosts);
+  const sf_params q = *prm;
   sf_patch local[kStaticMaxPatches];
   long long items = 0;
   for (int i = 0; i < npatch; ++i) {
@@ -675,7 +739,6 @@ extern "C" sf_status sf_batch_substep_static(const sf_params* prm, const sf_patc
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
     return set_error(SF_ECUDA, "no usable CUDA device");
   if (!status_ptr()) return set_error(SF_ECUDA, "no status word");
-  std::lock_guard<std::mutex> lock(g_static_mu);
   sf_status e = static_setup(dev);
   if (e) return e;
   cudaStream_t st = (cudaStream_t)stream;

@@ -40,7 +40,8 @@ def states_for(table, precision):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision,tol", [(capi.SF_FP64, 1e-13), (capi.SF_FP32_BULK_DW, 0.0)])
+@pytest.mark.parametrize("precision,tol", [(capi.SF_FP64, 1e-13), (capi.SF_FP32_BULK, 0.0),
+                                           (capi.SF_FP32_BULK_DW, 0.0)])
 def test_static_scratch_batch_matches_allocating_batch(precision, tol):
     # Both paths launch the same compiled persistent kernel, so for FP64 they
     # agree to rounding and for FP32 bit for bit (tolerance 0).
@@ -78,3 +79,35 @@ def test_static_scratch_rejects_requests_beyond_its_maximum():
     big = PatchState(capi.SF_Z4, (128, 128, 96), (0.01,) * 3, 0.001, precision=capi.SF_FP32_BULK_DW)
     with pytest.raises(capi.SfError, match="static scratch maximum"):
         capi.sf_batch_substep_static(capi.params(), [big.patch(big.B, big.A, big.C)] * 3, 0)
+
+
+@pytest.mark.gpu
+def test_static_scratch_honours_ghosts_none():
+    # SF_GHOSTS_NONE: the caller owns the ghost shells (patches that tile a
+    # level), so a stage writes the interior only, like sf_batch with NONE
+    table = inputs.amr_patch_table(6, seed=5, lo=6, hi=14)
+    a = states_for(table, capi.SF_FP64)
+    b = states_for(table, capi.SF_FP64)
+    prm = capi.params(ghosts=capi.SF_GHOSTS_NONE)
+    h = torch.cuda.current_stream().cuda_stream
+    for st in b:
+        st.B.fill_(float("nan"))
+    batch = capi.sf_batch_create(prm, [st.patch(st.B, st.A, st.C) for st in a])
+    try:
+        capi.sf_batch_substep(batch, 0, h)
+        capi.sf_batch_substep_static(prm, [st.patch(st.B, st.A, st.C) for st in b], 0, h)
+        torch.cuda.synchronize()
+        for x, y in zip(a, b):
+            ref = x.interior(x.B)
+            scale = ref.abs().amax(dim=(1, 2, 3)).clamp_min(1e-3)
+            err = ((y.interior(y.B) - ref).abs().amax(dim=(1, 2, 3)) / scale).max().item()
+            assert err <= 1e-13, err
+            shell = torch.ones_like(y.B, dtype=torch.bool)
+            g = y.g
+            shell[:, g:-g, g:-g, g:g + y.n[0]] = False
+            assert torch.isnan(y.B[shell]).all()
+    finally:
+        capi.sf_batch_destroy(batch)
+    with pytest.raises(capi.SfError, match="ghosts"):
+        capi.sf_batch_substep_static(capi.params(ghosts=7), [b[0].patch(b[0].B, b[0].A, b[0].C)], 0, h)
+    assert capi.sf_get_device_status(h) == capi.SF_OK
