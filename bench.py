@@ -142,8 +142,8 @@ class ClockSampler:
 # they are reported only while the kernel sources still hash to the value
 # recorded there (null once the kernel has changed).
 PROFILE = os.path.join(ROOT, "profiles", "z4_tma_fp32dw_96cubed.json")
-KERNEL_SOURCES = ["sf_common.cuh", "sf_dw.cuh", "sf_mbar.cuh", "sf_pair.cuh", "sf_z4.cuh", "sf_z4.cu",
-                  "sf_z4_tma.cu"]
+KERNEL_SOURCES = ["sf_common.cuh", "sf_dw.cuh", "sf_f2.cuh", "sf_mbar.cuh", "sf_pair.cuh", "sf_z4.cuh",
+                  "sf_z4.cu", "sf_z4_pair.cu"]
 
 
 def kernel_source_hash() -> str:
@@ -192,7 +192,8 @@ def whole_job_rate(world: int, cells: int, substeps: int, max_ms: float) -> floa
 
 
 # ---------------------------------------------------------------- GPU arm
-def make_state(precision: str, seed: int, device, float_pitch: int = FLOAT_PITCH):
+def make_state(precision: str, seed: int, device, float_pitch: int = FLOAT_PITCH,
+               x_offset: int = 1):
     import torch
     from paper_1806_04182_gb300 import capi, inputs
     from paper_1806_04182_gb300.state import PatchState
@@ -201,7 +202,8 @@ def make_state(precision: str, seed: int, device, float_pitch: int = FLOAT_PITCH
             "fp32dw": capi.SF_FP32_BULK_DW}[precision]
     st = PatchState(capi.SF_Z4, (N, N, N), dx, 0.25 * dx[0], precision=prec,
                     prm=capi.params(), device=device,
-                    x_pitch=None if precision == "fp64" else float_pitch)
+                    x_pitch=None if precision == "fp64" else float_pitch,
+                    x_offset=0 if precision == "fp64" else x_offset)
     st.upload(U0)
     torch.cuda.synchronize()
     return st
@@ -241,7 +243,7 @@ def time_e2e(st, steps: int, warmup: int):
     import torch
     from paper_1806_04182_gb300.state import HostPipeline
     pipe = HostPipeline(st.system, st.n, st.dx, st.dt, precision=st.precision, prm=st.prm,
-                        ghost=st.g, x_pitch=st.pitch)
+                        ghost=st.g, x_pitch=st.pitch, x_offset=st.xo)
     host_in = torch.empty(pipe.shape, dtype=pipe.dtype, pin_memory=True)
     host_in.copy_(st.A.cpu())
     host_out = torch.empty_like(host_in, pin_memory=True)
@@ -293,7 +295,8 @@ def gpu_arm(args):
     clocks = None
     precisions = ("fp32dw", "fp32", "fp64") if args.only is None else (args.only,)
     for precision in precisions:
-        st = make_state(precision, seed=rank, device=device, float_pitch=args.pitch)
+        st = make_state(precision, seed=rank, device=device, float_pitch=args.pitch,
+                        x_offset=args.x_offset)
         barrier()
         sampler = ClockSampler(local) if precision == "fp32dw" else None
         if sampler:
@@ -378,8 +381,7 @@ def gpu_arm(args):
                      "bytes_per_cell_update_kernel_passes": r32["bytes_per_cell_update"],
                      "achieved_kernel_passes": r32["achieved_gbs_kernel_passes"],
                      "frac_kernel_passes": r32["achieved_gbs_kernel_passes"] / hbm_peak,
-                     "kernel": ("z4_tma_kernel<dw,12,8> (TMA-staged stencils)" if args.pitch == FLOAT_PITCH
-                                else "z4_stage_kernel<float,dw> (global-load stencils)"),
+                     "kernel": headline_kernel(args),
                      "bytes_per_cell_update": r32["contract_bytes"],
                      "per_stage_ms": r32["per_stage_ms"], "per_stage_gbs": r32["per_stage_gbs"]},
         "alu_roofline": {
@@ -413,6 +415,14 @@ def gpu_arm(args):
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
     return line
+
+
+def headline_kernel(args) -> str:
+    if args.pitch % 4 == 0 and args.x_offset == 1:
+        return "z4_pair_kernel<DW2,8,7> (two points per thread on f32x2, TMA-staged stencils)"
+    if args.pitch % 4 == 0 and args.x_offset == 0:
+        return "z4_tma_kernel<dw,12,8> (TMA-staged stencils)"
+    return "z4_stage_kernel<float,dw> (global-load stencils)"
 
 
 def issue_roofline(r32, clocks) -> dict | None:
@@ -883,6 +893,9 @@ def main():
     ap.add_argument("--npatch", type=int, default=512, help="patches of the batch rows")
     ap.add_argument("--pitch", type=int, default=FLOAT_PITCH,
                     help="row pitch of the float arrays (102 = dense: global-load kernel)")
+    ap.add_argument("--x-offset", type=int, default=1,
+                    help="floats before each row's first ghost point of the float arrays (1: the "
+                         "two-point CCZ4 kernel; 0: the one-point TMA kernel)")
     ap.add_argument("--only", choices=["fp32dw", "fp32", "fp64"], default=None,
                     help="time one precision only (profiling runs)")
     args = ap.parse_args()

@@ -15,7 +15,9 @@ dJ/dphi0 = lambda_phi + sum_i D_i^T lambda_{d_i} = lambda_phi - sum_i D_i lambda
 dJ/dPi0 = lambda_Pi.  The D_i and D_i^T of the initial map are evaluated by
 ``sf_rhs`` of the wave system on states holding only the relevant fields
 (the RHS of d_i is -D_i Pi, the RHS of Pi is -sum_i D_i d_i, and KO of a zero
-field is zero).  Every arithmetic step runs in libsf.so.
+field is zero).  Every stencil, stage and adjoint step runs in libsf.so; the
+observer residuals and the misfit sum (n_obs values a step) are formed with
+torch.
 """
 from __future__ import annotations
 
@@ -67,7 +69,7 @@ class WaveMisfit(torch.autograd.Function):
             if s % K == 0:
                 ckpts.append(st.A.clone())
             st.step(1)
-            capi.sf_gather(p0, st.A.data_ptr(), 0, obs.data_ptr(), obs.numel(), vals.data_ptr())
+            capi.sf_gather(p0, st.ptr(st.A), 0, obs.data_ptr(), obs.numel(), vals.data_ptr())
             r = vals.double() - ref[s].double()
             J = J + 0.5 * (r * r).sum()
         ctx.save_for_backward(obs, ref)
@@ -99,12 +101,12 @@ class WaveMisfit(torch.autograd.Function):
             res = []
             for s in range(s0, s1):
                 fwd.step(1)
-                capi.sf_gather(p0, fwd.A.data_ptr(), 0, obs.data_ptr(), obs.numel(),
+                capi.sf_gather(p0, fwd.ptr(fwd.A), 0, obs.data_ptr(), obs.numel(),
                                vals.data_ptr())
                 res.append(((vals.double() - ref[s].double()) * gJ).to(st.dtype))
             # adjoint sweep through the segment, newest step first
             for s in range(s1 - 1, s0 - 1, -1):
-                capi.sf_scatter_add(p0, adj.A.data_ptr(), 0, obs.data_ptr(), obs.numel(),
+                capi.sf_scatter_add(p0, adj.ptr(adj.A), 0, obs.data_ptr(), obs.numel(),
                                     res[s - s0].data_ptr())
                 adj.fill_ghosts(adj.A)  # the injection changed interior points only
                 adj.adjoint_step(1)
@@ -126,7 +128,7 @@ def observe(phi0, Pi0, obs, dx, dt, nsteps, precision=capi.SF_FP64, prm=None):
     p0 = st.patch(st.A, st.A, st.B)
     for s in range(nsteps):
         st.step(1)
-        capi.sf_gather(p0, st.A.data_ptr(), 0, obs.data_ptr(), obs.numel(), out[s].data_ptr())
+        capi.sf_gather(p0, st.ptr(st.A), 0, obs.data_ptr(), obs.numel(), out[s].data_ptr())
     return out
 
 

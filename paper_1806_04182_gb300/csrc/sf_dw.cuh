@@ -17,6 +17,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace sf {
 
 struct dw {
@@ -139,6 +141,17 @@ template <> struct Isl<double> {
     return T(double(x) - a * double(y));
   }
   template <typename T> static __device__ __forceinline__ T to(H a) { return T(a); }
+  // a kept as its bulk rounding v plus the exact remainder (nothing kept
+  // when the bulk type is double itself)
+  template <typename V> using Resid = double;
+  template <typename V> static __device__ __forceinline__ double resid(H a, V v) {
+    if constexpr (std::is_same<V, double>::value) return 0.0;
+    else return a - double(v);
+  }
+  template <typename V> static __device__ __forceinline__ H join(V v, double r) {
+    if constexpr (std::is_same<V, double>::value) return v;
+    else return double(v) + r;
+  }
   // ln of a value close to 1, returned in the bulk type (r: 1/a, unused here)
   template <typename T> static __device__ __forceinline__ T log(H a, H) { return T(::log(a)); }
 };
@@ -166,6 +179,13 @@ template <> struct Isl<dw> {
     return dw_sub_prod_f(x, a, y);
   }
   template <typename T> static __device__ __forceinline__ T to(H a) { return T(a.hi + a.lo); }
+  // a as its float rounding v = fl(hi + lo) plus the exact remainder
+  // (FastTwoSum's error term), which together represent a exactly
+  template <typename V> using Resid = float;
+  template <typename V> static __device__ __forceinline__ float resid(H a, V v) {
+    return __fadd_rn(a.lo, -__fadd_rn(v, -a.hi));
+  }
+  template <typename V> static __device__ __forceinline__ H join(V v, float r) { return {v, r}; }
   // ln(hi + lo) = ln(hi) + ln(1 + lo/hi) ~ logf(hi) + lo/hi (|lo/hi| < 2^-24);
   // r is 1/a, so lo/hi = lo r.hi to far better than the term's own size
   template <typename T> static __device__ __forceinline__ T log(H a, H r) {

@@ -21,6 +21,11 @@ bool z4_tma_eligible(const sf_params& prm, const sf_patch& p);      // padded 96
 bool z4_tma_any_eligible(const sf_params& prm, const sf_patch& p);  // any size, 16-byte pitches
 sf_status launch_z4_tma(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                         void* rhs_out, cudaStream_t st);
+// Two-point (f32x2) TMA-staged CCZ4 kernel (sf_z4_pair.cu): padded 96^3-class
+// layout with a one-float row offset
+bool z4_pair_eligible(const sf_params& prm, const sf_patch& p, const void* rhs_out);
+sf_status launch_z4_pair(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
+                         void* rhs_out, cudaStream_t st);
 // TMA-staged CCZ4 kernel over the tiles of many patches (sf_z4_tma.cu), for
 // sf_batch: 32 x 12 x 1 or 16 x 24 x 1 tiles (a patch's maps are encoded for
 // its tile width), tensor maps in device memory (3 per patch: u_n, u_stage,

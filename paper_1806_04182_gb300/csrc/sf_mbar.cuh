@@ -1,7 +1,8 @@
-// Shared-memory mbarrier operations (PTX mbarrier.*) and the bounded wait
-// used by every kernel that waits on one: a wait that runs past its cycle
-// limit gives up and reports false, so no kernel of this library can wait
-// forever; the caller records the failure in the status word (ST_TIMEOUT).
+// Shared-memory mbarrier operations (PTX mbarrier.*), the bounded wait used by
+// every kernel that waits on one, and a bulk L2 prefetch of row segments.  A
+// wait that runs past its cycle limit gives up and reports false, so no
+// kernel of this library can wait forever; the caller records the failure in
+// the status word (ST_TIMEOUT).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -45,6 +46,19 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
 __device__ __forceinline__ void mbar_expect(uint64_t* b, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes)
                : "memory");
+}
+
+// Bulk L2 prefetch of the 128-byte row segment of every field that the RK
+// combination of this stage reads (U^n, the accumulator, the Kahan term):
+// those reads come late in the point's computation, one field at a time, and
+// would otherwise each wait for DRAM.
+template <int kBytes = 144>
+__device__ __forceinline__ void prefetch_rows(const float* base, long long F) {
+  static_assert(kBytes % 16 == 0, "bulk prefetch size");
+#pragma unroll 1
+  for (int f = 0; f < 25; ++f)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + f * F), "n"(kBytes)
+                 : "memory");
 }
 
 }  // namespace sf

@@ -1,0 +1,483 @@
+// CCZ4 stage kernel with two points per thread (Sec. V right-hand side with
+// the Sec. II.B.1 stencils, fused with the RK stage of Sec. II.C), float
+// storage, centred advection.
+//
+// Each thread computes two x-neighbours (i, i + 1), i even, and carries
+// every quantity of the right-hand side as a pair (F2): each add, multiply
+// and fused multiply-add of the per-point algebra is one .f32x2 instruction
+// for both points, and so are most of the stencil operations.  The kernel
+// is bound by instruction issue, so this halves the issue slots of the
+// arithmetic, of the address and control work and of the ring waits per
+// point.  It needs rows laid out so that points with even interior x sit on
+// 8-byte boundaries: a row pitch of a multiple of 4 floats with one float
+// before the first ghost point (arrays start 4 bytes past a 16-byte
+// boundary).  Then every stencil read is a 64-bit shared-memory load of an
+// aligned pair, and every RK read and write a 64-bit global access.
+//
+// Staging as in the one-point TMA kernel: a CTA of W warps computes a
+// 32 x 2W x 1 tile (half-warps take rows, 16 threads x 2 points each); the
+// 40 x (2W + 6) x 7 box of every field is brought into a ring of shared
+// memory slots by a cp.async.bulk.tensor load, fields in the order the
+// right-hand side opens them, with a "full" mbarrier (TMA transaction count)
+// and an "empty" mbarrier (one arrival per warp) per slot.  Every wait is
+// bounded (about a second of clock cycles); a wait that gives up sets
+// ST_TIMEOUT in the status word, the kernel finishes with whatever the slot
+// holds, waits (bounded) for its own loads in flight and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "sf_internal.cuh"
+#include "sf_mbar.cuh"
+#include "sf_z4.cuh"
+
+namespace sf {
+namespace {
+
+constexpr int kXB = 40, kTZ = 7;                  // box: 40 x (2W + 6) x 7 floats
+constexpr int kSY = 104, kSZ = 104 * 102;         // strides of the padded 96^3 layout
+constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at GB300 clocks
+
+template <int W, int KS>
+struct PCfg {
+  static constexpr int BY = 2 * W;  // tile rows
+  static constexpr int TY = BY + 6;
+  static constexpr int kBoxBytes = kXB * TY * kTZ * 4;
+  static constexpr int kSlotBytes = (kBoxBytes + 127) / 128 * 128;
+  static constexpr int kSlotFloats = kSlotBytes / 4;
+  static constexpr int kThreads = 32 * W;
+  static constexpr int kBarOffset = KS * kSlotBytes;
+  static constexpr int kRbufOffset = kBarOffset + 2 * KS * 8;
+  static constexpr int kSmemBytes = kRbufOffset + 25 * kThreads * 8;
+  static_assert(kSmemBytes <= 232448, "shared memory per CTA");
+};
+
+// The configuration in use: 8 warps (a 32 x 16 tile), 7 slots.
+constexpr int kW = 8, kKS = 7;
+
+// Order in which z4_rhs opens the fields' stencils.  Without the
+// Gamma-driver (shift frozen) the last three are not used.
+__constant__ signed char kPairFieldSeq[25] = {19, 20, 21, 1, 2, 3, 4, 5, 6, 14, 15, 16, 0,
+                                              18, 7, 17, 8, 9, 10, 11, 12, 13, 22, 23, 24};
+
+// Stencil weights as broadcast pairs (Sec. II.B.1), per direction d.
+struct PairCoef {
+  F2 d1[3], d2[3];         // D_d = (U+1 - U-1) d1 + (U-2 - U+2) d2: 8/(12 h), 1/(12 h)
+  F2 k1[3], k2[3], k3[3];  // KO: 15 s, -6 s, s on the sums at distance 1, 2, 3
+  F2 kc;                   // KO centre: -20 (s_x + s_y + s_z), s = sigma / (64 h)
+  F2 e1[3], e2[3], e0[3];  // D_dd: 16 e, -e, -30 e with e = 1 / (12 h^2)
+  F2 mx[3][3];             // mixed (xy, xz, yz): w, 8 w, 64 w with w = 1 / (144 h_a h_b)
+};
+
+PairCoef pair_coef(const sf_params& prm, const sf_patch& p) {
+  PairCoef c;
+  double kc = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const double h = p.dx[d], s = prm.sigma_ko / (64.0 * h), e = 1.0 / (12.0 * h * h);
+    auto b = [](double v) { F2 r; r.x = r.y = float(v); return r; };
+    c.d1[d] = b(8.0 / (12.0 * h));
+    c.d2[d] = b(1.0 / (12.0 * h));
+    c.k1[d] = b(15.0 * s);
+    c.k2[d] = b(-6.0 * s);
+    c.k3[d] = b(s);
+    kc += s;
+    c.e1[d] = b(16.0 * e);
+    c.e2[d] = b(-e);
+    c.e0[d] = b(-30.0 * e);
+  }
+  c.kc.x = c.kc.y = float(-20.0 * kc);
+  const double w[3] = {1.0 / (144.0 * p.dx[0] * p.dx[1]), 1.0 / (144.0 * p.dx[0] * p.dx[2]),
+                       1.0 / (144.0 * p.dx[1] * p.dx[2])};
+  for (int m = 0; m < 3; ++m)
+    for (int k = 0; k < 3; ++k) c.mx[m][k].x = c.mx[m][k].y = float(w[m] * (k == 0 ? 1.0 : k == 1 ? 8.0 : 64.0));
+  return c;
+}
+
+__device__ __forceinline__ void tma_load_4d(float* dst, const CUtensorMap* map, int x, int y, int z,
+                                            int f, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(f), "r"(saddr(bar))
+      : "memory");
+}
+
+// Stencil source of z4_rhs for the pair of points (i, i + 1): the staged
+// boxes in shared memory, the centre values (all fields, at the start) from
+// global memory.
+template <int W, int KS>
+struct PairSrc {
+  using C = PCfg<W, KS>;
+  static constexpr int kY = kXB;            // box row, floats
+  static constexpr int kZ = kXB * C::TY;    // box plane, floats
+  const float* __restrict__ u;  // global stage input at point i, field 0
+  long long F;
+  const PairCoef* pc;
+  float* tiles;
+  uint64_t* full;
+  uint64_t* empty;
+  const CUtensorMap* map;
+  unsigned* status;
+  int local;  // this thread's point i inside a box (an even float index)
+  int use, cur, nuses, issued;
+  int gx, gy, gz;  // tensor coordinates of the box origin
+  bool leader, lane0, dead;
+
+  __device__ __forceinline__ void fail() {
+    if (!dead) atomicOr(status, ST_TIMEOUT);
+    dead = true;
+  }
+  // leader: load field use j into its slot once the previous occupant
+  // (use j - KS) has been released by every warp
+  __device__ __forceinline__ void issue(int j) {
+    const int sl = j % KS;
+    if (j >= KS && !dead && !mbar_wait(&empty[sl], ((j / KS) - 1) & 1, kWaitCycles)) fail();
+    if (dead) return;
+    mbar_expect(&full[sl], C::kBoxBytes);
+    tma_load_4d(tiles + sl * C::kSlotFloats, map, gx, gy, gz, kPairFieldSeq[j], &full[sl]);
+    issued = j + 1;
+  }
+  __device__ __forceinline__ void prologue() {
+    if (leader)
+      for (int j = 0; j < KS - 2 && j < nuses; ++j) issue(j);
+  }
+  __device__ __forceinline__ void begin() {
+    const int i = use++;
+    if (leader && i + KS - 2 < nuses) issue(i + KS - 2);
+    if (i > 0) {
+      __syncwarp();
+      if (lane0) mbar_arrive(&empty[(i - 1) % KS]);
+    }
+    cur = i % KS;
+    if (!dead && !mbar_wait(&full[cur], (i / KS) & 1, kWaitCycles)) fail();
+  }
+  __device__ __forceinline__ void finish() {
+    if (leader && dead)
+      for (int j = use; j < issued; ++j) mbar_wait(&full[j % KS], (j / KS) & 1, kWaitCycles);
+  }
+
+  __device__ __forceinline__ const float* box() const { return tiles + cur * C::kSlotFloats + local; }
+  // aligned pair at float offset o (even) from point i
+  static __device__ __forceinline__ F2 L(const float* p, int o) { return *reinterpret_cast<const F2*>(p + o); }
+
+  __device__ __forceinline__ F2 centre(int f) const {
+    return *reinterpret_cast<const F2*>(u + f * F);
+  }
+
+  // 19-point cross of both points.  Along x the neighbours at odd distance
+  // straddle two aligned pairs: their sums and differences are formed lane
+  // by lane (two scalar instructions straight into a pair), everything else
+  // on pairs.
+  __device__ __forceinline__ Cross<F2> cross(int f, bool second) {
+    begin();
+    const float* p = box();
+    const PairCoef& c = *pc;
+    const F2 am4 = L(p, -4), am2 = L(p, -2), a0 = L(p, 0), a2 = L(p, 2), a4 = L(p, 4);
+    // x: values q(o) at offset o from point i; point i + 1 reads q(o + 1)
+    const F2 xs1(am2.y + a0.y, a0.x + a2.x);   // U-1 + U+1
+    const F2 xd1(a0.y - am2.y, a2.x - a0.x);   // U+1 - U-1
+    const F2 xs3(am4.y + a2.y, am2.x + a4.x);  // U-3 + U+3
+    const F2 xs2 = add2(am2, a2), xd2 = sub2(am2, a2);
+    const F2 ym1 = L(p, -kY), yp1 = L(p, kY), ym2 = L(p, -2 * kY), yp2 = L(p, 2 * kY),
+             ym3 = L(p, -3 * kY), yp3 = L(p, 3 * kY);
+    const F2 zm1 = L(p, -kZ), zp1 = L(p, kZ), zm2 = L(p, -2 * kZ), zp2 = L(p, 2 * kZ),
+             zm3 = L(p, -3 * kZ), zp3 = L(p, 3 * kZ);
+    const F2 ys1 = add2(ym1, yp1), yd1 = sub2(yp1, ym1), ys2 = add2(ym2, yp2), yd2 = sub2(ym2, yp2),
+             ys3 = add2(ym3, yp3);
+    const F2 zs1 = add2(zm1, zp1), zd1 = sub2(zp1, zm1), zs2 = add2(zm2, zp2), zd2 = sub2(zm2, zp2),
+             zs3 = add2(zm3, zp3);
+    Cross<F2> x;
+    x.c = a0;
+    x.d[0] = fma2(xd1, c.d1[0], mul2(xd2, c.d2[0]));
+    x.d[1] = fma2(yd1, c.d1[1], mul2(yd2, c.d2[1]));
+    x.d[2] = fma2(zd1, c.d1[2], mul2(zd2, c.d2[2]));
+    F2 ko = mul2(a0, c.kc);
+    ko = fma2(xs3, c.k3[0], ko);
+    ko = fma2(ys3, c.k3[1], ko);
+    ko = fma2(zs3, c.k3[2], ko);
+    ko = fma2(xs2, c.k2[0], ko);
+    ko = fma2(ys2, c.k2[1], ko);
+    ko = fma2(zs2, c.k2[2], ko);
+    ko = fma2(xs1, c.k1[0], ko);
+    ko = fma2(ys1, c.k1[1], ko);
+    x.ko = fma2(zs1, c.k1[2], ko);
+    if (second) {
+      x.dd[0] = fma2(xs1, c.e1[0], fma2(xs2, c.e2[0], mul2(a0, c.e0[0])));
+      x.dd[1] = fma2(ys1, c.e1[1], fma2(ys2, c.e2[1], mul2(a0, c.e0[1])));
+      x.dd[2] = fma2(zs1, c.e1[2], fma2(zs2, c.e2[2], mul2(a0, c.e0[2])));
+    } else {
+      x.dd[0] = x.dd[1] = x.dd[2] = F2(0.0f);
+    }
+    x.adv = F2(0.0f);
+    return x;
+  }
+
+  // D_xb with b = y (s = kY) or z (s = kZ): with r1(o) = U(-2) - U(+2) and
+  // r8(o) = U(+1) - U(-1) along x in the row at offset o across,
+  // D_xb = w (r1(-2) - r1(2)) + 8 w (r8(-2) - r8(2) + r1(1) - r1(-1)) + 64 w (r8(1) - r8(-1)).
+  __device__ __forceinline__ F2 mix_x(const float* p, int s, const F2* w) const {
+    F2 r1[4], r8[4];  // rows -2, -1, 1, 2
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int o = (q < 2 ? q - 2 : q - 1) * s;
+      const F2 am2 = L(p, o - 2), a0 = L(p, o), a2 = L(p, o + 2);
+      r1[q] = sub2(am2, a2);
+      r8[q] = F2(a0.y - am2.y, a2.x - a0.x);
+    }
+    const F2 x1 = sub2(r1[0], r1[3]);
+    const F2 x8 = add2(sub2(r8[0], r8[3]), sub2(r1[2], r1[1]));
+    const F2 x64 = sub2(r8[2], r8[1]);
+    return fma2(x64, w[2], fma2(x8, w[1], mul2(x1, w[0])));
+  }
+  // D_yz: the same along y, rows across in z
+  __device__ __forceinline__ F2 mix_yz(const float* p, const F2* w) const {
+    F2 r1[4], r8[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int o = (q < 2 ? q - 2 : q - 1) * kZ;
+      r1[q] = sub2(L(p, o - 2 * kY), L(p, o + 2 * kY));
+      r8[q] = sub2(L(p, o + kY), L(p, o - kY));
+    }
+    const F2 x1 = sub2(r1[0], r1[3]);
+    const F2 x8 = add2(sub2(r8[0], r8[3]), sub2(r1[2], r1[1]));
+    const F2 x64 = sub2(r8[2], r8[1]);
+    return fma2(x64, w[2], fma2(x8, w[1], mul2(x1, w[0])));
+  }
+  // mixed derivatives (xy, xz, yz) of the field whose cross was just read
+  __device__ __forceinline__ void mix3(int, F2* out) const {
+    const float* p = box();
+    out[0] = mix_x(p, kY, pc->mx[0]);
+    out[1] = mix_x(p, kZ, pc->mx[1]);
+    out[2] = mix_yz(p, pc->mx[2]);
+  }
+};
+
+// RK stage combination of one field value pair (sf_common.cuh's
+// stage_combine on pairs): writes the accumulator / Kahan term and returns
+// the next stage input.
+__device__ __forceinline__ F2 stage_combine2(const PatchArgs<float>& a, const StageArgs& s,
+                                             long long o, F2 centre, F2 un_m, F2 acc, F2 kh, F2 r) {
+  const F2 un = s.un_alias ? centre : un_m;
+  const F2 cn(a.c_next), ca(a.c_acc);
+  F2 out;
+  if (s.rk == SF_RK4) {
+    if (s.stage == 0) {
+      *reinterpret_cast<F2*>(a.acc + o) = s.kahan ? mul2(ca, r) : fma2(ca, r, un);
+      out = fma2(cn, r, un);
+    } else if (s.stage < 3) {
+      *reinterpret_cast<F2*>(a.acc + o) = fma2(ca, r, acc);
+      out = fma2(cn, r, un);
+    } else if (!s.kahan) {
+      out = fma2(cn, r, acc);
+    } else {
+      const F2 inc = fma2(cn, r, acc);
+      const F2 y = sub2(inc, kh);
+      const F2 t = add2(un, y);
+      *reinterpret_cast<F2*>(a.kh + o) = sub2(sub2(t, un), y);
+      out = t;
+    }
+  } else {
+    const F2 dt(a.dt);
+    if (s.stage == 0) out = fma2(dt, r, un);
+    else if (s.stage == 1) out = fma2(F2(0.75f), un, mul2(F2(0.25f), fma2(dt, r, centre)));
+    else out = fma2(un, F2(float(1.0 / 3.0)), mul2(F2(float(2.0 / 3.0)), fma2(dt, r, centre)));
+  }
+  return out;
+}
+
+// The stage write of the 25 fields of both points, right-hand sides parked
+// in shared memory (r[f * stride]); the scheme of write_fields (batches of
+// five fields with every read issued before the writes, periodic images of
+// boundary points in one rolled pass at the end) on 64-bit accesses.
+__device__ __forceinline__ void write_fields_pair(const PatchArgs<float>& a, const StageArgs& s,
+                                                  long long c, int i, int j, int k, F2* r,
+                                                  int stride) {
+  if (s.mode == 1) {
+    const long long oi = ((long long)k * a.n[1] + j) * a.n[0] + i;
+#pragma unroll 1
+    for (int f = 0; f < 25; ++f) {
+      const F2 v = r[f * stride];
+      a.nx[f * a.ninterior + oi] = v.x;
+      a.nx[f * a.ninterior + oi + 1] = v.y;
+    }
+    return;
+  }
+  const bool rk4 = s.rk == SF_RK4;
+  const bool need_centre = s.un_alias || !rk4;
+  const bool need_acc = rk4 && s.stage > 0;
+  const bool need_kh = rk4 && s.stage == 3 && s.kahan;
+  auto ld = [](const float* q) { return *reinterpret_cast<const F2*>(q); };
+#pragma unroll 1
+  for (int f0 = 0; f0 < 25; f0 += 5) {
+    F2 cen[5], un[5], acc[5], kh[5], rr[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const long long o = (f0 + q) * a.sf + c;
+      rr[q] = r[(f0 + q) * stride];
+      cen[q] = need_centre ? ld(a.us + o) : F2(0.0f);
+      un[q] = s.un_alias ? F2(0.0f) : ld(a.un + o);
+      acc[q] = need_acc ? ld(a.acc + o) : F2(0.0f);
+      kh[q] = need_kh ? ld(a.kh + o) : F2(0.0f);
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const long long o = (f0 + q) * a.sf + c;
+      const F2 out = stage_combine2(a, s, o, cen[q], un[q], acc[q], kh[q], rr[q]);
+      *reinterpret_cast<F2*>(a.nx + o) = out;
+      if (s.check_finite && !(finite_(out.x) && finite_(out.y))) atomicOr(s.status, ST_NONFINITE);
+      r[(f0 + q) * stride] = out;
+    }
+  }
+  const Images im0 = ghost_images(a, s, i, j, k), im1 = ghost_images(a, s, i + 1, j, k);
+  if (im0.mask | im1.mask) {
+#pragma unroll 1
+    for (int f = 0; f < 25; ++f) {
+      const F2 v = r[f * stride];
+      store_images(a, im0, f * a.sf + c, v.x);
+      store_images(a, im1, f * a.sf + c + 1, v.y);
+    }
+  }
+}
+
+}  // namespace
+
+template <typename H2, int W, int KS>
+__global__ void __launch_bounds__(32 * W, 1)
+    z4_pair_kernel(const __grid_constant__ CUtensorMap map, PatchArgs<float> a, StageArgs s,
+                   Z4Coef<float> zc, const __grid_constant__ PairCoef pc) {
+  using C = PCfg<W, KS>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* tiles = reinterpret_cast<float*>(smem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kBarOffset);
+  uint64_t* empty = full + KS;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  if (tid == 0) {
+    for (int q = 0; q < KS; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], W);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  // whole tiles only (checked on the host): every thread has two points
+  const int px = 2 * (threadIdx.x & 15);
+  const int ly = 2 * threadIdx.y + (threadIdx.x >> 4);
+  const int i = blockIdx.x * 32 + px;
+  const int j = blockIdx.y * C::BY + ly;
+  const int k = blockIdx.z;
+  const long long c = (long long)(k + 3) * kSZ + (long long)(j + 3) * kSY + (i + 3);
+  if ((threadIdx.x & 15) == 0 && s.mode == 0) {
+    // the row's 32 points start on a 16-byte boundary: prefetch their 128 B
+    // of every field the RK combination of this stage reads
+    if (!s.un_alias) prefetch_rows<128>(a.un + c, a.sf);
+    if (s.rk == SF_RK4 && s.stage > 0) prefetch_rows<128>(a.acc + c, a.sf);
+    if (s.kahan && s.stage == 3) prefetch_rows<128>(a.kh + c, a.sf);
+  }
+  PairSrc<W, KS> src;
+  src.u = a.us + c;
+  src.F = a.sf;
+  src.pc = &pc;
+  src.tiles = tiles;
+  src.full = full;
+  src.empty = empty;
+  src.map = &map;
+  src.status = s.status;
+  src.local = (3 * C::TY + ly + 3) * kXB + px + 4;
+  src.use = 0;
+  src.cur = 0;
+  src.nuses = zc.shift_frozen ? 22 : 25;
+  src.issued = 0;
+  src.gx = blockIdx.x * 32;  // tensor x = ghosted x + 1; the box starts 4 before point x0
+  src.gy = blockIdx.y * C::BY;
+  src.gz = k;
+  src.leader = tid == 0;
+  src.lane0 = threadIdx.x == 0;
+  src.dead = false;
+  src.prologue();
+  F2* rbuf = reinterpret_cast<F2*>(smem + C::kRbufOffset);
+  F2 be[3];
+  z4_rhs<F2, H2, false>(zc, src, be, [&](int f, F2 r, F2) { rbuf[f * C::kThreads + tid] = r; });
+  write_fields_pair(a, s, c, i, j, k, rbuf + tid, C::kThreads);
+}
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn_pair() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool offset_aligned(const void* q) {
+  return q && reinterpret_cast<uintptr_t>(q) % 16 == 4;
+}
+
+template <typename H2>
+sf_status launch_pair(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
+                      void* rhs_out, cudaStream_t st) {
+  using C = PCfg<kW, kKS>;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn_pair();
+  if (!enc) return set_error(SF_ECUDA, "cuTensorMapEncodeTiled not available");
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  // tensor x = ghosted x + 1: the map starts at the float before ghost point 0
+  const cuuint64_t dims[4] = {(cuuint64_t)(p.n[0] + 7), (cuuint64_t)(p.n[1] + 6),
+                              (cuuint64_t)(p.n[2] + 6), 25};
+  const cuuint64_t strides[3] = {(cuuint64_t)p.sy * 4, (cuuint64_t)p.sz * 4, (cuuint64_t)p.sf * 4};
+  const cuuint32_t box[4] = {kXB, (cuuint32_t)C::TY, kTZ, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  void* base = static_cast<char*>(p.u_stage) - 4;
+  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(SF_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(z4_pair_kernel<H2, kW, kKS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         C::kSmemBytes);
+  });
+  PatchArgs<float> a = make_args<float>(prm, p, stage, 25, rhs_out);
+  const Z4Coef<float> zc = z4_coef<float>(prm);
+  const PairCoef pc = pair_coef(prm, p);
+  dim3 grid(p.n[0] / 32, p.n[1] / C::BY, p.n[2]);
+  z4_pair_kernel<H2, kW, kKS><<<grid, dim3(32, kW, 1), C::kSmemBytes, st>>>(map, a, s, zc, pc);
+  return after_launch("z4_pair_kernel");
+}
+
+}  // namespace
+
+// The two-point kernel serves float storage with centred advection on the
+// padded 96^3-class layout with the one-float row offset: 3 ghosts, row
+// pitch 104 floats, plane pitch 104 x 102, field pitch a multiple of 4
+// floats, every array 4 bytes past a 16-byte boundary, whole 32 x 16 tiles.
+bool z4_pair_eligible(const sf_params& prm, const sf_patch& p, const void* rhs_out) {
+  using C = PCfg<kW, kKS>;
+  if (p.system != SF_Z4 || p.precision == SF_FP64 || prm.lopsided) return false;
+  if (p.ghost != 3 || p.sy != kSY || p.sz != kSZ || p.sf % 4) return false;
+  if (p.n[0] % 32 || p.n[1] % C::BY || p.n[0] + 7 > kSY || p.n[1] + 6 > 102) return false;
+  if (!offset_aligned(p.u_stage)) return false;
+  if (rhs_out) return true;  // RHS output: scalar stores
+  for (const void* q : {(const void*)p.u_n, (const void*)p.u_next, (const void*)p.acc})
+    if (q && !offset_aligned(q)) return false;
+  if (p.kahan && !offset_aligned(p.kahan)) return false;
+  return true;
+}
+
+sf_status launch_z4_pair(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
+                         void* rhs_out, cudaStream_t st) {
+  if (p.precision == SF_FP32_BULK_DW) return launch_pair<DW2>(prm, p, s, stage, rhs_out, st);
+  return launch_pair<D2>(prm, p, s, stage, rhs_out, st);
+}
+
+}  // namespace sf

@@ -83,8 +83,8 @@ static_assert(kTmaTileX16 == 16 && kTmaTileY16 == kBY16, "batch narrow tiles are
 // Order in which z4_cell opens the fields' stencils (cross, then the mixed
 // derivatives of the same field).  Without the Gamma-driver (shift frozen)
 // the last three are not used.
-__constant__ signed char kFieldSeq[25] = {19, 20, 21, 1, 2,  3,  4,  5,  6,  0,  18, 14, 15,
-                                          16, 7,  17, 8, 9, 10, 11, 12, 13, 22, 23, 24};
+__constant__ signed char kFieldSeq[25] = {19, 20, 21, 1, 2, 3, 4, 5, 6, 14, 15, 16, 0,
+                                          18, 7, 17, 8, 9, 10, 11, 12, 13, 22, 23, 24};
 
 __device__ __forceinline__ void tma_load_4d(float* dst, const CUtensorMap* map, int x, int y, int z,
                                             int f, uint64_t* bar) {
@@ -163,19 +163,6 @@ struct TmaSrc {
 };
 
 }  // namespace
-
-// Bulk L2 prefetch of the 128-byte row segment of every field that the RK
-// combination of this stage reads (U^n, the accumulator, the Kahan term):
-// those reads come late in the point's computation, one field at a time, and
-// would otherwise each wait for DRAM.
-template <int kBytes = 144>
-__device__ __forceinline__ void prefetch_rows(const float* base, long long F) {
-  static_assert(kBytes % 16 == 0, "bulk prefetch size");
-#pragma unroll 1
-  for (int f = 0; f < 25; ++f)
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + f * F), "n"(kBytes)
-                 : "memory");
-}
 
 template <typename H, int BY, int KS>
 __global__ void __launch_bounds__(Cfg<BY, KS>::kThreads, Cfg<BY, KS>::kMinBlocks)

@@ -30,11 +30,15 @@ def _stream_handle(stream) -> int:
 class PatchState:
     def __init__(self, system: int, n, dx, dt: float, precision: int = capi.SF_FP64,
                  prm: capi.sf_params | None = None, ghost: int = 3, device="cuda",
-                 x_pitch: int | None = None):
+                 x_pitch: int | None = None, x_offset: int = 0):
         """x_pitch: row length of the ghosted arrays in elements (default
         nx + 2 ghost).  A pitch that makes every row, plane and field start
         on a 16-byte boundary (a multiple of 4 floats) lets the float CCZ4
-        substep stage its stencils with TMA bulk-tensor copies."""
+        substep stage its stencils with TMA bulk-tensor copies.  x_offset:
+        elements before the first ghosted point of each row.  With a pitch of
+        a multiple of 4 floats and x_offset = 1, interior points with even x
+        sit on 8-byte boundaries, which the float CCZ4 kernel that computes
+        two neighbouring points per thread needs."""
         self.system = system
         self.n = tuple(int(v) for v in n)
         self.dx = tuple(float(v) for v in dx)
@@ -47,9 +51,10 @@ class PatchState:
         self.dtype = torch.float64 if precision == capi.SF_FP64 else torch.float32
         nx, ny, nz = self.n
         g = ghost
-        self.pitch = nx + 2 * g if x_pitch is None else int(x_pitch)
-        if self.pitch < nx + 2 * g:
-            raise ValueError("x_pitch shorter than a ghosted row")
+        self.xo = int(x_offset)
+        self.pitch = self.xo + nx + 2 * g if x_pitch is None else int(x_pitch)
+        if self.xo < 0 or self.pitch < self.xo + nx + 2 * g:
+            raise ValueError("x_pitch shorter than x_offset plus a ghosted row")
         self.shape = (self.nf, nz + 2 * g, ny + 2 * g, self.pitch)
         kw = dict(dtype=self.dtype, device=device)
         self.A = torch.zeros(self.shape, **kw)
@@ -61,6 +66,10 @@ class PatchState:
         self._rate = None  # MHD: device rate of the current U^n, if known
 
     # ------------------------------------------------------------------ ABI
+    def ptr(self, t: torch.Tensor) -> int:
+        """Device address of ghosted point (0, 0, 0) of field 0 of array t."""
+        return t.data_ptr() + self.xo * t.element_size()
+
     def patch(self, u_stage, u_n, u_next) -> capi.sf_patch:
         p = capi.sf_patch()
         p.n[:] = self.n
@@ -70,11 +79,11 @@ class PatchState:
         p.system = self.system
         p.precision = self.precision
         p.sy, p.sz, p.sf = self.strides
-        p.u_stage = u_stage.data_ptr()
-        p.u_n = u_n.data_ptr()
-        p.acc = self.D.data_ptr() if self.D is not None else None
-        p.u_next = u_next.data_ptr()
-        p.kahan = self.E.data_ptr() if self.E is not None else None
+        p.u_stage = self.ptr(u_stage)
+        p.u_n = self.ptr(u_n)
+        p.acc = self.ptr(self.D) if self.D is not None else None
+        p.u_next = self.ptr(u_next)
+        p.kahan = self.ptr(self.E) if self.E is not None else None
         p.cfl_rate = None
         return p
 
@@ -119,8 +128,8 @@ class PatchState:
             t = t.clone()
             for f in self.offset_fields:
                 t[f] -= 1.0
-        nx = self.n[0]
-        self.A[:, g:self.shape[1] - g, g:self.shape[2] - g, g:g + nx].copy_(t.to(self.dtype))
+        nx, xo = self.n[0], self.xo
+        self.A[:, g:self.shape[1] - g, g:self.shape[2] - g, xo + g:xo + g + nx].copy_(t.to(self.dtype))
         if self.E is not None:
             self.E.zero_()
         self._rate = None
@@ -134,7 +143,7 @@ class PatchState:
         for f in self.offset_fields:
             t[f] -= 1.0
         nx = self.n[0] + 2 * self.g
-        self.A[:, :, :, :nx].copy_(t.to(self.dtype))
+        self.A[:, :, :, self.xo:self.xo + nx].copy_(t.to(self.dtype))
         if self.E is not None:
             self.E.zero_()
         self._rate = None
@@ -151,14 +160,14 @@ class PatchState:
                 capi.sf_radiative_substep(self.prm, p, x0, u_inf, speed, s, h)
 
     def fill_ghosts(self, array: torch.Tensor, stream=None) -> None:
-        capi.sf_fill_ghosts_periodic(self.patch(array, array, array), array.data_ptr(), self.nf,
+        capi.sf_fill_ghosts_periodic(self.patch(array, array, array), self.ptr(array), self.nf,
                                      _stream_handle(stream))
 
     def interior(self, array: torch.Tensor | None = None) -> torch.Tensor:
         """Interior view of the stored values (float CCZ4: with offsets)."""
         a = self.A if array is None else array
         g = self.g
-        return a[:, g:self.shape[1] - g, g:self.shape[2] - g, g:g + self.n[0]]
+        return a[:, g:self.shape[1] - g, g:self.shape[2] - g, self.xo + g:self.xo + g + self.n[0]]
 
     def fields(self, array: torch.Tensor | None = None) -> torch.Tensor:
         """Interior field values in float64 (flat-space offsets added back)."""
@@ -222,14 +231,14 @@ class PatchState:
     def diagnostics(self, array: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         a = self.A if array is None else array
         out = torch.empty(5, dtype=torch.float64, device=a.device)
-        capi.sf_diagnostics(self.prm, self.patch(a, a, self.B), a.data_ptr(), out.data_ptr(),
+        capi.sf_diagnostics(self.prm, self.patch(a, a, self.B), self.ptr(a), out.data_ptr(),
                             _stream_handle(stream))
         return out
 
     def mhd_max_rate(self, array: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         a = self.A if array is None else array
         out = torch.empty(1, dtype=torch.float64, device=a.device)
-        capi.sf_mhd_max_rate(self.prm, self.patch(a, a, self.B), a.data_ptr(), out.data_ptr(),
+        capi.sf_mhd_max_rate(self.prm, self.patch(a, a, self.B), self.ptr(a), out.data_ptr(),
                              _stream_handle(stream))
         return out
 
@@ -241,6 +250,7 @@ class PatchState:
         metadata to `path` (.npz); `load` resumes bit for bit."""
         meta = dict(system=self.system, n=self.n, dx=self.dx, dt=self.dt,
                     precision=self.precision, ghost=self.g, step=step, t=t, pitch=self.pitch,
+                    x_offset=self.xo,
                     prm={f: getattr(self.prm, f) for f in self._PRM_FIELDS})
         arrays = {"A": self.A.cpu().numpy()}
         if self.E is not None:
@@ -254,7 +264,7 @@ class PatchState:
         meta = json.loads(str(z["meta"]))
         st = cls(meta["system"], meta["n"], meta["dx"], meta["dt"], precision=meta["precision"],
                  prm=capi.params(**meta["prm"]), ghost=meta["ghost"], device=device,
-                 x_pitch=meta.get("pitch"))
+                 x_pitch=meta.get("pitch"), x_offset=meta.get("x_offset", 0))
         st.A.copy_(torch.from_numpy(z["A"]))
         if st.E is not None and "E" in z:
             st.E.copy_(torch.from_numpy(z["E"]))

@@ -48,10 +48,11 @@ def oracle_params(prm: capi.sf_params):
                          flux_split=prm.flux_split)
 
 
-def run_stages(system, U0, dx, dt, prm, precision=capi.SF_FP64, pitch=None):
+def run_stages(system, U0, dx, dt, prm, precision=capi.SF_FP64, pitch=None, x_offset=0):
     """GPU stage outputs (interior, numpy float64) of one full step."""
     n = (U0.shape[3], U0.shape[2], U0.shape[1])
-    st = PatchState(system, n, dx, dt, precision=precision, prm=prm, x_pitch=pitch)
+    st = PatchState(system, n, dx, dt, precision=precision, prm=prm, x_pitch=pitch,
+                    x_offset=x_offset)
     st.upload(U0)
     outs = []
     for s in range(st.nstages):
@@ -230,6 +231,46 @@ def test_mhd_fp64_stages(variant, split):
         assert e.max() < TOL64, (s, e)
 
 
+# FP32 MHD (float storage and arithmetic; the suite's FP32 row) against the
+# FP64 oracle.  Bound: a stage output is U plus dt/dx_d times differences of
+# the six interface fluxes around the cell; each flux is formed with about
+# ten roundings of relative size eps32/2 of |F| <= S |U| (S the LLF speed),
+# and dt S / dx <= CFL = 0.3, so |error| <= (1 + 6 * 0.3 * 10) eps32 |U|
+# ~ 19 eps32 |U| per stage, plus the rounding of the input state itself;
+# the bound taken is 32 eps32 of each field's scale (floor 1e-3).  The
+# WENO weights' sensitivity to rounding stays inside it: where a smoothness
+# indicator is of rounding size the candidates agree to the same order.
+EPS32 = float(np.finfo(np.float32).eps)
+TOL32_MHD = 32 * EPS32
+
+
+@pytest.mark.parametrize("split", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_mhd_fp32_stages(variant, split):
+    n = (35, 10, 7)
+    U0, dx = inputs.mhd_blast(n, seed=4, radius=0.3)
+    prm = capi.params(rk=capi.SF_SSPRK3, weno_variant=variant, flux_split=split)
+    dt = 0.3 / oracle.mhd_max_rate(oracle.ghosted(U0), dx)
+    got = run_stages(capi.SF_MHD, U0, dx, dt, prm, precision=capi.SF_FP32_BULK)
+    want = oracle_stages(oracle.MHD, U0, dx, dt, prm)
+    for s in range(3):
+        e = rel_err(got[s], want[s], floor=1e-3)
+        assert e.max() < TOL32_MHD, (s, e / EPS32)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_mhd_fp32_brio_wu_stages(variant):
+    n = (256, 3, 3)
+    U0, dx = inputs.mhd_brio_wu(n)
+    prm = capi.params(rk=capi.SF_SSPRK3, weno_variant=variant, gamma_eos=2.0)
+    dt = 0.2 * dx[0]
+    got = run_stages(capi.SF_MHD, U0, dx, dt, prm, precision=capi.SF_FP32_BULK)
+    want = oracle_stages(oracle.MHD, U0, dx, dt, prm)
+    for s in range(3):
+        e = rel_err(got[s], want[s], floor=1e-3)
+        assert e.max() < TOL32_MHD, (s, e / EPS32)
+
+
 # The Brio & Wu shock tube (Sec. IV.B.2; Gamma = 2, dt = 0.2 dx): stage
 # outputs on discontinuous data, where the WENO weights are far from the
 # linear ones, from the initial jumps and from the developed waves after 30
@@ -401,16 +442,20 @@ def test_checkpoint_resume_is_bitwise(tmp_path, precision):
 # shared memory with cp.async.bulk.tensor loads.  Same right-hand side, same
 # float rounding bound against the oracle; against the global-load kernel on
 # the dense layout the only differences come from FMA contraction.
+# x_offset 0: the one-point TMA kernel; x_offset 1 (rows 4 bytes past a
+# 16-byte boundary): the two-point kernel, every stencil and the algebra on
+# f32x2 pairs, 32 x 16 tiles.
+@pytest.mark.parametrize("x_offset", [0, 1])
 @pytest.mark.parametrize("precision", [capi.SF_FP32_BULK, capi.SF_FP32_BULK_DW])
 @pytest.mark.parametrize("nx,nz", [(32, 7), (96, 5)])
-def test_z4_tma_kernel_matches_oracle(precision, nx, nz):
+def test_z4_tma_kernel_matches_oracle(precision, nx, nz, x_offset):
     n = (nx, 96, nz)
     U0, dx = inputs.z4_perturbed(n, seed=4, amp=0.05)
     prm = capi.params()
     dt = 0.25 * min(dx)
     eps32 = float(np.finfo(np.float32).eps)
     bound = 4 * 64 / 12 * eps32 * dt / min(dx) ** 2 / 1e-2
-    got = run_stages(capi.SF_Z4, U0, dx, dt, prm, precision=precision, pitch=104)
+    got = run_stages(capi.SF_Z4, U0, dx, dt, prm, precision=precision, pitch=104, x_offset=x_offset)
     dense = run_stages(capi.SF_Z4, U0, dx, dt, prm, precision=precision)
     want = oracle_stages(oracle.Z4, U0, dx, dt, prm)
     for s in range(4):
@@ -441,7 +486,8 @@ def test_z4_tma_any_size_matches_oracle(precision, n):
         assert rel_err(got[s], dense[s], floor=1e-2).max() < bound, s
 
 
-def test_z4_tma_kernel_frozen_shift_gauge_wave():
+@pytest.mark.parametrize("x_offset", [0, 1])
+def test_z4_tma_kernel_frozen_shift_gauge_wave(x_offset):
     # harmonic slicing and a frozen shift: the last three fields' stencils are
     # never opened, so the staged sequence is 22 boxes long
     n = (32, 96, 6)
@@ -450,14 +496,17 @@ def test_z4_tma_kernel_frozen_shift_gauge_wave():
     dt = 0.25 * min(dx)
     eps32 = float(np.finfo(np.float32).eps)
     bound = 4 * 64 / 12 * eps32 * dt / min(dx) ** 2 / 1e-2
-    got = run_stages(capi.SF_Z4, U0, dx, dt, prm, precision=capi.SF_FP32_BULK_DW, pitch=104)
+    got = run_stages(capi.SF_Z4, U0, dx, dt, prm, precision=capi.SF_FP32_BULK_DW, pitch=104,
+                     x_offset=x_offset)
     want = oracle_stages(oracle.Z4, U0, dx, dt, prm)
     assert rel_err(got[3], want[3], floor=1e-2).max() < bound
 
 
-def test_z4_tma_kernel_full_size_sampled():
+@pytest.mark.parametrize("x_offset", [0, 1])
+def test_z4_tma_kernel_full_size_sampled(x_offset):
     # the benchmark's launch configuration (96^3, FP32-bulk with double-word
-    # islands, row pitch 104): sampled points of the RHS against the oracle.
+    # islands, row pitch 104, one float before each row's first ghost point
+    # for the two-point kernel): sampled points of the RHS against the oracle.
     # Stored float values carry |U - U_flat| <= 0.05 here (flat-space offsets),
     # so a 1/dx^2 stencil holds ~64 eps32 * 0.05 / (12 dx^2) of rounding.
     n = (96, 96, 96)
@@ -466,7 +515,7 @@ def test_z4_tma_kernel_full_size_sampled():
     U0 = U0 + (pert - inputs.z4_minkowski(n))
     prm = capi.params()
     st = PatchState(capi.SF_Z4, n, dx, 0.25 * dx[0], precision=capi.SF_FP32_BULK_DW, prm=prm,
-                    x_pitch=104)
+                    x_pitch=104, x_offset=x_offset)
     st.upload(U0)
     r = st.rhs().cpu().numpy().reshape(25, -1).astype(np.float64)
     pts = inputs.observers(n, 2000, seed=13)

@@ -9,7 +9,8 @@ periodic ghost shell), the accumulator on the interior, and the padding must
 still be NaN; the final state must equal, bit for bit, the state of the same
 step run on clean buffers.  Covers the global-load, compile-time-stride and
 runtime TMA-staged CCZ4 kernels (the latter with tiles overhanging the
-patch), the wave and MHD kernels, and the batched dispatch.
+patch), the two-point CCZ4 kernel (rows with one float before the first ghost
+point, also poisoned), the wave and MHD kernels, and the batched dispatch.
 """
 import pytest
 import torch
@@ -37,41 +38,50 @@ def _data(system, n, q=0):
 
 
 def _box(st, arr):
-    return arr[..., :st.n[0] + 2 * st.g]
+    return arr[..., st.xo:st.xo + st.n[0] + 2 * st.g]
 
 
 def _pad(st, arr):
-    return arr[..., st.n[0] + 2 * st.g:]
+    # the row padding before the first ghost point and after the last
+    return torch.cat([arr[..., :st.xo], arr[..., st.xo + st.n[0] + 2 * st.g:]], dim=-1)
+
+
+def _fill_pad(st, arr, v):
+    arr[..., :st.xo].fill_(v)
+    arr[..., st.xo + st.n[0] + 2 * st.g:].fill_(v)
 
 
 def _inner(st, arr):
     g = st.g
-    return arr[:, g:-g, g:-g, g:g + st.n[0]]
+    return arr[:, g:-g, g:-g, st.xo + g:st.xo + g + st.n[0]]
 
 
 CASES = [
-    # system, n, precision, pitch (None: dense + 2 padding floats)
-    (capi.SF_Z4, (37, 13, 5), capi.SF_FP32_BULK_DW, 44),   # runtime TMA, overhanging tiles
-    (capi.SF_Z4, (37, 13, 5), capi.SF_FP32_BULK_DW, 45),   # global-load, runtime strides
-    (capi.SF_Z4, (11, 9, 7), capi.SF_FP64, 19),
-    (capi.SF_WAVE, (19, 7, 6), capi.SF_FP32_BULK, 27),
-    (capi.SF_WAVE, (19, 7, 6), capi.SF_FP64, 26),
-    (capi.SF_MHD, (12, 10, 8), capi.SF_FP64, 20),
+    # system, n, precision, pitch (None: dense + 2 padding floats), row offset
+    (capi.SF_Z4, (37, 13, 5), capi.SF_FP32_BULK_DW, 44, 0),   # runtime TMA, overhanging tiles
+    (capi.SF_Z4, (37, 13, 5), capi.SF_FP32_BULK_DW, 45, 0),   # global-load, runtime strides
+    (capi.SF_Z4, (32, 96, 3), capi.SF_FP32_BULK_DW, 104, 0),  # TMA, compile-time strides
+    (capi.SF_Z4, (32, 96, 3), capi.SF_FP32_BULK_DW, 104, 1),  # two-point kernel
+    (capi.SF_Z4, (32, 96, 3), capi.SF_FP32_BULK, 104, 1),     # two-point kernel, FP64 islands
+    (capi.SF_Z4, (11, 9, 7), capi.SF_FP64, 19, 0),
+    (capi.SF_WAVE, (19, 7, 6), capi.SF_FP32_BULK, 27, 0),
+    (capi.SF_WAVE, (19, 7, 6), capi.SF_FP64, 26, 0),
+    (capi.SF_MHD, (12, 10, 8), capi.SF_FP64, 20, 0),
 ]
 
 
-@pytest.mark.parametrize("system,n,precision,pitch", CASES)
-def test_stage_writes_every_output_and_reads_no_padding(system, n, precision, pitch):
+@pytest.mark.parametrize("system,n,precision,pitch,xo", CASES)
+def test_stage_writes_every_output_and_reads_no_padding(system, n, precision, pitch, xo):
     U0, dx = _data(system, n)
     dt = 0.25 * min(dx) if system != capi.SF_MHD else 1e-3
-    clean = PatchState(system, n, dx, dt, precision=precision, x_pitch=pitch)
+    clean = PatchState(system, n, dx, dt, precision=precision, x_pitch=pitch, x_offset=xo)
     clean.upload(U0)
     clean.step(1)
-    st = PatchState(system, n, dx, dt, precision=precision, x_pitch=pitch)
+    st = PatchState(system, n, dx, dt, precision=precision, x_pitch=pitch, x_offset=xo)
     st.upload(U0)
     for arr in (st.B, st.C) + ((st.D,) if st.D is not None else ()):
         arr.fill_(NAN)
-    _pad(st, st.A).fill_(NAN)
+    _fill_pad(st, st.A, NAN)
     for s in range(st.nstages):
         out = st.stage(s)
         torch.cuda.synchronize()
@@ -103,7 +113,7 @@ def test_batch_writes_every_output_and_reads_no_padding():
     for s_ in sts:
         for arr in (s_.B, s_.C, s_.D):
             arr.fill_(NAN)
-        _pad(s_, s_.A).fill_(NAN)
+        _fill_pad(s_, s_.A, NAN)
     h = torch.cuda.current_stream().cuda_stream
     bp = capi.sf_batch_create(capi.params(), [s_.patch(s_.B, s_.A, s_.C) for s_ in sts])
     bc = capi.sf_batch_create(capi.params(), [s_.patch(s_.B, s_.A, s_.C) for s_ in clean])
