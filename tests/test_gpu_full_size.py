@@ -3,9 +3,9 @@ configurations bench.py times (the 96^3 CCZ4 patch and the 128^3 adjoint have
 their own full-size tests in test_gpu_parity.py and test_gpu_adjoint.py):
 
 * wave, 64^3 FP64, one RK4 step: every point against the oracle's step;
-* MHD, 128^3 FP64 blast data (WENO5 + LLF, SSP-RK3, dt from the fused CFL
-  rate): sampled points of the first stage against the oracle's right-hand
-  side at those points;
+* MHD, 128^3 blast data (WENO5 + LLF, SSP-RK3, dt from the CFL rate), FP64
+  and FP32: sampled points of the first stage against the oracle's
+  right-hand side at those points;
 * the batched AMR step, 512 patches {16..64}^3, wave and CCZ4 mixed,
   FP32-bulk with double-word islands, CCZ4 rows padded to 16 bytes (TMA tile
   launch + persistent launch, tuned tiles): sampled points of the first stage
@@ -69,6 +69,26 @@ def test_mhd_128cubed_fp64_first_stage_sampled():
     r = oracle.rhs_points(oracle.MHD, oracle.ghosted(U0.copy()), dx, pts, oracle_params(st.prm))
     want = U0.reshape(8, -1)[:, pts] + st.dt * r
     assert rel(out[:, pts], want, 1e-3) < TOL64
+
+
+def test_mhd_128cubed_fp32_first_stage_sampled():
+    # the FP32 MHD row of the suite, same data and launch: float storage and
+    # arithmetic, against the FP64 oracle with the FP32 stage bound (32 eps32
+    # of each field's scale, derived at test_mhd_fp32_stages in
+    # test_gpu_parity.py)
+    n = (128, 128, 128)
+    U0, dx = inputs.mhd_blast(n, seed=0)
+    st = PatchState(capi.SF_MHD, n, dx, 1e-3, precision=capi.SF_FP32_BULK)
+    st.upload(U0)
+    rate = st.mhd_max_rate().item()
+    dt = 0.3 / oracle.mhd_max_rate(oracle.ghosted(U0.copy()), dx, oracle_params(st.prm))
+    assert rate == pytest.approx(1.0 / (dt / 0.3), rel=1e-6)
+    st.dt = dt
+    out = st.fields(st.stage(0)).cpu().numpy().reshape(8, -1)
+    pts = inputs.observers(n, 3000, seed=5)
+    r = oracle.rhs_points(oracle.MHD, oracle.ghosted(U0.copy()), dx, pts, oracle_params(st.prm))
+    want = U0.reshape(8, -1)[:, pts] + dt * r
+    assert rel(out[:, pts], want, 1e-3) < 32 * EPS32
 
 
 def test_batch_512_patches_first_stage_sampled():
