@@ -234,21 +234,31 @@ def time_device(st, steps: int, warmup: int):
     return total, per, launches
 
 
-def time_e2e(st, steps: int, warmup: int):
-    """Same steps through host buffers, with the library's host pipeline
-    (state.HostPipeline): every step uploads U^n from pinned host memory,
-    runs the four stages and downloads U^{n+1}; two device states alternate
-    so that the copies of neighbouring steps overlap the stages (copy streams
-    of their own).  The timed region spans all three streams."""
+def time_e2e(st, steps: int, warmup: int, chained: bool):
+    """The same steps through host buffers, by the C-ABI call sf_step_host
+    (state.HostPipeline): every step uploads its input state from pinned
+    host memory, runs the four stages and downloads U^{n+1}.
+    chained: one evolution kept in host memory (each step's input is the
+    previous step's output, one pinned buffer updated in place, one device
+    slot whose Kahan compensation carries over): the copies and the stages
+    of a step are serial.  Otherwise: independent states (the same input
+    every step, outputs alternating between two pinned buffers), two device
+    slots, the copies of neighbouring steps overlapping the stages on copy
+    streams of their own.  The timed region spans all three streams."""
     import torch
     from paper_1806_04182_gb300.state import HostPipeline
     pipe = HostPipeline(st.system, st.n, st.dx, st.dt, precision=st.precision, prm=st.prm,
-                        ghost=st.g, x_pitch=st.pitch, x_offset=st.xo)
-    host_in = torch.empty(pipe.shape, dtype=pipe.dtype, pin_memory=True)
-    host_in.copy_(st.A.cpu())
-    host_out = torch.empty_like(host_in, pin_memory=True)
-    for _ in range(warmup):
-        pipe.step(host_in, host_out)
+                        ghost=st.g, x_pitch=st.pitch, x_offset=st.xo, slots=1 if chained else 2)
+    host_in = pipe.host_buffer()
+    host_in.copy_(pipe.image(st.A).cpu())
+    if chained:
+        ins, outs = [host_in] * steps, [host_in] * steps
+        wins, wouts = [host_in] * warmup, [host_in] * warmup
+    else:
+        o = [pipe.host_buffer(), pipe.host_buffer()]
+        ins, outs = [host_in] * steps, [o[k % 2] for k in range(steps)]
+        wins, wouts = [host_in] * warmup, [o[k % 2] for k in range(warmup)]
+    pipe.run(wins, wouts, reset_kahan=not chained)
     pipe.synchronize()
     torch.cuda.synchronize()
     cur = torch.cuda.current_stream()
@@ -256,8 +266,7 @@ def time_e2e(st, steps: int, warmup: int):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(cur)
     pipe.start(cur)
-    for _ in range(steps):
-        pipe.step(host_in, host_out)
+    pipe.run(ins, outs, reset_kahan=not chained)
     pipe.join(cur)
     e1.record(cur)
     torch.cuda.synchronize()
@@ -331,10 +340,14 @@ def gpu_arm(args):
     # end to end through host buffers (FP32-bulk, double-word islands)
     st = res["fp32dw"]["state"]
     barrier()
-    e2e_ms, bi, bo = time_e2e(st, args.steps, args.warmup)
+    e2e_ms, bi, bo = time_e2e(st, args.steps, args.warmup, chained=True)
+    barrier()
+    ind_ms, _, _ = time_e2e(st, args.steps, args.warmup, chained=False)
     barrier()
     e2e_ms = max_over_ranks(e2e_ms, device)
+    ind_ms = max_over_ranks(ind_ms, device)
     e2e_value = whole_job_rate(world, cells, 4 * args.steps, e2e_ms)
+    ind_value = whole_job_rate(world, cells, 4 * args.steps, ind_ms)
     if world > 1:
         dist.destroy_process_group()
     if rank != 0:
@@ -407,8 +420,13 @@ def gpu_arm(args):
         "speedup_fp32_bulk_over_fp64": r32["value"] / r64["value"],
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo,
-                "path": "state.HostPipeline: pinned H2D of U^n, four stages, D2H of U^{n+1} "
-                        "every step; two device states alternate, copies on their own streams"},
+                "path": "C-ABI sf_step_host (state.HostPipeline): one evolution kept in pinned host "
+                        "memory, every step uploads U^n, runs the four stages and downloads U^{n+1} "
+                        "into the buffer the next step uploads (copies and stages serial)",
+                "independent_states": {
+                    "value": ind_value, "unit": UNIT,
+                    "path": "sf_step_host with two device slots: a new state every step (same input), "
+                            "the copies of neighbouring steps overlapping the stages on copy streams"}},
         "gpu_launches": int(r32["launches"]),
         "clocks": clocks,
     }

@@ -160,6 +160,66 @@ sf_status sf_substep(const sf_params* prm, const sf_patch* patches, int32_t npat
                      int32_t stage, void* stream);
 
 /*
+ * The device arrays of one patch state, in the buffer roles of sf_batch: u
+ * holds U^n and receives U^{n+1} from the last stage; s1 and s2 are stage
+ * scratch; acc is the RK4 accumulator (NULL under SSP-RK3); kahan the
+ * FP32-bulk compensation under RK4 (else NULL).  All share the layout
+ * (strides) of the patch they belong to.
+ */
+typedef struct {
+  void* u;
+  void* s1;
+  void* s2;
+  void* acc;
+  void* kahan;
+} sf_state;
+
+/* sf_step_host flag: zero the Kahan compensation of the slot at every upload. */
+#define SF_HOST_RESET_KAHAN 1u
+
+/*
+ * Elements of a state's host image: from ghosted point (0,0,0) of field 0 to
+ * the last ghosted point of field nf - 1 in the patch's strides,
+ * (nf - 1) sf + (n2 + 2g - 1) sz + (n1 + 2g - 1) sy + n0 + 2g (row padding
+ * in between included).  -1 for an unknown system.
+ */
+int64_t sf_state_span(const sf_patch* geom);
+
+/*
+ * RK steps of patch states held in host memory (Sec. II.C steps of the
+ * fused substep; the paper's patches live in host memory under SAMRAI).
+ * For k = 0 .. nsteps - 1: the host image host_in[k] (sf_state_span
+ * elements, the patch's layout and the storage convention of the stages:
+ * float CCZ4 fields chi, gt_ii, alpha minus 1) is copied to slot
+ * slots[k % nslots].u on h2d_stream, one full RK step of prm->rk runs on
+ * compute_stream (the stages of sf_substep, buffer roles u -> s1 -> s2 -> s1
+ * -> u for RK4, u -> s1 -> s2 -> u for SSP-RK3), and U^{n+1} is copied from
+ * slot.u to host_out[k] on d2h_stream.
+ *   geom: n, ghost, dx, strides, dt, system, precision of every step (its
+ *         pointer fields are ignored); nslots: 1 or 2 device states.
+ *   Ordering: with two slots the upload of step k + 1 and the download of
+ *   step k - 1 overlap the stages of step k.  An upload waits for the
+ *   download of the step that last used its slot and, when host_in[k]
+ *   overlaps host_out[k - 1], for that download, so an evolution kept in
+ *   host memory (host_in[k] = host_out[k - 1]) is correct with either slot
+ *   count.  The first upload of a call waits for the work already queued on
+ *   compute_stream and d2h_stream (earlier calls).
+ *   Kahan compensation: with SF_HOST_RESET_KAHAN it restarts from zero at
+ *   every upload (independent states); without it the slot's compensation
+ *   carries over, which continues an evolution exactly when each slot is
+ *   handed back the state it produced (one slot, chained buffers).
+ *   Host buffers should be pinned (page-locked) for the copies to overlap;
+ *   host_out[k] holds U^{n+1} once d2h_stream has passed the call's work.
+ *   NULL h2d_stream or d2h_stream means compute_stream.
+ * Asynchronous.  Errors (SF_EINVAL, nothing enqueued): NULL arguments,
+ * nslots not 1 or 2, unknown flags, a slot the stages would reject.
+ */
+sf_status sf_step_host(const sf_params* prm, const sf_patch* geom, const sf_state* slots,
+                       int32_t nslots, const void* const* host_in, void* const* host_out,
+                       int32_t nsteps, uint32_t flags, void* compute_stream, void* h2d_stream,
+                       void* d2h_stream);
+
+/*
  * Right-hand side only: rhs_out[f][k][j][i] = (L + Q_d)(u_stage) on the
  * interior, an unghosted contiguous array of nf * n[0]*n[1]*n[2] elements of
  * the patch's precision.  For tests and diagnostics.

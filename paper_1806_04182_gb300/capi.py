@@ -27,7 +27,9 @@ EXPORTS = ["sf_nfields", "sf_substep", "sf_rhs", "sf_fill_ghosts_periodic", "sf_
            "sf_batch_create", "sf_batch_substep", "sf_batch_tune", "sf_batch_capture",
            "sf_batch_launch", "sf_batch_launches_per_step", "sf_batch_destroy",
            "sf_batch_set_halo", "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong", "sf_bor_prolong", "sf_bor_prolong_boxes", "sf_radiative_substep",
-           "sf_selftest_wait_timeout", "sf_get_device_status", "sf_last_error", "sf_launch_count"]
+           "sf_selftest_wait_timeout", "sf_get_device_status", "sf_last_error", "sf_launch_count",
+           "sf_state_span", "sf_step_host"]
+SF_HOST_RESET_KAHAN = 1
 
 
 class SfError(RuntimeError):
@@ -85,6 +87,16 @@ class sf_patch(ctypes.Structure):
         ("u_next", ctypes.c_void_p),
         ("kahan", ctypes.c_void_p),
         ("cfl_rate", ctypes.c_void_p),
+    ]
+
+
+class sf_state(ctypes.Structure):
+    _fields_ = [
+        ("u", ctypes.c_void_p),
+        ("s1", ctypes.c_void_p),
+        ("s2", ctypes.c_void_p),
+        ("acc", ctypes.c_void_p),
+        ("kahan", ctypes.c_void_p),
     ]
 
 
@@ -156,6 +168,10 @@ def lib() -> ctypes.CDLL:
                                            P(ctypes.c_double), P(ctypes.c_double), i32, vp]
         L.sf_bor_prolong.argtypes = [P(sf_patch), i32, P(vp), i32, i32, i32, i32, P(i32), P(i32), vp,
                                      i64, i64, i64, vp]
+        L.sf_state_span.argtypes = [P(sf_patch)]
+        L.sf_state_span.restype = i64
+        L.sf_step_host.argtypes = [P(sf_params), P(sf_patch), P(sf_state), i32, P(vp), P(vp), i32,
+                                   ctypes.c_uint32, vp, vp, vp]
         L.sf_get_device_status.argtypes = [vp]
         L.sf_selftest_wait_timeout.argtypes = [i64, vp]
         L.sf_last_error.argtypes = []
@@ -167,7 +183,7 @@ def lib() -> ctypes.CDLL:
                      "sf_batch_create", "sf_batch_substep", "sf_batch_tune", "sf_batch_capture",
                      "sf_batch_launch", "sf_batch_destroy", "sf_get_device_status",
                      "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong",
-                     "sf_batch_set_halo", "sf_selftest_wait_timeout"):
+                     "sf_batch_set_halo", "sf_selftest_wait_timeout", "sf_step_host"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -183,6 +199,25 @@ def _patches(patches):
         patches = [patches]
     arr = (sf_patch * len(patches))(*patches)
     return arr, len(patches)
+
+
+def sf_state_span(geom: sf_patch) -> int:
+    return lib().sf_state_span(ctypes.byref(geom))
+
+
+def sf_step_host(prm: sf_params, geom: sf_patch, slots, host_in, host_out, flags: int = 0,
+                 compute_stream: int = 0, h2d_stream: int = 0, d2h_stream: int = 0) -> None:
+    """slots: one or two sf_state; host_in / host_out: host addresses, one per step."""
+    if isinstance(slots, sf_state):
+        slots = [slots]
+    sl = (sf_state * len(slots))(*slots)
+    n = len(host_in)
+    if len(host_out) != n:
+        raise ValueError("host_in and host_out need one buffer per step")
+    hin = (ctypes.c_void_p * max(n, 1))(*host_in)
+    hout = (ctypes.c_void_p * max(n, 1))(*host_out)
+    _check(lib().sf_step_host(ctypes.byref(prm), ctypes.byref(geom), sl, len(slots), hin, hout, n,
+                              flags, compute_stream, h2d_stream, d2h_stream), "sf_step_host")
 
 
 def sf_nfields(system: int) -> int:

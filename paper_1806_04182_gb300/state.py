@@ -272,24 +272,28 @@ class PatchState:
 
 
 class HostPipeline:
-    """RK steps of patch states that live in host memory.
+    """RK steps of patch states that live in host memory, through the C-ABI
+    call ``sf_step_host``.
 
-    Each ``step(host_in, host_out)`` copies a ghosted U^n (the layout and
-    storage convention of ``PatchState.A``, in pinned host memory) to the
-    device, runs one RK step there and copies U^{n+1} back into ``host_out``.
-    Two device ``PatchState``s alternate between steps, and the host-to-device
-    and device-to-host copies run on streams of their own, so the upload of
-    step k+1 and the download of step k-1 overlap the stages of step k; the
-    stages of successive steps stay in order on one compute stream.  A step's
-    host buffers must stay untouched until ``synchronize()`` (or a later
-    step's copies) has finished with them; ``host_out`` holds U^{n+1} after
-    ``synchronize()``.  The float Kahan compensation restarts from zero with
-    every uploaded state.
+    A state's host image is ``sf_state_span`` elements of the ghosted array
+    from ghosted point (0, 0, 0) (the layout and storage convention of
+    ``PatchState.A``; :meth:`image` gives that view of a device array, and
+    :meth:`host_buffer` a pinned buffer of that size).  ``run(host_in,
+    host_out)`` advances one RK step per entry: upload of ``host_in[k]``,
+    the stages, download into ``host_out[k]``, on three streams of the
+    pipeline.  With ``slots=2`` the copies of neighbouring steps overlap the
+    stages; a step whose input is an earlier step's output waits for that
+    download, so an evolution kept in host memory (``host_in[k] is
+    host_out[k - 1]``) is correct.  ``reset_kahan`` restarts the FP32-bulk
+    compensation from zero at every upload (independent states); without
+    it the device slot's compensation carries over (a continuing evolution,
+    one slot).  ``host_out`` holds the results after :meth:`synchronize` (or
+    once a stream waits on :meth:`join`).
     """
 
-    def __init__(self, *args, **kw):
+    def __init__(self, *args, slots: int = 2, **kw):
         """Arguments as for ``PatchState`` (one patch description)."""
-        self.states = (PatchState(*args, **kw), PatchState(*args, **kw))
+        self.states = tuple(PatchState(*args, **kw) for _ in range(slots))
         cur = torch.cuda.current_stream()
         self.compute = torch.cuda.Stream()
         self.up = torch.cuda.Stream()
@@ -302,41 +306,36 @@ class HostPipeline:
                 for t in (state.A, state.B, state.C, state.D, state.E):
                     if t is not None:
                         t.record_stream(st_)
-        self._uploaded = [torch.cuda.Event(), torch.cuda.Event()]
-        self._computed = [torch.cuda.Event(), torch.cuda.Event()]
-        self._downloaded = [torch.cuda.Event(), torch.cuda.Event()]
-        self._used = [False, False]
-        self._k = 0
-
-    @property
-    def shape(self):
-        return self.states[0].shape
+        st = self.states[0]
+        self.geom = st.patch(st.A, st.A, st.B)
+        self.span = capi.sf_state_span(self.geom)
+        self.slots = [capi.sf_state(u=s_.ptr(s_.A), s1=s_.ptr(s_.B), s2=s_.ptr(s_.C),
+                                    acc=s_.ptr(s_.D) if s_.D is not None else None,
+                                    kahan=s_.ptr(s_.E) if s_.E is not None else None)
+                      for s_ in self.states]
 
     @property
     def dtype(self):
         return self.states[0].dtype
 
-    def step(self, host_in: torch.Tensor, host_out: torch.Tensor) -> None:
-        q = self._k % 2
-        st = self.states[q]
-        if self._used[q]:
-            # buffer q was last read by the download of step k-2, which itself
-            # followed that step's stages
-            self.up.wait_event(self._downloaded[q])
-        with torch.cuda.stream(self.up):
-            st.A.copy_(host_in, non_blocking=True)
-            if st.E is not None:
-                st.E.zero_()
-        self._uploaded[q].record(self.up)
-        self.compute.wait_event(self._uploaded[q])
-        st.step(1, stream=self.compute)
-        self._computed[q].record(self.compute)
-        self.down.wait_event(self._computed[q])
-        with torch.cuda.stream(self.down):
-            host_out.copy_(st.A, non_blocking=True)
-        self._downloaded[q].record(self.down)
-        self._used[q] = True
-        self._k += 1
+    def image(self, array: torch.Tensor) -> torch.Tensor:
+        """The host-image view (span elements from ghosted (0,0,0)) of an array
+        laid out like the pipeline's states."""
+        xo = self.states[0].xo
+        return array.reshape(-1)[xo:xo + self.span]
+
+    def host_buffer(self) -> torch.Tensor:
+        return torch.empty(self.span, dtype=self.dtype, pin_memory=True)
+
+    def run(self, host_in, host_out, reset_kahan: bool = True) -> None:
+        st = self.states[0]
+        flags = capi.SF_HOST_RESET_KAHAN if (reset_kahan and st.E is not None) else 0
+        capi.sf_step_host(st.prm, self.geom, self.slots, [t.data_ptr() for t in host_in],
+                          [t.data_ptr() for t in host_out], flags, self.compute.cuda_stream,
+                          self.up.cuda_stream, self.down.cuda_stream)
+
+    def step(self, host_in: torch.Tensor, host_out: torch.Tensor, reset_kahan: bool = True) -> None:
+        self.run([host_in], [host_out], reset_kahan)
 
     def join(self, stream: torch.cuda.Stream | None = None) -> None:
         """Make `stream` (default: the current one) wait for all queued work."""

@@ -134,3 +134,33 @@ def test_batch_set_halo_rejects_null_batch(L):
         capi.sf_batch_set_halo(None, 0, [])
     assert e.value.status == capi.SF_EINVAL
     assert "batch is NULL" in str(e.value)
+
+
+def test_state_span_counts_the_ghosted_image(L):
+    p = fake_patch(n=(8, 8, 8), system=capi.SF_WAVE)
+    p.sy, p.sz, p.sf = 14, 14 * 14, 14 ** 3
+    assert capi.sf_state_span(p) == 5 * 14 ** 3  # dense layout: the whole array
+    p = fake_patch(n=(32, 96, 4), system=capi.SF_Z4, precision=capi.SF_FP32_BULK_DW)
+    p.sy, p.sz, p.sf = 104, 104 * 102, 104 * 102 * 10
+    assert capi.sf_state_span(p) == 24 * p.sf + 9 * p.sz + 101 * p.sy + 38
+    p.system = 9
+    assert capi.sf_state_span(p) == -1
+
+
+def test_step_host_rejects_bad_arguments(L):
+    p = fake_patch(n=(8, 8, 8), system=capi.SF_WAVE)
+    p.sy, p.sz, p.sf = 14, 14 * 14, 14 ** 3
+    base = 1 << 20
+    slot = capi.sf_state(u=base, s1=2 * base, s2=3 * base, acc=4 * base, kahan=None)
+    prm = capi.params()
+    with pytest.raises(capi.SfError, match="nslots"):
+        capi.sf_step_host(prm, p, [slot] * 3, [base], [base])
+    with pytest.raises(capi.SfError, match="flags"):
+        capi.sf_step_host(prm, p, [slot], [base], [base], flags=4)
+    with pytest.raises(capi.SfError, match="SF_HOST_RESET_KAHAN"):
+        capi.sf_step_host(prm, p, [slot], [base], [base], flags=capi.SF_HOST_RESET_KAHAN)
+    bad = capi.sf_state(u=base, s1=base, s2=3 * base, acc=4 * base, kahan=None)
+    with pytest.raises(capi.SfError, match="u_next"):
+        capi.sf_step_host(prm, p, [bad], [base], [base])
+    with pytest.raises(capi.SfError, match="NULL"):
+        capi.sf_step_host(prm, p, [slot], [0], [base])
