@@ -54,7 +54,11 @@ struct PCfg {
   static_assert(kSmemBytes <= 232448, "shared memory per CTA");
 };
 
-// The configuration in use: 8 warps (a 32 x 16 tile), 7 slots.
+// The configuration in use: 8 warps (a 32 x 16 tile), 7 slots.  Measured on
+// the 96^3 patch against 6 warps with 9 slots (32 x 12 tiles; 2.35e9 against
+// 2.81e9 cell-updates/s), 5 slots (2.75e9) and a persistent form in which
+// one CTA per SM walks the tiles with the ring running on from tile to tile
+// (1.84e9).
 constexpr int kW = 8, kKS = 7;
 
 // Order in which z4_rhs opens the fields' stencils.  Without the
