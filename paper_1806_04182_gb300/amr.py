@@ -68,8 +68,8 @@ def halo_boxes(grid: dict, which: str = "A") -> list:
                 else:
                     lo_src.append(0); lo_dst.append(0); ext.append(n[ax])
             bx = capi.sf_box_copy()
-            bx.src = src.data_ptr()
-            bx.dst = dst.data_ptr()
+            bx.src = nb.ptr(src)
+            bx.dst = st.ptr(dst)
             bx.src_off = _off(nb, *lo_src)
             bx.dst_off = _off(st, *lo_dst)
             bx.src_sy = bx.dst_sy = sy
@@ -113,8 +113,8 @@ def restrict_box(fine: PatchState, coarse: PatchState, ratio: int, coarse_origin
     fsy, fsz, fsf = _strides(fine)
     csy, csz, csf = _strides(coarse)
     bx = capi.sf_box_copy()
-    bx.src = fa.data_ptr()
-    bx.dst = ca.data_ptr()
+    bx.src = fine.ptr(fa)
+    bx.dst = coarse.ptr(ca)
     bx.src_off = _off(fine, *(ratio * (o - a) for o, a in zip(coarse_origin, fine_at)))
     bx.dst_off = _off(coarse, *coarse_origin)
     bx.src_sy, bx.src_sz, bx.src_sf = fsy, fsz, fsf
@@ -132,8 +132,8 @@ def whole_array_box(st: PatchState, src, dst) -> capi.sf_box_copy:
     nx, ny, nz = st.n
     g = st.g
     bx = capi.sf_box_copy()
-    bx.src = src.data_ptr()
-    bx.dst = dst.data_ptr()
+    bx.src = st.ptr(src)
+    bx.dst = st.ptr(dst)
     bx.src_off = bx.dst_off = 0
     bx.src_sy = bx.dst_sy = sy
     bx.src_sz = bx.dst_sz = sz
@@ -208,9 +208,8 @@ class SubcycledPair:
     def _states(self):
         c = self.coarse
         if self.rk == capi.SF_RK4:
-            return [self.S0.data_ptr(), c.B.data_ptr(), c.C.data_ptr(), self.S1.data_ptr(),
-                    c.A.data_ptr()]
-        return [self.S0.data_ptr(), c.B.data_ptr(), c.C.data_ptr(), c.A.data_ptr()]
+            return [c.ptr(self.S0), c.ptr(c.B), c.ptr(c.C), c.ptr(self.S1), c.ptr(c.A)]
+        return [c.ptr(self.S0), c.ptr(c.B), c.ptr(c.C), c.ptr(c.A)]
 
     def _coarse_stage_patch(self, s: int) -> capi.sf_patch:
         """The coarse patch's stage s; under RK4 U^(4) goes to S1."""
@@ -231,7 +230,7 @@ class SubcycledPair:
         boxes = []
         for lo, ext in self._shell:
             origin = tuple(R * a + l for a, l in zip(self.at, lo))
-            ptr = array.data_ptr() + _off(f, *lo) * es
+            ptr = f.ptr(array) + _off(f, *lo) * es
             boxes.append(capi.prolong_box(origin, ext, ptr, sy, sz, sf))
         # the six slabs of the shell in one launch
         capi.sf_bor_prolong_boxes(cpatch, self.rk, states, f.nf, R, r, stage, boxes, h)
