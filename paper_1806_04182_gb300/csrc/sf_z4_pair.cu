@@ -26,6 +26,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -334,14 +335,39 @@ __device__ __forceinline__ void write_fields_pair(const PatchArgs<float>& a, con
       r[(f0 + q) * stride] = out;
     }
   }
-  const Images im0 = ghost_images(a, s, i, j, k), im1 = ghost_images(a, s, i + 1, j, k);
-  if (im0.mask | im1.mask) {
+  // the y and z images of the pair (rows and planes next to a face): the x
+  // ghost columns of every row are filled afterwards by pair_xghost_kernel
+  // from the row's own interior, which by then includes these images
+  Images im = ghost_images(a, s, i, j, k);
+  im.mask &= ~3u;
+  if (im.mask) {
 #pragma unroll 1
     for (int f = 0; f < 25; ++f) {
       const F2 v = r[f * stride];
-      store_images(a, im0, f * a.sf + c, v.x);
-      store_images(a, im1, f * a.sf + c + 1, v.y);
+      store_images(a, im, f * a.sf + c, v.x);
+      store_images(a, im, f * a.sf + c + 1, v.y);
     }
+  }
+}
+
+// The x ghost columns of every ghosted row (y and z over the whole ghosted
+// range) of every field of u, from the same row's interior: ghost x = m
+// (m < 3) takes x = m + n0, ghost x = n0 + 3 + m takes x = 3 + m.  Run after
+// the stage kernel, whose fused y and z images have filled the interior part
+// of the ghost rows.  One thread per ghost value.
+__global__ void __launch_bounds__(256) pair_xghost_kernel(float* __restrict__ u, int nx, int ny,
+                                                          int nz, long long sf) {
+  const int Y = ny + 6, rows = Y * (nz + 6);
+  const long long total = 25LL * rows * 6;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(t % 6);
+    const long long row = t / 6;
+    const int f = (int)(row / rows), r = (int)(row - (long long)f * rows);
+    const int z = r / Y, y = r - z * Y;
+    float* b = u + f * sf + (long long)z * kSZ + (long long)y * kSY;
+    if (q < 3) b[q] = b[q + nx];
+    else b[nx + q] = b[q];
   }
 }
 
@@ -456,7 +482,12 @@ sf_status launch_pair(const sf_params& prm, const sf_patch& p, const StageArgs& 
   const PairCoef pc = pair_coef(prm, p);
   dim3 grid(p.n[0] / 32, p.n[1] / C::BY, p.n[2]);
   z4_pair_kernel<H2, kW, kKS><<<grid, dim3(32, kW, 1), C::kSmemBytes, st>>>(map, a, s, zc, pc);
-  return after_launch("z4_pair_kernel");
+  sf_status e = after_launch("z4_pair_kernel");
+  if (e || !s.ghosts || s.mode == 1) return e;
+  const long long total = 25LL * (p.n[1] + 6) * (p.n[2] + 6) * 6;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 8);
+  pair_xghost_kernel<<<blocks, 256, 0, st>>>(a.nx, p.n[0], p.n[1], p.n[2], p.sf);
+  return after_launch("pair_xghost_kernel");
 }
 
 }  // namespace
