@@ -259,13 +259,41 @@ struct PairSrc {
   }
 };
 
+// Forms of the RK combination fixed at compile time: the kernel is
+// instantiated per form, so that its write phase carries one form's code and
+// no branches on the stage (the generic form decides at run time).
+//   kRk4First: RK4 stage 0 with the Kahan accumulator (U^n = the stage input)
+//   kRk4Mid:   RK4 stages 1 and 2
+//   kRk4Last:  RK4 stage 3 with the Kahan compensation
+enum : int { kRkGeneric = 0, kRk4First = 1, kRk4Mid = 2, kRk4Last = 3 };
+
+int rk_form(const StageArgs& s) {
+  if (s.mode != 0 || s.rk != SF_RK4 || !s.kahan) return kRkGeneric;
+  if (s.stage == 0) return s.un_alias ? kRk4First : kRkGeneric;
+  return s.stage < 3 ? kRk4Mid : kRk4Last;
+}
+
 // RK stage combination of one field value pair (sf_common.cuh's
 // stage_combine on pairs): writes the accumulator / Kahan term and returns
 // the next stage input.
+template <int FORM>
 __device__ __forceinline__ F2 stage_combine2(const PatchArgs<float>& a, const StageArgs& s,
                                              long long o, F2 centre, F2 un_m, F2 acc, F2 kh, F2 r) {
-  const F2 un = s.un_alias ? centre : un_m;
   const F2 cn(a.c_next), ca(a.c_acc);
+  if constexpr (FORM == kRk4First) {
+    *reinterpret_cast<F2*>(a.acc + o) = mul2(ca, r);
+    return fma2(cn, r, centre);
+  } else if constexpr (FORM == kRk4Mid) {
+    *reinterpret_cast<F2*>(a.acc + o) = fma2(ca, r, acc);
+    return fma2(cn, r, un_m);
+  } else if constexpr (FORM == kRk4Last) {
+    const F2 inc = fma2(cn, r, acc);
+    const F2 y = sub2(inc, kh);
+    const F2 t = add2(un_m, y);
+    *reinterpret_cast<F2*>(a.kh + o) = sub2(sub2(t, un_m), y);
+    return t;
+  }
+  const F2 un = s.un_alias ? centre : un_m;
   F2 out;
   if (s.rk == SF_RK4) {
     if (s.stage == 0) {
@@ -296,10 +324,11 @@ __device__ __forceinline__ F2 stage_combine2(const PatchArgs<float>& a, const St
 // in shared memory (r[f * stride]); the scheme of write_fields (batches of
 // five fields with every read issued before the writes, periodic images of
 // boundary points in one rolled pass at the end) on 64-bit accesses.
+template <int FORM>
 __device__ __forceinline__ void write_fields_pair(const PatchArgs<float>& a, const StageArgs& s,
                                                   long long c, int i, int j, int k, F2* r,
                                                   int stride) {
-  if (s.mode == 1) {
+  if (FORM == kRkGeneric && s.mode == 1) {
     const long long oi = ((long long)k * a.n[1] + j) * a.n[0] + i;
 #pragma unroll 1
     for (int f = 0; f < 25; ++f) {
@@ -310,9 +339,10 @@ __device__ __forceinline__ void write_fields_pair(const PatchArgs<float>& a, con
     return;
   }
   const bool rk4 = s.rk == SF_RK4;
-  const bool need_centre = s.un_alias || !rk4;
-  const bool need_acc = rk4 && s.stage > 0;
-  const bool need_kh = rk4 && s.stage == 3 && s.kahan;
+  const bool need_centre = FORM == kRk4First || (FORM == kRkGeneric && (s.un_alias || !rk4));
+  const bool need_un = FORM == kRk4Mid || FORM == kRk4Last || (FORM == kRkGeneric && !s.un_alias);
+  const bool need_acc = FORM == kRk4Mid || FORM == kRk4Last || (FORM == kRkGeneric && rk4 && s.stage > 0);
+  const bool need_kh = FORM == kRk4Last || (FORM == kRkGeneric && rk4 && s.stage == 3 && s.kahan);
   auto ld = [](const float* q) { return *reinterpret_cast<const F2*>(q); };
 #pragma unroll 1
   for (int f0 = 0; f0 < 25; f0 += 5) {
@@ -322,14 +352,14 @@ __device__ __forceinline__ void write_fields_pair(const PatchArgs<float>& a, con
       const long long o = (f0 + q) * a.sf + c;
       rr[q] = r[(f0 + q) * stride];
       cen[q] = need_centre ? ld(a.us + o) : F2(0.0f);
-      un[q] = s.un_alias ? F2(0.0f) : ld(a.un + o);
+      un[q] = need_un ? ld(a.un + o) : F2(0.0f);
       acc[q] = need_acc ? ld(a.acc + o) : F2(0.0f);
       kh[q] = need_kh ? ld(a.kh + o) : F2(0.0f);
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
       const long long o = (f0 + q) * a.sf + c;
-      const F2 out = stage_combine2(a, s, o, cen[q], un[q], acc[q], kh[q], rr[q]);
+      const F2 out = stage_combine2<FORM>(a, s, o, cen[q], un[q], acc[q], kh[q], rr[q]);
       *reinterpret_cast<F2*>(a.nx + o) = out;
       if (s.check_finite && !(finite_(out.x) && finite_(out.y))) atomicOr(s.status, ST_NONFINITE);
       r[(f0 + q) * stride] = out;
@@ -373,7 +403,7 @@ __global__ void __launch_bounds__(256) pair_xghost_kernel(float* __restrict__ u,
 
 }  // namespace
 
-template <typename H2, int W, int KS>
+template <typename H2, int W, int KS, int FORM>
 __global__ void __launch_bounds__(32 * W, 1)
     z4_pair_kernel(const __grid_constant__ CUtensorMap map, PatchArgs<float> a, StageArgs s,
                    Z4Coef<float> zc, const __grid_constant__ PairCoef pc) {
@@ -430,7 +460,7 @@ __global__ void __launch_bounds__(32 * W, 1)
   F2* rbuf = reinterpret_cast<F2*>(smem + C::kRbufOffset);
   F2 be[3];
   z4_rhs<F2, H2, false>(zc, src, be, [&](int f, F2 r, F2) { rbuf[f * C::kThreads + tid] = r; });
-  write_fields_pair(a, s, c, i, j, k, rbuf + tid, C::kThreads);
+  write_fields_pair<FORM>(a, s, c, i, j, k, rbuf + tid, C::kThreads);
 }
 
 namespace {
@@ -474,14 +504,33 @@ sf_status launch_pair(const sf_params& prm, const sf_patch& p, const StageArgs& 
   if (r != CUDA_SUCCESS) return set_error(SF_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
-    cudaFuncSetAttribute(z4_pair_kernel<H2, kW, kKS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         C::kSmemBytes);
+    cudaFuncSetAttribute(z4_pair_kernel<H2, kW, kKS, kRkGeneric>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    cudaFuncSetAttribute(z4_pair_kernel<H2, kW, kKS, kRk4First>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    cudaFuncSetAttribute(z4_pair_kernel<H2, kW, kKS, kRk4Mid>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    cudaFuncSetAttribute(z4_pair_kernel<H2, kW, kKS, kRk4Last>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
   });
   PatchArgs<float> a = make_args<float>(prm, p, stage, 25, rhs_out);
   const Z4Coef<float> zc = z4_coef<float>(prm);
   const PairCoef pc = pair_coef(prm, p);
   dim3 grid(p.n[0] / 32, p.n[1] / C::BY, p.n[2]);
-  z4_pair_kernel<H2, kW, kKS><<<grid, dim3(32, kW, 1), C::kSmemBytes, st>>>(map, a, s, zc, pc);
+  const dim3 block(32, kW, 1);
+  switch (rk_form(s)) {
+    case kRk4First:
+      z4_pair_kernel<H2, kW, kKS, kRk4First><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc, pc);
+      break;
+    case kRk4Mid:
+      z4_pair_kernel<H2, kW, kKS, kRk4Mid><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc, pc);
+      break;
+    case kRk4Last:
+      z4_pair_kernel<H2, kW, kKS, kRk4Last><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc, pc);
+      break;
+    default:
+      z4_pair_kernel<H2, kW, kKS, kRkGeneric><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc, pc);
+  }
   sf_status e = after_launch("z4_pair_kernel");
   if (e || !s.ghosts || s.mode == 1) return e;
   const long long total = 25LL * (p.n[1] + 6) * (p.n[2] + 6) * 6;
