@@ -55,12 +55,19 @@ struct PCfg {
   static_assert(kSmemBytes <= 232448, "shared memory per CTA");
 };
 
+// RK inputs staged through the ring: boxes of 32 x 16 points x kRkChunk
+// fields of one array (a tile's rows), three chunks per array.
+constexpr int kRkChunk = 12;
+constexpr int kRkBoxBytes = 32 * 16 * kRkChunk * 4;
+
 // The configuration in use: 8 warps (a 32 x 16 tile), 7 slots.  Measured on
 // the 96^3 patch against 6 warps with 9 slots (32 x 12 tiles; 2.35e9 against
 // 2.81e9 cell-updates/s), 5 slots (2.75e9) and a persistent form in which
 // one CTA per SM walks the tiles with the ring running on from tile to tile
 // (1.84e9).
 constexpr int kW = 8, kKS = 7;
+static_assert(kRkBoxBytes <= PCfg<kW, kKS>::kSlotBytes && PCfg<kW, kKS>::BY == 16, "RK chunk fits a slot");
+static_assert(3 * kRkChunk >= 25, "three chunks cover the fields");
 
 // Order in which z4_rhs opens the fields' stencils.  Without the
 // Gamma-driver (shift frozen) the last three are not used.
@@ -112,7 +119,7 @@ __device__ __forceinline__ void tma_load_4d(float* dst, const CUtensorMap* map, 
 // Stencil source of z4_rhs for the pair of points (i, i + 1): the staged
 // boxes in shared memory, the centre values (all fields, at the start) from
 // global memory.
-template <int W, int KS>
+template <int W, int KS, int NARR = 0>
 struct PairSrc {
   using C = PCfg<W, KS>;
   static constexpr int kY = kXB;            // box row, floats
@@ -129,20 +136,47 @@ struct PairSrc {
   int use, cur, nuses, issued;
   int gx, gy, gz;  // tensor coordinates of the box origin
   bool leader, lane0, dead;
+  // NARR > 0: after the nfu field uses, the RK inputs of the tile (NARR
+  // arrays) follow as uses of the ring, 3 chunks of 12 fields per array,
+  // chunk-major, from the maps rkmap[0 .. NARR - 1] at tensor coordinates
+  // (rx, ry, rz); consumed by the write phase (acquire / release)
+  int nfu, done;
+  const CUtensorMap* rkmap;
+  int rx, ry, rz;
 
   __device__ __forceinline__ void fail() {
     if (!dead) atomicOr(status, ST_TIMEOUT);
     dead = true;
   }
-  // leader: load field use j into its slot once the previous occupant
-  // (use j - KS) has been released by every warp
+  // leader: load use j into its slot once the previous occupant (use j - KS)
+  // has been released by every warp
   __device__ __forceinline__ void issue(int j) {
     const int sl = j % KS;
     if (j >= KS && !dead && !mbar_wait(&empty[sl], ((j / KS) - 1) & 1, kWaitCycles)) fail();
     if (dead) return;
-    mbar_expect(&full[sl], C::kBoxBytes);
-    tma_load_4d(tiles + sl * C::kSlotFloats, map, gx, gy, gz, kPairFieldSeq[j], &full[sl]);
+    if (NARR == 0 || j < nfu) {
+      mbar_expect(&full[sl], C::kBoxBytes);
+      tma_load_4d(tiles + sl * C::kSlotFloats, map, gx, gy, gz, kPairFieldSeq[j], &full[sl]);
+    } else {
+      const int r = j - nfu;
+      mbar_expect(&full[sl], kRkBoxBytes);
+      tma_load_4d(tiles + sl * C::kSlotFloats, rkmap + r % NARR, rx, ry, rz, kRkChunk * (r / NARR),
+                  &full[sl]);
+    }
     issued = j + 1;
+  }
+  // write phase: wait for RK use i (kept until release(i)), after issuing
+  // the uses up to i + KS - NARR (their slots' previous uses are released)
+  __device__ __forceinline__ const float* acquire(int i) {
+    if (leader)
+      for (int q = issued; q <= i + KS - NARR && q < nuses && !dead; ++q) issue(q);
+    if (!dead && !mbar_wait(&full[i % KS], (i / KS) & 1, kWaitCycles)) fail();
+    done = i + 1;
+    return tiles + (i % KS) * C::kSlotFloats;
+  }
+  __device__ __forceinline__ void release(int i) {
+    __syncwarp();
+    if (lane0) mbar_arrive(&empty[i % KS]);
   }
   __device__ __forceinline__ void prologue() {
     if (leader)
@@ -158,9 +192,21 @@ struct PairSrc {
     cur = i % KS;
     if (!dead && !mbar_wait(&full[cur], (i / KS) & 1, kWaitCycles)) fail();
   }
+  // end of the field uses (z4_rhs's last call): with staged RK inputs the
+  // last field's slot is released for them; without, a leader whose wait
+  // gave up waits (bounded) for its loads still in flight
   __device__ __forceinline__ void finish() {
+    if constexpr (NARR > 0) {
+      release(use - 1);
+      done = use;
+    } else {
+      final_finish();
+    }
+  }
+  __device__ __forceinline__ void final_finish() {
+    const int from = NARR > 0 ? done : use;
     if (leader && dead)
-      for (int j = use; j < issued; ++j) mbar_wait(&full[j % KS], (j / KS) & 1, kWaitCycles);
+      for (int j = from; j < issued; ++j) mbar_wait(&full[j % KS], (j / KS) & 1, kWaitCycles);
   }
 
   __device__ __forceinline__ const float* box() const { return tiles + cur * C::kSlotFloats + local; }
@@ -365,9 +411,15 @@ __device__ __forceinline__ void write_fields_pair(const PatchArgs<float>& a, con
       r[(f0 + q) * stride] = out;
     }
   }
-  // the y and z images of the pair (rows and planes next to a face): the x
-  // ghost columns of every row are filled afterwards by pair_xghost_kernel
-  // from the row's own interior, which by then includes these images
+}
+
+// The y and z periodic images of the pair's new values (rows and planes next
+// to a face; r holds the values written): the x ghost columns of every row
+// are filled afterwards by pair_xghost_kernel from the row's own interior,
+// which by then includes these images.
+__device__ __forceinline__ void write_yz_images(const PatchArgs<float>& a, const StageArgs& s,
+                                                long long c, int i, int j, int k, const F2* r,
+                                                int stride) {
   Images im = ghost_images(a, s, i, j, k);
   im.mask &= ~3u;
   if (im.mask) {
@@ -403,10 +455,55 @@ __global__ void __launch_bounds__(256) pair_xghost_kernel(float* __restrict__ u,
 
 }  // namespace
 
+// The stage write with the RK inputs staged in the ring (the specialised
+// forms): per block of up to 12 fields, the chunks of the NARR input arrays
+// are acquired, every field of the block combined and stored, and the
+// chunks released.  Array order: kRk4First: u_stage (= U^n); kRk4Mid: U^n,
+// accumulator; kRk4Last: U^n, accumulator, Kahan term.
+template <int FORM, int NARR, typename Src>
+__device__ __forceinline__ void write_fields_staged(const PatchArgs<float>& a, const StageArgs& s,
+                                                    long long c, F2* r, int stride, Src& src,
+                                                    int lpos) {
+  static_assert(NARR >= 1 && NARR <= 3, "staged arrays");
+  auto ld = [](const float* q) { return *reinterpret_cast<const F2*>(q); };
+  bool bad = false;  // a non-finite value written (reported once, at the end)
+#pragma unroll 1
+  for (int blk = 0; blk < 3; ++blk) {
+    const float* in[NARR];
+#pragma unroll
+    for (int t = 0; t < NARR; ++t) in[t] = src.acquire(src.nfu + blk * NARR + t) + lpos;
+    const int nf = min(kRkChunk, 25 - kRkChunk * blk);
+#pragma unroll 1
+    for (int q = 0; q < nf; ++q) {
+      const int f = kRkChunk * blk + q;
+      const long long o = f * a.sf + c;
+      const F2 v0 = ld(in[0] + q * 512);
+      const F2 v1 = NARR > 1 ? ld(in[NARR > 1 ? 1 : 0] + q * 512) : F2(0.0f);
+      const F2 v2 = NARR > 2 ? ld(in[NARR > 2 ? 2 : 0] + q * 512) : F2(0.0f);
+      const F2 rr = r[f * stride];
+      // the first array is U^n (kRk4First: the stage input, which is U^n)
+      const F2 out = stage_combine2<FORM>(a, s, o, v0, v0, v1, v2, rr);
+      *reinterpret_cast<F2*>(a.nx + o) = out;
+      bad |= !(finite_(out.x) && finite_(out.y));
+      r[f * stride] = out;
+    }
+#pragma unroll
+    for (int t = 0; t < NARR; ++t) src.release(src.nfu + blk * NARR + t);
+  }
+  if (s.check_finite && bad) atomicOr(s.status, ST_NONFINITE);
+}
+
+// Tensor maps of the RK input arrays of a stage form (unused ones zero).
+struct RkMaps {
+  CUtensorMap m[3];
+};
+
 template <typename H2, int W, int KS, int FORM>
 __global__ void __launch_bounds__(32 * W, 1)
     z4_pair_kernel(const __grid_constant__ CUtensorMap map, PatchArgs<float> a, StageArgs s,
-                   Z4Coef<float> zc, const __grid_constant__ PairCoef pc) {
+                   Z4Coef<float> zc, const __grid_constant__ PairCoef pc,
+                   const __grid_constant__ RkMaps rk) {
+  constexpr int NARR = FORM == kRk4First ? 1 : (FORM == kRk4Mid ? 2 : (FORM == kRk4Last ? 3 : 0));
   using C = PCfg<W, KS>;
   extern __shared__ __align__(128) unsigned char smem[];
   float* tiles = reinterpret_cast<float*>(smem);
@@ -436,7 +533,7 @@ __global__ void __launch_bounds__(32 * W, 1)
     if (s.rk == SF_RK4 && s.stage > 0) prefetch_rows<128>(a.acc + c, a.sf);
     if (s.kahan && s.stage == 3) prefetch_rows<128>(a.kh + c, a.sf);
   }
-  PairSrc<W, KS> src;
+  PairSrc<W, KS, NARR> src;
   src.u = a.us + c;
   src.F = a.sf;
   src.pc = &pc;
@@ -448,7 +545,13 @@ __global__ void __launch_bounds__(32 * W, 1)
   src.local = (3 * C::TY + ly + 3) * kXB + px + 4;
   src.use = 0;
   src.cur = 0;
-  src.nuses = zc.shift_frozen ? 22 : 25;
+  src.nfu = zc.shift_frozen ? 22 : 25;
+  src.nuses = src.nfu + 3 * NARR;
+  src.done = 0;
+  src.rkmap = rk.m;
+  src.rx = blockIdx.x * 32 + 4;  // tensor x = ghosted x + 1 of point x0
+  src.ry = blockIdx.y * C::BY + 3;
+  src.rz = k + 3;
   src.issued = 0;
   src.gx = blockIdx.x * 32;  // tensor x = ghosted x + 1; the box starts 4 before point x0
   src.gy = blockIdx.y * C::BY;
@@ -460,7 +563,12 @@ __global__ void __launch_bounds__(32 * W, 1)
   F2* rbuf = reinterpret_cast<F2*>(smem + C::kRbufOffset);
   F2 be[3];
   z4_rhs<F2, H2, false>(zc, src, be, [&](int f, F2 r, F2) { rbuf[f * C::kThreads + tid] = r; });
-  write_fields_pair<FORM>(a, s, c, i, j, k, rbuf + tid, C::kThreads);
+  if constexpr (NARR > 0)
+    write_fields_staged<FORM, NARR>(a, s, c, rbuf + tid, C::kThreads, src, ly * 32 + px);
+  else
+    write_fields_pair<FORM>(a, s, c, i, j, k, rbuf + tid, C::kThreads);
+  write_yz_images(a, s, c, i, j, k, rbuf + tid, C::kThreads);
+  if constexpr (NARR > 0) src.final_finish();
 }
 
 namespace {
@@ -516,20 +624,43 @@ sf_status launch_pair(const sf_params& prm, const sf_patch& p, const StageArgs& 
   PatchArgs<float> a = make_args<float>(prm, p, stage, 25, rhs_out);
   const Z4Coef<float> zc = z4_coef<float>(prm);
   const PairCoef pc = pair_coef(prm, p);
+  const int form = rk_form(s);
+  // the RK inputs of the form, staged through the ring: boxes of the tile's
+  // 32 x 16 points x 12 fields
+  RkMaps rk;
+  memset(&rk, 0, sizeof(rk));
+  {
+    const void* arrs[3] = {nullptr, nullptr, nullptr};
+    if (form == kRk4First) arrs[0] = p.u_stage;
+    if (form == kRk4Mid || form == kRk4Last) {
+      arrs[0] = p.u_n;
+      arrs[1] = p.acc;
+    }
+    if (form == kRk4Last) arrs[2] = p.kahan;
+    const cuuint32_t rbox[4] = {32, (cuuint32_t)C::BY, 1, kRkChunk};
+    for (int q = 0; q < 3; ++q) {
+      if (!arrs[q]) continue;
+      CUresult rr = enc(&rk.m[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                        static_cast<char*>(const_cast<void*>(arrs[q])) - 4, dims, strides, rbox,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (rr != CUDA_SUCCESS) return set_error(SF_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)rr);
+    }
+  }
   dim3 grid(p.n[0] / 32, p.n[1] / C::BY, p.n[2]);
   const dim3 block(32, kW, 1);
-  switch (rk_form(s)) {
+  switch (form) {
     case kRk4First:
-      z4_pair_kernel<H2, kW, kKS, kRk4First><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc, pc);
+      z4_pair_kernel<H2, kW, kKS, kRk4First><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc, pc, rk);
       break;
     case kRk4Mid:
-      z4_pair_kernel<H2, kW, kKS, kRk4Mid><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc, pc);
+      z4_pair_kernel<H2, kW, kKS, kRk4Mid><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc, pc, rk);
       break;
     case kRk4Last:
-      z4_pair_kernel<H2, kW, kKS, kRk4Last><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc, pc);
+      z4_pair_kernel<H2, kW, kKS, kRk4Last><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc, pc, rk);
       break;
     default:
-      z4_pair_kernel<H2, kW, kKS, kRkGeneric><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc, pc);
+      z4_pair_kernel<H2, kW, kKS, kRkGeneric><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc, pc, rk);
   }
   sf_status e = after_launch("z4_pair_kernel");
   if (e || !s.ghosts || s.mode == 1) return e;
