@@ -157,7 +157,7 @@ struct PairSrc {
     if (NARR == 0 || j < nfu) {
       mbar_expect(&full[sl], C::kBoxBytes);
       tma_load_4d(tiles + sl * C::kSlotFloats, map, gx, gy, gz, kPairFieldSeq[j], &full[sl]);
-    } else {
+    } else if constexpr (NARR > 0) {
       const int r = j - nfu;
       mbar_expect(&full[sl], kRkBoxBytes);
       tma_load_4d(tiles + sl * C::kSlotFloats, rkmap + r % NARR, rx, ry, rz, kRkChunk * (r / NARR),
@@ -526,9 +526,12 @@ __global__ void __launch_bounds__(32 * W, 1)
   const int j = blockIdx.y * C::BY + ly;
   const int k = blockIdx.z;
   const long long c = (long long)(k + 3) * kSZ + (long long)(j + 3) * kSY + (i + 3);
-  if ((threadIdx.x & 15) == 0 && s.mode == 0) {
-    // the row's 32 points start on a 16-byte boundary: prefetch their 128 B
-    // of every field the RK combination of this stage reads
+  if (NARR == 0 && (threadIdx.x & 15) == 0 && s.mode == 0) {
+    // generic form (RK inputs read from global memory in the write phase):
+    // the row's 32 points start on a 16-byte boundary, prefetch their 128 B
+    // of every field the RK combination reads.  The RK4 forms stage those
+    // inputs through the TMA ring, where a prefetch only competes with the
+    // stencil boxes.
     if (!s.un_alias) prefetch_rows<128>(a.un + c, a.sf);
     if (s.rk == SF_RK4 && s.stage > 0) prefetch_rows<128>(a.acc + c, a.sf);
     if (s.kahan && s.stage == 3) prefetch_rows<128>(a.kh + c, a.sf);
