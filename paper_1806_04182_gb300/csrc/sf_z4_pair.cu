@@ -414,20 +414,68 @@ __device__ __forceinline__ void write_fields_pair(const PatchArgs<float>& a, con
 }
 
 // The y and z periodic images of the pair's new values (rows and planes next
-// to a face; r holds the values written): the x ghost columns of every row
-// are filled afterwards by pair_xghost_kernel from the row's own interior,
-// which by then includes these images.
+// to a face; r holds the values written), as aligned pairs: a shift in y or z
+// keeps the pair on its 8-byte boundary.  The x ghost columns are written by
+// write_x_images (RK4 forms) or by pair_xghost_kernel after the stage.
 __device__ __forceinline__ void write_yz_images(const PatchArgs<float>& a, const StageArgs& s,
                                                 long long c, int i, int j, int k, const F2* r,
                                                 int stride) {
-  Images im = ghost_images(a, s, i, j, k);
-  im.mask &= ~3u;
-  if (im.mask) {
+  const unsigned m = ghost_images(a, s, i, j, k).mask & ~3u;
+  if (!m) return;
 #pragma unroll 1
-    for (int f = 0; f < 25; ++f) {
-      const F2 v = r[f * stride];
-      store_images(a, im, f * a.sf + c, v.x);
-      store_images(a, im, f * a.sf + c + 1, v.y);
+  for (int f = 0; f < 25; ++f) {
+    const F2 v = r[f * stride];
+    float* q = a.nx + f * a.sf + c;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      if (p && !(m & (p == 1 ? 16u : 32u))) continue;
+      const long long oz = p == 0 ? 0 : (p == 1 ? 1 : -1) * (long long)a.n[2] * a.sz;
+#pragma unroll
+      for (int w = 0; w < 3; ++w) {
+        if (w && !(m & (w == 1 ? 4u : 8u))) continue;
+        const long long oy = w == 0 ? 0 : (w == 1 ? 1 : -1) * (long long)a.n[1] * a.sy;
+        if (p | w) *reinterpret_cast<F2*>(q + oz + oy) = v;
+      }
+    }
+  }
+}
+
+// The x periodic images of a tile's boundary columns, written by the CTA
+// from the tile's new values in shared memory (r: the pair of thread t for
+// field f at r[f * stride + t]).  First tile of a row: interior x = 0..2 go to
+// ghost x = n0 .. n0 + 2 (past the interior); last tile: x = n0 - 3 .. n0 - 1
+// go to x = -3 .. -1; each also at the y and z image rows of its point, so
+// that with write_yz_images every ghost value of the tile's points is written.
+// 16 rows x 25 fields x 3 columns per side, spread over the CTA's threads.
+__device__ __forceinline__ void write_x_images(const PatchArgs<float>& a, const StageArgs& s,
+                                               int bx, int tx, int y0, int k, const F2* r,
+                                               int stride, int tid) {
+  const bool lo = bx == 0, hi = bx == tx - 1;
+  if (!(lo || hi)) return;
+  const int nside = lo && hi ? 2 : 1;
+#pragma unroll 1
+  for (int v = tid; v < nside * 1200; v += stride) {
+    const int side = nside == 2 ? v / 1200 : (lo ? 0 : 1);
+    const int w = nside == 2 ? v - (v / 1200) * 1200 : v;
+    const int f = w / 48, rem = w - f * 48, row = rem / 3, mc = rem - row * 3;
+    const int xl = side == 0 ? mc : 29 + mc;  // tile-local x of the source point
+    // owner of (row, xl): warp row / 2, half-warp row % 2, lane xl / 2
+    const F2 pr = r[f * stride + (row >> 1) * 32 + (row & 1) * 16 + (xl >> 1)];
+    const float val = (xl & 1) ? pr.y : pr.x;
+    const int i = bx * 32 + xl, j = y0 + row;
+    const unsigned m = ghost_images(a, s, i, j, k).mask;
+    const long long o = f * a.sf + (long long)(k + 3) * a.sz + (long long)(j + 3) * a.sy + (i + 3) +
+                        (side == 0 ? a.n[0] : -a.n[0]);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      if (p && !(m & (p == 1 ? 16u : 32u))) continue;
+      const long long oz = p == 0 ? 0 : (p == 1 ? 1 : -1) * (long long)a.n[2] * a.sz;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (q && !(m & (q == 1 ? 4u : 8u))) continue;
+        const long long oy = q == 0 ? 0 : (q == 1 ? 1 : -1) * (long long)a.n[1] * a.sy;
+        a.nx[o + oz + oy] = val;
+      }
     }
   }
 }
@@ -524,7 +572,9 @@ __global__ void __launch_bounds__(32 * W, 1)
   const int ly = 2 * threadIdx.y + (threadIdx.x >> 4);
   const int i = blockIdx.x * 32 + px;
   const int j = blockIdx.y * C::BY + ly;
-  const int k = blockIdx.z;
+  // planes next to the z faces first (their tiles also write the z images, the
+  // slowest tiles), so that the partial last wave holds plain tiles
+  const int k = (int)((blockIdx.z + 3 * gridDim.z - 3) % gridDim.z);
   const long long c = (long long)(k + 3) * kSZ + (long long)(j + 3) * kSY + (i + 3);
   if (NARR == 0 && (threadIdx.x & 15) == 0 && s.mode == 0) {
     // generic form (RK inputs read from global memory in the write phase):
@@ -571,7 +621,13 @@ __global__ void __launch_bounds__(32 * W, 1)
   else
     write_fields_pair<FORM>(a, s, c, i, j, k, rbuf + tid, C::kThreads);
   write_yz_images(a, s, c, i, j, k, rbuf + tid, C::kThreads);
-  if constexpr (NARR > 0) src.final_finish();
+  if constexpr (NARR > 0) {
+    if (s.ghosts && s.mode == 0) {
+      __syncthreads();  // every new value of the tile is in rbuf
+      write_x_images(a, s, blockIdx.x, gridDim.x, blockIdx.y * C::BY, k, rbuf, C::kThreads, tid);
+    }
+    src.final_finish();
+  }
 }
 
 namespace {
@@ -666,7 +722,8 @@ sf_status launch_pair(const sf_params& prm, const sf_patch& p, const StageArgs& 
       z4_pair_kernel<H2, kW, kKS, kRkGeneric><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc, pc, rk);
   }
   sf_status e = after_launch("z4_pair_kernel");
-  if (e || !s.ghosts || s.mode == 1) return e;
+  // the RK4 forms write the x images themselves
+  if (e || !s.ghosts || s.mode == 1 || form != kRkGeneric) return e;
   const long long total = 25LL * (p.n[1] + 6) * (p.n[2] + 6) * 6;
   const int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 8);
   pair_xghost_kernel<<<blocks, 256, 0, st>>>(a.nx, p.n[0], p.n[1], p.n[2], p.sf);
