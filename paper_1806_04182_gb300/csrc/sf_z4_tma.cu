@@ -189,14 +189,6 @@ __global__ void __launch_bounds__(Cfg<BY, KS>::kThreads, Cfg<BY, KS>::kMinBlocks
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;
   const long long c = (long long)(k + 3) * kSZ + (long long)(j + 3) * kSY + (i + 3);
-  if (threadIdx.x == 0 && s.mode == 0) {
-    // the warp's 32 points sit at byte offsets 12 .. 139 from the 16-byte
-    // aligned address of ghosted x = 32 m (row pitch 416 B): prefetch 144 B
-    const long long c0 = c - 3;
-    if (!s.un_alias) prefetch_rows(a.un + c0, a.sf);
-    if (s.rk == SF_RK4 && s.stage > 0) prefetch_rows(a.acc + c0, a.sf);
-    if (s.kahan && s.stage == 3) prefetch_rows(a.kh + c0, a.sf);
-  }
   TmaSrc<BY, KS> src;
   src.u = a.us + c;
   src.F = a.sf;
@@ -252,14 +244,6 @@ __device__ __forceinline__ void tma_tile_runtime(const CUtensorMap* map, const P
   const bool valid = i < a.n[0] && j < a.n[1];
   const int ic = min(i, a.n[0] - 1), jc = min(j, a.n[1] - 1);
   const long long c = (long long)(k + 3) * a.sz + (long long)(jc + 3) * a.sy + (ic + 3);
-  if (lx == 0 && s.mode == 0 && x0 + XP <= a.n[0] && j < a.n[1]) {
-    // rows start on 16 bytes, so ghosted x = x0 does too: the row segment's
-    // XP points sit at byte offsets 12 .. 4 XP + 11, inside 4 XP + 16 bytes
-    const long long c0 = c - 3;
-    if (!s.un_alias) prefetch_rows<4 * XP + 16>(a.un + c0, a.sf);
-    if (s.rk == SF_RK4 && s.stage > 0) prefetch_rows<4 * XP + 16>(a.acc + c0, a.sf);
-    if (s.kahan && s.stage == 3) prefetch_rows<4 * XP + 16>(a.kh + c0, a.sf);
-  }
   TmaSrc<BY, kKS, XP> src;
   src.u = a.us + c;
   src.F = a.sf;
