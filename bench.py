@@ -654,31 +654,37 @@ def _amr_rows(hbm_peak: float) -> list[dict]:
                     "hbm_frac": alg * 20 / (ms * 1e-3) / 1e9 / hbm_peak,
                     "note": "6x6x6 Lagrange taps per fine point and field; algorithmic bytes = "
                             "fine writes + one read of each coarse array region"})
-    # sub-cycled two-level CCZ4 step: periodic 64^3 coarse, 64^3 fine patch (ratio 2) inside
+    # sub-cycled two-level CCZ4 step: periodic 64^3 coarse, 64^3 fine patch (ratio 2) inside,
+    # on two layouts: rows of 72 floats (16-byte rows: the one-point TMA-staged kernel) and
+    # the two-point kernel's layout (rows of 104 floats with one float before each row,
+    # planes of 102 rows)
     nc = (64, 64, 64)
-    Uc, dxc = inputs.z4_minkowski_noise(nc, seed=0, amp=1e-10)
-    # rows of 72 floats (16 bytes): both levels step with the TMA-staged kernel
-    coarse = PatchState(capi.SF_Z4, nc, dxc, 0.25 * dxc[0], precision=capi.SF_FP32_BULK_DW,
-                        x_pitch=72)
-    coarse.upload(Uc)
     nf = (64, 64, 64)
-    fine = PatchState(capi.SF_Z4, nf, tuple(v / 2 for v in dxc), 0.125 * dxc[0],
-                      precision=capi.SF_FP32_BULK_DW, prm=capi.params(ghosts=capi.SF_GHOSTS_NONE),
-                      x_pitch=72)
+    Uc, dxc = inputs.z4_minkowski_noise(nc, seed=0, amp=1e-10)
     Uf, _ = inputs.z4_minkowski_noise(nf, seed=1, amp=1e-10)
-    fine.upload(Uf)
-    pair = amr.SubcycledPair(coarse, fine, 2, (16, 16, 16))
-    steps = 5
-    ms_launch = _events_time(lambda: pair.step(1), steps, 2)
-    pair.capture(1)
-    ms = _events_time(pair.replay, steps, 2)
-    cells = 64 ** 3 * 4 + 64 ** 3 * 4 * 2
-    out.append({"workload": "subcycled_bor_ccz4_fp32dw_coarse64_fine64_ratio2", "value":
-                cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_coarse_step": ms / steps,
-                "ms_per_coarse_step_python_driver": ms_launch / steps,
-                "note": "one coarse RK4 step + 2 fine RK4 steps with BOR ghost fills before every "
-                        "fine stage (6 prolongation boxes each) and restriction, replayed as one "
-                        "CUDA graph (amr.SubcycledPair.capture)"})
+    for lname, lay in (("rows72", dict(x_pitch=72)),
+                       ("two_point_layout", dict(x_pitch=104, x_offset=1, plane_rows=102))):
+        coarse = PatchState(capi.SF_Z4, nc, dxc, 0.25 * dxc[0], precision=capi.SF_FP32_BULK_DW, **lay)
+        coarse.upload(Uc)
+        fine = PatchState(capi.SF_Z4, nf, tuple(v / 2 for v in dxc), 0.125 * dxc[0],
+                          precision=capi.SF_FP32_BULK_DW, prm=capi.params(ghosts=capi.SF_GHOSTS_NONE),
+                          **lay)
+        fine.upload(Uf)
+        pair = amr.SubcycledPair(coarse, fine, 2, (16, 16, 16))
+        steps = 5
+        ms_launch = _events_time(lambda: pair.step(1), steps, 2)
+        pair.capture(1)
+        ms = _events_time(pair.replay, steps, 2)
+        cells = 64 ** 3 * 4 + 64 ** 3 * 4 * 2
+        out.append({"workload": f"subcycled_bor_ccz4_fp32dw_coarse64_fine64_ratio2_{lname}", "value":
+                    cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_coarse_step": ms / steps,
+                    "ms_per_coarse_step_python_driver": ms_launch / steps,
+                    "layout": lay,
+                    "note": "one coarse RK4 step + 2 fine RK4 steps with BOR ghost fills before every "
+                            "fine stage (6 prolongation boxes each, on a second stream beside the "
+                            "fine stage before) and restriction, replayed as one CUDA graph "
+                            "(amr.SubcycledPair.capture)"})
+        del pair, coarse, fine
     return out
 
 

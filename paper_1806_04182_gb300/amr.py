@@ -236,8 +236,20 @@ class SubcycledPair:
         capi.sf_bor_prolong_boxes(cpatch, self.rk, states, f.nf, R, r, stage, boxes, h)
 
     def step(self, nsteps: int = 1, stream=None) -> None:
+        """Advance the pair by nsteps coarse steps on `stream` (default: the
+        current stream).  The BOR fill of each fine stage runs on a stream of
+        its own, at the same time as the fine stage before it: the fill writes
+        only the ghost shell of the next stage's input, which that stage
+        neither reads nor writes (it writes interior points).  A fill waits
+        for the coarse stages and for the fine stage two before it, the last
+        to read the ghost shell it overwrites (the stage inputs cycle
+        A, B, C, B); each fine stage waits for its own fill."""
         c, f, R = self.coarse, self.fine, self.R
-        h = _stream(stream)
+        main = _torch_stream(stream)
+        h = main.cuda_stream
+        if getattr(self, "_side", None) is None:
+            self._side = torch.cuda.Stream(device=c.A.device)
+        side = self._side
         for _ in range(nsteps):
             capi.sf_copy_boxes([self._box_S0], c.precision, h)
             for s in range(c.nstages):
@@ -245,10 +257,20 @@ class SubcycledPair:
                 capi.sf_substep(c.prm, cp, s, h)
                 if self.radiative is not None:
                     capi.sf_radiative_substep(c.prm, cp, *self.radiative, s, h)
+            side.wait_stream(main)  # the coarse stage states are complete
+            done = []  # event after each fine stage, in order
             for r in range(R):
                 for s in range(f.nstages):
-                    self.fill_fine_ghosts(f.roles(s)[0], r, s, h)
+                    if len(done) >= 2:
+                        side.wait_event(done[-2])
+                    self.fill_fine_ghosts(f.roles(s)[0], r, s, side.cuda_stream)
+                    filled = torch.cuda.Event()
+                    filled.record(side)
+                    main.wait_event(filled)
                     capi.sf_substep(f.prm, f.stage_patch(s), s, h)
+                    ev = torch.cuda.Event()
+                    ev.record(main)
+                    done.append(ev)
             capi.sf_copy_boxes([self._restrict], c.precision, h)
             if self.radiative is None and self._refresh_images:
                 c.fill_ghosts(c.A, h)
@@ -271,6 +293,14 @@ class SubcycledPair:
         if getattr(self, "_graph", None) is None:
             raise RuntimeError("capture() first")
         self._graph.replay()
+
+
+def _torch_stream(stream) -> torch.cuda.Stream:
+    if stream is None:
+        return torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return stream
+    return torch.cuda.ExternalStream(stream)
 
 
 def _stream(stream) -> int:

@@ -30,7 +30,7 @@ def _stream_handle(stream) -> int:
 class PatchState:
     def __init__(self, system: int, n, dx, dt: float, precision: int = capi.SF_FP64,
                  prm: capi.sf_params | None = None, ghost: int = 3, device="cuda",
-                 x_pitch: int | None = None, x_offset: int = 0):
+                 x_pitch: int | None = None, x_offset: int = 0, plane_rows: int | None = None):
         """x_pitch: row length of the ghosted arrays in elements (default
         nx + 2 ghost).  A pitch that makes every row, plane and field start
         on a 16-byte boundary (a multiple of 4 floats) lets the float CCZ4
@@ -38,7 +38,10 @@ class PatchState:
         elements before the first ghosted point of each row.  With a pitch of
         a multiple of 4 floats and x_offset = 1, interior points with even x
         sit on 8-byte boundaries, which the float CCZ4 kernel that computes
-        two neighbouring points per thread needs."""
+        two neighbouring points per thread needs.  plane_rows: rows per plane
+        (default ny + 2 ghost); that kernel's compile-time layout has planes of
+        102 rows of 104 floats, so a smaller patch reaches it with
+        x_pitch=104, x_offset=1, plane_rows=102."""
         self.system = system
         self.n = tuple(int(v) for v in n)
         self.dx = tuple(float(v) for v in dx)
@@ -55,7 +58,10 @@ class PatchState:
         self.pitch = self.xo + nx + 2 * g if x_pitch is None else int(x_pitch)
         if self.xo < 0 or self.pitch < self.xo + nx + 2 * g:
             raise ValueError("x_pitch shorter than x_offset plus a ghosted row")
-        self.shape = (self.nf, nz + 2 * g, ny + 2 * g, self.pitch)
+        self.rows = ny + 2 * g if plane_rows is None else int(plane_rows)
+        if self.rows < ny + 2 * g:
+            raise ValueError("plane_rows shorter than a ghosted plane")
+        self.shape = (self.nf, nz + 2 * g, self.rows, self.pitch)
         kw = dict(dtype=self.dtype, device=device)
         self.A = torch.zeros(self.shape, **kw)
         self.B = torch.zeros(self.shape, **kw)
@@ -129,7 +135,8 @@ class PatchState:
             for f in self.offset_fields:
                 t[f] -= 1.0
         nx, xo = self.n[0], self.xo
-        self.A[:, g:self.shape[1] - g, g:self.shape[2] - g, xo + g:xo + g + nx].copy_(t.to(self.dtype))
+        ny = self.n[1]
+        self.A[:, g:self.shape[1] - g, g:g + ny, xo + g:xo + g + nx].copy_(t.to(self.dtype))
         if self.E is not None:
             self.E.zero_()
         self._rate = None
@@ -142,8 +149,8 @@ class PatchState:
                             else ghosted).double().clone()
         for f in self.offset_fields:
             t[f] -= 1.0
-        nx = self.n[0] + 2 * self.g
-        self.A[:, :, :, self.xo:self.xo + nx].copy_(t.to(self.dtype))
+        nx, ny = self.n[0] + 2 * self.g, self.n[1] + 2 * self.g
+        self.A[:, :, :ny, self.xo:self.xo + nx].copy_(t.to(self.dtype))
         if self.E is not None:
             self.E.zero_()
         self._rate = None
@@ -167,7 +174,7 @@ class PatchState:
         """Interior view of the stored values (float CCZ4: with offsets)."""
         a = self.A if array is None else array
         g = self.g
-        return a[:, g:self.shape[1] - g, g:self.shape[2] - g, self.xo + g:self.xo + g + self.n[0]]
+        return a[:, g:self.shape[1] - g, g:g + self.n[1], self.xo + g:self.xo + g + self.n[0]]
 
     def fields(self, array: torch.Tensor | None = None) -> torch.Tensor:
         """Interior field values in float64 (flat-space offsets added back)."""
@@ -250,7 +257,7 @@ class PatchState:
         metadata to `path` (.npz); `load` resumes bit for bit."""
         meta = dict(system=self.system, n=self.n, dx=self.dx, dt=self.dt,
                     precision=self.precision, ghost=self.g, step=step, t=t, pitch=self.pitch,
-                    x_offset=self.xo,
+                    x_offset=self.xo, plane_rows=self.rows,
                     prm={f: getattr(self.prm, f) for f in self._PRM_FIELDS})
         arrays = {"A": self.A.cpu().numpy()}
         if self.E is not None:
@@ -264,7 +271,8 @@ class PatchState:
         meta = json.loads(str(z["meta"]))
         st = cls(meta["system"], meta["n"], meta["dx"], meta["dt"], precision=meta["precision"],
                  prm=capi.params(**meta["prm"]), ghost=meta["ghost"], device=device,
-                 x_pitch=meta.get("pitch"), x_offset=meta.get("x_offset", 0))
+                 x_pitch=meta.get("pitch"), x_offset=meta.get("x_offset", 0),
+                 plane_rows=meta.get("plane_rows"))
         st.A.copy_(torch.from_numpy(z["A"]))
         if st.E is not None and "E" in z:
             st.E.copy_(torch.from_numpy(z["E"]))

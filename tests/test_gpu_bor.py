@@ -190,6 +190,44 @@ def test_subcycled_graph_replay_equals_steps():
         assert torch.equal(a.A, b.A)
 
 
+def test_subcycled_two_point_layout_matches_one_point():
+    # both levels on the layout of the two-point float CCZ4 kernel (rows of
+    # 104 floats, one float before each row, planes of 102 rows) against the
+    # same pair on 16-byte rows (the one-point TMA kernel): the two kernels
+    # differ only in rounding order, so the levels agree to the float bound
+    # of the stage tests, per stage taken
+    data = lambda n: inputs.z4_perturbed(n, seed=7, amp=0.04)
+    nc, at, m, R, steps = (32, 32, 12), (8, 8, 3), (16, 16, 6), 2, 2
+    one = _pair(capi.SF_Z4, capi.SF_FP32_BULK_DW, nc, m, at, R, data, 0.2, steps, pitch4=True)
+    U0c, dxc = data(nc)
+    dtc = 0.2 * min(dxc)
+    lay = dict(x_pitch=104, x_offset=1, plane_rows=102)
+    coarse = PatchState(capi.SF_Z4, nc, dxc, dtc, precision=capi.SF_FP32_BULK_DW, **lay)
+    coarse.upload(U0c)
+    nfine = tuple(R * v for v in m)
+    fine = PatchState(capi.SF_Z4, nfine, tuple(v / R for v in dxc), dtc / R,
+                      precision=capi.SF_FP32_BULK_DW, prm=capi.params(ghosts=capi.SF_GHOSTS_NONE),
+                      **lay)
+    Uf_all, _ = data(tuple(R * v for v in nc))
+    fine.upload(np.ascontiguousarray(Uf_all[:, R * at[2]:R * at[2] + nfine[2],
+                                            R * at[1]:R * at[1] + nfine[1],
+                                            R * at[0]:R * at[0] + nfine[0]]))
+    two = amr.SubcycledPair(coarse, fine, R, at)
+    c0 = capi.sf_launch_count()
+    two.step(steps)
+    torch.cuda.synchronize()
+    eps32 = float(np.finfo(np.float32).eps)
+    per_stage = 64 / 12 * eps32 * dtc / min(dxc) ** 2 / 1e-2
+    # 4 coarse and 4 R fine stages a step, the fine ones at R times dt / dx^2
+    bound = 2 * steps * 4 * (1 + R * R) * per_stage
+    for a, b in ((one.coarse, two.coarse), (one.fine, two.fine)):
+        x, y = a.fields().cpu().numpy(), b.fields().cpu().numpy()
+        for f in range(25):
+            scale = max(np.abs(x[f]).max(), 1e-2)
+            assert np.abs(x[f] - y[f]).max() / scale < bound, (f, bound)
+    assert capi.sf_launch_count() - c0 > 0
+
+
 def test_subcycled_plane_wave_converges_at_fourth_order():
     R = 2
     errs = []
