@@ -750,18 +750,20 @@ def _batch_rows(hbm_peak: float, npatch: int = 512, per_patch: bool = True) -> l
         sts = states(capi.SF_FP32_BULK_DW, tma_pitch=tma)
         stream = torch.cuda.Stream()
         b = capi.sf_batch_create(capi.params(), [s_.patch(s_.B, s_.A, s_.C) for s_ in sts])
-        launches = capi.sf_batch_launches_per_step(b)
         with torch.cuda.stream(stream):
             capi.sf_batch_tune(b, stream.cuda_stream)
             capi.sf_batch_capture(b, stream.cuda_stream)
             ms = _events_time(lambda: capi.sf_batch_launch(b, stream.cuda_stream), 10, 3)
+        launches = capi.sf_batch_launches_per_step(b)
+        tuned = capi.sf_batch_tuned(b)
         capi.sf_batch_destroy(b)
         rate = cells * 4 * 10 / (ms * 1e-3)
         batch_rate = rate if batch_rate is None else batch_rate
         name = ("tma_ccz4_tiles_plus_persistent" if tma else "persistent_only")
         out.append({"workload": f"amr_batch_{npatch}_patches_fp32_bulk_dw_graph_{name}",
                     "value": rate, "unit": UNIT, "ms_per_step": ms / 10, "cells": cells,
-                    "launches_per_step": launches,
+                    "launches_per_step": launches, "launches_per_stage": launches / 4,
+                    "tuned": tuned,
                     "hbm_frac": bytes_step * 10 / (ms * 1e-3) / 1e9 / hbm_peak})
         del sts
     if not per_patch:

@@ -396,7 +396,10 @@ sf_status sf_bor_prolong_boxes(const sf_patch* coarse, int32_t rk, const void* c
  * sf_batch_create copies the patch table (and the TMA patches' tensor maps
  * and tile lists) to the device (allocates; not in the hot path).
  * sf_batch_tune times the tile shapes of the persistent kernel for each
- * (system, size class) on `stream` and keeps the fastest.  sf_batch_capture
+ * (system, size class) on `stream` and keeps the fastest, then, for each size
+ * class with TMA patches, both TMA tile widths (that class's tiles alone) and
+ * keeps the faster; it runs stage 1, which writes scratch roles only (the
+ * u_next role and the accumulator), never U^n.  sf_batch_capture
  * records the RK stages of one full step into a CUDA graph; sf_batch_launch
  * replays it.
  */
@@ -424,6 +427,14 @@ sf_status sf_batch_set_halo(sf_batch* b, int32_t role, const sf_box_copy* boxes,
 /* Number of kernel launches (TMA tile launches, persistent launches and halo
  * box-copy launches) made by one sf_batch_launch, i.e. one RK4 step. */
 int32_t sf_batch_launches_per_step(const sf_batch* b);
+/* The batch's tile choices per size class c (0: wave, max n <= 32; 1: wave,
+ * larger; 2: CCZ4, max n <= 32; 3: CCZ4, larger): shape_of_class[3c .. 3c+2]
+ * the persistent kernel's tile (x, y, z extents), tma_width_of_class[c] the
+ * TMA tile width (32: 32 x 12 points, 16: 16 x 24; -1 each patch of the class
+ * takes the width that covers it with fewer tiles, as before sf_batch_tune;
+ * 0 no TMA patch in the class).  Either array may be NULL (else 12 and 4
+ * entries).  Errors: SF_EINVAL for a NULL batch. */
+sf_status sf_batch_tuned(const sf_batch* b, int32_t* shape_of_class, int32_t* tma_width_of_class);
 sf_status sf_batch_destroy(sf_batch* b);
 
 /*

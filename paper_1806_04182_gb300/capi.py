@@ -28,7 +28,7 @@ EXPORTS = ["sf_nfields", "sf_substep", "sf_rhs", "sf_fill_ghosts_periodic", "sf_
            "sf_batch_launch", "sf_batch_launches_per_step", "sf_batch_destroy",
            "sf_batch_set_halo", "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong", "sf_bor_prolong", "sf_bor_prolong_boxes", "sf_radiative_substep",
            "sf_selftest_wait_timeout", "sf_get_device_status", "sf_last_error", "sf_launch_count",
-           "sf_state_span", "sf_step_host"]
+           "sf_state_span", "sf_step_host", "sf_batch_tuned"]
 SF_HOST_RESET_KAHAN = 1
 
 
@@ -172,6 +172,7 @@ def lib() -> ctypes.CDLL:
         L.sf_state_span.restype = i64
         L.sf_step_host.argtypes = [P(sf_params), P(sf_patch), P(sf_state), i32, P(vp), P(vp), i32,
                                    ctypes.c_uint32, vp, vp, vp]
+        L.sf_batch_tuned.argtypes = [vp, P(i32), P(i32)]
         L.sf_get_device_status.argtypes = [vp]
         L.sf_selftest_wait_timeout.argtypes = [i64, vp]
         L.sf_last_error.argtypes = []
@@ -183,7 +184,8 @@ def lib() -> ctypes.CDLL:
                      "sf_batch_create", "sf_batch_substep", "sf_batch_tune", "sf_batch_capture",
                      "sf_batch_launch", "sf_batch_destroy", "sf_get_device_status",
                      "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong",
-                     "sf_batch_set_halo", "sf_selftest_wait_timeout", "sf_step_host"):
+                     "sf_batch_set_halo", "sf_selftest_wait_timeout", "sf_step_host",
+                     "sf_batch_tuned"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -296,6 +298,18 @@ def sf_batch_set_halo(batch: int, role: int, boxes) -> None:
 
 def sf_batch_launches_per_step(batch: int) -> int:
     return lib().sf_batch_launches_per_step(batch)
+
+
+def sf_batch_tuned(batch: int) -> dict:
+    """Tile choices per size class (wave small/large, CCZ4 small/large): the
+    persistent kernel's tile and the TMA tile width (0: no TMA patch; -1:
+    per-patch rule, not tuned)."""
+    shapes = (ctypes.c_int32 * 12)()
+    widths = (ctypes.c_int32 * 4)()
+    _check(lib().sf_batch_tuned(batch, shapes, widths), "sf_batch_tuned")
+    names = ("wave_small", "wave_large", "z4_small", "z4_large")
+    return {n: {"persistent_tile": tuple(shapes[3 * c:3 * c + 3]), "tma_tile_width": widths[c]}
+            for c, n in enumerate(names)}
 
 
 def sf_batch_destroy(batch: int) -> None:

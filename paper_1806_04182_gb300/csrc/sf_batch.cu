@@ -96,6 +96,7 @@ struct sf_batch {
   int npatch;
   std::vector<sf_patch> patches;
   int shape_of_class[kClasses];
+  int tma_width_of_class[kClasses];  // TMA tile width per class: -1 the fewer-tiles rule, 0: 32 x 12, 1: 16 x 24
   int device;
   int grid[3];            // persistent grid size per precision
   void* d_args = nullptr; // PatchArgs<T>[4][npatch]
@@ -187,12 +188,18 @@ sf_status build_items(sf_batch* b, int only_class) {
 }
 
 // Tensor maps and the tile lists of the patches served by the TMA-staged
-// CCZ4 kernel (float precision, eligible layouts).  Each patch takes the
-// tile width (32 x 12 or 16 x 24 points, the same cost per tile) that covers
-// it with fewer tiles, i.e. with fewer idle lanes where tiles overhang it.
-sf_status build_tma(sf_batch* b) {
+// CCZ4 kernel (float precision, eligible layouts).  A patch takes its size
+// class's tile width where sf_batch_tune has measured one, else the width
+// (32 x 12 or 16 x 24 points) that covers it with fewer tiles, i.e. with
+// fewer idle lanes where tiles overhang it.  only_class >= 0 lists the tiles
+// of that class only (tuning); every eligible patch is still marked TMA.
+sf_status build_tma(sf_batch* b, int only_class = -1) {
   b->tma.assign(b->npatch, 0);
   b->ntiles = b->ntiles16 = 0;
+  if (b->d_maps) cudaFree(b->d_maps);
+  if (b->d_tiles) cudaFree(b->d_tiles);
+  b->d_maps = nullptr;
+  b->d_tiles = nullptr;
   if (b->precision == SF_FP64) return SF_OK;
   std::vector<unsigned char> maps((size_t)3 * b->npatch * kTmaMapBytes, 0);
   std::vector<TmaTile> tiles[2];  // [0]: 32 x 12, [1]: 16 x 24
@@ -203,7 +210,11 @@ sf_status build_tma(sf_batch* b) {
     auto count = [&](int tx, int ty) {
       return (long long)((p.n[0] + tx - 1) / tx) * ((p.n[1] + ty - 1) / ty);
     };
-    const int w = count(kTmaTileX16, kTmaTileY16) < count(kTmaTileX, kTmaTileY) ? 1 : 0;
+    const int cls = class_of(p);
+    const int w = b->tma_width_of_class[cls] >= 0
+                      ? b->tma_width_of_class[cls]
+                      : (count(kTmaTileX16, kTmaTileY16) < count(kTmaTileX, kTmaTileY) ? 1 : 0);
+    if (only_class >= 0 && cls != only_class) continue;
     const int tx = w ? kTmaTileX16 : kTmaTileX, ty = w ? kTmaTileY16 : kTmaTileY;
     const void* arr[3] = {p.u_n, p.u_stage, p.u_next};
     for (int r = 0; r < 3; ++r) {
@@ -326,7 +337,10 @@ sf_status sf_batch_create(const sf_params* prm, const sf_patch* patches, int32_t
       return set_error(SF_EINVAL, "batch patches need distinct u_n, u_stage and u_next buffers");
     }
   }
-  for (int c = 0; c < kClasses; ++c) b->shape_of_class[c] = 0;
+  for (int c = 0; c < kClasses; ++c) {
+    b->shape_of_class[c] = 0;
+    b->tma_width_of_class[c] = -1;
+  }
   cudaGetDevice(&b->device);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
@@ -425,10 +439,40 @@ sf_status sf_batch_tune(sf_batch* b, void* stream) {
     }
     b->shape_of_class[cls] = best_shape;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   b->ntiles = ntiles;
   b->ntiles16 = ntiles16;
+  // the TMA tile width of each class with TMA patches: the tiles of that
+  // class alone, stage 1 (it writes scratch only), each width timed
+  const int nitems = b->nitems;
+  b->nitems = 0;  // sf_batch_substep then launches the TMA tiles only
+  for (int cls = 0; cls < kClasses && !err && ntiles > 0; ++cls) {
+    bool any = false;
+    for (int q = 0; q < b->npatch; ++q)
+      any |= class_of(b->patches[q]) == cls && z4_tma_batch_eligible(b->prm, b->patches[q]);
+    if (!any) continue;
+    float best = 1e30f;
+    int best_w = 0;
+    for (int w = 0; w < 2 && !err; ++w) {
+      b->tma_width_of_class[cls] = w;
+      if ((err = build_tma(b, cls))) break;
+      for (int rep = 0; rep < 2 && !err; ++rep) err = sf_batch_substep(b, 1, stream);
+      cudaEventRecord(e0, st);
+      for (int rep = 0; rep < 3 && !err; ++rep) err = sf_batch_substep(b, 1, stream);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_w = w;
+      }
+    }
+    b->tma_width_of_class[cls] = best_w;
+  }
+  b->nitems = nitems;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!err) err = build_tma(b, -1);
   if (!err) err = build_items(b, -1);
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
@@ -487,6 +531,25 @@ int32_t sf_batch_launches_per_step(const sf_batch* b) {
     halo += box_copy_launches(h.data(), (int)h.size());
   }
   return 4 * per_stage + halo;
+}
+
+sf_status sf_batch_tuned(const sf_batch* b, int32_t* shape_of_class, int32_t* tma_width_of_class) {
+  if (!b) return set_error(SF_EINVAL, "batch is NULL");
+  for (int c = 0; c < kClasses; ++c) {
+    if (shape_of_class) {
+      const Shape sh = kShapes[b->shape_of_class[c]];
+      shape_of_class[3 * c] = sh.tx;
+      shape_of_class[3 * c + 1] = sh.ty;
+      shape_of_class[3 * c + 2] = sh.tz;
+    }
+    if (tma_width_of_class) {
+      bool any = false;
+      for (int q = 0; q < b->npatch; ++q) any |= class_of(b->patches[q]) == c && b->tma[q];
+      const int w = b->tma_width_of_class[c];
+      tma_width_of_class[c] = !any ? 0 : (w < 0 ? -1 : (w ? kTmaTileX16 : kTmaTileX));
+    }
+  }
+  return SF_OK;
 }
 
 sf_status sf_batch_destroy(sf_batch* b) {

@@ -128,6 +128,11 @@ def test_selftest_wait_limit_checked(L):
         assert "limit_cycles" in str(e.value)
 
 
+def test_batch_tuned_rejects_null_batch(L):
+    with pytest.raises(capi.SfError, match="batch is NULL"):
+        capi.sf_batch_tuned(None)
+
+
 def test_batch_set_halo_rejects_null_batch(L):
     # rejected on the host: no batch, so nothing reaches the device
     with pytest.raises(capi.SfError) as e:

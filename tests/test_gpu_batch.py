@@ -215,7 +215,7 @@ def test_batch_tma_tiles_match_oracle_through_graph():
         # launches per stage
         assert capi.sf_batch_launches_per_step(b) == expected_launches_per_step(states) == 8
         with torch.cuda.stream(stream):
-            capi.sf_batch_tune(b, stream.cuda_stream)  # nothing to tune: no persistent items
+            capi.sf_batch_tune(b, stream.cuda_stream)  # no persistent items: TMA widths only
             capi.sf_batch_capture(b, stream.cuda_stream)
             capi.sf_batch_launch(b, stream.cuda_stream)
         stream.synchronize()
@@ -230,3 +230,44 @@ def test_batch_tma_tiles_match_oracle_through_graph():
         for f in range(want.shape[0]):
             e = np.abs(got[f] - want[f]).max() / max(np.abs(want[f]).max(), 1e-2)
             assert e < bound, (st.n, f, e, bound)
+
+
+def test_batch_tune_measures_tma_tile_width():
+    # the tuner times both TMA tile widths for every size class with TMA
+    # patches and keeps one; the two widths are separate kernel instances of
+    # the same per-point code, so a step after tuning equals a step before it
+    # within the float bound of two separately compiled kernels
+    table = small_table(12, seed=5)
+    a = make_states(table, capi.SF_FP32_BULK_DW, tma_pitch=True)
+    c = make_states(table, capi.SF_FP32_BULK_DW, tma_pitch=True)
+    ba = capi.sf_batch_create(capi.params(), batch_patches(a))
+    bc = capi.sf_batch_create(capi.params(), batch_patches(c))
+    stream = torch.cuda.Stream()
+    try:
+        before = capi.sf_batch_tuned(bc)
+        with torch.cuda.stream(stream):
+            # tuning runs stage 1, which writes scratch only; reset it after
+            capi.sf_batch_tune(bc, stream.cuda_stream)
+        stream.synchronize()
+        after = capi.sf_batch_tuned(bc)
+        for name, v in after.items():
+            if name.startswith("z4"):
+                assert v["tma_tile_width"] in ((16, 32) if before[name]["tma_tile_width"] else (0,))
+            else:
+                assert v["tma_tile_width"] == 0
+        h = torch.cuda.current_stream().cuda_stream
+        for st in c:
+            for t in (st.B, st.C, st.D):
+                t.zero_()
+        for b in (ba, bc):
+            for s in range(4):
+                capi.sf_batch_substep(b, s, h)
+        torch.cuda.synchronize()
+        for x, y in zip(a, c):
+            r, g = x.interior(), y.interior()
+            scale = r.abs().amax(dim=(1, 2, 3)).clamp_min(1e-2)
+            err = ((g - r).abs().amax(dim=(1, 2, 3)) / scale).max().item()
+            assert err < fp_bound(capi.SF_FP32_BULK_DW, x, steps=1), err
+    finally:
+        capi.sf_batch_destroy(ba)
+        capi.sf_batch_destroy(bc)
