@@ -604,32 +604,37 @@ def _amr_rows(hbm_peak: float) -> list[dict]:
     # stage's TMA tile launch ends with the halo copies of the buffer it wrote, and one RK4
     # step of the level (stages + synchronisation) is one captured graph
     Ub, dxb = inputs.z4_minkowski_noise((96, 96, 96), seed=0, amp=1e-10)
-    level = {}
-    for a in range(2):
-        for b_ in range(2):
-            for c in range(2):
-                st = PatchState(capi.SF_Z4, m, dxb, 0.25 * dxb[0], precision=capi.SF_FP32_BULK_DW,
-                                prm=capi.params(ghosts=capi.SF_GHOSTS_NONE), x_pitch=56)
-                st.upload(np.ascontiguousarray(Ub[:, c * 48:(c + 1) * 48, b_ * 48:(b_ + 1) * 48,
-                                                  a * 48:(a + 1) * 48]))
-                level[(a, b_, c)] = st
-    gs = torch.cuda.Stream()
-    gs.wait_stream(torch.cuda.current_stream())
-    lb = amr.level_batch(level)
-    try:
-        with torch.cuda.stream(gs):
-            capi.sf_copy_boxes(amr.halo_boxes(level, "A"), capi.SF_FP32_BULK_DW, gs.cuda_stream)
-            capi.sf_batch_capture(lb, gs.cuda_stream)
-            nlevel = 20
-            ms = _events_time(lambda: capi.sf_batch_launch(lb, gs.cuda_stream), nlevel, 3)
-        out.append({"workload": "level_8_patches_48cubed_ccz4_fp32dw_batch_halo_graph",
-                    "value": 96 ** 3 * 4 * nlevel / (ms * 1e-3), "unit": UNIT,
-                    "ms_per_step": ms / nlevel, "launches_per_step": capi.sf_batch_launches_per_step(lb),
-                    "note": "96^3 CCZ4 box as 2x2x2 patches of 48^3 (rows of 56 floats): per stage one "
-                            "TMA tile launch over all patches + one launch of the 208 halo box copies, "
-                            "one graph per RK4 step (amr.level_batch)"})
-    finally:
-        capi.sf_batch_destroy(lb)
+    for lname, lay, kern in (("rows56", dict(x_pitch=56), "one-point TMA tile launch"),
+                             ("two_point_layout", dict(x_pitch=56, x_offset=1),
+                              "two-point tile launch (32 x 16 tiles, the second in x half used)")):
+        level = {}
+        for a in range(2):
+            for b_ in range(2):
+                for c in range(2):
+                    st = PatchState(capi.SF_Z4, m, dxb, 0.25 * dxb[0], precision=capi.SF_FP32_BULK_DW,
+                                    prm=capi.params(ghosts=capi.SF_GHOSTS_NONE), **lay)
+                    st.upload(np.ascontiguousarray(Ub[:, c * 48:(c + 1) * 48, b_ * 48:(b_ + 1) * 48,
+                                                      a * 48:(a + 1) * 48]))
+                    level[(a, b_, c)] = st
+        gs = torch.cuda.Stream()
+        gs.wait_stream(torch.cuda.current_stream())
+        lb = amr.level_batch(level)
+        try:
+            with torch.cuda.stream(gs):
+                capi.sf_copy_boxes(amr.halo_boxes(level, "A"), capi.SF_FP32_BULK_DW, gs.cuda_stream)
+                capi.sf_batch_capture(lb, gs.cuda_stream)
+                nlevel = 20
+                ms = _events_time(lambda: capi.sf_batch_launch(lb, gs.cuda_stream), nlevel, 3)
+            out.append({"workload": f"level_8_patches_48cubed_ccz4_fp32dw_batch_halo_graph_{lname}",
+                        "value": 96 ** 3 * 4 * nlevel / (ms * 1e-3), "unit": UNIT,
+                        "ms_per_step": ms / nlevel,
+                        "launches_per_step": capi.sf_batch_launches_per_step(lb), "layout": lay,
+                        "note": f"96^3 CCZ4 box as 2x2x2 patches of 48^3: per stage one {kern} over "
+                                "all patches + one launch of the 208 halo box copies, one graph per "
+                                "RK4 step (amr.level_batch)"})
+        finally:
+            capi.sf_batch_destroy(lb)
+        del level
     # prolongation of a 96^3 fine box (ratio 2) from a 48^3 coarse CCZ4 patch, and the BOR form
     cst = PatchState(capi.SF_Z4, m, (2 / 96,) * 3, 0.5 / 96, precision=capi.SF_FP32_BULK_DW)
     U0, _ = inputs.z4_perturbed(m, seed=1, amp=0.02)
@@ -719,9 +724,10 @@ def _batch_rows(hbm_peak: float, npatch: int = 512, per_patch: bool = True) -> l
     # batched AMR step: npatch patches, one persistent launch per stage in a CUDA graph
     table = inputs.amr_patch_table(npatch, seed=0)
 
-    def states(precision, tma_pitch=False):
+    def states(precision, tma_pitch=False, pair=False):
         # tma_pitch: float CCZ4 rows padded to a multiple of 4 floats, which
-        # sends those patches to the TMA-staged kernel inside the batch; the
+        # sends those patches to the TMA-staged kernel inside the batch; pair:
+        # the same with one float before each row (the two-point kernel); the
         # other run keeps every CCZ4 row off that multiple (persistent only)
         sts = []
         for q, t in enumerate(table):
@@ -731,14 +737,16 @@ def _batch_rows(hbm_peak: float, npatch: int = 512, per_patch: bool = True) -> l
                 U0, _ = inputs.wave_plane(t["n"], seed=q, length=t["n"][0] * h)
             else:
                 U0, _ = inputs.z4_minkowski_noise(t["n"], seed=q)
-            pitch = None
+            pitch, xo = None, 0
             if system == capi.SF_Z4:
                 # a multiple of 4 floats for the TMA-staged kernel; otherwise a
                 # pitch that is not, so every CCZ4 patch takes the persistent kernel
                 row = t["n"][0] + 6
                 pitch = (row + 3) // 4 * 4 if tma_pitch else (row + 1 if row % 4 == 0 else row)
+                if pair:
+                    pitch, xo = (row + 1 + 3) // 4 * 4, 1
             sts.append(PatchState(system, t["n"], (h, h, h), t["dt"], precision=precision,
-                                  x_pitch=pitch))
+                                  x_pitch=pitch, x_offset=xo))
             sts[-1].upload(U0)
         return sts
 
@@ -746,8 +754,10 @@ def _batch_rows(hbm_peak: float, npatch: int = 512, per_patch: bool = True) -> l
     bytes_step = sum(t["n"][0] * t["n"][1] * t["n"][2] * (19 * (25 if t["system"] == "z4" else 5) * 4)
                      for t in table)
     batch_rate = None
-    for tma in (True, False):
-        sts = states(capi.SF_FP32_BULK_DW, tma_pitch=tma)
+    for name, tma, pair in (("pair_ccz4_tiles_plus_persistent", True, True),
+                            ("tma_ccz4_tiles_plus_persistent", True, False),
+                            ("persistent_only", False, False)):
+        sts = states(capi.SF_FP32_BULK_DW, tma_pitch=tma, pair=pair)
         stream = torch.cuda.Stream()
         b = capi.sf_batch_create(capi.params(), [s_.patch(s_.B, s_.A, s_.C) for s_ in sts])
         with torch.cuda.stream(stream):
@@ -759,7 +769,6 @@ def _batch_rows(hbm_peak: float, npatch: int = 512, per_patch: bool = True) -> l
         capi.sf_batch_destroy(b)
         rate = cells * 4 * 10 / (ms * 1e-3)
         batch_rate = rate if batch_rate is None else batch_rate
-        name = ("tma_ccz4_tiles_plus_persistent" if tma else "persistent_only")
         out.append({"workload": f"amr_batch_{npatch}_patches_fp32_bulk_dw_graph_{name}",
                     "value": rate, "unit": UNIT, "ms_per_step": ms / 10, "cells": cells,
                     "launches_per_step": launches, "launches_per_stage": launches / 4,

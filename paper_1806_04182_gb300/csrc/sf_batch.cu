@@ -106,6 +106,11 @@ struct sf_batch {
   int nitems = 0;
   unsigned int* d_counter = nullptr;
   std::vector<char> tma;  // patch q goes to the TMA-staged CCZ4 kernel
+  std::vector<char> pair;  // patch q goes to the two-point CCZ4 kernel (takes precedence)
+  void* d_pmaps = nullptr;   // its tensor maps, 6 per patch
+  void* d_pcoefs = nullptr;  // its stencil weights, one block per patch
+  TmaTile* d_ptiles = nullptr;  // its 32 x 16 tiles
+  int npair = 0;                // two-point tiles
   void* d_maps = nullptr; // tensor maps, 3 per patch (u_n, u_stage, u_next roles)
   TmaTile* d_tiles = nullptr;   // 32 x 12 tiles, then 16 x 24 tiles
   int ntiles = 0;               // all TMA tiles
@@ -163,6 +168,7 @@ sf_status build_items(sf_batch* b, int only_class) {
       const bool z4 = p.system == SF_Z4;
       if ((pass == 0) != z4) continue;
       if (!b->tma.empty() && b->tma[q]) continue;
+      if (!b->pair.empty() && b->pair[q]) continue;
       const int cls = class_of(p);
       const Shape sh = kShapes[b->shape_of_class[cls]];
       shapes[q] = make_int2(sh.tx, sh.tz);
@@ -187,6 +193,42 @@ sf_status build_items(sf_batch* b, int only_class) {
   return SF_OK;
 }
 
+// Tensor maps, stencil weights and tile lists of the patches served by the
+// two-point CCZ4 kernel (double-word islands, the one-float row offset
+// layout): 32 x 16 tiles of every plane, overhanging the patch where its
+// size is not a multiple.
+sf_status build_pair(sf_batch* b) {
+  b->pair.assign(b->npatch, 0);
+  b->npair = 0;
+  if (b->precision != SF_FP32_BULK_DW) return SF_OK;
+  const size_t cb = z4_pair_coef_bytes();
+  std::vector<unsigned char> maps((size_t)6 * b->npatch * kTmaMapBytes, 0), coefs(cb * b->npatch, 0);
+  std::vector<TmaTile> tiles;
+  for (int q = 0; q < b->npatch; ++q) {
+    const sf_patch& p = b->patches[q];
+    if (!z4_pair_batch_eligible(b->prm, p)) continue;
+    b->pair[q] = 1;
+    sf_status e = encode_z4_pair_batch(maps.data() + (size_t)6 * q * kTmaMapBytes, coefs.data() + cb * q,
+                                       b->prm, p);
+    if (e) return e;
+    for (int z = 0; z < p.n[2]; ++z)
+      for (int y = 0; y < p.n[1]; y += kPairTileY)
+        for (int x = 0; x < p.n[0]; x += kPairTileX) tiles.push_back(TmaTile{q, x, y, z});
+  }
+  b->npair = (int)tiles.size();
+  if (tiles.empty()) return SF_OK;
+  if (cudaMalloc(&b->d_pmaps, maps.size()) != cudaSuccess ||
+      cudaMalloc(&b->d_pcoefs, coefs.size()) != cudaSuccess ||
+      cudaMalloc(&b->d_ptiles, tiles.size() * sizeof(TmaTile)) != cudaSuccess)
+    return set_error(SF_ECUDA, "batch: cudaMalloc of two-point tiles failed");
+  if (cudaMemcpy(b->d_pmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_pcoefs, coefs.data(), coefs.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_ptiles, tiles.data(), tiles.size() * sizeof(TmaTile), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return set_error(SF_ECUDA, "batch: upload of two-point tiles failed");
+  return SF_OK;
+}
+
 // Tensor maps and the tile lists of the patches served by the TMA-staged
 // CCZ4 kernel (float precision, eligible layouts).  A patch takes its size
 // class's tile width where sf_batch_tune has measured one, else the width
@@ -205,7 +247,7 @@ sf_status build_tma(sf_batch* b, int only_class = -1) {
   std::vector<TmaTile> tiles[2];  // [0]: 32 x 12, [1]: 16 x 24
   for (int q = 0; q < b->npatch; ++q) {
     const sf_patch& p = b->patches[q];
-    if (!z4_tma_batch_eligible(b->prm, p)) continue;
+    if (!z4_tma_batch_eligible(b->prm, p) || (!b->pair.empty() && b->pair[q])) continue;
     b->tma[q] = 1;
     auto count = [&](int tx, int ty) {
       return (long long)((p.n[0] + tx - 1) / tx) * ((p.n[1] + ty - 1) / ty);
@@ -255,15 +297,18 @@ StageArgs batch_stage_args(const sf_batch* b, int stage, unsigned int* status) {
 
 template <typename T, typename H>
 sf_status launch_stage(sf_batch* b, int stage, cudaStream_t st, unsigned int* status) {
-  if (b->ntiles > 0) {
+  if (b->ntiles > 0 || b->npair > 0) {
     // stage roles of the stage input: A (u_n), B (u_stage), C (u_next), B
     const int role[4] = {0, 1, 2, 1};
     const PatchArgs<float>* fargs =
         static_cast<const PatchArgs<float>*>(b->d_args) + (size_t)stage * b->npatch;
     const StageArgs sa = batch_stage_args(b, stage, status);
+    sf_status e = launch_z4_pair_batch(b->prm, b->d_pmaps, role[stage], fargs, b->d_pcoefs,
+                                       b->d_ptiles, b->npair, sa, st);
     const int n32 = b->ntiles - b->ntiles16;
-    sf_status e = launch_z4_tma_batch(b->prm, b->precision, b->d_maps, role[stage], fargs,
-                                      b->d_tiles, n32, kTmaTileX, sa, st);
+    if (!e)
+      e = launch_z4_tma_batch(b->prm, b->precision, b->d_maps, role[stage], fargs, b->d_tiles, n32,
+                              kTmaTileX, sa, st);
     if (!e)
       e = launch_z4_tma_batch(b->prm, b->precision, b->d_maps, role[stage], fargs, b->d_tiles + n32,
                               b->ntiles16, kTmaTileX16, sa, st);
@@ -359,6 +404,7 @@ sf_status sf_batch_create(const sf_params* prm, const sf_patch* patches, int32_t
   }
   cudaMemcpy(b->d_sys, sys.data(), npatch * sizeof(int), cudaMemcpyHostToDevice);
   sf_status e = b->precision == SF_FP64 ? upload_args<double>(b) : upload_args<float>(b);
+  if (!e) e = build_pair(b);
   if (!e) e = build_tma(b);
   if (!e) e = build_items(b, -1);
   if (e) {
@@ -413,8 +459,8 @@ sf_status sf_batch_tune(sf_batch* b, void* stream) {
   cudaEventCreate(&e1);
   sf_status err = SF_OK;
   // the TMA-staged patches have a fixed tile: time the persistent kernel alone
-  const int ntiles = b->ntiles, ntiles16 = b->ntiles16;
-  b->ntiles = b->ntiles16 = 0;
+  const int ntiles = b->ntiles, ntiles16 = b->ntiles16, npair = b->npair;
+  b->ntiles = b->ntiles16 = b->npair = 0;
   for (int cls = 0; cls < kClasses && !err; ++cls) {
     bool any = false;
     for (int q = 0; q < b->npatch; ++q) any |= class_of(b->patches[q]) == cls && !b->tma[q];
@@ -470,6 +516,7 @@ sf_status sf_batch_tune(sf_batch* b, void* stream) {
     b->tma_width_of_class[cls] = best_w;
   }
   b->nitems = nitems;
+  b->npair = npair;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (!err) err = build_tma(b, -1);
@@ -523,8 +570,8 @@ sf_status sf_batch_launch(sf_batch* b, void* stream) {
 int32_t sf_batch_launches_per_step(const sf_batch* b) {
   if (!b) return 0;
   const int n32 = b->ntiles - b->ntiles16;
-  const int per_stage = (n32 > 0 ? 1 : 0) + (b->ntiles16 > 0 ? 1 : 0) +
-                        (b->ntiles == 0 || b->nitems > 0 ? 1 : 0);
+  const int per_stage = (b->npair > 0 ? 1 : 0) + (n32 > 0 ? 1 : 0) + (b->ntiles16 > 0 ? 1 : 0) +
+                        ((b->ntiles == 0 && b->npair == 0) || b->nitems > 0 ? 1 : 0);
   int halo = 0;
   for (int s = 0; s < 4; ++s) {
     const std::vector<sf_box_copy>& h = b->halo[kOutRole[s]];
@@ -563,6 +610,9 @@ sf_status sf_batch_destroy(sf_batch* b) {
   if (b->d_counter) cudaFree(b->d_counter);
   if (b->d_maps) cudaFree(b->d_maps);
   if (b->d_tiles) cudaFree(b->d_tiles);
+  if (b->d_pmaps) cudaFree(b->d_pmaps);
+  if (b->d_pcoefs) cudaFree(b->d_pcoefs);
+  if (b->d_ptiles) cudaFree(b->d_ptiles);
   delete b;
   return SF_OK;
 }

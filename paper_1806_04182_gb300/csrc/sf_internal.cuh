@@ -37,6 +37,19 @@ constexpr int kTmaTileX = 32, kTmaTileY = 12;      // the wide tile
 constexpr int kTmaTileX16 = 16, kTmaTileY16 = 24;  // the narrow tile
 constexpr size_t kTmaMapBytes = 128;  // sizeof(CUtensorMap)
 bool z4_tma_batch_eligible(const sf_params& prm, const sf_patch& p);
+// Two-point tiles of many patches (sf_z4_pair.cu), 32 x 16 x 1, for float
+// CCZ4 batch patches with double-word islands on the one-float row offset
+// layout: six tensor maps per patch (RK chunks of u_n, acc, kahan; stencil
+// boxes of the u_n, u_stage, u_next roles) and the patch's stencil weights
+// (z4_pair_coef_bytes each) in device memory.
+constexpr int kPairTileX = 32, kPairTileY = 16;
+bool z4_pair_batch_eligible(const sf_params& prm, const sf_patch& p);
+size_t z4_pair_coef_bytes();
+sf_status encode_z4_pair_batch(void* maps6, void* coef, const sf_params& prm, const sf_patch& p);
+sf_status launch_z4_pair_batch(const sf_params& prm, const void* d_maps, int role,
+                               const PatchArgs<float>* d_args, const void* d_coefs,
+                               const TmaTile* d_tiles, int ntiles, const StageArgs& s,
+                               cudaStream_t st);
 sf_status encode_z4_tma_map(void* map, const sf_patch& p, const void* base, int xp);
 sf_status launch_z4_tma_batch(const sf_params& prm, int precision, const void* d_maps, int role,
                               const PatchArgs<float>* d_args, const TmaTile* d_tiles, int ntiles,

@@ -319,24 +319,37 @@ int rk_form(const StageArgs& s) {
   return s.stage < 3 ? kRk4Mid : kRk4Last;
 }
 
+// Store of a value pair; MASKED (tiles that overhang the patch): vm bit 0
+// for point i, bit 1 for point i + 1 (never set without bit 0).
+template <bool MASKED>
+__device__ __forceinline__ void store2(float* p, F2 v, unsigned vm) {
+  if constexpr (MASKED) {
+    if (vm == 3u) *reinterpret_cast<F2*>(p) = v;
+    else if (vm & 1u) p[0] = v.x;
+  } else {
+    *reinterpret_cast<F2*>(p) = v;
+  }
+}
+
 // RK stage combination of one field value pair (sf_common.cuh's
 // stage_combine on pairs): writes the accumulator / Kahan term and returns
 // the next stage input.
-template <int FORM>
+template <int FORM, bool MASKED = false>
 __device__ __forceinline__ F2 stage_combine2(const PatchArgs<float>& a, const StageArgs& s,
-                                             long long o, F2 centre, F2 un_m, F2 acc, F2 kh, F2 r) {
+                                             long long o, F2 centre, F2 un_m, F2 acc, F2 kh, F2 r,
+                                             unsigned vm = 3u) {
   const F2 cn(a.c_next), ca(a.c_acc);
   if constexpr (FORM == kRk4First) {
-    *reinterpret_cast<F2*>(a.acc + o) = mul2(ca, r);
+    store2<MASKED>(a.acc + o, mul2(ca, r), vm);
     return fma2(cn, r, centre);
   } else if constexpr (FORM == kRk4Mid) {
-    *reinterpret_cast<F2*>(a.acc + o) = fma2(ca, r, acc);
+    store2<MASKED>(a.acc + o, fma2(ca, r, acc), vm);
     return fma2(cn, r, un_m);
   } else if constexpr (FORM == kRk4Last) {
     const F2 inc = fma2(cn, r, acc);
     const F2 y = sub2(inc, kh);
     const F2 t = add2(un_m, y);
-    *reinterpret_cast<F2*>(a.kh + o) = sub2(sub2(t, un_m), y);
+    store2<MASKED>(a.kh + o, sub2(sub2(t, un_m), y), vm);
     return t;
   }
   const F2 un = s.un_alias ? centre : un_m;
@@ -417,9 +430,11 @@ __device__ __forceinline__ void write_fields_pair(const PatchArgs<float>& a, con
 // to a face; r holds the values written), as aligned pairs: a shift in y or z
 // keeps the pair on its 8-byte boundary.  The x ghost columns are written by
 // write_x_images (RK4 forms) or by pair_xghost_kernel after the stage.
+template <bool MASKED = false>
 __device__ __forceinline__ void write_yz_images(const PatchArgs<float>& a, const StageArgs& s,
                                                 long long c, int i, int j, int k, const F2* r,
-                                                int stride) {
+                                                int stride, unsigned vm = 3u) {
+  if (MASKED && !(vm & 1u)) return;
   const unsigned m = ghost_images(a, s, i, j, k).mask & ~3u;
   if (!m) return;
 #pragma unroll 1
@@ -434,38 +449,42 @@ __device__ __forceinline__ void write_yz_images(const PatchArgs<float>& a, const
       for (int w = 0; w < 3; ++w) {
         if (w && !(m & (w == 1 ? 4u : 8u))) continue;
         const long long oy = w == 0 ? 0 : (w == 1 ? 1 : -1) * (long long)a.n[1] * a.sy;
-        if (p | w) *reinterpret_cast<F2*>(q + oz + oy) = v;
+        if (p | w) store2<MASKED>(q + oz + oy, v, vm);
       }
     }
   }
 }
 
-// The x periodic images of a tile's boundary columns, written by the CTA
-// from the tile's new values in shared memory (r: the pair of thread t for
-// field f at r[f * stride + t]).  First tile of a row: interior x = 0..2 go to
-// ghost x = n0 .. n0 + 2 (past the interior); last tile: x = n0 - 3 .. n0 - 1
-// go to x = -3 .. -1; each also at the y and z image rows of its point, so
-// that with write_yz_images every ghost value of the tile's points is written.
-// 16 rows x 25 fields x 3 columns per side, spread over the CTA's threads.
+// The x periodic images of the patch's boundary columns that lie in a tile
+// (x0 .. x0 + 31, rows y0 .. y0 + 15 of plane k), written by the CTA from the
+// tile's new values in shared memory (r: the pair of thread t for field f at
+// r[f * stride + t]).  Interior x = 0..2 go to ghost x = n0 .. n0 + 2 (past
+// the interior), x = n0 - 3 .. n0 - 1 to x = -3 .. -1; each also at the y and
+// z image rows of its point, so that with write_yz_images every ghost value
+// of the tile's points is written.  Spread over the CTA's threads.
 __device__ __forceinline__ void write_x_images(const PatchArgs<float>& a, const StageArgs& s,
-                                               int bx, int tx, int y0, int k, const F2* r,
-                                               int stride, int tid) {
-  const bool lo = bx == 0, hi = bx == tx - 1;
-  if (!(lo || hi)) return;
-  const int nside = lo && hi ? 2 : 1;
+                                               int x0, int y0, int k, const F2* r, int stride,
+                                               int tid) {
+  const int n0 = a.n[0];
+  const int lo0 = x0, lo1 = min(min(3, n0), x0 + 32);          // columns with an image at +n0
+  const int hi0 = max(n0 - 3, x0), hi1 = min(n0, x0 + 32);      // columns with an image at -n0
+  const int nlo = max(0, lo1 - lo0), nhi = max(0, hi1 - hi0), ncol = nlo + nhi;
+  if (!ncol) return;
+  const int rows = min(16, a.n[1] - y0);
 #pragma unroll 1
-  for (int v = tid; v < nside * 1200; v += stride) {
-    const int side = nside == 2 ? v / 1200 : (lo ? 0 : 1);
-    const int w = nside == 2 ? v - (v / 1200) * 1200 : v;
-    const int f = w / 48, rem = w - f * 48, row = rem / 3, mc = rem - row * 3;
-    const int xl = side == 0 ? mc : 29 + mc;  // tile-local x of the source point
+  for (int v = tid; v < ncol * 16 * 25; v += stride) {
+    const int f = v / (ncol * 16), rem = v - f * (ncol * 16), row = rem / ncol, cc = rem - row * ncol;
+    if (row >= rows) continue;
+    const bool low = cc < nlo;
+    const int x = low ? lo0 + cc : hi0 + (cc - nlo);
+    const int xl = x - x0;  // tile-local x of the source point
     // owner of (row, xl): warp row / 2, half-warp row % 2, lane xl / 2
     const F2 pr = r[f * stride + (row >> 1) * 32 + (row & 1) * 16 + (xl >> 1)];
     const float val = (xl & 1) ? pr.y : pr.x;
-    const int i = bx * 32 + xl, j = y0 + row;
-    const unsigned m = ghost_images(a, s, i, j, k).mask;
-    const long long o = f * a.sf + (long long)(k + 3) * a.sz + (long long)(j + 3) * a.sy + (i + 3) +
-                        (side == 0 ? a.n[0] : -a.n[0]);
+    const int j = y0 + row;
+    const unsigned m = ghost_images(a, s, x, j, k).mask;
+    const long long o = f * a.sf + (long long)(k + 3) * a.sz + (long long)(j + 3) * a.sy + (x + 3) +
+                        (low ? n0 : -n0);
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
       if (p && !(m & (p == 1 ? 16u : 32u))) continue;
@@ -508,10 +527,10 @@ __global__ void __launch_bounds__(256) pair_xghost_kernel(float* __restrict__ u,
 // are acquired, every field of the block combined and stored, and the
 // chunks released.  Array order: kRk4First: u_stage (= U^n); kRk4Mid: U^n,
 // accumulator; kRk4Last: U^n, accumulator, Kahan term.
-template <int FORM, int NARR, typename Src>
+template <int FORM, int NARR, bool MASKED = false, typename Src>
 __device__ __forceinline__ void write_fields_staged(const PatchArgs<float>& a, const StageArgs& s,
                                                     long long c, F2* r, int stride, Src& src,
-                                                    int lpos) {
+                                                    int lpos, unsigned vm = 3u) {
   static_assert(NARR >= 1 && NARR <= 3, "staged arrays");
   auto ld = [](const float* q) { return *reinterpret_cast<const F2*>(q); };
   bool bad = false;  // a non-finite value written (reported once, at the end)
@@ -530,9 +549,12 @@ __device__ __forceinline__ void write_fields_staged(const PatchArgs<float>& a, c
       const F2 v2 = NARR > 2 ? ld(in[NARR > 2 ? 2 : 0] + q * 512) : F2(0.0f);
       const F2 rr = r[f * stride];
       // the first array is U^n (kRk4First: the stage input, which is U^n)
-      const F2 out = stage_combine2<FORM>(a, s, o, v0, v0, v1, v2, rr);
-      *reinterpret_cast<F2*>(a.nx + o) = out;
-      bad |= !(finite_(out.x) && finite_(out.y));
+      const F2 out = stage_combine2<FORM, MASKED>(a, s, o, v0, v0, v1, v2, rr, vm);
+      store2<MASKED>(a.nx + o, out, vm);
+      if constexpr (MASKED)
+        bad |= ((vm & 1u) && !finite_(out.x)) || ((vm & 2u) && !finite_(out.y));
+      else
+        bad |= !(finite_(out.x) && finite_(out.y));
       r[f * stride] = out;
     }
 #pragma unroll
@@ -546,14 +568,20 @@ struct RkMaps {
   CUtensorMap m[3];
 };
 
-template <typename H2, int W, int KS, int FORM>
-__global__ void __launch_bounds__(32 * W, 1)
-    z4_pair_kernel(const __grid_constant__ CUtensorMap map, PatchArgs<float> a, StageArgs s,
-                   Z4Coef<float> zc, const __grid_constant__ PairCoef pc,
-                   const __grid_constant__ RkMaps rk) {
+// One tile of 32 x 16 points of plane k, lower corner (x0, y0): the stencil
+// boxes staged through the ring, the right-hand side, the stage write and the
+// periodic images of its points.  BATCH: the patch's strides come from `a`
+// and the tile may overhang the patch (points outside write nothing, their
+// centre reads are clamped into the patch); otherwise the compile-time
+// strides of the padded 96^3-class layout and whole tiles.
+template <typename H2, int W, int KS, int FORM, bool BATCH>
+__device__ __forceinline__ void pair_tile(const CUtensorMap* map, const CUtensorMap* rkmaps,
+                                          const PatchArgs<float>& a, const StageArgs& s,
+                                          const Z4Coef<float>& zc, const PairCoef* pc, int x0,
+                                          int y0, int k, unsigned char* smem) {
   constexpr int NARR = FORM == kRk4First ? 1 : (FORM == kRk4Mid ? 2 : (FORM == kRk4Last ? 3 : 0));
+  static_assert(!BATCH || NARR > 0, "batched tiles take the RK4 stage forms");
   using C = PCfg<W, KS>;
-  extern __shared__ __align__(128) unsigned char smem[];
   float* tiles = reinterpret_cast<float*>(smem);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kBarOffset);
   uint64_t* empty = full + KS;
@@ -567,15 +595,19 @@ __global__ void __launch_bounds__(32 * W, 1)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
-  // whole tiles only (checked on the host): every thread has two points
   const int px = 2 * (threadIdx.x & 15);
   const int ly = 2 * threadIdx.y + (threadIdx.x >> 4);
-  const int i = blockIdx.x * 32 + px;
-  const int j = blockIdx.y * C::BY + ly;
-  // planes next to the z faces first (their tiles also write the z images, the
-  // slowest tiles), so that the partial last wave holds plain tiles
-  const int k = (int)((blockIdx.z + 3 * gridDim.z - 3) % gridDim.z);
-  const long long c = (long long)(k + 3) * kSZ + (long long)(j + 3) * kSY + (i + 3);
+  const int i = x0 + px;
+  const int j = y0 + ly;
+  long long c;
+  unsigned vm = 3u;  // bit 0: point i in the patch, bit 1: point i + 1
+  if constexpr (BATCH) {
+    vm = j < a.n[1] ? (i < a.n[0] ? 1u : 0u) | (i + 1 < a.n[0] ? 2u : 0u) : 0u;
+    const int ic = min(i, (a.n[0] - 1) & ~1), jc = min(j, a.n[1] - 1);
+    c = (long long)(k + 3) * a.sz + (long long)(jc + 3) * a.sy + (ic + 3);
+  } else {
+    c = (long long)(k + 3) * kSZ + (long long)(j + 3) * kSY + (i + 3);
+  }
   if (NARR == 0 && (threadIdx.x & 15) == 0 && s.mode == 0) {
     // generic form (RK inputs read from global memory in the write phase):
     // the row's 32 points start on a 16-byte boundary, prefetch their 128 B
@@ -589,11 +621,11 @@ __global__ void __launch_bounds__(32 * W, 1)
   PairSrc<W, KS, NARR> src;
   src.u = a.us + c;
   src.F = a.sf;
-  src.pc = &pc;
+  src.pc = pc;
   src.tiles = tiles;
   src.full = full;
   src.empty = empty;
-  src.map = &map;
+  src.map = map;
   src.status = s.status;
   src.local = (3 * C::TY + ly + 3) * kXB + px + 4;
   src.use = 0;
@@ -601,13 +633,13 @@ __global__ void __launch_bounds__(32 * W, 1)
   src.nfu = zc.shift_frozen ? 22 : 25;
   src.nuses = src.nfu + 3 * NARR;
   src.done = 0;
-  src.rkmap = rk.m;
-  src.rx = blockIdx.x * 32 + 4;  // tensor x = ghosted x + 1 of point x0
-  src.ry = blockIdx.y * C::BY + 3;
+  src.rkmap = rkmaps;
+  src.rx = x0 + 4;  // tensor x = ghosted x + 1 of point x0
+  src.ry = y0 + 3;
   src.rz = k + 3;
   src.issued = 0;
-  src.gx = blockIdx.x * 32;  // tensor x = ghosted x + 1; the box starts 4 before point x0
-  src.gy = blockIdx.y * C::BY;
+  src.gx = x0;  // tensor x = ghosted x + 1; the box starts 4 before point x0
+  src.gy = y0;
   src.gz = k;
   src.leader = tid == 0;
   src.lane0 = threadIdx.x == 0;
@@ -617,17 +649,60 @@ __global__ void __launch_bounds__(32 * W, 1)
   F2 be[3];
   z4_rhs<F2, H2, false>(zc, src, be, [&](int f, F2 r, F2) { rbuf[f * C::kThreads + tid] = r; });
   if constexpr (NARR > 0)
-    write_fields_staged<FORM, NARR>(a, s, c, rbuf + tid, C::kThreads, src, ly * 32 + px);
+    write_fields_staged<FORM, NARR, BATCH>(a, s, c, rbuf + tid, C::kThreads, src, ly * 32 + px, vm);
   else
     write_fields_pair<FORM>(a, s, c, i, j, k, rbuf + tid, C::kThreads);
-  write_yz_images(a, s, c, i, j, k, rbuf + tid, C::kThreads);
+  write_yz_images<BATCH>(a, s, c, i, j, k, rbuf + tid, C::kThreads, vm);
   if constexpr (NARR > 0) {
     if (s.ghosts && s.mode == 0) {
       __syncthreads();  // every new value of the tile is in rbuf
-      write_x_images(a, s, blockIdx.x, gridDim.x, blockIdx.y * C::BY, k, rbuf, C::kThreads, tid);
+      write_x_images(a, s, x0, y0, k, rbuf, C::kThreads, tid);
     }
     src.final_finish();
   }
+}
+
+template <typename H2, int W, int KS, int FORM>
+__global__ void __launch_bounds__(32 * W, 1)
+    z4_pair_kernel(const __grid_constant__ CUtensorMap map, PatchArgs<float> a, StageArgs s,
+                   Z4Coef<float> zc, const __grid_constant__ PairCoef pc,
+                   const __grid_constant__ RkMaps rk) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  // planes next to the z faces first (their tiles also write the z images, the
+  // slowest tiles), so that the partial last wave holds plain tiles
+  const int k = (int)((blockIdx.z + 3 * gridDim.z - 3) % gridDim.z);
+  pair_tile<H2, W, KS, FORM, false>(&map, rk.m, a, s, zc, &pc, blockIdx.x * 32,
+                                    blockIdx.y * PCfg<W, KS>::BY, k, smem);
+}
+
+// The same over the tiles of many patches (the float CCZ4 patches of a batch
+// on the two-point layout): one CTA per tile, the tile's patch from `tl`, its
+// stage arguments and stencil weights copied into shared memory, its tensor
+// maps from `maps` (six per patch: RK chunks of U^n, accumulator and Kahan
+// term, then the stencil boxes of the u_n, u_stage and u_next buffer roles;
+// `role` picks the stage input).
+template <typename H2, int W, int KS, int FORM>
+__global__ void __launch_bounds__(32 * W, 1)
+    z4_pair_batch_kernel(const CUtensorMap* __restrict__ maps, int role,
+                         const PatchArgs<float>* __restrict__ args, const PairCoef* __restrict__ coefs,
+                         const TmaTile* __restrict__ tl, StageArgs s, Z4Coef<float> zc) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ PatchArgs<float> pa;
+  __shared__ PairCoef pcs;
+  const TmaTile w = tl[blockIdx.x];
+  {
+    static_assert(sizeof(PatchArgs<float>) % 4 == 0 && sizeof(PairCoef) % 4 == 0, "word copy");
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int* from = reinterpret_cast<const int*>(args + w.patch);
+    int* to = reinterpret_cast<int*>(&pa);
+    for (int q = tid; q < (int)(sizeof(PatchArgs<float>) / 4); q += 32 * W) to[q] = from[q];
+    from = reinterpret_cast<const int*>(coefs + w.patch);
+    to = reinterpret_cast<int*>(&pcs);
+    for (int q = tid; q < (int)(sizeof(PairCoef) / 4); q += 32 * W) to[q] = from[q];
+  }
+  // (pair_tile's first barrier orders these copies before their reads)
+  const CUtensorMap* pm = maps + 6 * (size_t)w.patch;
+  pair_tile<H2, W, KS, FORM, true>(pm + 3 + role, pm, pa, s, zc, &pcs, w.x0, w.y0, w.z0, smem);
 }
 
 namespace {
@@ -753,6 +828,88 @@ sf_status launch_z4_pair(const sf_params& prm, const sf_patch& p, const StageArg
                          void* rhs_out, cudaStream_t st) {
   if (p.precision == SF_FP32_BULK_DW) return launch_pair<DW2>(prm, p, s, stage, rhs_out, st);
   return launch_pair<D2>(prm, p, s, stage, rhs_out, st);
+}
+
+// Batch form: float CCZ4 with double-word islands, centred advection, 3
+// ghosts, row / plane / field pitches of a multiple of 4 floats with room for
+// the float before each row (row pitch >= n0 + 7), every array 4 bytes past
+// a 16-byte boundary; any interior size (tiles may overhang).
+bool z4_pair_batch_eligible(const sf_params& prm, const sf_patch& p) {
+  if (p.system != SF_Z4 || p.precision != SF_FP32_BULK_DW || prm.lopsided) return false;
+  if (p.ghost != 3 || p.sy % 4 || p.sz % 4 || p.sf % 4 || p.sy < p.n[0] + 7) return false;
+  for (const void* q : {(const void*)p.u_n, (const void*)p.u_stage, (const void*)p.u_next,
+                        (const void*)p.acc, (const void*)p.kahan})
+    if (!offset_aligned(q)) return false;
+  return true;
+}
+
+size_t z4_pair_coef_bytes() { return sizeof(PairCoef); }
+
+// The six tensor maps of a batch patch (RK chunks of u_n, acc, kahan; stencil
+// boxes of u_n, u_stage, u_next) and its stencil weights.
+sf_status encode_z4_pair_batch(void* maps6, void* coef, const sf_params& prm, const sf_patch& p) {
+  using C = PCfg<kW, kKS>;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn_pair();
+  if (!enc) return set_error(SF_ECUDA, "cuTensorMapEncodeTiled not available");
+  const cuuint64_t dims[4] = {(cuuint64_t)(p.n[0] + 7), (cuuint64_t)(p.n[1] + 6),
+                              (cuuint64_t)(p.n[2] + 6), 25};
+  const cuuint64_t strides[3] = {(cuuint64_t)p.sy * 4, (cuuint64_t)p.sz * 4, (cuuint64_t)p.sf * 4};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const cuuint32_t rbox[4] = {32, (cuuint32_t)C::BY, 1, kRkChunk};
+  const cuuint32_t sbox[4] = {kXB, (cuuint32_t)C::TY, kTZ, 1};
+  const void* arr[6] = {p.u_n, p.acc, p.kahan, p.u_n, p.u_stage, p.u_next};
+  for (int q = 0; q < 6; ++q) {
+    CUtensorMap m;
+    memset(&m, 0, sizeof(m));
+    // tensor x = ghosted x + 1: the map starts at the float before ghost point 0
+    CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                     static_cast<char*>(const_cast<void*>(arr[q])) - 4, dims, strides,
+                     q < 3 ? rbox : sbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(SF_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    memcpy(static_cast<char*>(maps6) + q * sizeof(CUtensorMap), &m, sizeof(m));
+  }
+  const PairCoef pc = pair_coef(prm, p);
+  memcpy(coef, &pc, sizeof(pc));
+  return SF_OK;
+}
+
+sf_status launch_z4_pair_batch(const sf_params& prm, const void* d_maps, int role,
+                               const PatchArgs<float>* d_args, const void* d_coefs,
+                               const TmaTile* d_tiles, int ntiles, const StageArgs& s,
+                               cudaStream_t st) {
+  if (ntiles <= 0) return SF_OK;
+  using C = PCfg<kW, kKS>;
+  const int form = rk_form(s);
+  if (form == kRkGeneric) return set_error(SF_EINVAL, "batched two-point tiles need the RK4 Kahan forms");
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(z4_pair_batch_kernel<DW2, kW, kKS, kRk4First>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    cudaFuncSetAttribute(z4_pair_batch_kernel<DW2, kW, kKS, kRk4Mid>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    cudaFuncSetAttribute(z4_pair_batch_kernel<DW2, kW, kKS, kRk4Last>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+  });
+  const Z4Coef<float> zc = z4_coef<float>(prm);
+  const CUtensorMap* maps = static_cast<const CUtensorMap*>(d_maps);
+  const PairCoef* coefs = static_cast<const PairCoef*>(d_coefs);
+  const dim3 block(32, kW, 1);
+  switch (form) {
+    case kRk4First:
+      z4_pair_batch_kernel<DW2, kW, kKS, kRk4First><<<ntiles, block, C::kSmemBytes, st>>>(
+          maps, role, d_args, coefs, d_tiles, s, zc);
+      break;
+    case kRk4Mid:
+      z4_pair_batch_kernel<DW2, kW, kKS, kRk4Mid><<<ntiles, block, C::kSmemBytes, st>>>(
+          maps, role, d_args, coefs, d_tiles, s, zc);
+      break;
+    default:
+      z4_pair_batch_kernel<DW2, kW, kKS, kRk4Last><<<ntiles, block, C::kSmemBytes, st>>>(
+          maps, role, d_args, coefs, d_tiles, s, zc);
+  }
+  return after_launch("z4_pair_batch_kernel");
 }
 
 }  // namespace sf

@@ -20,9 +20,11 @@ def lib():
     return capi.lib()
 
 
-def make_states(table, precision, seed=0, tma_pitch=False):
+def make_states(table, precision, seed=0, tma_pitch=False, pair_layout=False):
     """tma_pitch: CCZ4 rows padded to a multiple of 4 floats, so that a float
-    batch sends those patches to the TMA-staged kernel."""
+    batch sends those patches to the TMA-staged kernel.  pair_layout: CCZ4
+    rows of a multiple of 4 floats with one float before each row, so that a
+    double-word batch sends them to the two-point kernel."""
     states = []
     for q, t in enumerate(table):
         n = t["n"]
@@ -33,10 +35,13 @@ def make_states(table, precision, seed=0, tma_pitch=False):
             U0 = U0 * 1e-2
         else:
             U0, _ = inputs.z4_perturbed(n, seed=seed + q, amp=0.03)
-        pitch = None
+        pitch, xo = None, 0
         if tma_pitch and system == capi.SF_Z4:
             pitch = (n[0] + 6 + 3) // 4 * 4
-        st = PatchState(system, n, (h, h, h), t["dt"], precision=precision, x_pitch=pitch)
+        if pair_layout and system == capi.SF_Z4:
+            pitch, xo = (n[0] + 7 + 3) // 4 * 4, 1
+        st = PatchState(system, n, (h, h, h), t["dt"], precision=precision, x_pitch=pitch,
+                        x_offset=xo)
         st.upload(U0)
         st.U0 = U0
         states.append(st)
@@ -271,3 +276,108 @@ def test_batch_tune_measures_tma_tile_width():
     finally:
         capi.sf_batch_destroy(ba)
         capi.sf_batch_destroy(bc)
+
+
+# ------------------------------------------------------------------ two-point CCZ4 tiles
+def test_batch_pair_tiles_equal_per_patch_launches():
+    # double-word CCZ4 patches on the one-float row offset layout go to the
+    # two-point kernel in 32 x 16 tiles that overhang every patch here (sizes
+    # 6..21, odd ones included), the wave patches to the persistent kernel;
+    # per-patch launches run the global-load kernel on the same layouts
+    table = small_table(10, seed=11)
+    ref_states = make_states(table, capi.SF_FP32_BULK_DW, pair_layout=True)
+    for st in ref_states:
+        st.step(2)
+    states = make_states(table, capi.SF_FP32_BULK_DW, pair_layout=True)
+    b = capi.sf_batch_create(capi.params(), batch_patches(states))
+    try:
+        assert capi.sf_batch_launches_per_step(b) == 8  # two-point tiles + persistent, 4 stages
+        for _ in range(2):
+            for s in range(4):
+                capi.sf_batch_substep(b, s, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert capi.sf_get_device_status() == capi.SF_OK
+        for st, ref in zip(states, ref_states):
+            a, r = st.interior(), ref.interior()
+            scale = r.abs().amax(dim=(1, 2, 3)).clamp_min(1e-2)
+            err = ((a - r).abs().amax(dim=(1, 2, 3)) / scale).max().item()
+            assert err < fp_bound(capi.SF_FP32_BULK_DW, st), err
+            # the periodic ghost shell written by the tiles equals a fresh fill
+            g = st.A.clone()
+            st.fill_ghosts(g)
+            torch.cuda.synchronize()
+            assert torch.equal(g, st.A)
+    finally:
+        capi.sf_batch_destroy(b)
+
+
+def test_batch_pair_tiles_match_oracle_through_graph():
+    # sizes across the 32 x 16 tile edges, odd widths included, one RK4 step
+    # through the captured graph against the FP64 oracle (float bound of the
+    # single-patch TMA test)
+    eps32 = float(np.finfo(np.float32).eps)
+    states = []
+    for q, n in enumerate(((32, 16, 4), (33, 17, 5), (7, 25, 3), (45, 11, 6), (64, 32, 3))):
+        U0, dx = inputs.z4_perturbed(n, seed=40 + q, amp=0.05)
+        st = PatchState(capi.SF_Z4, n, dx, 0.25 * min(dx), precision=capi.SF_FP32_BULK_DW,
+                        x_pitch=(n[0] + 7 + 3) // 4 * 4, x_offset=1)
+        st.upload(U0)
+        st.U0 = U0
+        states.append(st)
+    b = capi.sf_batch_create(capi.params(), batch_patches(states))
+    stream = torch.cuda.Stream()
+    try:
+        assert capi.sf_batch_launches_per_step(b) == 4  # one two-point launch per stage
+        with torch.cuda.stream(stream):
+            capi.sf_batch_tune(b, stream.cuda_stream)
+            capi.sf_batch_capture(b, stream.cuda_stream)
+            capi.sf_batch_launch(b, stream.cuda_stream)
+        stream.synchronize()
+        assert capi.sf_get_device_status() == capi.SF_OK
+    finally:
+        capi.sf_batch_destroy(b)
+    for st in states:
+        G = oracle.ghosted(st.U0.copy())
+        oracle.rk4_step(oracle.Z4, G, st.dx, st.dt, oracle.params())
+        want = oracle.interior(G)
+        got = st.fields().cpu().numpy()
+        bound = 4 * 64 / 12 * eps32 * st.dt / min(st.dx) ** 2 / 1e-2
+        for f in range(want.shape[0]):
+            e = np.abs(got[f] - want[f]).max() / max(np.abs(want[f]).max(), 1e-2)
+            assert e < bound, (st.n, f, e, bound)
+
+
+def test_batch_pair_tiles_write_every_ghost_and_no_padding():
+    # scratch roles and row padding filled with NaN: after a step through the
+    # two-point tiles every ghosted point of the new state is finite, the
+    # padding (the float before each row, the row tails, the extra plane
+    # rows) is still NaN, and the state equals a clean run bit for bit
+    shapes = ((33, 17, 5), (45, 11, 6))
+    def run(poison):
+        states = []
+        for q, n in enumerate(shapes):
+            U0, dx = inputs.z4_perturbed(n, seed=60 + q, amp=0.05)
+            st = PatchState(capi.SF_Z4, n, dx, 0.25 * min(dx), precision=capi.SF_FP32_BULK_DW,
+                            x_pitch=(n[0] + 7 + 3) // 4 * 4 + 4, x_offset=1, plane_rows=n[1] + 8)
+            if poison:
+                for t in (st.A, st.B, st.C, st.D):
+                    t.fill_(float("nan"))
+            st.upload(U0)
+            states.append(st)
+        b = capi.sf_batch_create(capi.params(), batch_patches(states))
+        try:
+            for s in range(4):
+                capi.sf_batch_substep(b, s, torch.cuda.current_stream().cuda_stream)
+            torch.cuda.synchronize()
+        finally:
+            capi.sf_batch_destroy(b)
+        return states
+    clean, dirty = run(False), run(True)
+    for c_, d_ in zip(clean, dirty):
+        n, xo, g = d_.n, d_.xo, d_.g
+        box = d_.A[:, :, :n[1] + 2 * g, xo:xo + n[0] + 2 * g]
+        assert torch.isfinite(box).all()
+        assert torch.isnan(d_.A[..., 0]).all()                      # before each row
+        assert torch.isnan(d_.A[..., xo + n[0] + 2 * g:]).all()     # row tails
+        assert torch.isnan(d_.A[:, :, n[1] + 2 * g:, :]).all()      # extra plane rows
+        assert torch.equal(box, c_.A[:, :, :n[1] + 2 * g, xo:xo + n[0] + 2 * g])
