@@ -26,6 +26,12 @@ sf_status launch_z4_tma(const sf_params& prm, const sf_patch& p, const StageArgs
 bool z4_pair_eligible(const sf_params& prm, const sf_patch& p, const void* rhs_out);
 sf_status launch_z4_pair(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                          void* rhs_out, cudaStream_t st);
+// the same tile body for any patch size on that layout (runtime strides,
+// overhanging tiles; double-word islands, RK4 Kahan stage forms)
+bool z4_pair_any_eligible(const sf_params& prm, const sf_patch& p, const StageArgs& s,
+                          const void* rhs_out);
+sf_status launch_z4_pair_any(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
+                             cudaStream_t st);
 // TMA-staged CCZ4 kernel over the tiles of many patches (sf_z4_tma.cu), for
 // sf_batch: 32 x 12 x 1 or 16 x 24 x 1 tiles (a patch's maps are encoded for
 // its tile width), tensor maps in device memory (3 per patch: u_n, u_stage,

@@ -57,6 +57,7 @@ static sf_status launch(const sf_params& prm, const sf_patch& p, const StageArgs
 sf_status launch_z4(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                     void* rhs_out, cudaStream_t st) {
   if (z4_pair_eligible(prm, p, rhs_out)) return launch_z4_pair(prm, p, s, stage, rhs_out, st);
+  if (z4_pair_any_eligible(prm, p, s, rhs_out)) return launch_z4_pair_any(prm, p, s, stage, st);
   if (z4_tma_any_eligible(prm, p)) return launch_z4_tma(prm, p, s, stage, rhs_out, st);
   if (p.precision == SF_FP64) return launch<double, double>(prm, p, s, stage, rhs_out, st);
   if (p.precision == SF_FP32_BULK_DW) return launch<float, dw>(prm, p, s, stage, rhs_out, st);

@@ -675,6 +675,19 @@ __global__ void __launch_bounds__(32 * W, 1)
                                     blockIdx.y * PCfg<W, KS>::BY, k, smem);
 }
 
+// Any patch size on the one-float row offset layout (runtime strides, tiles
+// that overhang the patch), the RK4 Kahan forms: one CTA per 32 x 16 tile.
+template <typename H2, int W, int KS, int FORM>
+__global__ void __launch_bounds__(32 * W, 1)
+    z4_pair_any_kernel(const __grid_constant__ CUtensorMap map, PatchArgs<float> a, StageArgs s,
+                       Z4Coef<float> zc, const __grid_constant__ PairCoef pc,
+                       const __grid_constant__ RkMaps rk) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int k = (int)((blockIdx.z + 3 * gridDim.z - 3) % gridDim.z);
+  pair_tile<H2, W, KS, FORM, true>(&map, rk.m, a, s, zc, &pc, blockIdx.x * 32,
+                                   blockIdx.y * PCfg<W, KS>::BY, k, smem);
+}
+
 // The same over the tiles of many patches (the float CCZ4 patches of a batch
 // on the two-point layout): one CTA per tile, the tile's patch from `tl`, its
 // stage arguments and stencil weights copied into shared memory, its tensor
@@ -725,7 +738,7 @@ bool offset_aligned(const void* q) {
   return q && reinterpret_cast<uintptr_t>(q) % 16 == 4;
 }
 
-template <typename H2>
+template <typename H2, bool ANY = false>
 sf_status launch_pair(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                       void* rhs_out, cudaStream_t st) {
   using C = PCfg<kW, kKS>;
@@ -754,6 +767,14 @@ sf_status launch_pair(const sf_params& prm, const sf_patch& p, const StageArgs& 
                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     cudaFuncSetAttribute(z4_pair_kernel<H2, kW, kKS, kRk4Last>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    if constexpr (ANY) {
+      cudaFuncSetAttribute(z4_pair_any_kernel<H2, kW, kKS, kRk4First>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+      cudaFuncSetAttribute(z4_pair_any_kernel<H2, kW, kKS, kRk4Mid>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+      cudaFuncSetAttribute(z4_pair_any_kernel<H2, kW, kKS, kRk4Last>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    }
   });
   PatchArgs<float> a = make_args<float>(prm, p, stage, 25, rhs_out);
   const Z4Coef<float> zc = z4_coef<float>(prm);
@@ -781,8 +802,22 @@ sf_status launch_pair(const sf_params& prm, const sf_patch& p, const StageArgs& 
       if (rr != CUDA_SUCCESS) return set_error(SF_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)rr);
     }
   }
-  dim3 grid(p.n[0] / 32, p.n[1] / C::BY, p.n[2]);
   const dim3 block(32, kW, 1);
+  if constexpr (ANY) {
+    const dim3 grid((p.n[0] + 31) / 32, (p.n[1] + C::BY - 1) / C::BY, p.n[2]);
+    switch (form) {
+      case kRk4First:
+        z4_pair_any_kernel<H2, kW, kKS, kRk4First><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc, pc, rk);
+        break;
+      case kRk4Mid:
+        z4_pair_any_kernel<H2, kW, kKS, kRk4Mid><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc, pc, rk);
+        break;
+      default:
+        z4_pair_any_kernel<H2, kW, kKS, kRk4Last><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc, pc, rk);
+    }
+    return after_launch("z4_pair_any_kernel");
+  }
+  dim3 grid(p.n[0] / 32, p.n[1] / C::BY, p.n[2]);
   switch (form) {
     case kRk4First:
       z4_pair_kernel<H2, kW, kKS, kRk4First><<<grid, block, C::kSmemBytes, st>>>(map, a, s, zc, pc, rk);
@@ -828,6 +863,20 @@ sf_status launch_z4_pair(const sf_params& prm, const sf_patch& p, const StageArg
                          void* rhs_out, cudaStream_t st) {
   if (p.precision == SF_FP32_BULK_DW) return launch_pair<DW2>(prm, p, s, stage, rhs_out, st);
   return launch_pair<D2>(prm, p, s, stage, rhs_out, st);
+}
+
+// Any size on the one-float row offset layout: double-word islands, the RK4
+// Kahan stage forms, pitches of a multiple of 4 floats with room for the
+// float before each row, every array 4 bytes past a 16-byte boundary.
+bool z4_pair_any_eligible(const sf_params& prm, const sf_patch& p, const StageArgs& s,
+                          const void* rhs_out) {
+  if (rhs_out || rk_form(s) == kRkGeneric) return false;
+  return z4_pair_batch_eligible(prm, p);
+}
+
+sf_status launch_z4_pair_any(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
+                             cudaStream_t st) {
+  return launch_pair<DW2, true>(prm, p, s, stage, nullptr, st);
 }
 
 // Batch form: float CCZ4 with double-word islands, centred advection, 3

@@ -486,6 +486,26 @@ def test_z4_tma_any_size_matches_oracle(precision, n):
         assert rel_err(got[s], dense[s], floor=1e-2).max() < bound, s
 
 
+# Any patch size on the two-point layout (rows of a multiple of 4 floats with
+# one float before each row): the two-point tile body with runtime strides and
+# 32 x 16 tiles overhanging the patch, odd widths included.  Against the
+# oracle with the float bound, and against the global-load kernel on dense rows.
+@pytest.mark.parametrize("n", [(37, 13, 5), (48, 21, 4), (7, 40, 3)])
+def test_z4_two_point_any_size_matches_oracle(n):
+    U0, dx = inputs.z4_perturbed(n, seed=8, amp=0.05)
+    prm = capi.params()
+    dt = 0.25 * min(dx)
+    eps32 = float(np.finfo(np.float32).eps)
+    bound = 4 * 64 / 12 * eps32 * dt / min(dx) ** 2 / 1e-2
+    got = run_stages(capi.SF_Z4, U0, dx, dt, prm, precision=capi.SF_FP32_BULK_DW,
+                     pitch=(n[0] + 7 + 3) // 4 * 4, x_offset=1)
+    dense = run_stages(capi.SF_Z4, U0, dx, dt, prm, precision=capi.SF_FP32_BULK_DW)
+    want = oracle_stages(oracle.Z4, U0, dx, dt, prm)
+    for s in range(4):
+        assert rel_err(got[s], want[s], floor=1e-2).max() < bound, s
+        assert rel_err(got[s], dense[s], floor=1e-2).max() < bound, s
+
+
 @pytest.mark.parametrize("x_offset", [0, 1])
 def test_z4_tma_kernel_frozen_shift_gauge_wave(x_offset):
     # harmonic slicing and a frozen shift: the last three fields' stencils are

@@ -10,7 +10,9 @@ still be NaN; the final state must equal, bit for bit, the state of the same
 step run on clean buffers.  Covers the global-load, compile-time-stride and
 runtime TMA-staged CCZ4 kernels (the latter with tiles overhanging the
 patch), the two-point CCZ4 kernel (rows with one float before the first ghost
-point, also poisoned), the wave and MHD kernels, and the batched dispatch.
+point, also poisoned; whole tiles with compile-time strides, and any size with
+tiles overhanging the patch), the wave and MHD kernels, and the batched
+dispatch.
 """
 import pytest
 import torch
@@ -63,6 +65,8 @@ CASES = [
     (capi.SF_Z4, (32, 96, 3), capi.SF_FP32_BULK_DW, 104, 0),  # TMA, compile-time strides
     (capi.SF_Z4, (32, 96, 3), capi.SF_FP32_BULK_DW, 104, 1),  # two-point kernel
     (capi.SF_Z4, (32, 96, 3), capi.SF_FP32_BULK, 104, 1),     # two-point kernel, FP64 islands
+    (capi.SF_Z4, (37, 13, 5), capi.SF_FP32_BULK_DW, 48, 1),   # two-point, any size, overhanging tiles
+    (capi.SF_Z4, (48, 21, 4), capi.SF_FP32_BULK_DW, 56, 1),   # two-point, any size, even width
     (capi.SF_Z4, (11, 9, 7), capi.SF_FP64, 19, 0),
     (capi.SF_WAVE, (19, 7, 6), capi.SF_FP32_BULK, 27, 0),
     (capi.SF_WAVE, (19, 7, 6), capi.SF_FP64, 26, 0),
