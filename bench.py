@@ -242,13 +242,13 @@ def time_e2e(st, steps: int, warmup: int, chained: bool):
     previous step's output, one pinned buffer updated in place, one device
     slot whose Kahan compensation carries over): the copies and the stages
     of a step are serial.  Otherwise: independent states (the same input
-    every step, outputs alternating between two pinned buffers), two device
-    slots, the copies of neighbouring steps overlapping the stages on copy
+    every step, outputs alternating between two pinned buffers), three
+    device slots, the copies of other steps overlapping the stages on copy
     streams of their own.  The timed region spans all three streams."""
     import torch
     from paper_1806_04182_gb300.state import HostPipeline
     pipe = HostPipeline(st.system, st.n, st.dx, st.dt, precision=st.precision, prm=st.prm,
-                        ghost=st.g, x_pitch=st.pitch, x_offset=st.xo, slots=1 if chained else 2)
+                        ghost=st.g, x_pitch=st.pitch, x_offset=st.xo, slots=1 if chained else 3)
     host_in = pipe.host_buffer()
     host_in.copy_(pipe.image(st.A).cpu())
     if chained:
@@ -428,8 +428,8 @@ def gpu_arm(args):
                         "into the buffer the next step uploads (copies and stages serial)",
                 "independent_states": {
                     "value": ind_value, "unit": UNIT,
-                    "path": "sf_step_host with two device slots: a new state every step (same input), "
-                            "the copies of neighbouring steps overlapping the stages on copy streams"}},
+                    "path": "sf_step_host with three device slots: a new state every step (same input), "
+                            "the copies of other steps overlapping the stages on copy streams"}},
         "gpu_launches": int(r32["launches"]),
         "clocks": clocks,
     }

@@ -196,13 +196,16 @@ int64_t sf_state_span(const sf_patch* geom);
  * -> u for RK4, u -> s1 -> s2 -> u for SSP-RK3), and U^{n+1} is copied from
  * slot.u to host_out[k] on d2h_stream.
  *   geom: n, ghost, dx, strides, dt, system, precision of every step (its
- *         pointer fields are ignored); nslots: 1 or 2 device states.
- *   Ordering: with two slots the upload of step k + 1 and the download of
- *   step k - 1 overlap the stages of step k.  An upload waits for the
- *   download of the step that last used its slot and, when host_in[k]
- *   overlaps host_out[k - 1], for that download, so an evolution kept in
- *   host memory (host_in[k] = host_out[k - 1]) is correct with either slot
- *   count.  The first upload of a call waits for the work already queued on
+ *         pointer fields are ignored); nslots: 1 to 4 device states.
+ *   Ordering: with two or more slots the uploads of later steps and the
+ *   downloads of earlier ones overlap the stages of step k.  An upload waits
+ *   for the download of the step that last used its slot and, when host_in[k]
+ *   overlaps the host_out of a step still in flight, for that download, so
+ *   an evolution kept in host memory (host_in[k] = host_out[k - 1]) is
+ *   correct with any slot count.  With two slots the upload of step k + 1
+ *   waits for the download of step k - 1; with three it does not, so
+ *   independent steps run at the rate of the stages when the copies are
+ *   shorter.  The first upload of a call waits for the work already queued on
  *   compute_stream and d2h_stream (earlier calls).
  *   Kahan compensation: with SF_HOST_RESET_KAHAN it restarts from zero at
  *   every upload (independent states); without it the slot's compensation
@@ -212,7 +215,7 @@ int64_t sf_state_span(const sf_patch* geom);
  *   host_out[k] holds U^{n+1} once d2h_stream has passed the call's work.
  *   NULL h2d_stream or d2h_stream means compute_stream.
  * Asynchronous.  Errors (SF_EINVAL, nothing enqueued): NULL arguments,
- * nslots not 1 or 2, unknown flags, a slot the stages would reject.
+ * nslots not in 1..4, unknown flags, a slot the stages would reject.
  */
 sf_status sf_step_host(const sf_params* prm, const sf_patch* geom, const sf_state* slots,
                        int32_t nslots, const void* const* host_in, void* const* host_out,

@@ -1,10 +1,13 @@
 // RK steps of patch states held in host memory: each step copies its input
 // state to the device, runs every stage of the RK method there (Sec. II.C,
 // the fused substep of sf_substep) and copies the new state back.  With two
-// device slots the upload of step k + 1 and the download of step k - 1 run on
-// copy streams of their own while step k computes; a step whose input is an
-// earlier step's output (an evolution kept in host memory) waits for that
-// download first.
+// or more device slots the uploads of the next steps and the downloads of the
+// previous ones run on copy streams of their own while a step computes (a
+// slot is uploaded again once the download of its previous step is done, so
+// with three slots an upload no longer waits on the download just before it);
+// a step whose input is an earlier step's output (an evolution kept in host
+// memory) waits for that download first.
+#include <algorithm>
 #include <cstring>
 
 #include "sf_internal.cuh"
@@ -15,9 +18,10 @@ namespace {
 // Events of the pipeline, per host thread and device; created once and kept
 // (a step's events are re-recorded two steps later, after every wait on
 // them has been enqueued).
+constexpr int kMaxSlots = 4;
 struct HostEvents {
   int dev = -1;
-  cudaEvent_t up[2], comp[2], down[2], entry;
+  cudaEvent_t up[kMaxSlots], comp[kMaxSlots], down[kMaxSlots], entry;
 };
 thread_local HostEvents t_ev;
 
@@ -26,7 +30,13 @@ sf_status host_events(HostEvents** out) {
   if (cudaGetDevice(&dev) != cudaSuccess) return set_error(SF_ECUDA, "no CUDA device");
   HostEvents& e = t_ev;
   if (e.dev != dev) {
-    cudaEvent_t* all[7] = {&e.up[0], &e.up[1], &e.comp[0], &e.comp[1], &e.down[0], &e.down[1], &e.entry};
+    cudaEvent_t* all[3 * kMaxSlots + 1];
+    for (int q = 0; q < kMaxSlots; ++q) {
+      all[3 * q] = &e.up[q];
+      all[3 * q + 1] = &e.comp[q];
+      all[3 * q + 2] = &e.down[q];
+    }
+    all[3 * kMaxSlots] = &e.entry;
     if (e.dev >= 0)
       for (cudaEvent_t* q : all) cudaEventDestroy(*q);
     e.dev = -1;
@@ -67,7 +77,8 @@ sf_status sf_step_host(const sf_params* prm, const sf_patch* geom, const sf_stat
                        int32_t nsteps, uint32_t flags, void* compute_stream, void* h2d_stream,
                        void* d2h_stream) {
   if (!prm || !geom || !slots || !host_in || !host_out) return set_error(SF_EINVAL, "NULL argument");
-  if (nslots < 1 || nslots > 2) return set_error(SF_EINVAL, "nslots = %d not 1 or 2", nslots);
+  if (nslots < 1 || nslots > kMaxSlots)
+    return set_error(SF_EINVAL, "nslots = %d not in 1..%d", nslots, kMaxSlots);
   if (nsteps < 0) return set_error(SF_EINVAL, "nsteps = %d < 0", nsteps);
   if (flags & ~SF_HOST_RESET_KAHAN) return set_error(SF_EINVAL, "unknown flags 0x%x", flags);
   const int nst = prm->rk == SF_RK4 ? 4 : (prm->rk == SF_SSPRK3 ? 3 : 0);
@@ -112,13 +123,15 @@ sf_status sf_step_host(const sf_params* prm, const sf_patch* geom, const sf_stat
     return set_error(SF_ECUDA, "stream ordering failed");
   for (int k = 0; k < nsteps; ++k) {
     const sf_state& d = slots[k % nslots];
-    const int b = k & 1;
-    // the slot's previous download, and a download this input depends on
-    if (k >= nslots && cudaStreamWaitEvent(up, ev->down[(k - nslots) & 1], 0) != cudaSuccess)
+    const int b = k % nslots;
+    // the slot's previous download, and the downloads this input depends on
+    // (an earlier step of this call whose output it overlaps)
+    if (k >= nslots && cudaStreamWaitEvent(up, ev->down[b], 0) != cudaSuccess)
       return set_error(SF_ECUDA, "stream ordering failed");
-    if (nslots == 2 && k >= 1 && overlap(host_in[k], host_out[k - 1], bytes) &&
-        cudaStreamWaitEvent(up, ev->down[(k - 1) & 1], 0) != cudaSuccess)
-      return set_error(SF_ECUDA, "stream ordering failed");
+    for (int j = std::max(0, k - nslots + 1); j < k; ++j)
+      if (overlap(host_in[k], host_out[j], bytes) &&
+          cudaStreamWaitEvent(up, ev->down[j % nslots], 0) != cudaSuccess)
+        return set_error(SF_ECUDA, "stream ordering failed");
     if (cudaMemcpyAsync(d.u, host_in[k], bytes, cudaMemcpyHostToDevice, up) != cudaSuccess)
       return set_error(SF_ECUDA, "upload of step %d failed", k);
     if ((flags & SF_HOST_RESET_KAHAN) && cudaMemsetAsync(d.kahan, 0, bytes, up) != cudaSuccess)

@@ -289,8 +289,9 @@ class HostPipeline:
     :meth:`host_buffer` a pinned buffer of that size).  ``run(host_in,
     host_out)`` advances one RK step per entry: upload of ``host_in[k]``,
     the stages, download into ``host_out[k]``, on three streams of the
-    pipeline.  With ``slots=2`` the copies of neighbouring steps overlap the
-    stages; a step whose input is an earlier step's output waits for that
+    pipeline.  With ``slots`` of 2 to 4 the copies of other steps overlap the
+    stages (with 3 an upload no longer waits for the download just before
+    it); a step whose input is an earlier step's output waits for that
     download, so an evolution kept in host memory (``host_in[k] is
     host_out[k - 1]``) is correct.  ``reset_kahan`` restarts the FP32-bulk
     compensation from zero at every upload (independent states); without

@@ -159,7 +159,7 @@ def test_step_host_rejects_bad_arguments(L):
     slot = capi.sf_state(u=base, s1=2 * base, s2=3 * base, acc=4 * base, kahan=None)
     prm = capi.params()
     with pytest.raises(capi.SfError, match="nslots"):
-        capi.sf_step_host(prm, p, [slot] * 3, [base], [base])
+        capi.sf_step_host(prm, p, [slot] * 5, [base], [base])
     with pytest.raises(capi.SfError, match="flags"):
         capi.sf_step_host(prm, p, [slot], [base], [base], flags=4)
     with pytest.raises(capi.SfError, match="SF_HOST_RESET_KAHAN"):

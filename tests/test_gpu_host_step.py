@@ -4,10 +4,10 @@
   step's output, one pinned buffer updated in place) equals, bit for bit, the
   same steps run on a device-resident state: FP64 with one and two device
   slots; FP32-bulk with one slot (the Kahan compensation carries over) and
-  with two slots and SF_HOST_RESET_KAHAN (against a device run that zeroes
-  the compensation before every step).
-* Independent steps from one input (two slots, copies overlapping the
-  stages) each equal one device step from that input.
+  with two or three slots and SF_HOST_RESET_KAHAN (against a device run that
+  zeroes the compensation before every step).
+* Independent steps from one input (two or three slots, copies overlapping
+  the stages) each equal one device step from that input.
 """
 import pytest
 import torch
@@ -63,13 +63,13 @@ def pinned_copy(t):
 
 
 @pytest.mark.parametrize("system,n,precision,pitch,xo", CASES)
-@pytest.mark.parametrize("nslots", [1, 2])
+@pytest.mark.parametrize("nslots", [1, 2, 3])
 def test_chained_host_evolution_equals_device_run(system, n, precision, pitch, xo, nslots):
     steps = 6
     ref = make(system, n, precision, pitch, xo)
     work = [make(system, n, precision, pitch, xo) for _ in range(nslots)]
     h = pinned_copy(image(ref, ref.A))
-    reset = precision != capi.SF_FP64 and nslots == 2
+    reset = precision != capi.SF_FP64 and nslots > 1
     for _ in range(steps):
         if reset:
             ref.E.zero_()
@@ -89,7 +89,8 @@ def test_chained_host_evolution_equals_device_run(system, n, precision, pitch, x
 
 
 @pytest.mark.parametrize("system,n,precision,pitch,xo", CASES)
-def test_independent_host_steps_equal_one_device_step(system, n, precision, pitch, xo):
+@pytest.mark.parametrize("nslots", [2, 3])
+def test_independent_host_steps_equal_one_device_step(system, n, precision, pitch, xo, nslots):
     steps = 5
     ref = make(system, n, precision, pitch, xo, seed=3)
     h_in = pinned_copy(image(ref, ref.A))
@@ -98,7 +99,7 @@ def test_independent_host_steps_equal_one_device_step(system, n, precision, pitc
         ref.E.zero_()
     ref.step(1)
     want = image(ref, ref.A).cpu()
-    work = [make(system, n, precision, pitch, xo) for _ in range(2)]
+    work = [make(system, n, precision, pitch, xo) for _ in range(nslots)]
     cs = torch.cuda.current_stream()
     up, down = torch.cuda.Stream(), torch.cuda.Stream()
     up.wait_stream(cs)
