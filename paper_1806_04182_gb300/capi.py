@@ -28,8 +28,9 @@ EXPORTS = ["sf_nfields", "sf_substep", "sf_rhs", "sf_fill_ghosts_periodic", "sf_
            "sf_batch_launch", "sf_batch_launches_per_step", "sf_batch_destroy",
            "sf_batch_set_halo", "sf_batch_substep_static", "sf_copy_boxes", "sf_prolong", "sf_bor_prolong", "sf_bor_prolong_boxes", "sf_radiative_substep",
            "sf_selftest_wait_timeout", "sf_get_device_status", "sf_last_error", "sf_launch_count",
-           "sf_state_span", "sf_step_host", "sf_batch_tuned"]
+           "sf_state_span", "sf_step_host", "sf_batch_tuned", "sf_interior_span"]
 SF_HOST_RESET_KAHAN = 1
+SF_HOST_INTERIOR = 2
 
 
 class SfError(RuntimeError):
@@ -170,6 +171,8 @@ def lib() -> ctypes.CDLL:
                                      i64, i64, i64, vp]
         L.sf_state_span.argtypes = [P(sf_patch)]
         L.sf_state_span.restype = i64
+        L.sf_interior_span.argtypes = [P(sf_patch)]
+        L.sf_interior_span.restype = i64
         L.sf_step_host.argtypes = [P(sf_params), P(sf_patch), P(sf_state), i32, P(vp), P(vp), i32,
                                    ctypes.c_uint32, vp, vp, vp]
         L.sf_batch_tuned.argtypes = [vp, P(i32), P(i32)]
@@ -201,6 +204,10 @@ def _patches(patches):
         patches = [patches]
     arr = (sf_patch * len(patches))(*patches)
     return arr, len(patches)
+
+
+def sf_interior_span(geom: sf_patch) -> int:
+    return int(lib().sf_interior_span(ctypes.byref(geom)))
 
 
 def sf_state_span(geom: sf_patch) -> int:

@@ -54,12 +54,112 @@ bool overlap(const void* a, const void* b, size_t n) {
   return x < y + n && y < x + n;
 }
 
+struct Layout {
+  int n0, n1, n2, g, nf;
+  long long sy, sz, sf;
+};
+
+// Interior host images (SF_HOST_INTERIOR): the dense interior (field, z, y,
+// x) copied into the patch layout, every ghost point taking the interior
+// point congruent to it modulo n (the periodic shell).  Each warp walks whole
+// rows (ghosted rows of every ghosted plane of every field), its lanes along
+// x with four values in flight; a few CTAs per SM loop over the rows.
+__device__ __forceinline__ int wrap(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) interior_scatter_kernel(T* __restrict__ u,
+                                                               const T* __restrict__ dense, Layout L) {
+  const int X = L.n0 + 2 * L.g, Y = L.n1 + 2 * L.g, Z = L.n2 + 2 * L.g;
+  const int rows = L.nf * Z * Y;
+  const int lane = threadIdx.x & 31;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += (gridDim.x * blockDim.x) >> 5) {
+    const int y = r % Y, zf = r / Y, z = zf % Z, f = zf / Z;
+    const int yi = wrap(y - L.g, L.n1), zi = wrap(z - L.g, L.n2);
+    const T* src = dense + (((long long)f * L.n2 + zi) * L.n1 + yi) * L.n0;
+    T* dst = u + f * L.sf + (long long)z * L.sz + (long long)y * L.sy;
+    for (int x0 = 0; x0 < X; x0 += 128) {
+      T v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int x = x0 + 32 * q + lane;
+        if (x < X) v[q] = src[wrap(x - L.g, L.n0)];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int x = x0 + 32 * q + lane;
+        if (x < X) dst[x] = v[q];
+      }
+    }
+  }
+}
+
+// The interior of the patch layout gathered into a dense array, warps along
+// interior rows.
+template <typename T>
+__global__ void __launch_bounds__(256) interior_gather_kernel(T* __restrict__ dense,
+                                                              const T* __restrict__ u, Layout L) {
+  const int rows = L.nf * L.n2 * L.n1;
+  const int lane = threadIdx.x & 31;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += (gridDim.x * blockDim.x) >> 5) {
+    const int y = r % L.n1, zf = r / L.n1, z = zf % L.n2, f = zf / L.n2;
+    const T* src = u + f * L.sf + (long long)(z + L.g) * L.sz + (long long)(y + L.g) * L.sy + L.g;
+    T* dst = dense + (long long)r * L.n0;
+    for (int x0 = 0; x0 < L.n0; x0 += 128) {
+      T v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int x = x0 + 32 * q + lane;
+        if (x < L.n0) v[q] = src[x];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int x = x0 + 32 * q + lane;
+        if (x < L.n0) dst[x] = v[q];
+      }
+    }
+  }
+}
+
+sf_status interior_copy(bool scatter, bool fp64, void* arr, void* dense, const Layout& L,
+                        cudaStream_t st) {
+  const long long rows = scatter ? (long long)L.nf * (L.n2 + 2 * L.g) * (L.n1 + 2 * L.g)
+                                 : (long long)L.nf * L.n2 * L.n1;
+  if (rows > 0x7fffffffLL) return set_error(SF_EINVAL, "patch too large for an interior host image");
+  const int blocks = (int)std::min<long long>((rows + 7) / 8, 152LL * 8);
+  if (scatter) {
+    if (fp64)
+      interior_scatter_kernel<double><<<blocks, 256, 0, st>>>(static_cast<double*>(arr),
+                                                              static_cast<const double*>(dense), L);
+    else
+      interior_scatter_kernel<float><<<blocks, 256, 0, st>>>(static_cast<float*>(arr),
+                                                             static_cast<const float*>(dense), L);
+    return after_launch("interior_scatter_kernel");
+  }
+  if (fp64)
+    interior_gather_kernel<double><<<blocks, 256, 0, st>>>(static_cast<double*>(dense),
+                                                           static_cast<const double*>(arr), L);
+  else
+    interior_gather_kernel<float><<<blocks, 256, 0, st>>>(static_cast<float*>(dense),
+                                                          static_cast<const float*>(arr), L);
+  return after_launch("interior_gather_kernel");
+}
+
 }  // namespace
 }  // namespace sf
 
 using namespace sf;
 
 extern "C" {
+
+int64_t sf_interior_span(const sf_patch* geom) {
+  if (!geom) return -1;
+  const int nf = sf_nfields(geom->system);
+  if (nf < 0) return -1;
+  return (long long)nf * geom->n[0] * geom->n[1] * geom->n[2];
+}
 
 int64_t sf_state_span(const sf_patch* geom) {
   if (!geom) return -1;
@@ -80,12 +180,21 @@ sf_status sf_step_host(const sf_params* prm, const sf_patch* geom, const sf_stat
   if (nslots < 1 || nslots > kMaxSlots)
     return set_error(SF_EINVAL, "nslots = %d not in 1..%d", nslots, kMaxSlots);
   if (nsteps < 0) return set_error(SF_EINVAL, "nsteps = %d < 0", nsteps);
-  if (flags & ~SF_HOST_RESET_KAHAN) return set_error(SF_EINVAL, "unknown flags 0x%x", flags);
+  if (flags & ~(SF_HOST_RESET_KAHAN | SF_HOST_INTERIOR)) return set_error(SF_EINVAL, "unknown flags 0x%x", flags);
+  const bool interior = (flags & SF_HOST_INTERIOR) != 0;
+  if (interior && prm->ghosts != SF_GHOSTS_PERIODIC)
+    return set_error(SF_EINVAL, "SF_HOST_INTERIOR needs periodic ghosts (prm->ghosts)");
   const int nst = prm->rk == SF_RK4 ? 4 : (prm->rk == SF_SSPRK3 ? 3 : 0);
   if (!nst) return set_error(SF_EINVAL, "unknown rk %d", prm->rk);
   const long long span = sf_state_span(geom);
   if (span <= 0) return set_error(SF_EINVAL, "unknown system %d", geom->system);
-  const size_t bytes = (size_t)span * (geom->precision == SF_FP64 ? 8 : 4);
+  const size_t es = geom->precision == SF_FP64 ? 8 : 4;
+  const size_t bytes = (size_t)span * es;
+  // what crosses the host link per step: the state image, or its interior
+  const size_t hbytes = interior ? (size_t)sf_interior_span(geom) * es : bytes;
+  sf_patch gp = *geom;
+  normalise_strides(gp, sf_nfields(gp.system));
+  const Layout lay{gp.n[0], gp.n[1], gp.n[2], gp.ghost, sf_nfields(gp.system), gp.sy, gp.sz, gp.sf};
   // every stage of every slot, checked before anything is enqueued
   for (int q = 0; q < nslots; ++q) {
     const sf_state& d = slots[q];
@@ -129,11 +238,15 @@ sf_status sf_step_host(const sf_params* prm, const sf_patch* geom, const sf_stat
     if (k >= nslots && cudaStreamWaitEvent(up, ev->down[b], 0) != cudaSuccess)
       return set_error(SF_ECUDA, "stream ordering failed");
     for (int j = std::max(0, k - nslots + 1); j < k; ++j)
-      if (overlap(host_in[k], host_out[j], bytes) &&
+      if (overlap(host_in[k], host_out[j], hbytes) &&
           cudaStreamWaitEvent(up, ev->down[j % nslots], 0) != cudaSuccess)
         return set_error(SF_ECUDA, "stream ordering failed");
-    if (cudaMemcpyAsync(d.u, host_in[k], bytes, cudaMemcpyHostToDevice, up) != cudaSuccess)
+    // interior images land in the slot's s2 (stage scratch, free until stage
+    // 1 writes it) and are spread into u with their periodic ghost shell
+    if (cudaMemcpyAsync(interior ? d.s2 : d.u, host_in[k], hbytes, cudaMemcpyHostToDevice, up) !=
+        cudaSuccess)
       return set_error(SF_ECUDA, "upload of step %d failed", k);
+    if (interior && (e = interior_copy(true, geom->precision == SF_FP64, d.u, d.s2, lay, up))) return e;
     if ((flags & SF_HOST_RESET_KAHAN) && cudaMemsetAsync(d.kahan, 0, bytes, up) != cudaSuccess)
       return set_error(SF_ECUDA, "Kahan reset of step %d failed", k);
     if (cudaEventRecord(ev->up[b], up) != cudaSuccess || cudaStreamWaitEvent(cs, ev->up[b], 0) != cudaSuccess)
@@ -151,9 +264,13 @@ sf_status sf_step_host(const sf_params* prm, const sf_patch* geom, const sf_stat
       e = sf_substep(prm, &p, 1, s, compute_stream);
       if (e) return e;
     }
+    // interior images: U^{n+1}'s interior gathered into s2 (free after the
+    // last stage) for the download
+    if (interior && (e = interior_copy(false, geom->precision == SF_FP64, d.u, d.s2, lay, cs))) return e;
     if (cudaEventRecord(ev->comp[b], cs) != cudaSuccess || cudaStreamWaitEvent(dn, ev->comp[b], 0) != cudaSuccess)
       return set_error(SF_ECUDA, "stream ordering failed");
-    if (cudaMemcpyAsync(host_out[k], d.u, bytes, cudaMemcpyDeviceToHost, dn) != cudaSuccess)
+    if (cudaMemcpyAsync(host_out[k], interior ? d.s2 : d.u, hbytes, cudaMemcpyDeviceToHost, dn) !=
+        cudaSuccess)
       return set_error(SF_ECUDA, "download of step %d failed", k);
     if (cudaEventRecord(ev->down[b], dn) != cudaSuccess) return set_error(SF_ECUDA, "event record failed");
   }

@@ -297,12 +297,15 @@ class HostPipeline:
     compensation from zero at every upload (independent states); without
     it the device slot's compensation carries over (a continuing evolution,
     one slot).  ``host_out`` holds the results after :meth:`synchronize` (or
-    once a stream waits on :meth:`join`).
+    once a stream waits on :meth:`join`).  ``interior=True`` (periodic
+    patches): host images hold the interior only (``sf_interior_span``
+    elements, field, z, y, x), the ghost shell rebuilt on the device.
     """
 
-    def __init__(self, *args, slots: int = 2, **kw):
+    def __init__(self, *args, slots: int = 2, interior: bool = False, **kw):
         """Arguments as for ``PatchState`` (one patch description)."""
         self.states = tuple(PatchState(*args, **kw) for _ in range(slots))
+        self.interior = bool(interior)
         cur = torch.cuda.current_stream()
         self.compute = torch.cuda.Stream()
         self.up = torch.cuda.Stream()
@@ -317,7 +320,8 @@ class HostPipeline:
                         t.record_stream(st_)
         st = self.states[0]
         self.geom = st.patch(st.A, st.A, st.B)
-        self.span = capi.sf_state_span(self.geom)
+        self.span = (capi.sf_interior_span(self.geom) if self.interior
+                     else capi.sf_state_span(self.geom))
         self.slots = [capi.sf_state(u=s_.ptr(s_.A), s1=s_.ptr(s_.B), s2=s_.ptr(s_.C),
                                     acc=s_.ptr(s_.D) if s_.D is not None else None,
                                     kahan=s_.ptr(s_.E) if s_.E is not None else None)
@@ -328,8 +332,11 @@ class HostPipeline:
         return self.states[0].dtype
 
     def image(self, array: torch.Tensor) -> torch.Tensor:
-        """The host-image view (span elements from ghosted (0,0,0)) of an array
-        laid out like the pipeline's states."""
+        """The host image of an array laid out like the pipeline's states: a
+        view of span elements from ghosted (0,0,0), or (interior images) a
+        dense copy of the interior."""
+        if self.interior:
+            return self.states[0].interior(array).contiguous().reshape(-1)
         xo = self.states[0].xo
         return array.reshape(-1)[xo:xo + self.span]
 
@@ -339,6 +346,8 @@ class HostPipeline:
     def run(self, host_in, host_out, reset_kahan: bool = True) -> None:
         st = self.states[0]
         flags = capi.SF_HOST_RESET_KAHAN if (reset_kahan and st.E is not None) else 0
+        if self.interior:
+            flags |= capi.SF_HOST_INTERIOR
         capi.sf_step_host(st.prm, self.geom, self.slots, [t.data_ptr() for t in host_in],
                           [t.data_ptr() for t in host_out], flags, self.compute.cuda_stream,
                           self.up.cuda_stream, self.down.cuda_stream)

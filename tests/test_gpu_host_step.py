@@ -113,3 +113,48 @@ def test_independent_host_steps_equal_one_device_step(system, n, precision, pitc
     torch.cuda.synchronize()
     for o in outs:
         assert torch.equal(o, want)
+
+
+# ------------------------------------------------------------------ interior host images
+def interior_image(st, arr):
+    return st.interior(arr).contiguous().reshape(-1)
+
+
+@pytest.mark.parametrize("system,n,precision,pitch,xo", CASES)
+@pytest.mark.parametrize("nslots", [1, 3])
+def test_interior_images_chained_evolution_equals_device_run(system, n, precision, pitch, xo, nslots):
+    # host images without ghost shell or padding: the upload is spread into
+    # the patch layout with its periodic ghost shell on the device, the new
+    # interior gathered back; the evolution kept in host memory equals the
+    # device run bit for bit
+    steps = 4
+    ref = make(system, n, precision, pitch, xo)
+    work = [make(system, n, precision, pitch, xo) for _ in range(nslots)]
+    assert capi.sf_interior_span(ref.patch(ref.A, ref.A, ref.A)) == ref.nf * n[0] * n[1] * n[2]
+    h = pinned_copy(interior_image(ref, ref.A))
+    reset = precision != capi.SF_FP64 and nslots > 1
+    for _ in range(steps):
+        if reset:
+            ref.E.zero_()
+        ref.step(1)
+    cs = torch.cuda.current_stream()
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    up.wait_stream(cs)
+    down.wait_stream(cs)
+    flags = capi.SF_HOST_INTERIOR | (capi.SF_HOST_RESET_KAHAN if reset else 0)
+    capi.sf_step_host(ref.prm, ref.patch(ref.A, ref.A, ref.B), [slot_of(w) for w in work],
+                      [h.data_ptr()] * steps, [h.data_ptr()] * steps, flags=flags,
+                      compute_stream=cs.cuda_stream, h2d_stream=up.cuda_stream,
+                      d2h_stream=down.cuda_stream)
+    down.synchronize()
+    torch.cuda.synchronize()
+    assert torch.equal(h, interior_image(ref, ref.A).cpu())
+
+
+def test_interior_images_need_periodic_ghosts():
+    st = make(capi.SF_Z4, (12, 9, 7), capi.SF_FP64, None, 0)
+    prm = capi.params(ghosts=capi.SF_GHOSTS_NONE)
+    h = pinned_copy(interior_image(st, st.A))
+    with pytest.raises(capi.SfError, match="periodic"):
+        capi.sf_step_host(prm, st.patch(st.A, st.A, st.B), [slot_of(st)], [h.data_ptr()],
+                          [h.data_ptr()], flags=capi.SF_HOST_INTERIOR)
