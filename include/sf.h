@@ -210,7 +210,10 @@ int64_t sf_state_span(const sf_patch* geom);
  *   for the download of the step that last used its slot and, when host_in[k]
  *   overlaps the host_out of a step still in flight, for that download, so
  *   an evolution kept in host memory (host_in[k] = host_out[k - 1]) is
- *   correct with any slot count.  With two slots the upload of step k + 1
+ *   correct with any slot count.  Copies go in eight pieces of the image,
+ *   and an upload piece waits only for the download pieces it overlaps, so
+ *   in such an evolution the next upload runs beside the rest of the
+ *   download.  With two slots the upload of step k + 1
  *   waits for the download of step k - 1; with three it does not, so
  *   independent steps run at the rate of the stages when the copies are
  *   shorter.  The first upload of a call waits for the work already queued on

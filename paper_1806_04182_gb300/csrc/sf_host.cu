@@ -19,9 +19,14 @@ namespace {
 // (a step's events are re-recorded two steps later, after every wait on
 // them has been enqueued).
 constexpr int kMaxSlots = 4;
+// Copies go in kChunks pieces of the image, each download piece with an
+// event of its own: the upload of a piece that an earlier step's download
+// writes waits for that piece only, so in an evolution kept in host memory
+// the next step's upload runs beside the rest of this step's download.
+constexpr int kChunks = 8;
 struct HostEvents {
   int dev = -1;
-  cudaEvent_t up[kMaxSlots], comp[kMaxSlots], down[kMaxSlots], entry;
+  cudaEvent_t up[kMaxSlots], comp[kMaxSlots], down[kMaxSlots][kChunks], entry;
 };
 thread_local HostEvents t_ev;
 
@@ -30,13 +35,14 @@ sf_status host_events(HostEvents** out) {
   if (cudaGetDevice(&dev) != cudaSuccess) return set_error(SF_ECUDA, "no CUDA device");
   HostEvents& e = t_ev;
   if (e.dev != dev) {
-    cudaEvent_t* all[3 * kMaxSlots + 1];
+    cudaEvent_t* all[(2 + kChunks) * kMaxSlots + 1];
+    int na = 0;
     for (int q = 0; q < kMaxSlots; ++q) {
-      all[3 * q] = &e.up[q];
-      all[3 * q + 1] = &e.comp[q];
-      all[3 * q + 2] = &e.down[q];
+      all[na++] = &e.up[q];
+      all[na++] = &e.comp[q];
+      for (int c = 0; c < kChunks; ++c) all[na++] = &e.down[q][c];
     }
-    all[3 * kMaxSlots] = &e.entry;
+    all[na++] = &e.entry;
     if (e.dev >= 0)
       for (cudaEvent_t* q : all) cudaEventDestroy(*q);
     e.dev = -1;
@@ -49,9 +55,9 @@ sf_status host_events(HostEvents** out) {
   return SF_OK;
 }
 
-bool overlap(const void* a, const void* b, size_t n) {
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
   const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
-  return x < y + n && y < x + n;
+  return x < y + nb && y < x + na;
 }
 
 struct Layout {
@@ -233,19 +239,32 @@ sf_status sf_step_host(const sf_params* prm, const sf_patch* geom, const sf_stat
   for (int k = 0; k < nsteps; ++k) {
     const sf_state& d = slots[k % nslots];
     const int b = k % nslots;
-    // the slot's previous download, and the downloads this input depends on
-    // (an earlier step of this call whose output it overlaps)
-    if (k >= nslots && cudaStreamWaitEvent(up, ev->down[b], 0) != cudaSuccess)
-      return set_error(SF_ECUDA, "stream ordering failed");
-    for (int j = std::max(0, k - nslots + 1); j < k; ++j)
-      if (overlap(host_in[k], host_out[j], hbytes) &&
-          cudaStreamWaitEvent(up, ev->down[j % nslots], 0) != cudaSuccess)
-        return set_error(SF_ECUDA, "stream ordering failed");
+    // the image in kChunks pieces [piece(c), piece(c + 1)), 256-byte aligned
+    auto piece = [&](int c) -> size_t {
+      return c >= kChunks ? hbytes : hbytes / kChunks / 256 * 256 * c;
+    };
+    char* dbuf = static_cast<char*>(interior ? d.s2 : d.u);
+    const char* hin = static_cast<const char*>(host_in[k]);
     // interior images land in the slot's s2 (stage scratch, free until stage
     // 1 writes it) and are spread into u with their periodic ghost shell
-    if (cudaMemcpyAsync(interior ? d.s2 : d.u, host_in[k], hbytes, cudaMemcpyHostToDevice, up) !=
-        cudaSuccess)
-      return set_error(SF_ECUDA, "upload of step %d failed", k);
+    for (int c = 0; c < kChunks; ++c) {
+      const size_t lo = piece(c), hi = piece(c + 1);
+      if (hi <= lo) continue;
+      // the slot's previous download of this piece of its device buffer, and
+      // the downloads of earlier steps of this call into the host memory it reads
+      if (k >= nslots && cudaStreamWaitEvent(up, ev->down[b][c], 0) != cudaSuccess)
+        return set_error(SF_ECUDA, "stream ordering failed");
+      for (int j = std::max(0, k - nslots + 1); j < k; ++j)
+        for (int c2 = 0; c2 < kChunks; ++c2) {
+          const size_t lo2 = piece(c2), hi2 = piece(c2 + 1);
+          if (hi2 > lo2 &&
+              overlap(hin + lo, hi - lo, static_cast<const char*>(host_out[j]) + lo2, hi2 - lo2) &&
+              cudaStreamWaitEvent(up, ev->down[j % nslots][c2], 0) != cudaSuccess)
+            return set_error(SF_ECUDA, "stream ordering failed");
+        }
+      if (cudaMemcpyAsync(dbuf + lo, hin + lo, hi - lo, cudaMemcpyHostToDevice, up) != cudaSuccess)
+        return set_error(SF_ECUDA, "upload of step %d failed", k);
+    }
     if (interior && (e = interior_copy(true, geom->precision == SF_FP64, d.u, d.s2, lay, up))) return e;
     if ((flags & SF_HOST_RESET_KAHAN) && cudaMemsetAsync(d.kahan, 0, bytes, up) != cudaSuccess)
       return set_error(SF_ECUDA, "Kahan reset of step %d failed", k);
@@ -269,10 +288,14 @@ sf_status sf_step_host(const sf_params* prm, const sf_patch* geom, const sf_stat
     if (interior && (e = interior_copy(false, geom->precision == SF_FP64, d.u, d.s2, lay, cs))) return e;
     if (cudaEventRecord(ev->comp[b], cs) != cudaSuccess || cudaStreamWaitEvent(dn, ev->comp[b], 0) != cudaSuccess)
       return set_error(SF_ECUDA, "stream ordering failed");
-    if (cudaMemcpyAsync(host_out[k], interior ? d.s2 : d.u, hbytes, cudaMemcpyDeviceToHost, dn) !=
-        cudaSuccess)
-      return set_error(SF_ECUDA, "download of step %d failed", k);
-    if (cudaEventRecord(ev->down[b], dn) != cudaSuccess) return set_error(SF_ECUDA, "event record failed");
+    for (int c = 0; c < kChunks; ++c) {
+      const size_t lo = piece(c), hi = piece(c + 1);
+      if (hi <= lo) continue;
+      if (cudaMemcpyAsync(static_cast<char*>(host_out[k]) + lo, dbuf + lo, hi - lo,
+                          cudaMemcpyDeviceToHost, dn) != cudaSuccess)
+        return set_error(SF_ECUDA, "download of step %d failed", k);
+      if (cudaEventRecord(ev->down[b][c], dn) != cudaSuccess) return set_error(SF_ECUDA, "event record failed");
+    }
   }
   return SF_OK;
 }
