@@ -433,7 +433,8 @@ def gpu_arm(args):
                 "path": "C-ABI sf_step_host (state.HostPipeline, interior host images): one evolution "
                         "kept in pinned host memory, every step uploads U^n's interior, rebuilds the "
                         "ghost shell on the device, runs the four stages and downloads U^{n+1}'s "
-                        "interior into the buffer the next step uploads (copies and stages serial)",
+                        "interior into the buffer the next step uploads; copies in eight pieces, the "
+                        "next upload beside the rest of the download, stages serial with the copies",
                 "independent_states": {
                     "value": ind_value, "unit": UNIT, "h2d_bytes_per_step": ibi,
                     "d2h_bytes_per_step": ibo,
