@@ -890,13 +890,24 @@ def cpu_baseline(seconds: float = 15.0, nz: int = ORACLE_NZ) -> dict:
     rate1, steps1, el1, _ = _oracle_rate(1, seconds / 2, nz)
     import oracle
     oracle.set_threads(cores)
-    return {"value": rate, "unit": UNIT, "cores": min(used, N * nz), "kind": "oracle",
+    p = min(used, N * nz)
+    speedup = rate / rate1
+    # Amdahl's serial share of the single-thread step implied by the speed-up
+    serial = (1.0 / speedup - 1.0 / p) / (1.0 - 1.0 / p) if p > 1 else 1.0
+    return {"value": rate, "unit": UNIT, "cores": p, "kind": "oracle",
             "sample": f"{steps} RK4 steps of a 96x96x{nz} periodic slab of the 96^3 workload "
                       f"(same dx, data, params), {el:.1f} s, OpenMP over its {N * nz} (z, y) rows",
             "cpu": host_cpu(), "nproc": cores,
             "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
                               "sample": f"{steps1} RK4 steps of the same slab, {el1:.1f} s"},
-            "parallel_speedup": rate / rate1}
+            "parallel_speedup": speedup,
+            "serial_share": serial,
+            "parallel_note": "the oracle's right-hand-side sweep runs in parallel over the slab's "
+                             "(z, y) rows; its RK combinations, periodic ghost fills and the "
+                             "zero-filled stage arrays it allocates every step run on one thread. "
+                             "serial_share is that part of the single-thread step as implied by "
+                             "Amdahl's law from the two rates, and it caps the speed-up below "
+                             "the thread count"}
 
 
 def reference_arm(args):
