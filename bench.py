@@ -136,6 +136,85 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class NvmlSampler:
+    """Read-only NVML samples (SM clock, clock-event reasons) every ~2 ms
+    between mark_start() and mark_stop(): the timed region of the headline is
+    tens of milliseconds, shorter than nvidia-smi's sampling interval.  Loads
+    libnvidia-ml through ctypes; without it (no driver) it reports nothing."""
+
+    # nvmlClocksEventReasons bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, index: int, period_s: float = 0.002):
+        import ctypes
+        self.period = period_s
+        self.samples: list[tuple[float, int, int]] = []
+        self.max_mhz = None
+        self.lib = None
+        self.window = [None, None]
+        self._stop = threading.Event()
+        self.thread = None
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h)) != 0:
+                return
+            self.h = h
+            self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            m = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(h, ctypes.c_int(1), ctypes.byref(m)) == 0:
+                self.max_mhz = m.value
+            self.lib = lib
+        except (OSError, AttributeError):
+            self.lib = None
+
+    def _poll(self):
+        import ctypes
+        mhz, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            t = time.perf_counter()
+            if (self.lib.nvmlDeviceGetClockInfo(self.h, ctypes.c_int(1), ctypes.byref(mhz)) == 0 and
+                    self.reasons_fn(self.h, ctypes.byref(rs)) == 0):
+                self.samples.append((t, mhz.value, rs.value))
+            time.sleep(self.period)
+
+    def start(self):
+        if self.lib is not None:
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+
+    def mark_start(self):
+        self.window[0] = time.perf_counter()
+
+    def mark_stop(self):
+        self.window[1] = time.perf_counter()
+
+    def stop(self) -> dict | None:
+        if self.lib is None:
+            return None
+        self._stop.set()
+        self.thread.join(timeout=5)
+        return self.summary(self.samples, self.window, self.max_mhz)
+
+    @classmethod
+    def summary(cls, samples, window, max_mhz) -> dict:
+        """Samples taken inside [window[0], window[1]]: median SM clock and the
+        reasons active in any of them."""
+        lo, hi = window
+        inside = [s for s in samples if lo is not None and hi is not None and lo <= s[0] <= hi]
+        reasons = sorted({nm for _, _, r in inside for bit, nm in cls.REASONS.items() if r & bit})
+        return {"source": "NVML, ~2 ms polling, host-clock window from the first timed launch to "
+                          "the synchronize after the last",
+                "samples_in_timed_region": len(inside),
+                "sm_mhz": statistics.median([m for _, m, _ in inside]) if inside else None,
+                "sm_mhz_min": min([m for _, m, _ in inside]) if inside else None,
+                "sm_max_mhz": max_mhz, "reasons": reasons}
+
+
 # ---------------------------------------------------------------- traffic
 # DRAM traffic and the instruction count of the headline kernel come from one
 # ncu capture, recorded in a JSON file beside its summary under profiles/;
@@ -209,8 +288,9 @@ def make_state(precision: str, seed: int, device, float_pitch: int = FLOAT_PITCH
     return st
 
 
-def time_device(st, steps: int, warmup: int):
-    """Per-launch CUDA-event durations (ms) of `steps` RK4 steps after warm-up."""
+def time_device(st, steps: int, warmup: int, marks=None):
+    """Per-launch CUDA-event durations (ms) of `steps` RK4 steps after warm-up
+    (`marks`: mark_start() / mark_stop() around the timed region)."""
     import torch
     from paper_1806_04182_gb300 import capi
     stream = torch.cuda.current_stream()
@@ -222,12 +302,16 @@ def time_device(st, steps: int, warmup: int):
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4 * steps + 1)]
     c0 = capi.sf_launch_count()
+    if marks:
+        marks.mark_start()
     ev[0].record(stream)
     for k in range(steps):
         for s in range(4):
             capi.sf_substep(st.prm, patches[s], s, h)
             ev[4 * k + s + 1].record(stream)
     torch.cuda.synchronize()
+    if marks:
+        marks.mark_stop()
     launches = capi.sf_launch_count() - c0
     per = np.array([ev[q].elapsed_time(ev[q + 1]) for q in range(4 * steps)]).reshape(steps, 4)
     total = ev[0].elapsed_time(ev[-1])
@@ -317,11 +401,16 @@ def gpu_arm(args):
         st = make_state(precision, seed=rank, device=device, float_pitch=args.pitch, x_offset=xo)
         barrier()
         sampler = ClockSampler(local) if precision == "fp32dw" else None
+        nvml = NvmlSampler(local) if precision == "fp32dw" else None
         if sampler:
             sampler.start()
-        total_ms, per, launches = time_device(st, args.steps, args.warmup)
+            nvml.start()
+        total_ms, per, launches = time_device(st, args.steps, args.warmup, marks=nvml)
         if sampler:
+            fine = nvml.stop()
             clocks = sampler.stop()
+            if fine is not None:
+                clocks["timed_region_nvml"] = fine
         barrier()
         total_ms = max_over_ranks(total_ms, device)
         substeps = 4 * args.steps

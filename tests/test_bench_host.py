@@ -42,3 +42,24 @@ def test_issue_roofline_needs_the_profiled_source(monkeypatch):
 
 def test_whole_job_rate_counts_every_rank():
     assert bench.whole_job_rate(4, 96 ** 3, 40, 10.0) == 4 * 96 ** 3 * 40 / 0.01
+
+
+def test_nvml_summary_keeps_the_timed_window_only():
+    # (host time, SM MHz, clock-event reason bits): the sample at t = 3.0 lies
+    # after the window and carries hw_slowdown, which must not be reported
+    samples = [(0.4, 1200, 0x1), (1.0, 2070, 0), (1.5, 2050, 0x4), (3.0, 1000, 0x8)]
+    s = bench.NvmlSampler.summary(samples, [0.5, 2.0], 2070)
+    assert s["samples_in_timed_region"] == 2
+    assert s["sm_mhz"] == 2060.0 and s["sm_mhz_min"] == 2050 and s["sm_max_mhz"] == 2070
+    assert s["reasons"] == ["sw_power_cap"]
+    empty = bench.NvmlSampler.summary(samples, [None, None], None)
+    assert empty["samples_in_timed_region"] == 0 and empty["sm_mhz"] is None
+
+
+def test_nvml_sampler_without_a_driver_reports_nothing():
+    s = bench.NvmlSampler(0)
+    if s.lib is None:
+        s.start()
+        s.mark_start()
+        s.mark_stop()
+        assert s.stop() is None
