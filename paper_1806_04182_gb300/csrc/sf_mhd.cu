@@ -26,8 +26,8 @@ __device__ __forceinline__ T wz_pow(T x, T q) {
   return q == T(2) ? x * x : (q == T(1) ? x : pow(x, q));
 }
 
-// App. B: left state at i+1/2 from w[0..4] = U_{i-2..i+2}
-template <typename T>
+// App. B: left state at i+1/2 from w[0..4] = U_{i-2..i+2}; Z: WENO-Z weights
+template <typename T, bool Z>
 __device__ __forceinline__ T weno_left(const T* w, T eps, const MhdCoef<T>& mc) {
   const T c0 = (T(2) * w[2] + T(5) * w[3] - w[4]) * T(1.0 / 6.0);
   const T c1 = (-w[1] + T(5) * w[2] + T(2) * w[3]) * T(1.0 / 6.0);
@@ -39,7 +39,7 @@ __device__ __forceinline__ T weno_left(const T* w, T eps, const MhdCoef<T>& mc) 
   const T be1 = T(13.0 / 12.0) * a1 * a1 + T(0.25) * b1 * b1;
   const T be2 = T(13.0 / 12.0) * a2 * a2 + T(0.25) * b2 * b2;
   T al0, al1, al2;
-  if (mc.variant == 1) {
+  if constexpr (Z) {
     const T tau = fabs(be0 - be2);
     al0 = T(0.3) * (T(1) + wz_pow(tau / (eps + be0), mc.q));
     al1 = T(0.6) * (T(1) + wz_pow(tau / (eps + be1), mc.q));
@@ -53,8 +53,8 @@ __device__ __forceinline__ T weno_left(const T* w, T eps, const MhdCoef<T>& mc) 
   return (al0 * c0 + al1 * c1 + al2 * c2) / (al0 + al1 + al2);
 }
 
-// App. B: right state at i-1/2 from w[0..4] = U_{i-2..i+2}
-template <typename T>
+// App. B: right state at i-1/2 from w[0..4] = U_{i-2..i+2}; Z: WENO-Z weights
+template <typename T, bool Z>
 __device__ __forceinline__ T weno_right(const T* w, T eps, const MhdCoef<T>& mc) {
   const T c0 = (T(2) * w[4] - T(7) * w[3] + T(11) * w[2]) * T(1.0 / 6.0);
   const T c1 = (-w[3] + T(5) * w[2] + T(2) * w[1]) * T(1.0 / 6.0);
@@ -66,7 +66,7 @@ __device__ __forceinline__ T weno_right(const T* w, T eps, const MhdCoef<T>& mc)
   const T be1 = T(13.0 / 12.0) * a1 * a1 + T(0.25) * b1 * b1;
   const T be2 = T(13.0 / 12.0) * a2 * a2 + T(0.25) * b2 * b2;
   T al0, al1, al2;
-  if (mc.variant == 1) {
+  if constexpr (Z) {
     const T tau = fabs(be0 - be2);
     al0 = T(0.1) * (T(1) + wz_pow(tau / (eps + be0), mc.q));
     al1 = T(0.6) * (T(1) + wz_pow(tau / (eps + be1), mc.q));
@@ -128,8 +128,9 @@ __device__ __forceinline__ T flux_speed(const T* q, int d, const MhdCoef<T>& mc,
   return fabs(vd) + sqrt(cf2);
 }
 
-// LLF flux through the face between the cell at p and its +d neighbour
-template <typename T>
+// LLF flux through the face between the cell at p and its +d neighbour;
+// VAR: the reconstruction (0 WENO5-JS, 1 WENO5-Z, 2 WENO3)
+template <typename T, int VAR>
 __device__ __forceinline__ void face_flux(const T* __restrict__ p, long long F, long long s, int d,
                                           const MhdCoef<T>& mc, T* Fout) {
   T UL[8], UR[8];
@@ -139,12 +140,12 @@ __device__ __forceinline__ void face_flux(const T* __restrict__ p, long long F, 
     T w[6];
 #pragma unroll
     for (int o = 0; o < 6; ++o) w[o] = __ldg(q + (o - 2) * s);
-    if (mc.variant == 2) {
+    if constexpr (VAR == 2) {
       UL[f] = weno3_left(w, mc.eps[d]);
       UR[f] = weno3_right(w + 1, mc.eps[d]);
     } else {
-      UL[f] = weno_left(w, mc.eps[d], mc);
-      UR[f] = weno_right(w + 1, mc.eps[d], mc);
+      UL[f] = weno_left<T, VAR == 1>(w, mc.eps[d], mc);
+      UR[f] = weno_right<T, VAR == 1>(w + 1, mc.eps[d], mc);
     }
   }
   T FL[8], FR[8];
@@ -159,7 +160,7 @@ __device__ __forceinline__ void face_flux(const T* __restrict__ p, long long F, 
 // (Sec. II.B.2, Lax-Friedrichs splitting): S = the largest signal speed over
 // the six cells p-2..p+3, F+- = (F(U) +- S U)/2 at each cell, F+ reconstructed
 // from the left (cells p-2..p+2) plus F- from the right (cells p-1..p+3).
-template <typename T>
+template <typename T, int VAR>
 __device__ __forceinline__ void face_flux_split(const T* __restrict__ p, long long F, long long s,
                                                 int d, const MhdCoef<T>& mc, T* Fout) {
   T Uc[6][8], Fc[6][8];
@@ -179,43 +180,60 @@ __device__ __forceinline__ void face_flux_split(const T* __restrict__ p, long lo
       wp[c] = T(0.5) * (Fc[c][f] + S * Uc[c][f]);
       wm[c] = T(0.5) * (Fc[c][f] - S * Uc[c][f]);
     }
-    if (mc.variant == 2)
+    if constexpr (VAR == 2)
       Fout[f] = weno3_left(wp, mc.eps[d]) + weno3_right(wm + 1, mc.eps[d]);
     else
-      Fout[f] = weno_left(wp, mc.eps[d], mc) + weno_right(wm + 1, mc.eps[d], mc);
+      Fout[f] = weno_left<T, VAR == 1>(wp, mc.eps[d], mc) + weno_right<T, VAR == 1>(wm + 1, mc.eps[d], mc);
   }
 }
 
-template <typename T, bool SPLIT>
+template <typename T, bool SPLIT, int VAR>
 __device__ __forceinline__ void interface_flux(const T* __restrict__ p, long long F, long long s,
                                                int d, const MhdCoef<T>& mc, T* Fout) {
-  if (SPLIT)
-    face_flux_split(p, F, s, d, mc, Fout);
+  if constexpr (SPLIT)
+    face_flux_split<T, VAR>(p, F, s, d, mc, Fout);
   else
-    face_flux(p, F, s, d, mc, Fout);
+    face_flux<T, VAR>(p, F, s, d, mc, Fout);
 }
 
 // Stage kernel.  Each interface flux is evaluated once: a block of 32 x 8
 // threads owns 31 x 7 output cells of a plane; thread (tx, ty) evaluates the
 // x-face at i - 1/2 and the y-face at j - 1/2 of its column, so the +1/2
 // faces of the output cells come from lane tx + 1 (warp shuffle) and row
-// ty + 1 (shared memory).  Each thread marches MZ planes in z and carries the
-// z-face below the current plane in registers.  Faces are only evaluated at
-// positions 0..n along their direction, whose WENO stencils (cells p-3..p+2)
-// lie inside the 3-point ghost zone.
-constexpr int MX = 32, MY = 8, MZ = 16;
+// ty + 1 (shared memory).  Each thread marches mz planes in z and carries the
+// z-face below the current plane in registers (the block also evaluates the
+// z-face below its first plane, one face in 3 mz + 1, in a first pass of the
+// plane loop that evaluates nothing else, so that the kernel holds one copy
+// of the z-face code).  VAR is the reconstruction (0 WENO5-JS, 1 WENO5-Z,
+// 2 WENO3), a template argument so that each instance carries one
+// reconstruction: the kernel's code is large enough for instruction fetch to
+// be its top stall.  mz is chosen per
+// launch (mhd_planes_per_block) so that the grid fills whole waves of
+// resident blocks.  Faces are only evaluated at positions 0..n along their
+// direction, whose WENO stencils (cells p-3..p+2) lie inside the 3-point
+// ghost zone.
+constexpr int MX = 32, MY = 8;
 
+// Float without flux splitting asks for 3 resident blocks per SM (at most
+// 85 registers a thread; it fits in 80 without spills; left to itself the
+// compiler takes 96, 2 blocks per SM, 15% slower at 128^3); the other forms
+// keep the compiler's choice.
 template <typename T, bool SPLIT>
-__global__ void __launch_bounds__(MX * MY) mhd_stage_kernel(PatchArgs<T> a, StageArgs s,
-                                                           MhdCoef<T> mc) {
+constexpr int mhd_min_blocks() {
+  return sizeof(T) == 4 && !SPLIT ? 3 : 1;
+}
+
+template <typename T, bool SPLIT, int VAR>
+__global__ void __launch_bounds__(MX * MY, mhd_min_blocks<T, SPLIT>())
+    mhd_stage_kernel(PatchArgs<T> a, StageArgs s, MhdCoef<T> mc, int mz) {
   __shared__ T fy[MY][MX][8];
   __shared__ double s_rate[MX * MY / 32];
   const int tx = threadIdx.x, ty = threadIdx.y;
   double rate = 0.0;  // max signal rate of this thread's outputs (fused CFL reduction)
   const int i = blockIdx.x * (MX - 1) + tx;
   const int j = blockIdx.y * (MY - 1) + ty;
-  const int k0 = blockIdx.z * MZ;
-  const int k1 = min(k0 + MZ, a.n[2]);
+  const int k0 = blockIdx.z * mz;
+  const int k1 = min(k0 + mz, a.n[2]);
   const int g = a.g;
   const bool out = tx < MX - 1 && ty < MY - 1 && i < a.n[0] && j < a.n[1];
   const bool xface = i <= a.n[0] && j < a.n[1];
@@ -224,24 +242,34 @@ __global__ void __launch_bounds__(MX * MY) mhd_stage_kernel(PatchArgs<T> a, Stag
     return a.us + (long long)(kk + g) * a.sz + (long long)(jj + g) * a.sy + (ii + g);
   };
   T Fzm[8];
-  if (out) interface_flux<T, SPLIT>(at(i, j, k0 - 1), a.sf, a.sz, 2, mc, Fzm);
-  for (int k = k0; k < k1; ++k) {
+  // pass k = k0 - 1 evaluates only the z-face below the first plane (Fzm);
+  // `body` is the same for the whole block, so the barriers below are taken
+  // by every thread or by none
+  for (int k = k0 - 1; k < k1; ++k) {
+    const bool body = k >= k0;
     T Fx[8], Fy[8], Fz[8];
-    if (xface) {
-      interface_flux<T, SPLIT>(at(i - 1, j, k), a.sf, 1, 0, mc, Fx);
-    } else {
+    if (body) {
+      if (xface) {
+        interface_flux<T, SPLIT, VAR>(at(i - 1, j, k), a.sf, 1, 0, mc, Fx);
+      } else {
 #pragma unroll
-      for (int f = 0; f < 8; ++f) Fx[f] = T(0);
+        for (int f = 0; f < 8; ++f) Fx[f] = T(0);
+      }
+      if (yface) {
+        interface_flux<T, SPLIT, VAR>(at(i, j - 1, k), a.sf, a.sy, 1, mc, Fy);
+      } else {
+#pragma unroll
+        for (int f = 0; f < 8; ++f) Fy[f] = T(0);
+      }
+#pragma unroll
+      for (int f = 0; f < 8; ++f) fy[ty][tx][f] = Fy[f];
     }
-    if (yface) {
-      interface_flux<T, SPLIT>(at(i, j - 1, k), a.sf, a.sy, 1, mc, Fy);
-    } else {
+    if (out) interface_flux<T, SPLIT, VAR>(at(i, j, k), a.sf, a.sz, 2, mc, Fz);
+    if (!body) {
 #pragma unroll
-      for (int f = 0; f < 8; ++f) Fy[f] = T(0);
+      for (int f = 0; f < 8; ++f) Fzm[f] = Fz[f];
+      continue;
     }
-#pragma unroll
-    for (int f = 0; f < 8; ++f) fy[ty][tx][f] = Fy[f];
-    if (out) interface_flux<T, SPLIT>(at(i, j, k), a.sf, a.sz, 2, mc, Fz);
     T Fxp[8];
 #pragma unroll
     for (int f = 0; f < 8; ++f) Fxp[f] = __shfl_down_sync(0xffffffffu, Fx[f], 1);
@@ -331,6 +359,65 @@ static MhdCoef<T> coef(const sf_params& prm, const sf_patch& p) {
   return mc;
 }
 
+// Planes per block along z: each block evaluates 3 mz + 1 interface fluxes
+// per column, and a launch of B blocks takes ceil(B / resident) rounds of
+// the resident blocks (blocks per SM x SMs), so mz in [4, 16] minimises
+// ceil(B(mz) / resident) (3 mz + 1); ties go to the larger mz.
+static int mhd_planes_per_block(int gx, int gy, int nz, int resident) {
+  int best = 16;
+  long long best_cost = -1;
+  for (int mz = 16; mz >= 4; --mz) {
+    const long long blocks = (long long)gx * gy * ((nz + mz - 1) / mz);
+    const long long rounds = resident > 0 ? (blocks + resident - 1) / resident : blocks;
+    const long long cost = rounds * (3 * mz + 1);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = mz;
+    }
+  }
+  return best;
+}
+
+// Resident blocks of the stage kernel instance on the current device
+// (blocks per SM x SMs), cached per instance and device; 0 if unknown.
+template <typename T, bool SPLIT, int VAR>
+static int resident_blocks() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (!cache[dev]) {
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mhd_stage_kernel<T, SPLIT, VAR>, MX * MY,
+                                                      0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return 0;
+    cache[dev] = per_sm * sms;
+  }
+  return cache[dev];
+}
+
+// One launch of the instance for (T, SPLIT, VAR) with its chunk length.
+template <typename T, bool SPLIT, int VAR>
+static void launch_instance(const PatchArgs<T>& a, const StageArgs& s, const MhdCoef<T>& mc,
+                            const sf_patch& p, cudaStream_t st) {
+  const dim3 block(MX, MY, 1);
+  const int gx = (p.n[0] + MX - 2) / (MX - 1), gy = (p.n[1] + MY - 2) / (MY - 1);
+  const int mz = mhd_planes_per_block(gx, gy, p.n[2], resident_blocks<T, SPLIT, VAR>());
+  const dim3 grid(gx, gy, (p.n[2] + mz - 1) / mz);
+  mhd_stage_kernel<T, SPLIT, VAR><<<grid, block, 0, st>>>(a, s, mc, mz);
+}
+
+template <typename T, bool SPLIT>
+static void launch_variant(const PatchArgs<T>& a, const StageArgs& s, const MhdCoef<T>& mc,
+                           const sf_patch& p, cudaStream_t st) {
+  if (mc.variant == 1)
+    launch_instance<T, SPLIT, 1>(a, s, mc, p, st);
+  else if (mc.variant == 2)
+    launch_instance<T, SPLIT, 2>(a, s, mc, p, st);
+  else
+    launch_instance<T, SPLIT, 0>(a, s, mc, p, st);
+}
+
 template <typename T>
 static sf_status launch(const sf_params& prm, const sf_patch& p, const StageArgs& s, int stage,
                         void* rhs_out, cudaStream_t st) {
@@ -341,12 +428,11 @@ static sf_status launch(const sf_params& prm, const sf_patch& p, const StageArgs
       return set_error(SF_ECUDA, "reset of cfl_rate failed");
     a.rate = p.cfl_rate;
   }
-  dim3 block(MX, MY, 1);
-  dim3 grid((p.n[0] + MX - 2) / (MX - 1), (p.n[1] + MY - 2) / (MY - 1), (p.n[2] + MZ - 1) / MZ);
+  const MhdCoef<T> mc = coef<T>(prm, p);
   if (prm.flux_split)
-    mhd_stage_kernel<T, true><<<grid, block, 0, st>>>(a, s, coef<T>(prm, p));
+    launch_variant<T, true>(a, s, mc, p, st);
   else
-    mhd_stage_kernel<T, false><<<grid, block, 0, st>>>(a, s, coef<T>(prm, p));
+    launch_variant<T, false>(a, s, mc, p, st);
   return after_launch("mhd_stage_kernel");
 }
 
