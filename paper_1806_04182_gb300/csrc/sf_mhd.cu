@@ -104,6 +104,13 @@ __device__ __forceinline__ T weno3_right(const T* w, T eps) {
   return (a0 * c0 + a1 * c1) / (a0 + a1);
 }
 
+// one of three values by a direction d that may be known only at run time
+// (selects, not an indexed array, so that nothing goes to local memory)
+template <typename T>
+__device__ __forceinline__ T by_dir(int d, T x, T y, T z) {
+  return d == 0 ? x : (d == 1 ? y : z);
+}
+
 // physical flux along d and the largest signal speed |v_d| + c_fast,d
 template <typename T>
 __device__ __forceinline__ T flux_speed(const T* q, int d, const MhdCoef<T>& mc, T* F) {
@@ -115,10 +122,11 @@ __device__ __forceinline__ T flux_speed(const T* q, int d, const MhdCoef<T>& mc,
   const T pr = (mc.gamma - T(1)) * (q[4] - T(0.5) * S2v - T(0.5) * B2);
   const T ptot = pr + T(0.5) * B2;
   const T vB = v[0] * B[0] + v[1] * B[1] + v[2] * B[2];
-  const T vd = v[d], Bd = B[d];
-  F[0] = q[1 + d];
+  const T vd = by_dir(d, v[0], v[1], v[2]), Bd = by_dir(d, B[0], B[1], B[2]);
+  const T Sd = by_dir(d, q[1], q[2], q[3]);
+  F[0] = Sd;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) F[1 + a] = q[1 + d] * v[a] - Bd * B[a] + (a == d ? ptot : T(0));
+  for (int a = 0; a < 3; ++a) F[1 + a] = Sd * v[a] - Bd * B[a] + (a == d ? ptot : T(0));
   F[4] = (q[4] + ptot) * vd - vB * Bd;
 #pragma unroll
   for (int a = 0; a < 3; ++a) F[5 + a] = vd * B[a] - v[a] * Bd;
@@ -133,6 +141,7 @@ __device__ __forceinline__ T flux_speed(const T* q, int d, const MhdCoef<T>& mc,
 template <typename T, int VAR>
 __device__ __forceinline__ void face_flux(const T* __restrict__ p, long long F, long long s, int d,
                                           const MhdCoef<T>& mc, T* Fout) {
+  const T eps = by_dir(d, mc.eps[0], mc.eps[1], mc.eps[2]);
   T UL[8], UR[8];
 #pragma unroll
   for (int f = 0; f < 8; ++f) {
@@ -141,11 +150,11 @@ __device__ __forceinline__ void face_flux(const T* __restrict__ p, long long F, 
 #pragma unroll
     for (int o = 0; o < 6; ++o) w[o] = __ldg(q + (o - 2) * s);
     if constexpr (VAR == 2) {
-      UL[f] = weno3_left(w, mc.eps[d]);
-      UR[f] = weno3_right(w + 1, mc.eps[d]);
+      UL[f] = weno3_left(w, eps);
+      UR[f] = weno3_right(w + 1, eps);
     } else {
-      UL[f] = weno_left<T, VAR == 1>(w, mc.eps[d], mc);
-      UR[f] = weno_right<T, VAR == 1>(w + 1, mc.eps[d], mc);
+      UL[f] = weno_left<T, VAR == 1>(w, eps, mc);
+      UR[f] = weno_right<T, VAR == 1>(w + 1, eps, mc);
     }
   }
   T FL[8], FR[8];
@@ -163,6 +172,7 @@ __device__ __forceinline__ void face_flux(const T* __restrict__ p, long long F, 
 template <typename T, int VAR>
 __device__ __forceinline__ void face_flux_split(const T* __restrict__ p, long long F, long long s,
                                                 int d, const MhdCoef<T>& mc, T* Fout) {
+  const T eps = by_dir(d, mc.eps[0], mc.eps[1], mc.eps[2]);
   T Uc[6][8], Fc[6][8];
   T S = T(0);
 #pragma unroll
@@ -181,9 +191,9 @@ __device__ __forceinline__ void face_flux_split(const T* __restrict__ p, long lo
       wm[c] = T(0.5) * (Fc[c][f] - S * Uc[c][f]);
     }
     if constexpr (VAR == 2)
-      Fout[f] = weno3_left(wp, mc.eps[d]) + weno3_right(wm + 1, mc.eps[d]);
+      Fout[f] = weno3_left(wp, eps) + weno3_right(wm + 1, eps);
     else
-      Fout[f] = weno_left<T, VAR == 1>(wp, mc.eps[d], mc) + weno_right<T, VAR == 1>(wm + 1, mc.eps[d], mc);
+      Fout[f] = weno_left<T, VAR == 1>(wp, eps, mc) + weno_right<T, VAR == 1>(wm + 1, eps, mc);
   }
 }
 
@@ -248,23 +258,29 @@ __global__ void __launch_bounds__(MX * MY, mhd_min_blocks<T, SPLIT>())
   for (int k = k0 - 1; k < k1; ++k) {
     const bool body = k >= k0;
     T Fx[8], Fy[8], Fz[8];
+    // the x-face at i - 1/2, the y-face at j - 1/2 and the z-face at k + 1/2
+    // in one rolled loop over the direction (one copy of the face code)
+#pragma unroll 1
+    for (int d = body ? 0 : 2; d < 3; ++d) {
+      T Fd[8];
+      if (d == 0 ? xface : (d == 1 ? yface : out)) {
+        const T* base = d == 0 ? at(i - 1, j, k) : (d == 1 ? at(i, j - 1, k) : at(i, j, k));
+        interface_flux<T, SPLIT, VAR>(base, a.sf, d == 0 ? 1LL : (d == 1 ? a.sy : a.sz), d, mc, Fd);
+      } else {
+#pragma unroll
+        for (int f = 0; f < 8; ++f) Fd[f] = T(0);
+      }
+#pragma unroll
+      for (int f = 0; f < 8; ++f) {
+        Fx[f] = d == 0 ? Fd[f] : Fx[f];
+        Fy[f] = d == 1 ? Fd[f] : Fy[f];
+        Fz[f] = d == 2 ? Fd[f] : Fz[f];
+      }
+    }
     if (body) {
-      if (xface) {
-        interface_flux<T, SPLIT, VAR>(at(i - 1, j, k), a.sf, 1, 0, mc, Fx);
-      } else {
-#pragma unroll
-        for (int f = 0; f < 8; ++f) Fx[f] = T(0);
-      }
-      if (yface) {
-        interface_flux<T, SPLIT, VAR>(at(i, j - 1, k), a.sf, a.sy, 1, mc, Fy);
-      } else {
-#pragma unroll
-        for (int f = 0; f < 8; ++f) Fy[f] = T(0);
-      }
 #pragma unroll
       for (int f = 0; f < 8; ++f) fy[ty][tx][f] = Fy[f];
     }
-    if (out) interface_flux<T, SPLIT, VAR>(at(i, j, k), a.sf, a.sz, 2, mc, Fz);
     if (!body) {
 #pragma unroll
       for (int f = 0; f < 8; ++f) Fzm[f] = Fz[f];
