@@ -41,9 +41,28 @@ __device__ __forceinline__ T weno_left(const T* w, T eps, const MhdCoef<T>& mc) 
   T al0, al1, al2;
   if constexpr (Z) {
     const T tau = fabs(be0 - be2);
-    al0 = T(0.3) * (T(1) + wz_pow(tau / (eps + be0), mc.q));
-    al1 = T(0.6) * (T(1) + wz_pow(tau / (eps + be1), mc.q));
-    al2 = T(0.1) * (T(1) + wz_pow(tau / (eps + be2), mc.q));
+    if (sizeof(T) == 8 && mc.q == T(2)) {
+      // q = 2: 1 + (tau / e)^2 = (e^2 + tau^2) / e^2, over the common
+      // denominator e0^2 e1^2 e2^2 as in the JS weights below
+      const T e0 = eps + be0, e1 = eps + be1, e2 = eps + be2, t2 = tau * tau;
+      const T q0 = e0 * e0, q1 = e1 * e1, q2 = e2 * e2;
+      al0 = T(0.3) * (q0 + t2) * (q1 * q2);
+      al1 = T(0.6) * (q1 + t2) * (q0 * q2);
+      al2 = T(0.1) * (q2 + t2) * (q0 * q1);
+    } else {
+      al0 = T(0.3) * (T(1) + wz_pow(tau / (eps + be0), mc.q));
+      al1 = T(0.6) * (T(1) + wz_pow(tau / (eps + be1), mc.q));
+      al2 = T(0.1) * (T(1) + wz_pow(tau / (eps + be2), mc.q));
+    }
+  } else if constexpr (sizeof(T) == 8) {
+    // the same weights over the common denominator e0^2 e1^2 e2^2, which
+    // cancels in the normalisation: one division instead of four (double
+    // only: the products of squares would underflow float on fine grids)
+    const T e0 = eps + be0, e1 = eps + be1, e2 = eps + be2;
+    const T q0 = e0 * e0, q1 = e1 * e1, q2 = e2 * e2;
+    al0 = T(0.3) * (q1 * q2);
+    al1 = T(0.6) * (q0 * q2);
+    al2 = T(0.1) * (q0 * q1);
   } else {
     const T e0 = eps + be0, e1 = eps + be1, e2 = eps + be2;
     al0 = T(0.3) / (e0 * e0);
@@ -68,9 +87,24 @@ __device__ __forceinline__ T weno_right(const T* w, T eps, const MhdCoef<T>& mc)
   T al0, al1, al2;
   if constexpr (Z) {
     const T tau = fabs(be0 - be2);
-    al0 = T(0.1) * (T(1) + wz_pow(tau / (eps + be0), mc.q));
-    al1 = T(0.6) * (T(1) + wz_pow(tau / (eps + be1), mc.q));
-    al2 = T(0.3) * (T(1) + wz_pow(tau / (eps + be2), mc.q));
+    if (sizeof(T) == 8 && mc.q == T(2)) {  // common denominator, as in weno_left
+      const T e0 = eps + be0, e1 = eps + be1, e2 = eps + be2, t2 = tau * tau;
+      const T q0 = e0 * e0, q1 = e1 * e1, q2 = e2 * e2;
+      al0 = T(0.1) * (q0 + t2) * (q1 * q2);
+      al1 = T(0.6) * (q1 + t2) * (q0 * q2);
+      al2 = T(0.3) * (q2 + t2) * (q0 * q1);
+    } else {
+      al0 = T(0.1) * (T(1) + wz_pow(tau / (eps + be0), mc.q));
+      al1 = T(0.6) * (T(1) + wz_pow(tau / (eps + be1), mc.q));
+      al2 = T(0.3) * (T(1) + wz_pow(tau / (eps + be2), mc.q));
+    }
+  } else if constexpr (sizeof(T) == 8) {
+    // common denominator, as in weno_left
+    const T e0 = eps + be0, e1 = eps + be1, e2 = eps + be2;
+    const T q0 = e0 * e0, q1 = e1 * e1, q2 = e2 * e2;
+    al0 = T(0.1) * (q1 * q2);
+    al1 = T(0.6) * (q0 * q2);
+    al2 = T(0.3) * (q0 * q1);
   } else {
     const T e0 = eps + be0, e1 = eps + be1, e2 = eps + be2;
     al0 = T(0.1) / (e0 * e0);
@@ -88,6 +122,10 @@ __device__ __forceinline__ T weno3_left(const T* w, T eps) {
   const T b0 = (w[3] - w[2]) * (w[3] - w[2]);
   const T b1 = (w[2] - w[1]) * (w[2] - w[1]);
   const T e0 = eps + b0, e1 = eps + b1;
+  if constexpr (sizeof(T) == 8) {  // common denominator e0^2 e1^2 (see weno_left)
+    const T a0 = T(2.0 / 3.0) * (e1 * e1), a1 = T(1.0 / 3.0) * (e0 * e0);
+    return (a0 * c0 + a1 * c1) / (a0 + a1);
+  }
   const T a0 = T(2.0 / 3.0) / (e0 * e0), a1 = T(1.0 / 3.0) / (e1 * e1);
   return (a0 * c0 + a1 * c1) / (a0 + a1);
 }
@@ -100,6 +138,10 @@ __device__ __forceinline__ T weno3_right(const T* w, T eps) {
   const T b0 = (w[2] - w[3]) * (w[2] - w[3]);
   const T b1 = (w[1] - w[2]) * (w[1] - w[2]);
   const T e0 = eps + b0, e1 = eps + b1;
+  if constexpr (sizeof(T) == 8) {  // common denominator e0^2 e1^2 (see weno_left)
+    const T a0 = T(1.0 / 3.0) * (e1 * e1), a1 = T(2.0 / 3.0) * (e0 * e0);
+    return (a0 * c0 + a1 * c1) / (a0 + a1);
+  }
   const T a0 = T(1.0 / 3.0) / (e0 * e0), a1 = T(2.0 / 3.0) / (e1 * e1);
   return (a0 * c0 + a1 * c1) / (a0 + a1);
 }
