@@ -231,6 +231,26 @@ def test_mhd_fp64_stages(variant, split):
         assert e.max() < TOL64, (s, e)
 
 
+# The MHD stage kernel marches a number of planes per block that it picks per
+# launch from the grid and the resident blocks (the last block of a column
+# may hold fewer planes; a patch thinner than the smallest choice is one
+# block deep).  Thin and ragged z extents (at least the 3 ghosts that fused
+# periodic ghost writes need), both precisions, against the oracle's stages.
+@pytest.mark.parametrize("precision", [capi.SF_FP64, capi.SF_FP32_BULK])
+@pytest.mark.parametrize("nz", [3, 4, 5, 9, 17])
+def test_mhd_plane_chunks_any_depth(nz, precision):
+    n = (13, 9, nz)
+    U0, dx = inputs.mhd_blast(n, seed=nz, radius=0.3)
+    prm = capi.params(rk=capi.SF_SSPRK3)
+    dt = 0.3 / oracle.mhd_max_rate(oracle.ghosted(U0), dx)
+    got = run_stages(capi.SF_MHD, U0, dx, dt, prm, precision=precision)
+    want = oracle_stages(oracle.MHD, U0, dx, dt, prm)
+    tol = TOL64 if precision == capi.SF_FP64 else TOL32_MHD
+    for s in range(3):
+        e = rel_err(got[s], want[s], floor=1e-3)
+        assert e.max() < tol, (nz, s, e)
+
+
 # FP32 MHD (float storage and arithmetic; the suite's FP32 row) against the
 # FP64 oracle.  Bound: a stage output is U plus dt/dx_d times differences of
 # the six interface fluxes around the cell; each flux is formed with about
