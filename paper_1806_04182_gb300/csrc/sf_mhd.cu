@@ -26,93 +26,89 @@ __device__ __forceinline__ T wz_pow(T x, T q) {
   return q == T(2) ? x * x : (q == T(1) ? x : pow(x, q));
 }
 
-// App. B: left state at i+1/2 from w[0..4] = U_{i-2..i+2}; Z: WENO-Z weights
+// App. B smoothness indicators of the three WENO5 stencils of cell c, from
+// w[0..4] = U_{c-2..c+2}: beta_0 of cells c..c+2, beta_1 of c-1..c+1, beta_2
+// of c-2..c.  They measure the candidate polynomials on cell c, so the
+// reconstructions at both edges of the cell use the same three numbers.
+template <typename T>
+__device__ __forceinline__ void weno5_beta(const T* w, T& be0, T& be1, T& be2) {
+  const T a0 = w[2] - T(2) * w[3] + w[4], b0 = T(3) * w[2] - T(4) * w[3] + w[4];
+  const T a1 = w[1] - T(2) * w[2] + w[3], b1 = w[1] - w[3];
+  const T a2 = w[0] - T(2) * w[1] + w[2], b2 = w[0] - T(4) * w[1] + T(3) * w[2];
+  be0 = T(13.0 / 12.0) * a0 * a0 + T(0.25) * b0 * b0;
+  be1 = T(13.0 / 12.0) * a1 * a1 + T(0.25) * b1 * b1;
+  be2 = T(13.0 / 12.0) * a2 * a2 + T(0.25) * b2 * b2;
+}
+
+// App. B nonlinear combination of the candidates c_k of stencils k = 0, 1, 2
+// with linear weights g_k and smoothness indicators be_k: JS weights
+// g_k / (eps + be_k)^2, or with Z the WENO-Z weights g_k (1 + (tau / (eps +
+// be_k))^q), tau = |be_0 - be_2|, normalised by their sum.  In double the
+// weights are formed over the common denominator (eps + be_0)^2 (eps + be_1)^2
+// (eps + be_2)^2 (WENO-Z for q = 2), which cancels in the normalisation: one
+// division instead of four (the products of squares would underflow float on
+// fine grids, so float keeps the per-weight divisions).
+template <typename T, bool Z>
+__device__ __forceinline__ T weno5_combine(T c0, T c1, T c2, T g0, T g1, T g2, T be0, T be1, T be2,
+                                           T eps, const MhdCoef<T>& mc) {
+  T al0, al1, al2;
+  if constexpr (Z) {
+    const T tau = fabs(be0 - be2);
+    if (sizeof(T) == 8 && mc.q == T(2)) {
+      const T e0 = eps + be0, e1 = eps + be1, e2 = eps + be2, t2 = tau * tau;
+      const T q0 = e0 * e0, q1 = e1 * e1, q2 = e2 * e2;
+      al0 = g0 * (q0 + t2) * (q1 * q2);
+      al1 = g1 * (q1 + t2) * (q0 * q2);
+      al2 = g2 * (q2 + t2) * (q0 * q1);
+    } else {
+      al0 = g0 * (T(1) + wz_pow(tau / (eps + be0), mc.q));
+      al1 = g1 * (T(1) + wz_pow(tau / (eps + be1), mc.q));
+      al2 = g2 * (T(1) + wz_pow(tau / (eps + be2), mc.q));
+    }
+  } else if constexpr (sizeof(T) == 8) {
+    const T e0 = eps + be0, e1 = eps + be1, e2 = eps + be2;
+    const T q0 = e0 * e0, q1 = e1 * e1, q2 = e2 * e2;
+    al0 = g0 * (q1 * q2);
+    al1 = g1 * (q0 * q2);
+    al2 = g2 * (q0 * q1);
+  } else {
+    const T e0 = eps + be0, e1 = eps + be1, e2 = eps + be2;
+    al0 = g0 / (e0 * e0);
+    al1 = g1 / (e1 * e1);
+    al2 = g2 / (e2 * e2);
+  }
+  return (al0 * c0 + al1 * c1 + al2 * c2) / (al0 + al1 + al2);
+}
+
+// App. B: left state at i+1/2 (the right edge of cell i) from w[0..4] =
+// U_{i-2..i+2}; Z: WENO-Z weights
 template <typename T, bool Z>
 __device__ __forceinline__ T weno_left(const T* w, T eps, const MhdCoef<T>& mc) {
   const T c0 = (T(2) * w[2] + T(5) * w[3] - w[4]) * T(1.0 / 6.0);
   const T c1 = (-w[1] + T(5) * w[2] + T(2) * w[3]) * T(1.0 / 6.0);
   const T c2 = (T(2) * w[0] - T(7) * w[1] + T(11) * w[2]) * T(1.0 / 6.0);
-  const T a0 = w[2] - T(2) * w[3] + w[4], b0 = T(3) * w[2] - T(4) * w[3] + w[4];
-  const T a1 = w[1] - T(2) * w[2] + w[3], b1 = w[1] - w[3];
-  const T a2 = w[0] - T(2) * w[1] + w[2], b2 = w[0] - T(4) * w[1] + T(3) * w[2];
-  const T be0 = T(13.0 / 12.0) * a0 * a0 + T(0.25) * b0 * b0;
-  const T be1 = T(13.0 / 12.0) * a1 * a1 + T(0.25) * b1 * b1;
-  const T be2 = T(13.0 / 12.0) * a2 * a2 + T(0.25) * b2 * b2;
-  T al0, al1, al2;
-  if constexpr (Z) {
-    const T tau = fabs(be0 - be2);
-    if (sizeof(T) == 8 && mc.q == T(2)) {
-      // q = 2: 1 + (tau / e)^2 = (e^2 + tau^2) / e^2, over the common
-      // denominator e0^2 e1^2 e2^2 as in the JS weights below
-      const T e0 = eps + be0, e1 = eps + be1, e2 = eps + be2, t2 = tau * tau;
-      const T q0 = e0 * e0, q1 = e1 * e1, q2 = e2 * e2;
-      al0 = T(0.3) * (q0 + t2) * (q1 * q2);
-      al1 = T(0.6) * (q1 + t2) * (q0 * q2);
-      al2 = T(0.1) * (q2 + t2) * (q0 * q1);
-    } else {
-      al0 = T(0.3) * (T(1) + wz_pow(tau / (eps + be0), mc.q));
-      al1 = T(0.6) * (T(1) + wz_pow(tau / (eps + be1), mc.q));
-      al2 = T(0.1) * (T(1) + wz_pow(tau / (eps + be2), mc.q));
-    }
-  } else if constexpr (sizeof(T) == 8) {
-    // the same weights over the common denominator e0^2 e1^2 e2^2, which
-    // cancels in the normalisation: one division instead of four (double
-    // only: the products of squares would underflow float on fine grids)
-    const T e0 = eps + be0, e1 = eps + be1, e2 = eps + be2;
-    const T q0 = e0 * e0, q1 = e1 * e1, q2 = e2 * e2;
-    al0 = T(0.3) * (q1 * q2);
-    al1 = T(0.6) * (q0 * q2);
-    al2 = T(0.1) * (q0 * q1);
-  } else {
-    const T e0 = eps + be0, e1 = eps + be1, e2 = eps + be2;
-    al0 = T(0.3) / (e0 * e0);
-    al1 = T(0.6) / (e1 * e1);
-    al2 = T(0.1) / (e2 * e2);
-  }
-  return (al0 * c0 + al1 * c1 + al2 * c2) / (al0 + al1 + al2);
+  T be0, be1, be2;
+  weno5_beta(w, be0, be1, be2);
+  return weno5_combine<T, Z>(c0, c1, c2, T(0.3), T(0.6), T(0.1), be0, be1, be2, eps, mc);
 }
 
-// App. B: right state at i-1/2 from w[0..4] = U_{i-2..i+2}; Z: WENO-Z weights
+// App. B: right state at i-1/2 (the left edge of cell i) from w[0..4] =
+// U_{i-2..i+2}; Z: WENO-Z weights
 template <typename T, bool Z>
 __device__ __forceinline__ T weno_right(const T* w, T eps, const MhdCoef<T>& mc) {
   const T c0 = (T(2) * w[4] - T(7) * w[3] + T(11) * w[2]) * T(1.0 / 6.0);
   const T c1 = (-w[3] + T(5) * w[2] + T(2) * w[1]) * T(1.0 / 6.0);
   const T c2 = (T(2) * w[2] + T(5) * w[1] - w[0]) * T(1.0 / 6.0);
-  const T a0 = w[4] - T(2) * w[3] + w[2], b0 = w[4] - T(4) * w[3] + T(3) * w[2];
-  const T a1 = w[3] - T(2) * w[2] + w[1], b1 = w[3] - w[1];
-  const T a2 = w[2] - T(2) * w[1] + w[0], b2 = T(3) * w[2] - T(4) * w[1] + w[0];
-  const T be0 = T(13.0 / 12.0) * a0 * a0 + T(0.25) * b0 * b0;
-  const T be1 = T(13.0 / 12.0) * a1 * a1 + T(0.25) * b1 * b1;
-  const T be2 = T(13.0 / 12.0) * a2 * a2 + T(0.25) * b2 * b2;
-  T al0, al1, al2;
-  if constexpr (Z) {
-    const T tau = fabs(be0 - be2);
-    if (sizeof(T) == 8 && mc.q == T(2)) {  // common denominator, as in weno_left
-      const T e0 = eps + be0, e1 = eps + be1, e2 = eps + be2, t2 = tau * tau;
-      const T q0 = e0 * e0, q1 = e1 * e1, q2 = e2 * e2;
-      al0 = T(0.1) * (q0 + t2) * (q1 * q2);
-      al1 = T(0.6) * (q1 + t2) * (q0 * q2);
-      al2 = T(0.3) * (q2 + t2) * (q0 * q1);
-    } else {
-      al0 = T(0.1) * (T(1) + wz_pow(tau / (eps + be0), mc.q));
-      al1 = T(0.6) * (T(1) + wz_pow(tau / (eps + be1), mc.q));
-      al2 = T(0.3) * (T(1) + wz_pow(tau / (eps + be2), mc.q));
-    }
-  } else if constexpr (sizeof(T) == 8) {
-    // common denominator, as in weno_left
-    const T e0 = eps + be0, e1 = eps + be1, e2 = eps + be2;
-    const T q0 = e0 * e0, q1 = e1 * e1, q2 = e2 * e2;
-    al0 = T(0.1) * (q1 * q2);
-    al1 = T(0.6) * (q0 * q2);
-    al2 = T(0.3) * (q0 * q1);
-  } else {
-    const T e0 = eps + be0, e1 = eps + be1, e2 = eps + be2;
-    al0 = T(0.1) / (e0 * e0);
-    al1 = T(0.6) / (e1 * e1);
-    al2 = T(0.3) / (e2 * e2);
-  }
-  return (al0 * c0 + al1 * c1 + al2 * c2) / (al0 + al1 + al2);
+  T be0, be1, be2;
+  weno5_beta(w, be0, be1, be2);
+  return weno5_combine<T, Z>(c0, c1, c2, T(0.1), T(0.6), T(0.3), be0, be1, be2, eps, mc);
 }
+
+// Both edge values of cell c from w[0..4] = U_{c-2..c+2} (VAR 0 WENO5-JS,
+// 1 WENO5-Z, 2 WENO3): er = the left state at c + 1/2, el = the right state
+// at c - 1/2, with the smoothness indicators formed once
+template <typename T, int VAR>
+__device__ __forceinline__ void weno_edges(const T* w, T eps, const MhdCoef<T>& mc, T& er, T& el);
 
 // App. A: WENO3 left state at i+1/2 from w[1..3] = U_{i-1..i+1}
 template <typename T>
@@ -122,7 +118,7 @@ __device__ __forceinline__ T weno3_left(const T* w, T eps) {
   const T b0 = (w[3] - w[2]) * (w[3] - w[2]);
   const T b1 = (w[2] - w[1]) * (w[2] - w[1]);
   const T e0 = eps + b0, e1 = eps + b1;
-  if constexpr (sizeof(T) == 8) {  // common denominator e0^2 e1^2 (see weno_left)
+  if constexpr (sizeof(T) == 8) {  // common denominator e0^2 e1^2 (see weno5_combine)
     const T a0 = T(2.0 / 3.0) * (e1 * e1), a1 = T(1.0 / 3.0) * (e0 * e0);
     return (a0 * c0 + a1 * c1) / (a0 + a1);
   }
@@ -138,7 +134,7 @@ __device__ __forceinline__ T weno3_right(const T* w, T eps) {
   const T b0 = (w[2] - w[3]) * (w[2] - w[3]);
   const T b1 = (w[1] - w[2]) * (w[1] - w[2]);
   const T e0 = eps + b0, e1 = eps + b1;
-  if constexpr (sizeof(T) == 8) {  // common denominator e0^2 e1^2 (see weno_left)
+  if constexpr (sizeof(T) == 8) {  // common denominator e0^2 e1^2 (see weno5_combine)
     const T a0 = T(1.0 / 3.0) * (e1 * e1), a1 = T(2.0 / 3.0) * (e0 * e0);
     return (a0 * c0 + a1 * c1) / (a0 + a1);
   }
@@ -151,6 +147,25 @@ __device__ __forceinline__ T weno3_right(const T* w, T eps) {
 template <typename T>
 __device__ __forceinline__ T by_dir(int d, T x, T y, T z) {
   return d == 0 ? x : (d == 1 ? y : z);
+}
+
+template <typename T, int VAR>
+__device__ __forceinline__ void weno_edges(const T* w, T eps, const MhdCoef<T>& mc, T& er, T& el) {
+  if constexpr (VAR == 2) {
+    er = weno3_left(w, eps);
+    el = weno3_right(w, eps);
+  } else {
+    T be0, be1, be2;
+    weno5_beta(w, be0, be1, be2);
+    er = weno5_combine<T, VAR == 1>((T(2) * w[2] + T(5) * w[3] - w[4]) * T(1.0 / 6.0),
+                                    (-w[1] + T(5) * w[2] + T(2) * w[3]) * T(1.0 / 6.0),
+                                    (T(2) * w[0] - T(7) * w[1] + T(11) * w[2]) * T(1.0 / 6.0), T(0.3),
+                                    T(0.6), T(0.1), be0, be1, be2, eps, mc);
+    el = weno5_combine<T, VAR == 1>((T(2) * w[4] - T(7) * w[3] + T(11) * w[2]) * T(1.0 / 6.0),
+                                    (-w[3] + T(5) * w[2] + T(2) * w[1]) * T(1.0 / 6.0),
+                                    (T(2) * w[2] + T(5) * w[1] - w[0]) * T(1.0 / 6.0), T(0.1),
+                                    T(0.6), T(0.3), be0, be1, be2, eps, mc);
+  }
 }
 
 // physical flux along d and the largest signal speed |v_d| + c_fast,d
@@ -205,6 +220,55 @@ __device__ __forceinline__ void face_flux(const T* __restrict__ p, long long F, 
   const T S = sl > sr ? sl : sr;
 #pragma unroll
   for (int f = 0; f < 8; ++f) Fout[f] = T(0.5) * (FL[f] + FR[f] - S * (UR[f] - UL[f]));
+}
+
+// z-faces of a thread marching up its column (double, reconstruction of the
+// evolved fields): the flux at k + 1/2 from the carried right-edge values of
+// cell k (er, 8 fields) and both edge values of cell k + 1 (cells k-1 .. k+3
+// around p1), whose right-edge values then replace er.  Each cell is
+// reconstructed once for both of its edges, its smoothness indicators formed
+// once instead of twice.
+template <typename T, int VAR>
+__device__ __forceinline__ void zface_carry(const T* __restrict__ p1, long long F, long long s,
+                                            const MhdCoef<T>& mc, T* er, T* Fout) {
+  const T eps = mc.eps[2];
+  T UR[8], ERn[8];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    const T* q = p1 + f * F;
+    T w[5];
+#pragma unroll
+    for (int o = 0; o < 5; ++o) w[o] = __ldg(q + (o - 2) * s);
+    weno_edges<T, VAR>(w, eps, mc, ERn[f], UR[f]);
+  }
+  T FL[8], FR[8];
+  const T sl = flux_speed(er, 2, mc, FL);
+  const T sr = flux_speed(UR, 2, mc, FR);
+  const T S = sl > sr ? sl : sr;
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    Fout[f] = T(0.5) * (FL[f] + FR[f] - S * (UR[f] - er[f]));
+    er[f] = ERn[f];
+  }
+}
+
+// The right-edge values (left state at c + 1/2 along z) of the cell at p, to
+// start the carry of zface_carry.
+template <typename T, int VAR>
+__device__ __forceinline__ void zedge_right(const T* __restrict__ p, long long F, long long s,
+                                            const MhdCoef<T>& mc, T* er) {
+  const T eps = mc.eps[2];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    const T* q = p + f * F;
+    T w[5];
+#pragma unroll
+    for (int o = 0; o < 5; ++o) w[o] = __ldg(q + (o - 2) * s);
+    if constexpr (VAR == 2)
+      er[f] = weno3_left(w, eps);
+    else
+      er[f] = weno_left<T, VAR == 1>(w, eps, mc);
+  }
 }
 
 // Flux through the same face from the reconstruction of the split fluxes
@@ -293,7 +357,10 @@ __global__ void __launch_bounds__(MX * MY, mhd_min_blocks<T, SPLIT>())
   auto at = [&](int ii, int jj, int kk) {
     return a.us + (long long)(kk + g) * a.sz + (long long)(jj + g) * a.sy + (ii + g);
   };
-  T Fzm[8];
+  // double without flux splitting: the z-faces by zface_carry (each cell's
+  // z reconstruction serves both of its z-faces), er its carried values
+  constexpr bool ZC = sizeof(T) == 8 && !SPLIT;
+  T Fzm[8], er[8];
   // pass k = k0 - 1 evaluates only the z-face below the first plane (Fzm);
   // `body` is the same for the whole block, so the barriers below are taken
   // by every thread or by none
@@ -301,9 +368,10 @@ __global__ void __launch_bounds__(MX * MY, mhd_min_blocks<T, SPLIT>())
     const bool body = k >= k0;
     T Fx[8], Fy[8], Fz[8];
     // the x-face at i - 1/2, the y-face at j - 1/2 and the z-face at k + 1/2
-    // in one rolled loop over the direction (one copy of the face code)
+    // in one rolled loop over the direction (one copy of the face code); with
+    // ZC the z-face comes from zface_carry after the loop
 #pragma unroll 1
-    for (int d = body ? 0 : 2; d < 3; ++d) {
+    for (int d = body ? 0 : 2; d < (ZC ? 2 : 3); ++d) {
       T Fd[8];
       if (d == 0 ? xface : (d == 1 ? yface : out)) {
         const T* base = d == 0 ? at(i - 1, j, k) : (d == 1 ? at(i, j - 1, k) : at(i, j, k));
@@ -317,6 +385,12 @@ __global__ void __launch_bounds__(MX * MY, mhd_min_blocks<T, SPLIT>())
         Fx[f] = d == 0 ? Fd[f] : Fx[f];
         Fy[f] = d == 1 ? Fd[f] : Fy[f];
         Fz[f] = d == 2 ? Fd[f] : Fz[f];
+      }
+    }
+    if constexpr (ZC) {
+      if (out) {
+        if (!body) zedge_right<T, VAR>(at(i, j, k), a.sf, a.sz, mc, er);
+        zface_carry<T, VAR>(at(i, j, k + 1), a.sf, a.sz, mc, er, Fz);
       }
     }
     if (body) {
