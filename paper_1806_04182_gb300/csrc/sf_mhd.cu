@@ -312,8 +312,9 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ p, long lon
     face_flux<T, VAR>(p, F, s, d, mc, Fout);
 }
 
-// Stage kernel.  Each interface flux is evaluated once: a block of 32 x 8
-// threads owns 31 x 7 output cells of a plane; thread (tx, ty) evaluates the
+// Stage kernel.  Each interface flux is evaluated once: a block of 32 x MY
+// threads owns 31 x (MY - 1) output cells of a plane (MY = 12 for float
+// without flux splitting, 8 otherwise: mhd_rows); thread (tx, ty) evaluates the
 // x-face at i - 1/2 and the y-face at j - 1/2 of its column, so the +1/2
 // faces of the output cells come from lane tx + 1 (warp shuffle) and row
 // ty + 1 (shared memory).  Each thread marches mz planes in z and carries the
@@ -328,20 +329,28 @@ __device__ __forceinline__ void interface_flux(const T* __restrict__ p, long lon
 // resident blocks.  Faces are only evaluated at positions 0..n along their
 // direction, whose WENO stencils (cells p-3..p+2) lie inside the 3-point
 // ghost zone.
-constexpr int MX = 32, MY = 8;
+constexpr int MX = 32;
+template <typename T, bool SPLIT>
+constexpr int mhd_rows() {
+  return sizeof(T) == 4 && !SPLIT ? 12 : 8;
+}
 
-// Float without flux splitting asks for 3 resident blocks per SM (at most
-// 85 registers a thread; it fits in 80 without spills; left to itself the
-// compiler takes 96, 2 blocks per SM, 15% slower at 128^3); the other forms
-// keep the compiler's choice.
+// Float without flux splitting: blocks of 32 x 12 threads, 2 resident per SM
+// (at most 85 registers a thread, 24 warps per SM), so that 11 of 12 rows
+// output cells (7 of 8 with 32 x 8: 2.51e9 against 2.83e9 cell-updates/s at
+// 128^3; 32 x 24, one block per SM: 2.82e9; 32 x 8 left to the compiler's
+// register choice, 96 a thread and 16 warps per SM, was 15% slower than
+// 32 x 8 at 3 blocks per SM).  The other forms keep 32 x 8 and the compiler's
+// register choice.
 template <typename T, bool SPLIT>
 constexpr int mhd_min_blocks() {
-  return sizeof(T) == 4 && !SPLIT ? 3 : 1;
+  return sizeof(T) == 4 && !SPLIT ? 2 : 1;
 }
 
 template <typename T, bool SPLIT, int VAR>
-__global__ void __launch_bounds__(MX * MY, mhd_min_blocks<T, SPLIT>())
+__global__ void __launch_bounds__(MX * mhd_rows<T, SPLIT>(), mhd_min_blocks<T, SPLIT>())
     mhd_stage_kernel(PatchArgs<T> a, StageArgs s, MhdCoef<T> mc, int mz) {
+  constexpr int MY = mhd_rows<T, SPLIT>();
   __shared__ T fy[MY][MX][8];
   __shared__ double s_rate[MX * MY / 32];
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -519,7 +528,8 @@ static int resident_blocks() {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   if (!cache[dev]) {
     int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mhd_stage_kernel<T, SPLIT, VAR>, MX * MY,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mhd_stage_kernel<T, SPLIT, VAR>,
+                                                      MX * mhd_rows<T, SPLIT>(),
                                                       0) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return 0;
@@ -532,6 +542,7 @@ static int resident_blocks() {
 template <typename T, bool SPLIT, int VAR>
 static void launch_instance(const PatchArgs<T>& a, const StageArgs& s, const MhdCoef<T>& mc,
                             const sf_patch& p, cudaStream_t st) {
+  constexpr int MY = mhd_rows<T, SPLIT>();
   const dim3 block(MX, MY, 1);
   const int gx = (p.n[0] + MX - 2) / (MX - 1), gy = (p.n[1] + MY - 2) / (MY - 1);
   const int mz = mhd_planes_per_block(gx, gy, p.n[2], resident_blocks<T, SPLIT, VAR>());
