@@ -503,11 +503,13 @@ static MhdCoef<T> coef(const sf_params& prm, const sf_patch& p) {
 // Planes per block along z: each block evaluates 3 mz + 1 interface fluxes
 // per column, and a launch of B blocks takes ceil(B / resident) rounds of
 // the resident blocks (blocks per SM x SMs), so mz in [4, 16] minimises
-// ceil(B(mz) / resident) (3 mz + 1); ties go to the larger mz.
+// ceil(B(mz) / resident) (3 mz + 1); ties go to the larger mz.  Only chunk
+// lengths whose grid fits gridDim.z (65535) are considered.
 static int mhd_planes_per_block(int gx, int gy, int nz, int resident) {
   int best = 16;
   long long best_cost = -1;
   for (int mz = 16; mz >= 4; --mz) {
+    if ((nz + mz - 1) / mz > 65535) break;
     const long long blocks = (long long)gx * gy * ((nz + mz - 1) / mz);
     const long long rounds = resident > 0 ? (blocks + resident - 1) / resident : blocks;
     const long long cost = rounds * (3 * mz + 1);
